@@ -1,0 +1,553 @@
+"""Plain, slow FP64 reference of the additive-kernel fast summation.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): the product path never
+imports this module.
+
+Paper: "Preconditioned Additive Gaussian Processes with Fourier Acceleration"
+(arXiv 2504.00480). Every function names the passage it follows. Where the
+paper is silent or ambiguous this module takes the following readings:
+
+* The paper's bandwidth m is called ``N`` here; ``I_N = {-N/2, ..., N/2-1}^d``.
+* The fast sum outputs the REAL part of eq. (3.3); with the asymmetric index
+  set the complex sum has a small imaginary part, and the paper's own 1-D
+  figure (Sec. 3.1) shows the real cosine series.
+* ``kappa_R(l/N)`` at ``l_t = -N/2`` is the plain kernel value (no boundary
+  smoothing, Sec. 3.1).
+* One lengthscale and one ``sigma_f`` are shared by all windows (Sec. 2.1).
+* NFFT (Appendix A): Kaiser-Bessel window with oversampling ``sigma_os``
+  (default 2, so the oversampled grid has ``n_os = 2N`` points per dimension).
+  Its Fourier transform is the standard closed form in the modified Bessel
+  function I0, which the paper mentions but does not print.
+
+Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
+
+* ``kernel``/``kernel_der_ell``: textbook values, finite differences in ell.
+* ``dense_matvec``: brute-force double loop on tiny n, identical points
+  (closed form), translation invariance, symmetry, positive definiteness.
+* ``fourier_coeffs``: the paper's worked example (1-D Matern, ell=0.3, N=8,
+  golden file), the geometric-series closed form of 1-D Matern, the Gaussian
+  Fourier transform at small ell, separability of the Gaussian.
+* ``truncated_matvec``: exact agreement with the dense sum on lattice points
+  (trigonometric interpolation property), convergence to the dense sum at
+  small ell, exact symmetry, eq. (3.4) derivative consistency.
+* ``kb_window_hat``: numerical quadrature of the truncated window.
+* ``nfft``/``nfft_adjoint``: error against the exact NDFT below the window
+  error bound of Appendix A.
+* ``cg``: dense Cholesky solve; ``slq_quadratic``: eigendecomposition-based
+  matrix logarithm with full Krylov space; ``nlml_exact``: scipy's
+  multivariate normal log density.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.special
+
+__all__ = [
+    "kernel", "kernel_der_ell", "window_points",
+    "dense_matvec", "dense_deriv_matvec", "dense_matrix",
+    "index_set", "fourier_coeffs", "ndft_adjoint", "ndft",
+    "truncated_matvec", "truncated_deriv_matvec",
+    "bins", "kb_shape", "kb_window", "kb_window_hat",
+    "nfft_adjoint", "nfft", "nfft_fastsum_matvec",
+    "cg", "lanczos_tridiag_from_cg", "slq_quadratic",
+    "nlml_exact", "nlml_estimate",
+]
+
+TWO_PI = 2.0 * math.pi
+
+
+# ---------------------------------------------------------------------------
+# Kernels (Sec. 2.1)
+# ---------------------------------------------------------------------------
+
+def kernel(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
+    """Windowed sub-kernel kappa_s as a function of the distance r = |x - y|_2.
+
+    Sec. 2.1, eq. (2.2): Gaussian exp(-r^2 / (2 ell^2)) and Matern(1/2)
+    exp(-r / ell); neither carries sigma_f (it multiplies the sum)."""
+    r = np.asarray(r, dtype=np.float64)
+    if kind == "gauss":
+        return np.exp(-(r * r) / (2.0 * ell * ell))
+    if kind == "matern12":
+        return np.exp(-r / ell)
+    raise ValueError(kind)
+
+
+def kernel_der_ell(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
+    """Derivative of kappa_s with respect to ell, Sec. 2.1 eq. (2.3):
+    Gaussian r^2/ell^3 kappa^G, Matern(1/2) r/ell^2 kappa^M."""
+    r = np.asarray(r, dtype=np.float64)
+    if kind == "gauss":
+        return (r * r) / ell ** 3 * kernel(kind, r, ell)
+    if kind == "matern12":
+        return r / ell ** 2 * kernel(kind, r, ell)
+    raise ValueError(kind)
+
+
+def window_points(X: np.ndarray, window) -> np.ndarray:
+    """x_i^{W_s}: the columns of X listed in the window W_s (Sec. 2.1)."""
+    return np.asarray(X, dtype=np.float64)[:, list(window)]
+
+
+# ---------------------------------------------------------------------------
+# O1: dense additive kernel sum (Sec. 2.1 eqs. (2.1)-(2.3))
+# ---------------------------------------------------------------------------
+
+def _dense_window_apply(kind, xw, V, ell, rows, der):
+    n = xw.shape[0]
+    rows = np.arange(n) if rows is None else np.asarray(rows)
+    out = np.zeros((len(rows), V.shape[1]))
+    f = kernel_der_ell if der else kernel
+    step = max(1, 2_000_000 // max(n, 1))
+    for a in range(0, len(rows), step):
+        ri = rows[a:a + step]
+        diff = xw[ri, None, :] - xw[None, :, :]
+        r = np.sqrt(np.sum(diff * diff, axis=-1))
+        out[a:a + step] = f(kind, r, ell) @ V
+    return out
+
+
+def dense_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, rows=None,
+                 add_noise=True):
+    """(K_hat V)[rows] with K_hat = sigma_f^2 sum_s K_s + sigma_eps^2 I.
+
+    Sec. 2.1: the additive kernel eq. (2.1) with the windowed sub-kernels of
+    eq. (2.2), regularised by sigma_eps^2 I (Sec. 1). ``rows`` selects output
+    rows (every output row still sums over all n points)."""
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    out = 0.0
+    for w in windows:
+        out = out + _dense_window_apply(kind, window_points(X, w), V, ell, rows, False)
+    out = sigma_f ** 2 * out
+    if add_noise:
+        vr = V if rows is None else V[np.asarray(rows)]
+        out = out + sigma_eps ** 2 * vr
+    return out
+
+
+def dense_deriv_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, which,
+                       rows=None):
+    """(dK_hat/dtheta V)[rows] for theta in {"ell", "sigma_f", "sigma_eps"}.
+
+    Sec. 2.1: dK_hat/dell = sigma_f^2 sum_s K_s^der (eq. (2.3));
+    dK_hat/dsigma_f = 2 sigma_f sum_s K_s; dK_hat/dsigma_eps = 2 sigma_eps I."""
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    if which == "sigma_eps":
+        vr = V if rows is None else V[np.asarray(rows)]
+        return 2.0 * sigma_eps * vr
+    der = which == "ell"
+    out = 0.0
+    for w in windows:
+        out = out + _dense_window_apply(kind, window_points(X, w), V, ell, rows, der)
+    if which == "ell":
+        return sigma_f ** 2 * out
+    if which == "sigma_f":
+        return 2.0 * sigma_f * out
+    raise ValueError(which)
+
+
+def dense_matrix(X, windows, kind, ell, sigma_f, sigma_eps, which=None):
+    """K_hat (or one of its derivative matrices) as an explicit n x n array."""
+    n = X.shape[0]
+    E = np.eye(n)
+    if which is None:
+        return dense_matvec(X, windows, kind, ell, sigma_f, sigma_eps, E)
+    return dense_deriv_matvec(X, windows, kind, ell, sigma_f, sigma_eps, E, which)
+
+
+# ---------------------------------------------------------------------------
+# O2: Fourier-truncated sum (Sec. 3.1 eqs. (3.1)-(3.3), Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+def index_set(N: int) -> np.ndarray:
+    """I_N = {-N/2, ..., N/2 - 1} (Sec. 3.1, one dimension)."""
+    if N % 2:
+        raise ValueError("N must be even")
+    return np.arange(-N // 2, N // 2)
+
+
+def fourier_coeffs(kind: str, ell: float, N: int, d: int, der: bool = False):
+    """Discrete Fourier coefficients b_k(kappa_R), k in I_N^d.
+
+    Sec. 3.1 eq. (3.2): b_k = N^{-d} sum_{l in I_N^d} kappa_R(l/N) e^{-2 pi i l.k/N}.
+    The samples l/N lie in [-1/2, 1/2)^d, where kappa_R is kappa itself (no
+    boundary smoothing). With der=True the samples are those of the
+    ell-derivative kernel (Sec. 3.2). The d-dimensional sum is evaluated one
+    axis at a time (the exponential factorises over the axes).
+    Returns a complex array indexed [k_1 + N/2, ..., k_d + N/2]."""
+    idx = index_set(N)
+    grids = np.meshgrid(*([idx / N] * d), indexing="ij")
+    r = np.sqrt(sum(g * g for g in grids))
+    samples = (kernel_der_ell if der else kernel)(kind, r, ell).astype(np.complex128)
+    F = np.exp(-1j * TWO_PI * np.outer(idx, idx) / N) / N   # F[k, l]
+    b = samples
+    for axis in range(d):
+        b = np.moveaxis(np.tensordot(F, b, axes=([1], [axis])), 0, axis)
+    return b
+
+
+def _exp_factors(x, N, sign):
+    """Per-axis factors e^{sign 2 pi i k_t x_t}, shape (d, n, N)."""
+    k = index_set(N)
+    return [np.exp(sign * 1j * TWO_PI * np.outer(x[:, t], k)) for t in range(x.shape[1])]
+
+
+_LETTERS = "abc"
+
+
+def ndft_adjoint(x, V, N, chunk=4096):
+    """c_k = sum_j v_j e^{-2 pi i k.x_j} for k in I_N^d (the inner sum of
+    eq. (3.3), i.e. the exact adjoint NDFT). x: (n, d); V: (n, R).
+    Returns complex (N,)*d + (R,). The sum over j is accumulated in chunks."""
+    x = np.asarray(x, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    n, d = x.shape
+    ks = _LETTERS[:d]
+    expr = ",".join("j" + c for c in ks) + ",jr->" + ks + "r"
+    out = np.zeros((N,) * d + (V.shape[1],), dtype=np.complex128)
+    for a in range(0, n, chunk):
+        E = _exp_factors(x[a:a + chunk], N, -1.0)
+        out += np.einsum(expr, *E, V[a:a + chunk], optimize=True)
+    return out
+
+
+def ndft(x, C, N, chunk=256):
+    """f(x_i) = sum_{k in I_N^d} C_k e^{2 pi i k.x_i} (the outer sum of
+    eq. (3.3), i.e. the exact NDFT). C: complex (N,)*d + (R,). Returns (n, R)
+    complex."""
+    x = np.asarray(x, dtype=np.float64)
+    n, d = x.shape
+    ks = _LETTERS[:d]
+    expr = ks + "r," + ",".join("i" + c for c in ks) + "->ir"
+    out = np.zeros((n, C.shape[-1]), dtype=np.complex128)
+    for a in range(0, n, chunk):
+        E = _exp_factors(x[a:a + chunk], N, +1.0)
+        out[a:a + chunk] = np.einsum(expr, C, *E, optimize=True)
+    return out
+
+
+def _truncated_window_apply(kind, xw, V, ell, N, der, rows):
+    d = xw.shape[1]
+    b = fourier_coeffs(kind, ell, N, d, der)
+    c = ndft_adjoint(xw, V, N)
+    f = b[..., None] * c
+    xo = xw if rows is None else xw[np.asarray(rows)]
+    return np.real(ndft(xo, f, N))
+
+
+def truncated_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, rows=None,
+                     add_noise=True):
+    """K_hat V with every sub-kernel replaced by its truncated Fourier series.
+
+    Sec. 3.1: per window, h(x_i) = Re sum_{k in I_N} b_k (sum_j v_j
+    e^{-2 pi i k.x_j}) e^{2 pi i k.x_i} (eq. (3.3)); "the approximate products
+    K_s v are then summed up and weighted" (end of Sec. 3.1):
+    sigma_f^2 sum_s h_s + sigma_eps^2 v. ``N`` is an int or one per window."""
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    Ns = [N] * len(windows) if np.isscalar(N) else list(N)
+    out = 0.0
+    for w, Nw in zip(windows, Ns):
+        out = out + _truncated_window_apply(kind, window_points(X, w), V, ell, Nw,
+                                            False, rows)
+    out = sigma_f ** 2 * out
+    if add_noise:
+        vr = V if rows is None else V[np.asarray(rows)]
+        out = out + sigma_eps ** 2 * vr
+    return out
+
+
+def truncated_deriv_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, which,
+                           rows=None):
+    """Derivative operators of the truncated sum. For ell the coefficients are
+    those of the derivative kernel, which Sec. 3.2 eq. (3.4) shows equal the
+    ell-derivative of the truncated series; sigma_f and sigma_eps as in
+    Sec. 2.1."""
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    if which == "sigma_eps":
+        vr = V if rows is None else V[np.asarray(rows)]
+        return 2.0 * sigma_eps * vr
+    Ns = [N] * len(windows) if np.isscalar(N) else list(N)
+    out = 0.0
+    for w, Nw in zip(windows, Ns):
+        out = out + _truncated_window_apply(kind, window_points(X, w), V, ell, Nw,
+                                            which == "ell", rows)
+    if which == "ell":
+        return sigma_f ** 2 * out
+    if which == "sigma_f":
+        return 2.0 * sigma_f * out
+    raise ValueError(which)
+
+
+# ---------------------------------------------------------------------------
+# NFFT (Appendix A): Kaiser-Bessel window, adjoint NFFT and NFFT
+# ---------------------------------------------------------------------------
+
+def bins(x: np.ndarray, n_os: int) -> np.ndarray:
+    """Index of the oversampled-grid cell that holds each coordinate:
+    floor(x * n_os). The grid points are l / n_os (Appendix A)."""
+    return np.floor(np.asarray(x, dtype=np.float64) * n_os).astype(np.int64)
+
+
+def kb_shape(sigma_os: float) -> float:
+    """Kaiser-Bessel shape parameter b = pi (2 - 1/sigma) (Appendix A)."""
+    return math.pi * (2.0 - 1.0 / sigma_os)
+
+
+def kb_window(x, n_os: int, s: int, sigma_os: float = 2.0):
+    """Truncated Kaiser-Bessel window phi(x) of Appendix A:
+    (1/pi) sinh(b sqrt(s^2 - n_os^2 x^2)) / sqrt(s^2 - n_os^2 x^2) for
+    |x| <= s / n_os, and 0 outside (the truncation). At the support edge the
+    value is the limit b/pi."""
+    b = kb_shape(sigma_os)
+    x = np.asarray(x, dtype=np.float64)
+    t = s * s - (n_os * x) ** 2
+    out = np.zeros_like(x)
+    inside = t >= 0
+    root = np.sqrt(np.where(inside, t, 0.0))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        val = np.where(root > 0, np.sinh(b * root) / np.where(root > 0, root, 1.0), b)
+    out[inside] = val[inside] / math.pi
+    return out
+
+
+def kb_window_hat(k, n_os: int, s: int, sigma_os: float = 2.0):
+    """Fourier transform of the Kaiser-Bessel window at frequency k:
+    (1/n_os) I0(s sqrt(b^2 - (2 pi k / n_os)^2)). This is the standard
+    closed form (Kaiser-Bessel transform pair) that Appendix A refers to; it
+    holds for |2 pi k / n_os| < b, which every k in I_N satisfies."""
+    b = kb_shape(sigma_os)
+    w = TWO_PI * np.asarray(k, dtype=np.float64) / n_os
+    if np.any(np.abs(w) >= b):
+        raise ValueError("frequency outside the I0 branch")
+    return scipy.special.i0(s * np.sqrt(b * b - w * w)) / n_os
+
+
+def _spread_grid(x, V, n_os, s, sigma_os):
+    """G_l = sum_j v_j prod_t phi~(x_jt - l_t/n_os), l in I_{n_os}^d, stored
+    at array index l + n_os/2 (l taken modulo n_os: phi~ is the 1-periodic
+    window)."""
+    n, d = x.shape
+    R = V.shape[1]
+    G = np.zeros((n_os,) * d + (R,))
+    base = np.floor(x * n_os).astype(np.int64) - s          # (n, d)
+    offs = np.arange(0, 2 * s + 1)            # every l with |x n_os - l| <= s
+    # per-axis weights w[t][j, o] = phi(x_jt - (base_jt + o)/n_os)
+    W = [kb_window(x[:, t, None] - (base[:, t, None] + offs[None, :]) / n_os,
+                   n_os, s, sigma_os) for t in range(d)]
+    for o in np.ndindex(*([len(offs)] * d)):
+        w = np.ones(n)
+        idx = []
+        for t in range(d):
+            w = w * W[t][:, o[t]]
+            idx.append((base[:, t] + offs[o[t]] + n_os // 2) % n_os)
+        np.add.at(G, tuple(idx), w[:, None] * V)
+    return G
+
+
+def _interp_grid(x, G, n_os, s, sigma_os):
+    """f_i = sum_l G_l prod_t phi~(x_it - l_t/n_os) (sparse window sum,
+    Appendix A step 3)."""
+    n, d = x.shape
+    out = np.zeros((n,) + G.shape[d:], dtype=G.dtype)
+    base = np.floor(x * n_os).astype(np.int64) - s
+    offs = np.arange(0, 2 * s + 1)
+    W = [kb_window(x[:, t, None] - (base[:, t, None] + offs[None, :]) / n_os,
+                   n_os, s, sigma_os) for t in range(d)]
+    for o in np.ndindex(*([len(offs)] * d)):
+        w = np.ones(n)
+        idx = []
+        for t in range(d):
+            w = w * W[t][:, o[t]]
+            idx.append((base[:, t] + offs[o[t]] + n_os // 2) % n_os)
+        out += w[:, None] * G[tuple(idx)]
+    return out
+
+
+def _window_hat_nd(N, n_os, s, sigma_os, d):
+    """prod_t phi_hat(k_t) on I_N^d."""
+    h = kb_window_hat(index_set(N), n_os, s, sigma_os)
+    out = h
+    for _ in range(d - 1):
+        out = np.multiply.outer(out, h)
+    return out
+
+
+def nfft_adjoint(x, V, N, s, sigma_os=2.0):
+    """Approximate c_k = sum_j v_j e^{-2 pi i k.x_j}, k in I_N^d, by the adjoint
+    of the three NFFT steps of Appendix A: spread onto the oversampled grid
+    with the periodised window, FFT, divide by the window's Fourier transform
+    and by n_os^d."""
+    x = np.asarray(x, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    d = x.shape[1]
+    n_os = int(round(sigma_os * N))
+    G = _spread_grid(x, V, n_os, s, sigma_os)
+    # sum_l G_l e^{-2 pi i k.l/n_os} with l centred: move l=0 to index 0
+    Gh = np.fft.fftn(np.fft.ifftshift(G, axes=tuple(range(d))), axes=tuple(range(d)))
+    sel = np.ix_(*([index_set(N) % n_os] * d))
+    Gk = Gh[sel]
+    return Gk / (n_os ** d * _window_hat_nd(N, n_os, s, sigma_os, d))[..., None]
+
+
+def nfft(x, C, N, s, sigma_os=2.0):
+    """Approximate f(x_i) = sum_k C_k e^{2 pi i k.x_i} by the three NFFT steps of
+    Appendix A: (1) divide by the window's Fourier transform and zero-pad to
+    I_{n_os}; (2) FFT to grid values g_l (with the 1/n_os^d of the inverse
+    transform); (3) sparse window sum at the points."""
+    x = np.asarray(x, dtype=np.float64)
+    d = x.shape[1]
+    n_os = int(round(sigma_os * N))
+    Gk = np.zeros((n_os,) * d + C.shape[d:], dtype=np.complex128)
+    sel = np.ix_(*([index_set(N) % n_os] * d))
+    Gk[sel] = C / _window_hat_nd(N, n_os, s, sigma_os, d)[..., None]
+    g = np.fft.ifftn(Gk, axes=tuple(range(d)))            # includes 1/n_os^d
+    g = np.fft.fftshift(g, axes=tuple(range(d)))            # index l + n_os/2
+    return _interp_grid(x, g, n_os, s, sigma_os)
+
+
+def nfft_fastsum_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, s,
+                        sigma_os=2.0, add_noise=True):
+    """The method itself on the CPU: eq. (3.3) with the inner sum by the
+    adjoint NFFT and the outer sum by the NFFT (Sec. 3.1 and Appendix A),
+    real part, then the weighted window sum."""
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    Ns = [N] * len(windows) if np.isscalar(N) else list(N)
+    out = 0.0
+    for w, Nw in zip(windows, Ns):
+        xw = window_points(X, w)
+        b = fourier_coeffs(kind, ell, Nw, xw.shape[1])
+        chat = nfft_adjoint(xw, V, Nw, s, sigma_os)
+        out = out + np.real(nfft(xw, b[..., None] * chat, Nw, s, sigma_os))
+    out = sigma_f ** 2 * out
+    if add_noise:
+        out = out + sigma_eps ** 2 * V
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Iterative solvers and the likelihood (Sec. 1)
+# ---------------------------------------------------------------------------
+
+def cg(apply_A, B, rtol=1e-4, maxit=200, fixed_iters=None):
+    """Conjugate gradients for A X = B, one independent recursion per column,
+    zero initial guess, stopping when |b - A x|_2 / |b|_2 <= rtol (Sec. 1 and
+    the CG setup of Sec. 5.1). With ``fixed_iters`` every column runs exactly
+    that many steps (the Lanczos use). Returns X, iterations, relative
+    residuals, and the per-column alpha and beta sequences."""
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    n, R = B.shape
+    X = np.zeros_like(B)
+    iters = np.zeros(R, dtype=np.int64)
+    relres = np.ones(R)
+    alphas = [[] for _ in range(R)]
+    betas = [[] for _ in range(R)]
+    for c in range(R):
+        b = B[:, c]
+        bn = np.linalg.norm(b)
+        if bn == 0:
+            relres[c] = 0.0
+            continue
+        x = np.zeros(n)
+        r = b.copy()
+        p = r.copy()
+        rr = r @ r
+        lim = fixed_iters if fixed_iters is not None else maxit
+        for it in range(lim):
+            q = apply_A(p[:, None])[:, 0]
+            a = rr / (p @ q)
+            x = x + a * p
+            r = r - a * q
+            rr_new = r @ r
+            beta = rr_new / rr
+            alphas[c].append(a)
+            betas[c].append(beta)
+            iters[c] = it + 1
+            relres[c] = math.sqrt(rr_new) / bn
+            rr = rr_new
+            if fixed_iters is None and relres[c] <= rtol:
+                break
+            p = r + beta * p
+        X[:, c] = x
+    return X, iters, relres, alphas, betas
+
+
+def lanczos_tridiag_from_cg(alphas, betas):
+    """Lanczos tridiagonal matrix T from the CG coefficients (the standard
+    CG-Lanczos relation used by stochastic Lanczos quadrature, cited in
+    Sec. 1): T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+    T_{j,j+1} = sqrt(beta_j)/alpha_j."""
+    m = len(alphas)
+    T = np.zeros((m, m))
+    for j in range(m):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < m:
+            T[j, j + 1] = T[j + 1, j] = math.sqrt(betas[j]) / alphas[j]
+    return T
+
+
+def slq_quadratic(T, znorm2):
+    """Gauss quadrature estimate of z^T logm(A) z from the Lanczos matrix T of
+    the Krylov space started at z: |z|^2 sum_k tau_k^2 log theta_k with
+    (theta_k, u_k) the eigenpairs of T and tau_k = u_k[0] (Sec. 1, SLQ)."""
+    theta, U = np.linalg.eigh(T)
+    return znorm2 * float(np.sum(U[0, :] ** 2 * np.log(theta)))
+
+
+def nlml_exact(K_hat, y):
+    """Z = 1/2 (y^T K_hat^{-1} y + log det K_hat + n log 2 pi), Sec. 1 eq. (1.2),
+    by a dense Cholesky factorisation."""
+    L = np.linalg.cholesky(K_hat)
+    a = np.linalg.solve(L.T, np.linalg.solve(L, y))
+    n = len(y)
+    return 0.5 * (y @ a + 2.0 * np.sum(np.log(np.diag(L))) + n * math.log(TWO_PI))
+
+
+def nlml_estimate(apply_K, apply_dK, y, Z, lanczos_steps, rtol=1e-10, maxit=None):
+    """Estimate of the NLML and its gradient with M = I (no preconditioner).
+
+    Sec. 1 eq. (1.4) with M = I: Z~ = 1/2 (y^T alpha + (1/n_z) sum_i z_i^T
+    logm(K_hat) z_i + n log 2 pi), each quadratic form by SLQ with
+    ``lanczos_steps`` CG steps started at z_i. Eq. (1.5) with M = I:
+    dZ~/dtheta = 1/2 (-alpha^T dK alpha + (1/n_z) sum_i u_i^T dK z_i),
+    u_i = K_hat^{-1} z_i (the CG solution after ``lanczos_steps`` steps).
+    alpha solves K_hat alpha = y by CG to ``rtol``.
+
+    apply_dK: dict theta -> callable. Returns (nlml, {theta: grad})."""
+    y = np.asarray(y, dtype=np.float64).reshape(-1)
+    n = y.shape[0]
+    alpha, _, _, _, _ = cg(apply_K, y[:, None], rtol=rtol,
+                           maxit=maxit if maxit is not None else 10 * n)
+    alpha = alpha[:, 0]
+    U, _, _, al, be = cg(apply_K, Z, fixed_iters=lanczos_steps)
+    nz = Z.shape[1]
+    logdet = 0.0
+    for i in range(nz):
+        T = lanczos_tridiag_from_cg(al[i], be[i])
+        logdet += slq_quadratic(T, float(Z[:, i] @ Z[:, i]))
+    logdet /= nz
+    nlml = 0.5 * (y @ alpha + logdet + n * math.log(TWO_PI))
+    grads = {}
+    for th, f in apply_dK.items():
+        da = f(alpha[:, None])[:, 0]
+        dz = f(Z)
+        tr = float(np.sum(U * dz)) / nz
+        grads[th] = 0.5 * (-(alpha @ da) + tr)
+    return nlml, grads

@@ -1,0 +1,89 @@
+"""Pins of the oracle's CG, SLQ and likelihood (Sec. 1) to dense linear algebra
+and to scipy's multivariate normal density."""
+import math
+
+import numpy as np
+import pytest
+import scipy.stats
+
+import oracle as O
+
+
+def _problem(n=12, seed=50):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-0.24, 0.24, size=(n, 4))
+    W = [[0, 1], [2, 3]]
+    th = dict(ell=0.2, sigma_f=0.9, sigma_eps=0.6)
+    return X, W, th, rng
+
+
+def test_cg_matches_cholesky_solve():
+    X, W, th, rng = _problem(40)
+    K = O.dense_matrix(X, W, "gauss", th["ell"], th["sigma_f"], th["sigma_eps"])
+    B = rng.standard_normal((40, 3))
+    Xs, it, rel, _, _ = O.cg(lambda P: K @ P, B, rtol=1e-12, maxit=400)
+    np.testing.assert_allclose(Xs, np.linalg.solve(K, B), rtol=1e-8, atol=1e-9)
+    assert np.all(rel <= 1e-12) and np.all(it > 0)
+
+
+def test_cg_zero_rhs_and_iteration_cap():
+    X, W, th, rng = _problem(30)
+    K = O.dense_matrix(X, W, "gauss", th["ell"], th["sigma_f"], 0.01)
+    B = np.zeros((30, 2))
+    B[:, 1] = rng.standard_normal(30)
+    Xs, it, rel, _, _ = O.cg(lambda P: K @ P, B, rtol=1e-14, maxit=3)
+    assert it[0] == 0 and rel[0] == 0 and np.all(Xs[:, 0] == 0)
+    assert it[1] == 3 and rel[1] > 1e-14
+
+
+def test_slq_exact_with_full_krylov_space():
+    # With as many Lanczos steps as the dimension, Gauss quadrature is exact:
+    # z^T logm(A) z = |z|^2 sum tau^2 log theta.
+    X, W, th, rng = _problem(12)
+    K = O.dense_matrix(X, W, "gauss", th["ell"], th["sigma_f"], th["sigma_eps"])
+    lam, Q = np.linalg.eigh(K)
+    logK = (Q * np.log(lam)) @ Q.T
+    z = rng.choice([-1.0, 1.0], size=12)
+    _, _, _, al, be = O.cg(lambda P: K @ P, z[:, None], fixed_iters=12)
+    T = O.lanczos_tridiag_from_cg(al[0], be[0])
+    assert O.slq_quadratic(T, z @ z) == pytest.approx(z @ logK @ z, rel=1e-9)
+
+
+def test_nlml_exact_matches_scipy_logpdf():
+    X, W, th, rng = _problem(25)
+    K = O.dense_matrix(X, W, "matern12", th["ell"], th["sigma_f"], th["sigma_eps"])
+    y = rng.standard_normal(25)
+    want = -scipy.stats.multivariate_normal(mean=np.zeros(25), cov=K).logpdf(y)
+    assert O.nlml_exact(K, y) == pytest.approx(want, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["gauss", "matern12"])
+def test_nlml_estimate_exact_with_orthogonal_probes(kind):
+    # Probes sqrt(n) q_i from an orthogonal basis make Hutchinson exact, and n
+    # Lanczos steps make each quadrature exact, so the estimator must return
+    # the exact NLML and the exact gradient (finite differences of scipy's
+    # log density).
+    n = 12
+    X, W, th, rng = _problem(n)
+    y = rng.standard_normal(n)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Z = math.sqrt(n) * Q
+
+    def Kmat(**kw):
+        t = dict(th, **kw)
+        return O.dense_matrix(X, W, kind, t["ell"], t["sigma_f"], t["sigma_eps"])
+
+    K = Kmat()
+    dK = {w: O.dense_matrix(X, W, kind, th["ell"], th["sigma_f"], th["sigma_eps"], which=w)
+          for w in ["ell", "sigma_f", "sigma_eps"]}
+    nl, g = O.nlml_estimate(lambda P: K @ P, {w: (lambda P, M=M: M @ P) for w, M in dK.items()},
+                            y, Z, lanczos_steps=n)
+
+    def Zexact(**kw):
+        return -scipy.stats.multivariate_normal(mean=np.zeros(n), cov=Kmat(**kw)).logpdf(y)
+
+    assert nl == pytest.approx(Zexact(), rel=1e-8)
+    h = 1e-6
+    for w in ["ell", "sigma_f", "sigma_eps"]:
+        fd = (Zexact(**{w: th[w] + h}) - Zexact(**{w: th[w] - h})) / (2 * h)
+        assert g[w] == pytest.approx(fd, rel=1e-5, abs=1e-7)
