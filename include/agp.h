@@ -1,0 +1,178 @@
+/*
+ * agp.h -- C ABI of the GB300 additive-kernel NFFT fast summation library.
+ *
+ * Paper: "Preconditioned Additive Gaussian Processes with Fourier Acceleration"
+ * (arXiv 2504.00480). The library applies the regularised additive kernel
+ * matrix
+ *
+ *     K_hat = sigma_f^2 (K_1 + ... + K_P) + sigma_eps^2 I        (Sec. 2.1)
+ *
+ * and its hyperparameter derivatives to blocks of vectors. Each sub-kernel
+ * K_s acts on the features of one window W_s (d_s <= 3) and is applied by the
+ * NFFT-based fast summation of Sec. 3.1 eq. (3.3): Kaiser-Bessel spreading
+ * onto an oversampled grid (adjoint NFFT), a d-dimensional DFT, a multiply by
+ * the kernel's Fourier coefficients b_k (eq. (3.2)), an inverse DFT and
+ * interpolation back to the points (NFFT), Appendix A. The output is the real
+ * part of eq. (3.3).
+ *
+ * Conventions shared by every entry point
+ *  - Precision: a plan is FP32 or FP64 (agp_prec); X, V, Out and every other
+ *    floating-point device buffer of that plan have that element type.
+ *  - Layout: point data are row-major [n][ld] (one row per point). Blocks of
+ *    right-hand sides are RHS-minor: column r of V is V[i*ldv + r].
+ *  - Ownership: the caller owns every buffer passed in and the CUDA stream;
+ *    the plan owns its sorted copies of the points and all scratch. Device
+ *    pointers are plain CUDA device addresses (e.g. a torch tensor's
+ *    data_ptr()). `stream` is a cudaStream_t (NULL = legacy default stream).
+ *  - Asynchrony: compute calls only enqueue work on `stream` and return;
+ *    calls that return host values (marked "synchronises") wait for it.
+ *  - Errors: every call returns an agp_status; nothing is printed and nothing
+ *    exits. agp_status_string() names a status; agp_last_error() gives the
+ *    message of the last failing call on this thread.
+ *  - Thread safety: calls on one plan must not overlap; distinct plans are
+ *    independent.
+ */
+#ifndef AGP_H
+#define AGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct agp_plan_s* agp_plan;
+
+typedef enum {
+  AGP_OK = 0,
+  AGP_EINVAL = 1,        /* invalid argument (sizes, pointers, unsupported combination) */
+  AGP_EDOMAIN = 2,       /* a point of some window lies outside [-1/4, 1/4)^d (Sec. 3.1) */
+  AGP_ECUDA = 3,         /* a CUDA runtime call failed */
+  AGP_ENOMEM = 4,        /* device allocation failed */
+  AGP_NOT_CONVERGED = 5, /* an iterative solve stopped at maxit above its tolerance */
+  AGP_TIMEOUT = 6,       /* a bounded device wait expired */
+  AGP_ENAN = 7           /* a non-finite value was met */
+} agp_status;
+
+typedef enum { AGP_GAUSS = 0, AGP_MATERN12 = 1 } agp_kernel;   /* Sec. 2.1 eq. (2.2) */
+typedef enum { AGP_F32 = 0, AGP_F64 = 1 } agp_prec;
+typedef enum { AGP_D_ELL = 0, AGP_D_SIGMA_F = 1, AGP_D_SIGMA_EPS = 2 } agp_param;
+
+/* Plan description (Sec. 2.1 and Sec. 3.1).
+ *  n, p, X, ldx : n points with p features, device [n][ldx], ldx >= p.
+ *                 X may be freed after agp_plan_create returns.
+ *  P, win_ptr, win_feat : feature windows W_1..W_P as a host CSR array:
+ *                 window s uses features win_feat[win_ptr[s] .. win_ptr[s+1]-1]
+ *                 (0-based, 1 <= d_s <= 3, windows disjoint).
+ *  N            : host [P], Fourier bandwidth per window (the paper's m; the
+ *                 index set is I_N = {-N/2..N/2-1}^d). N in {8, 16, 32, 64}.
+ *  cutoff       : window half-support s in oversampled grid cells, 2 <= s <= 6
+ *                 and s <= N/2 (Appendix A).
+ *  sigma_os     : oversampling factor of the NFFT grid, must be 2 (grid of
+ *                 n_os = 2N points per dimension).
+ *  kernel, ell, sigma_f, sigma_eps : kernel and hyperparameters (ell > 0).
+ *  prec         : element type of every floating-point buffer of the plan.
+ * Every point of every window must lie in [-1/4, 1/4)^{d_s} (Sec. 3.1 scales
+ * the data there); otherwise agp_plan_create returns AGP_EDOMAIN. */
+typedef struct {
+  int64_t n;
+  int p;
+  const void* X;
+  int64_t ldx;
+  int P;
+  const int* win_ptr;
+  const int* win_feat;
+  const int* N;
+  int cutoff;
+  int sigma_os;
+  agp_kernel kernel;
+  double ell, sigma_f, sigma_eps;
+  agp_prec prec;
+} agp_plan_desc;
+
+/* Build a plan: sort every window's points into grid cells (cell index
+ * floor(x * n_os) per coordinate, exact for the power-of-two n_os), copy the
+ * sorted coordinates, and compute the Fourier coefficients b_k of the kernel
+ * and of its ell-derivative (Sec. 3.1 eq. (3.2), Sec. 3.2 eq. (3.4)) with the
+ * Kaiser-Bessel deconvolution factors (Appendix A). Synchronises `stream`.
+ * On success *out owns device memory until agp_plan_destroy. */
+agp_status agp_plan_create(agp_plan* out, const agp_plan_desc* desc, void* stream);
+
+/* Release the plan and all its device memory. Synchronises the device. */
+agp_status agp_plan_destroy(agp_plan plan);
+
+/* New hyperparameters (ell > 0, sigma_f, sigma_eps). Recomputes b_k for the
+ * kernel and its ell-derivative on `stream` (Sec. 3.1 eq. (3.2)); asynchronous. */
+agp_status agp_set_hyper(agp_plan plan, double ell, double sigma_f, double sigma_eps,
+                         void* stream);
+
+/* Out = K_hat V (add_noise = 1) or sigma_f^2 sum_s K_s V (add_noise = 0), with
+ * each K_s applied by the fast summation of Sec. 3.1 eq. (3.3) (real part).
+ * V: device [n][ldv], columns 0..R-1 used; Out: device [n][ldo]; R >= 1;
+ * ldv, ldo >= R. Out must not overlap V. Asynchronous on `stream`. */
+agp_status agp_matvec(agp_plan plan, const void* V, int64_t ldv, void* Out, int64_t ldo,
+                      int R, int add_noise, void* stream);
+
+/* Out = (dK_hat / dtheta) V for theta = ell (sigma_f^2 sum_s K_s^der, Sec. 2.1
+ * eq. (2.3), applied with the derivative-kernel coefficients of Sec. 3.2
+ * eq. (3.4)), sigma_f (2 sigma_f sum_s K_s) or sigma_eps (2 sigma_eps I).
+ * Arguments as agp_matvec. Asynchronous on `stream`. */
+agp_status agp_deriv_matvec(agp_plan plan, agp_param which, const void* V, int64_t ldv,
+                            void* Out, int64_t ldo, int R, void* stream);
+
+/* Adjoint NFFT of one window (Appendix A, the inner sum of eq. (3.3)):
+ * chat[r][k] ~= sum_j V[j][r] exp(-2 pi i k . x_j^{W_s}), k in I_N^d, stored
+ * row-major over (k_1 + N/2, ..., k_d + N/2), as interleaved (re, im) pairs.
+ * chat: device [R][N^d][2]. Asynchronous on `stream`. */
+agp_status agp_adjoint_nfft(agp_plan plan, int window, const void* V, int64_t ldv, int R,
+                            void* chat, void* stream);
+
+/* Real part of the NFFT of one window (Appendix A, the outer sum of
+ * eq. (3.3)): Out[i][r] = Re sum_{k in I_N^d} fhat[r][k] exp(2 pi i k . x_i).
+ * fhat: device [R][N^d][2] laid out as agp_adjoint_nfft's output; Out:
+ * device [n][ldo] (overwritten). Asynchronous on `stream`. */
+agp_status agp_nfft_real(agp_plan plan, int window, const void* fhat, int R, void* Out,
+                         int64_t ldo, void* stream);
+
+/* Grid-cell index floor(x_t * n_os) of every point in one window, in the
+ * caller's point order: bins: device int32 [n][d]. Asynchronous. */
+agp_status agp_plan_bins(agp_plan plan, int window, int32_t* bins, void* stream);
+
+/* Fourier coefficients b_k (deriv = 0) or those of the ell-derivative kernel
+ * (deriv = 1) of one window for the current ell, as computed on the device:
+ * b: host double [N^d], row-major over (k_1 + N/2, ..., k_d + N/2).
+ * Synchronises `stream`. */
+agp_status agp_plan_coeffs(agp_plan plan, int window, int deriv, double* b, void* stream);
+
+/* Size queries: n, number of windows, and the number of work items (point
+ * chunks) of one window. */
+agp_status agp_plan_query(agp_plan plan, int64_t* n, int* P, int window, int* d,
+                          int* N, int64_t* n_items);
+
+/* Stage profiler (tracing). When enabled, the library records a pair of CUDA
+ * events on the caller's stream around every kernel launch of the matvec
+ * path, per stage: 0 = spreading, 1 = DFT + spectral multiply, 2 =
+ * interpolation, 3 = other (output init, solver vector kernels).
+ * agp_profile_read (synchronises `stream`) returns, per stage, the summed
+ * device time in milliseconds and the number of kernel launches since the
+ * last reset, and resets when reset != 0. Launch counts are kept even when
+ * timing is disabled. */
+typedef struct {
+  double ms[4];
+  int64_t launches[4];
+} agp_profile_t;
+
+agp_status agp_profile_enable(agp_plan plan, int enable);
+agp_status agp_profile_read(agp_plan plan, agp_profile_t* out, int reset, void* stream);
+
+/* Name of a status code (static string). */
+const char* agp_status_string(agp_status s);
+
+/* Message of the last failing call on the calling thread (static storage). */
+const char* agp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AGP_H */

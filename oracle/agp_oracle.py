@@ -198,39 +198,48 @@ def _exp_factors(x, N, sign):
     return [np.exp(sign * 1j * TWO_PI * np.outer(x[:, t], k)) for t in range(x.shape[1])]
 
 
-_LETTERS = "abc"
-
-
 def ndft_adjoint(x, V, N, chunk=4096):
     """c_k = sum_j v_j e^{-2 pi i k.x_j} for k in I_N^d (the inner sum of
     eq. (3.3), i.e. the exact adjoint NDFT). x: (n, d); V: (n, R).
-    Returns complex (N,)*d + (R,). The sum over j is accumulated in chunks."""
+    Returns complex (N,)*d + (R,).
+
+    The exponential factorises over the axes, so for a chunk of points the
+    sum over j is one matrix product: [prod_{t<d} e_t(j, k_t)]^T times
+    [e_d(j, k_d) v_j]. Chunks of points are summed in order."""
     x = np.asarray(x, dtype=np.float64)
     V = np.asarray(V, dtype=np.float64)
     if V.ndim == 1:
         V = V[:, None]
     n, d = x.shape
-    ks = _LETTERS[:d]
-    expr = ",".join("j" + c for c in ks) + ",jr->" + ks + "r"
-    out = np.zeros((N,) * d + (V.shape[1],), dtype=np.complex128)
+    R = V.shape[1]
+    out = np.zeros((N ** (d - 1), N * R), dtype=np.complex128)
     for a in range(0, n, chunk):
         E = _exp_factors(x[a:a + chunk], N, -1.0)
-        out += np.einsum(expr, *E, V[a:a + chunk], optimize=True)
-    return out
+        m = E[0].shape[0]
+        left = np.ones((m, 1), dtype=np.complex128)
+        for t in range(d - 1):
+            left = (left[:, :, None] * E[t][:, None, :]).reshape(m, -1)
+        right = (E[d - 1][:, :, None] * V[a:a + chunk, None, :]).reshape(m, N * R)
+        out += left.T @ right
+    return out.reshape((N,) * d + (R,))
 
 
 def ndft(x, C, N, chunk=256):
     """f(x_i) = sum_{k in I_N^d} C_k e^{2 pi i k.x_i} (the outer sum of
     eq. (3.3), i.e. the exact NDFT). C: complex (N,)*d + (R,). Returns (n, R)
-    complex."""
+    complex. The sum is taken one axis at a time (the exponential
+    factorises), for a chunk of points at once."""
     x = np.asarray(x, dtype=np.float64)
     n, d = x.shape
-    ks = _LETTERS[:d]
-    expr = ks + "r," + ",".join("i" + c for c in ks) + "->ir"
-    out = np.zeros((n, C.shape[-1]), dtype=np.complex128)
+    R = C.shape[-1]
+    out = np.zeros((n, R), dtype=np.complex128)
     for a in range(0, n, chunk):
         E = _exp_factors(x[a:a + chunk], N, +1.0)
-        out[a:a + chunk] = np.einsum(expr, C, *E, optimize=True)
+        m = E[0].shape[0]
+        T = E[0] @ C.reshape(N, -1)                    # sum over k_1: (m, N^(d-1) R)
+        for t in range(1, d):
+            T = np.einsum("mkx,mk->mx", T.reshape(m, N, -1), E[t])
+        out[a:a + chunk] = T.reshape(m, R)
     return out
 
 

@@ -1,0 +1,302 @@
+"""Thin Python binding of the C ABI in include/agp.h (ctypes).
+
+Only argument marshalling happens here: torch tensors are passed to the
+library as raw device pointers with their row stride, on the current torch
+CUDA stream. Every step of the computation runs in the CUDA kernels of
+libagp.so; if that library is missing or fails to load, every call raises.
+
+Module-level functions carry the C names (``agp_plan_create``,
+``agp_matvec``, ...). ``Plan`` bundles them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_int32, c_int64, c_void_p
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libagp.so")
+
+AGP_OK, AGP_EINVAL, AGP_EDOMAIN, AGP_ECUDA, AGP_ENOMEM, AGP_NOT_CONVERGED, AGP_TIMEOUT, AGP_ENAN = range(8)
+KERNELS = {"gauss": 0, "matern12": 1}
+PARAMS = {"ell": 0, "sigma_f": 1, "sigma_eps": 2}
+
+
+class AgpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("n", c_int64), ("p", c_int), ("X", c_void_p), ("ldx", c_int64), ("P", c_int),
+        ("win_ptr", POINTER(c_int)), ("win_feat", POINTER(c_int)), ("N", POINTER(c_int)),
+        ("cutoff", c_int), ("sigma_os", c_int), ("kernel", c_int),
+        ("ell", c_double), ("sigma_f", c_double), ("sigma_eps", c_double), ("prec", c_int),
+    ]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", c_double * 4), ("launches", c_int64 * 4)]
+
+
+STAGES = ("spread", "fft", "interp", "other")
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "agp_plan_create": (c_int, [POINTER(c_void_p), POINTER(_Desc), c_void_p]),
+    "agp_plan_destroy": (c_int, [c_void_p]),
+    "agp_set_hyper": (c_int, [c_void_p, c_double, c_double, c_double, c_void_p]),
+    "agp_matvec": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_int, c_void_p]),
+    "agp_deriv_matvec": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p, c_int64, c_int,
+                                 c_void_p]),
+    "agp_adjoint_nfft": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_int, c_void_p, c_void_p]),
+    "agp_nfft_real": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_int64, c_void_p]),
+    "agp_plan_bins": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "agp_plan_coeffs": (c_int, [c_void_p, c_int, c_int, POINTER(c_double), c_void_p]),
+    "agp_plan_query": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int), c_int, POINTER(c_int),
+                               POINTER(c_int), POINTER(c_int64)]),
+    "agp_profile_enable": (c_int, [c_void_p, c_int]),
+    "agp_profile_read": (c_int, [c_void_p, POINTER(Profile), c_int, c_void_p]),
+    "agp_status_string": (ctypes.c_char_p, [c_int]),
+    "agp_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libagp.so (built by ``paper_2504_00480_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2504_00480_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(status: int):
+    if status != AGP_OK:
+        lib = load_library()
+        raise AgpError(status, f"{lib.agp_status_string(status).decode()}: "
+                               f"{lib.agp_last_error().decode()}")
+
+
+def _stream():
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _block(t: torch.Tensor, dtype, what: str):
+    """(pointer, leading dimension, R) of an [n][R] RHS-minor block."""
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{what} must be {dtype}, got {t.dtype}")
+    if t.dim() == 1:
+        if t.stride(0) != 1:
+            raise ValueError(f"{what} must be contiguous")
+        return t.data_ptr(), 1, 1
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{what} must be 2-D with unit column stride")
+    return t.data_ptr(), t.stride(0), t.shape[1]
+
+
+# ---------------------------------------------------------------------------
+# C-named functions
+# ---------------------------------------------------------------------------
+
+def agp_plan_create(X: torch.Tensor, windows, N, cutoff: int, kernel: str = "gauss",
+                    ell: float = 1.0, sigma_f: float = 1.0, sigma_eps: float = 0.0,
+                    sigma_os: int = 2) -> c_void_p:
+    lib = load_library()
+    if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
+    if X.dtype not in (torch.float32, torch.float64):
+        raise ValueError("X must be float32 or float64")
+    P = len(windows)
+    Ns = [int(N)] * P if np.isscalar(N) else [int(v) for v in N]
+    ptr = [0]
+    feat = []
+    for w in windows:
+        feat += [int(f) for f in w]
+        ptr.append(len(feat))
+    wp = (c_int * len(ptr))(*ptr)
+    wf = (c_int * max(1, len(feat)))(*feat)
+    Na = (c_int * P)(*Ns)
+    d = _Desc(n=X.shape[0], p=X.shape[1], X=X.data_ptr(), ldx=X.stride(0), P=P,
+              win_ptr=wp, win_feat=wf, N=Na, cutoff=int(cutoff), sigma_os=int(sigma_os),
+              kernel=KERNELS[kernel], ell=float(ell), sigma_f=float(sigma_f),
+              sigma_eps=float(sigma_eps), prec=0 if X.dtype == torch.float32 else 1)
+    h = c_void_p()
+    _check(lib.agp_plan_create(byref(h), byref(d), _stream()))
+    return h
+
+
+def agp_plan_destroy(plan: c_void_p):
+    _check(load_library().agp_plan_destroy(plan))
+
+
+def agp_set_hyper(plan: c_void_p, ell: float, sigma_f: float, sigma_eps: float):
+    _check(load_library().agp_set_hyper(plan, float(ell), float(sigma_f), float(sigma_eps),
+                                        _stream()))
+
+
+def agp_matvec(plan: c_void_p, V: torch.Tensor, Out: torch.Tensor, add_noise: bool = True):
+    vp, ldv, R = _block(V, V.dtype, "V")
+    op, ldo, Ro = _block(Out, V.dtype, "Out")
+    if Ro != R or Out.shape[0] != V.shape[0]:
+        raise ValueError("Out must have V's shape")
+    _check(load_library().agp_matvec(plan, vp, ldv, op, ldo, R, int(bool(add_noise)), _stream()))
+
+
+def agp_deriv_matvec(plan: c_void_p, which: str, V: torch.Tensor, Out: torch.Tensor):
+    vp, ldv, R = _block(V, V.dtype, "V")
+    op, ldo, Ro = _block(Out, V.dtype, "Out")
+    if Ro != R or Out.shape[0] != V.shape[0]:
+        raise ValueError("Out must have V's shape")
+    _check(load_library().agp_deriv_matvec(plan, PARAMS[which], vp, ldv, op, ldo, R, _stream()))
+
+
+def agp_adjoint_nfft(plan: c_void_p, window: int, V: torch.Tensor, chat: torch.Tensor):
+    vp, ldv, R = _block(V, V.dtype, "V")
+    if not chat.is_cuda or not chat.is_contiguous():
+        raise ValueError("chat must be a contiguous CUDA tensor")
+    _check(load_library().agp_adjoint_nfft(plan, window, vp, ldv, R, chat.data_ptr(), _stream()))
+
+
+def agp_nfft_real(plan: c_void_p, window: int, fhat: torch.Tensor, Out: torch.Tensor):
+    op, ldo, R = _block(Out, Out.dtype, "Out")
+    if not fhat.is_cuda or not fhat.is_contiguous():
+        raise ValueError("fhat must be a contiguous CUDA tensor")
+    _check(load_library().agp_nfft_real(plan, window, fhat.data_ptr(), R, op, ldo, _stream()))
+
+
+def agp_plan_bins(plan: c_void_p, window: int, bins: torch.Tensor):
+    if bins.dtype != torch.int32 or not bins.is_cuda or not bins.is_contiguous():
+        raise ValueError("bins must be a contiguous int32 CUDA tensor")
+    _check(load_library().agp_plan_bins(plan, window, bins.data_ptr(), _stream()))
+
+
+def agp_plan_coeffs(plan: c_void_p, window: int, deriv: bool, out: np.ndarray):
+    if out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array")
+    _check(load_library().agp_plan_coeffs(plan, window, int(bool(deriv)),
+                                          out.ctypes.data_as(POINTER(c_double)), _stream()))
+
+
+def agp_plan_query(plan: c_void_p, window: int = 0):
+    n, P, d, N, it = c_int64(), c_int(), c_int(), c_int(), c_int64()
+    _check(load_library().agp_plan_query(plan, byref(n), byref(P), window, byref(d), byref(N),
+                                         byref(it)))
+    return {"n": n.value, "P": P.value, "d": d.value, "N": N.value, "n_items": it.value}
+
+
+def agp_profile_enable(plan: c_void_p, enable: bool = True):
+    _check(load_library().agp_profile_enable(plan, int(bool(enable))))
+
+
+def agp_profile_read(plan: c_void_p, reset: bool = True) -> dict:
+    p = Profile()
+    _check(load_library().agp_profile_read(plan, byref(p), int(bool(reset)), _stream()))
+    return {s: {"ms": p.ms[i], "launches": p.launches[i]} for i, s in enumerate(STAGES)}
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Plan:
+    """A plan over fixed points X (CUDA tensor [n][p], float32 or float64)."""
+
+    def __init__(self, X: torch.Tensor, windows, N, cutoff: int, kernel: str = "gauss",
+                 ell: float = 1.0, sigma_f: float = 1.0, sigma_eps: float = 0.0,
+                 sigma_os: int = 2):
+        self.windows = [list(w) for w in windows]
+        self.N = [int(N)] * len(windows) if np.isscalar(N) else [int(v) for v in N]
+        self.cutoff = int(cutoff)
+        self.kernel = kernel
+        self.dtype = X.dtype
+        self.device = X.device
+        self.n = X.shape[0]
+        self.ell, self.sigma_f, self.sigma_eps = float(ell), float(sigma_f), float(sigma_eps)
+        self._h = agp_plan_create(X, windows, N, cutoff, kernel, ell, sigma_f, sigma_eps, sigma_os)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            agp_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_hyper(self, ell: float, sigma_f: float, sigma_eps: float):
+        agp_set_hyper(self._h, ell, sigma_f, sigma_eps)
+        self.ell, self.sigma_f, self.sigma_eps = float(ell), float(sigma_f), float(sigma_eps)
+
+    def matvec(self, V: torch.Tensor, out: torch.Tensor | None = None, add_noise: bool = True):
+        out = torch.empty_like(V) if out is None else out
+        agp_matvec(self._h, V, out, add_noise)
+        return out
+
+    def deriv_matvec(self, which: str, V: torch.Tensor, out: torch.Tensor | None = None):
+        out = torch.empty_like(V) if out is None else out
+        agp_deriv_matvec(self._h, which, V, out)
+        return out
+
+    def adjoint_nfft(self, window: int, V: torch.Tensor) -> torch.Tensor:
+        d = len(self.windows[window])
+        N = self.N[window]
+        R = 1 if V.dim() == 1 else V.shape[1]
+        cdt = torch.complex64 if self.dtype == torch.float32 else torch.complex128
+        chat = torch.empty((R,) + (N,) * d, dtype=cdt, device=V.device)
+        agp_adjoint_nfft(self._h, window, V, chat)
+        return chat
+
+    def nfft_real(self, window: int, fhat: torch.Tensor, out: torch.Tensor | None = None):
+        R = fhat.shape[0]
+        if out is None:
+            out = torch.empty((self.n, R), dtype=self.dtype, device=fhat.device)
+        agp_nfft_real(self._h, window, fhat.contiguous(), out)
+        return out
+
+    def bins(self, window: int) -> torch.Tensor:
+        d = len(self.windows[window])
+        b = torch.empty((self.n, d), dtype=torch.int32, device=self.device)
+        agp_plan_bins(self._h, window, b)
+        return b
+
+    def coeffs(self, window: int, deriv: bool = False) -> np.ndarray:
+        d = len(self.windows[window])
+        out = np.empty((self.N[window],) * d, dtype=np.float64)
+        agp_plan_coeffs(self._h, window, deriv, out)
+        return out
+
+    def profile(self, enable: bool = True):
+        agp_profile_enable(self._h, enable)
+
+    def profile_read(self, reset: bool = True) -> dict:
+        return agp_profile_read(self._h, reset)
+
+    def query(self, window: int = 0):
+        return agp_plan_query(self._h, window)

@@ -1,0 +1,147 @@
+// Internal declarations of the GB300 additive-kernel fast summation library.
+//
+// Geometry of one feature window (Sec. 3.1 and Appendix A of the paper):
+//   * d <= 3 coordinates per point, scaled into [-1/4, 1/4)^d.
+//   * Bandwidth N (index set I_N = {-N/2..N/2-1}^d), oversampled grid of
+//     n_os = 2N points per dimension at positions l / n_os.
+//   * A point with u = x * n_os has base cell b = floor(u) in [-N/2, N/2) and
+//     touches the 2s grid points l = b-s+1 .. b+s per dimension (Kaiser-Bessel
+//     window of half-support s). Because |x| < 1/4 and s <= N/2 those grid
+//     points never wrap around, and together they fill the "active box"
+//     l in [lo, lo + W) with lo = -N/2 - s + 1 and W = N + 2s - 1. The grids
+//     of this library store only that box: active index a = l - lo, and the
+//     point's taps are a = c + t, c = b + N/2 (its cell), t = 0 .. 2s-1.
+//   * Spectra keep k_1..k_{d-1} in [-N/2, N/2] (K = N+1 values) and the last
+//     coordinate k_d in [0, N/2] (Kh = N/2+1 values, Hermitian half).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "agp.h"
+
+namespace agp {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxWindows = 64;
+constexpr int kItemPoints = 256;     // points per work item (one grid cell or part of one)
+
+// Per-window view handed to the spreading / interpolation kernels.
+template <typename T>
+struct WinDev {
+  const T* xs;            // sorted coordinates, [d][n]
+  const int32_t* perm;    // sorted position -> caller's point index
+  T* grid;                // active-box grid, [W^d][RC]
+  int64_t n;
+  int N, n_os, W;
+};
+
+// Kaiser-Bessel window of Appendix A in grid units, divided by I0(b s) so that
+// its values are O(1) in FP32: psi(delta) = sinh(b r) / (pi I0(b s) r),
+// r = sqrt(s^2 - delta^2), delta = x n_os - l in (-s, s]. `norm` = 1/(pi I0(b s)).
+__device__ __forceinline__ float kb_psi(float delta, float s, float b, float norm) {
+  float r2 = (s - delta) * (s + delta);
+  if (r2 <= 0.f) return b * norm;
+  float r = sqrtf(r2);
+  return sinhf(b * r) / r * norm;
+}
+__device__ __forceinline__ double kb_psi(double delta, double s, double b, double norm) {
+  double r2 = (s - delta) * (s + delta);
+  if (r2 <= 0.0) return b * norm;
+  double r = sqrt(r2);
+  return sinh(b * r) / r * norm;
+}
+
+__device__ __forceinline__ float dev_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double dev_floor(double x) { return floor(x); }
+
+// One window of a plan (host side).
+struct Window {
+  int d = 0, N = 0, n_os = 0, W = 0, K = 0, Kh = 0, s = 0;
+  int feat[kMaxDim] = {0, 0, 0};
+  int64_t cells = 0;         // N^d
+  int64_t grid_elems = 0;    // W^d (per RHS column)
+  int64_t spec_elems = 0;    // W^(d-1) * Kh (complex, per RHS column): max intermediate
+  int64_t dmul_elems = 0;    // K^(d-1) * Kh
+  // device buffers
+  int32_t* perm = nullptr;       // [n]
+  void* xs = nullptr;            // [d][n]
+  int32_t* cell_start = nullptr; // [cells + 1]
+  int4* items = nullptr;         // work items (window, cell, start, count)
+  int64_t n_items = 0;
+  double* b = nullptr;           // b_k on I_N^d (FP64)
+  double* bder = nullptr;        // b_k of the ell-derivative kernel
+  void* dmul = nullptr;          // spectral multiplier for K_s     [dmul_elems]
+  void* dmul_der = nullptr;      // spectral multiplier for K_s^der [dmul_elems]
+  void* winhat = nullptr;        // per-dim deconvolution n_os psi_hat(k), k in [-N/2, N/2] (prec)
+  void* tw = nullptr;            // twiddles exp(-2 pi i k (a + lo) / n_os), [K][W] complex (prec)
+  void* grid = nullptr;          // [grid_elems][rc_max] (prec)
+  void* specA = nullptr;         // complex scratch [spec_elems][rc_max]
+  void* specB = nullptr;
+  std::vector<double> winhat_h;  // host copy of n_os psi_hat(k)
+};
+
+}  // namespace agp
+
+struct agp_plan_s {
+  int64_t n = 0;
+  int p = 0;
+  int P = 0;
+  int s = 0;
+  int sigma_os = 2;
+  agp_kernel kernel = AGP_GAUSS;
+  agp_prec prec = AGP_F32;
+  double ell = 1, sigma_f = 1, sigma_eps = 0;
+  double kb_b = 0, kb_norm = 0;
+  int rc_max = 32;
+  std::vector<agp::Window> win;
+  void* wins_dev = nullptr;      // WinDev<T>[P]
+  int4* items_all = nullptr;     // work items of every window, grouped by d
+  int64_t items_by_d[agp::kMaxDim + 1] = {0, 0, 0, 0};   // offsets of each d group
+  int* err_dev = nullptr;        // device error flags
+  // stage profiler
+  bool prof = false;
+  struct Ev { int stage; cudaEvent_t a, b; };
+  std::vector<Ev> prof_ev;
+  int64_t launches[4] = {0, 0, 0, 0};
+};
+
+namespace agp {
+
+// ---- error plumbing (agp_plan.cu) ----
+agp_status set_error(agp_status s, const std::string& msg);
+agp_status cuda_status(cudaError_t e, const char* what);
+
+// ---- kernel launchers ----
+// Spread the columns V[:, 0..R) of every window with dimension d onto the
+// grids (grids must be zeroed). RC = grid column count (32, 8, 1 for FP32;
+// 4, 1 for FP64). (agp_nufft.cu)
+template <typename T>
+cudaError_t launch_spread(const agp_plan_s* plan, int d, int RC, const T* V, int64_t ldv,
+                          int R, cudaStream_t st);
+// Interpolate the grids of every window with dimension d and add
+// scale * result into Out[:, 0..R). (agp_nufft.cu)
+template <typename T>
+cudaError_t launch_interp(const agp_plan_s* plan, int d, int RC, T* Out, int64_t ldo, int R,
+                          T scale, cudaStream_t st);
+// Single-window variants (adjoint NFFT / NFFT entry points).
+template <typename T>
+cudaError_t launch_spread_window(const agp_plan_s* plan, int w, int RC, const T* V,
+                                 int64_t ldv, int R, cudaStream_t st);
+template <typename T>
+cudaError_t launch_interp_window(const agp_plan_s* plan, int w, int RC, T* Out, int64_t ldo,
+                                 int R, T scale, cudaStream_t st);
+
+// Grid -> half spectrum (forward DFT over the active box), spectrum ->
+// grid (inverse), and the spectral multiply. (agp_fft.cu)
+template <typename T>
+cudaError_t fft_forward(const Window& w, int RC, cudaStream_t st);   // grid -> specA (k layout)
+template <typename T>
+cudaError_t fft_inverse(const Window& w, int RC, cudaStream_t st);   // specA (k layout) -> grid
+template <typename T>
+cudaError_t spectral_multiply(const Window& w, const void* dmul, int RC, cudaStream_t st);
+
+}  // namespace agp

@@ -1,0 +1,916 @@
+// Plan construction and the C ABI of include/agp.h.
+//
+// Plan creation (once per point set):
+//   a0  per window: grid-cell index floor(x_t n_os) of every point (exact:
+//       n_os is a power of two), domain check x in [-1/4, 1/4)^d (Sec. 3.1),
+//       counting sort of the points by cell, sorted coordinate copies, and
+//       the list of work items (up to kItemPoints points of one cell each).
+//   a1  per window: Fourier coefficients b_k of the kernel and of its
+//       ell-derivative (Sec. 3.1 eq. (3.2), Sec. 3.2 eq. (3.4)) in FP64, and
+//       the spectral multipliers b_k / prod_t (n_os psi_hat(k_t))^2 (Appendix A
+//       deconvolution, applied once on each side of the transform pair).
+// Matvec (Sec. 3.1 eq. (3.3), real part, then the weighted window sum):
+//   out = sigma_eps^2 V; per block of RC right-hand sides: zero the grids,
+//   spread, forward DFT, multiply, inverse DFT, interpolate (+= sigma_f^2 h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "agp_internal.cuh"
+
+namespace agp {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+agp_status set_error(agp_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+agp_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return AGP_OK;
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(AGP_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+  return set_error(AGP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define AGP_CUDA(call)                                             \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_status(e_, #call);          \
+  } while (0)
+
+#define AGP_TRY(call)                                              \
+  do {                                                             \
+    agp_status s_ = (call);                                        \
+    if (s_ != AGP_OK) return s_;                                   \
+  } while (0)
+
+namespace {
+
+enum : int { kErrDomain = 1 };
+
+// ---------------------------------------------------------------------------
+// a0: binning and counting sort
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_bin_count(const T* __restrict__ X, int64_t ldx, int64_t n, int d, int f0, int f1,
+                            int f2, int N, int n_os, int32_t* __restrict__ cell_of,
+                            int32_t* __restrict__ counts, int* err) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int f[3] = {f0, f1, f2};
+  int cell = 0;
+  bool bad = false;
+  for (int t = 0; t < d; ++t) {
+    const T u = X[i * ldx + f[t]] * T(n_os);   // exact: n_os is a power of two
+    const T fl = dev_floor(u);
+    // cell coordinate c = floor(u) + N/2 must lie in [0, N)
+    if (!(fl >= T(-N / 2) && fl < T(N / 2))) {
+      bad = true;
+    }
+    int c = bad ? 0 : (int)fl + N / 2;
+    cell = cell * N + c;
+  }
+  if (bad) {
+    atomicOr(err, kErrDomain);
+    cell = 0;
+  }
+  cell_of[i] = cell;
+  atomicAdd(counts + cell, 1);
+}
+
+// Exclusive scan of `in` [n] into `out` [n + 1] by one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_exclusive(const int32_t* __restrict__ in,
+                                                         int32_t* __restrict__ out, int64_t n) {
+  __shared__ int64_t part[1024];
+  const int tid = threadIdx.x;
+  const int64_t per = (n + 1023) / 1024;
+  const int64_t a = tid * per, b = min(n, a + per);
+  int64_t s = 0;
+  for (int64_t i = a; i < b; ++i) s += in[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    int64_t run = 0;
+    for (int k = 0; k < 1024; ++k) {
+      const int64_t v = part[k];
+      part[k] = run;
+      run += v;
+    }
+    out[n] = (int32_t)run;
+  }
+  __syncthreads();
+  int64_t run = part[tid];
+  for (int64_t i = a; i < b; ++i) {
+    out[i] = (int32_t)run;
+    run += in[i];
+  }
+}
+
+template <typename T>
+__global__ void k_scatter(const T* __restrict__ X, int64_t ldx, int64_t n, int d, int f0, int f1,
+                          int f2, const int32_t* __restrict__ cell_of,
+                          const int32_t* __restrict__ cell_start, int32_t* __restrict__ fill,
+                          int32_t* __restrict__ perm, T* __restrict__ xs) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cell = cell_of[i];
+  const int64_t pos = cell_start[cell] + atomicAdd(fill + cell, 1);
+  perm[pos] = (int32_t)i;
+  const int f[3] = {f0, f1, f2};
+  for (int t = 0; t < d; ++t) xs[t * n + pos] = X[i * ldx + f[t]];
+}
+
+__global__ void k_chunks_per_cell(const int32_t* __restrict__ cell_start, int64_t cells,
+                                  int32_t* __restrict__ nchunks) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= cells) return;
+  const int cnt = cell_start[c + 1] - cell_start[c];
+  nchunks[c] = (cnt + kItemPoints - 1) / kItemPoints;
+}
+
+__global__ void k_make_items(const int32_t* __restrict__ cell_start,
+                             const int32_t* __restrict__ chunk_start, int64_t cells, int window,
+                             int4* __restrict__ items) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= cells) return;
+  const int a = cell_start[c], b = cell_start[c + 1];
+  int o = chunk_start[c];
+  for (int s = a; s < b; s += kItemPoints) items[o++] = make_int4(window, (int)c, s, min(kItemPoints, b - s));
+}
+
+// bins of every point in the caller's order: floor(x_t n_os) (a signed index)
+template <typename T>
+__global__ void k_bins_out(const T* __restrict__ xs, const int32_t* __restrict__ perm, int64_t n,
+                           int d, int n_os, int32_t* __restrict__ bins) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t i = perm[j];
+  for (int t = 0; t < d; ++t) bins[i * d + t] = (int32_t)dev_floor(xs[t * n + j] * T(n_os));
+}
+
+// ---------------------------------------------------------------------------
+// a1: Fourier coefficients (FP64)
+// ---------------------------------------------------------------------------
+// samples[l] = kappa(|l / N|) (or its ell-derivative), l in I_N^d row-major.
+__global__ void k_kernel_samples(double* __restrict__ out, int N, int d, int kernel, double ell,
+                                 int der) {
+  int64_t total = 1;
+  for (int t = 0; t < d; ++t) total *= N;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int64_t rem = e;
+  double r2 = 0.0;
+  for (int t = d - 1; t >= 0; --t) {
+    const int l = (int)(rem % N) - N / 2;
+    rem /= N;
+    const double x = (double)l / N;
+    r2 += x * x;
+  }
+  double v;
+  if (kernel == AGP_GAUSS) {
+    v = exp(-r2 / (2.0 * ell * ell));
+    if (der) v *= r2 / (ell * ell * ell);
+  } else {
+    const double r = sqrt(r2);
+    v = exp(-r / ell);
+    if (der) v *= r / (ell * ell);
+  }
+  out[e] = v;
+}
+
+// One axis of the d-dimensional DFT of eq. (3.2). The samples are real and
+// even in every coordinate (kappa depends on |r| and the sample at
+// l_t = -N/2 multiplies exp(i pi k_t) = (-1)^k_t), so the transform along each
+// axis is the cosine sum (1/N) sum_l in[l] cos(2 pi l k / N).
+__global__ void k_cos_axis(const double* __restrict__ in, double* __restrict__ out, int N, int d,
+                           int axis) {
+  int64_t total = 1, stride = 1;
+  for (int t = 0; t < d; ++t) total *= N;
+  for (int t = d - 1; t > axis; --t) stride *= N;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int kk = (int)((e / stride) % N);
+  const int k = kk - N / 2;
+  const int64_t base = e - (int64_t)kk * stride;
+  double s = 0.0;
+  for (int li = 0; li < N; ++li) {
+    const int l = li - N / 2;
+    // cos(2 pi l k / N) = cospi(2 l k / N); 2lk/N is exact in binary.
+    s += in[base + (int64_t)li * stride] * cospi(2.0 * (double)l * (double)k / (double)N);
+  }
+  out[e] = s / N;
+}
+
+// Spectral multiplier on the half-spectrum layout [K]^(d-1) x [Kh]:
+//   D(k) = w(k) b_{|k|} / prod_t winhat(k_t)^2,
+//   w(k) = (1[k in I_N] + 1[-k in I_N]) / 2,
+// the real-part symmetrisation of eq. (3.3) over the asymmetric I_N.
+template <typename T>
+__global__ void k_build_dmul(const double* __restrict__ b, const double* __restrict__ winhat,
+                             int N, int d, T* __restrict__ dmul) {
+  const int K = N + 1, Kh = N / 2 + 1;
+  int64_t total = Kh;
+  for (int t = 0; t < d - 1; ++t) total *= K;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int k[3];
+  int64_t rem = e;
+  k[d - 1] = (int)(rem % Kh);
+  rem /= Kh;
+  for (int t = d - 2; t >= 0; --t) {
+    k[t] = (int)(rem % K) - N / 2;
+    rem /= K;
+  }
+  bool in_pos = true, in_neg = true;
+  int64_t bidx = 0;
+  double den = 1.0;
+  for (int t = 0; t < d; ++t) {
+    const int kt = k[t];
+    in_pos = in_pos && (kt >= -N / 2) && (kt <= N / 2 - 1);
+    in_neg = in_neg && (-kt >= -N / 2) && (-kt <= N / 2 - 1);
+    const int ka = kt < 0 ? -kt : kt;
+    const int bi = (ka == N / 2) ? 0 : ka + N / 2;   // b is even and N-periodic
+    bidx = bidx * N + bi;
+    const double wh = winhat[kt + N / 2];
+    den *= wh * wh;
+  }
+  const double wgt = 0.5 * ((in_pos ? 1.0 : 0.0) + (in_neg ? 1.0 : 0.0));
+  dmul[e] = (T)(wgt * b[bidx] / den);
+}
+
+// Half spectrum (forward-DFT layout) -> full I_N^d spectrum divided by the
+// window transform: chat[r][k] = X(k) / prod_t winhat(k_t), with
+// X(k) = conj(X(-k)) for k_d < 0.
+template <typename T, typename T2>
+__global__ void k_extract_spectrum(const T2* __restrict__ spec, const double* __restrict__ winhat,
+                                   int N, int d, int RC, int R, T2* __restrict__ out) {
+  const int K = N + 1, Kh = N / 2 + 1;
+  int64_t cells = 1;
+  for (int t = 0; t < d; ++t) cells *= N;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= cells * R) return;
+  const int r = (int)(e / cells);
+  int64_t rem = e - (int64_t)r * cells;
+  int k[3];
+  for (int t = d - 1; t >= 0; --t) {
+    k[t] = (int)(rem % N) - N / 2;
+    rem /= N;
+  }
+  const bool conj = k[d - 1] < 0;
+  int64_t si = 0;
+  double den = 1.0;
+  for (int t = 0; t < d; ++t) {
+    const int kk = conj ? -k[t] : k[t];
+    si = (t == d - 1) ? si * Kh + kk : si * K + (kk + N / 2);
+    den *= winhat[k[t] + N / 2];
+  }
+  T2 v = spec[si * RC + r];
+  if (conj) v.y = -v.y;
+  v.x = (T)(v.x / den);
+  v.y = (T)(v.y / den);
+  out[e] = v;
+}
+
+// Full spectrum fhat[r][k] on I_N^d -> Hermitian half layout for the inverse
+// DFT: X(k) = (F(k) + conj(F(-k))) / 2, F(k) = fhat(k) / prod winhat(k_t)
+// (zero outside I_N), k in [-N/2, N/2]^(d-1) x [0, N/2].
+template <typename T, typename T2>
+__global__ void k_insert_spectrum(const T2* __restrict__ fhat, const double* __restrict__ winhat,
+                                  int N, int d, int RC, int R, T2* __restrict__ spec) {
+  const int K = N + 1, Kh = N / 2 + 1;
+  int64_t total = Kh;
+  for (int t = 0; t < d - 1; ++t) total *= K;
+  int64_t cells = 1;
+  for (int t = 0; t < d; ++t) cells *= N;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= total * RC) return;
+  const int r = (int)(e % RC);
+  int64_t rem = e / RC;
+  int k[3];
+  k[d - 1] = (int)(rem % Kh);
+  rem /= Kh;
+  for (int t = d - 2; t >= 0; --t) {
+    k[t] = (int)(rem % K) - N / 2;
+    rem /= K;
+  }
+  T2 out;
+  out.x = out.y = T(0);
+  if (r < R) {
+    double den = 1.0;
+    bool in_pos = true, in_neg = true;
+    int64_t ip = 0, ineg = 0;
+    for (int t = 0; t < d; ++t) {
+      in_pos = in_pos && k[t] <= N / 2 - 1;
+      in_neg = in_neg && -k[t] <= N / 2 - 1;
+      ip = ip * N + (k[t] + N / 2);
+      ineg = ineg * N + (-k[t] + N / 2);
+      den *= winhat[k[t] + N / 2];
+    }
+    double re = 0.0, im = 0.0;
+    if (in_pos) {
+      const T2 f = fhat[(int64_t)r * cells + ip];
+      re += f.x;
+      im += f.y;
+    }
+    if (in_neg) {
+      const T2 f = fhat[(int64_t)r * cells + ineg];
+      re += f.x;
+      im -= f.y;
+    }
+    out.x = (T)(0.5 * re / den);
+    out.y = (T)(0.5 * im / den);
+  }
+  spec[e] = out;
+}
+
+template <typename T>
+__global__ void k_init_out(T* __restrict__ Out, int64_t ldo, const T* __restrict__ V, int64_t ldv,
+                           int64_t n, int R, T alpha) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * R) return;
+  const int64_t i = e / R;
+  const int r = (int)(e - i * R);
+  Out[i * ldo + r] = (alpha == T(0)) ? T(0) : alpha * V[i * ldv + r];
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Modified Bessel function I0 by its power series sum_j ((x/2)^2)^j / (j!)^2
+// (all terms positive, so it converges without cancellation).
+double bessel_i0(double x) {
+  const double q = 0.25 * x * x;
+  double term = 1.0, sum = 1.0;
+  for (int j = 1; j < 500; ++j) {
+    term *= q / ((double)j * (double)j);
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+size_t elem_size(agp_prec p) { return p == AGP_F64 ? 8 : 4; }
+
+agp_status validate(const agp_plan_desc* d) {
+  if (!d) return set_error(AGP_EINVAL, "desc is NULL");
+  if (d->n < 1 || d->n > (int64_t)INT32_MAX - 1) return set_error(AGP_EINVAL, "n out of range");
+  if (d->p < 1 || !d->X || d->ldx < d->p) return set_error(AGP_EINVAL, "bad X / p / ldx");
+  if (d->P < 1 || d->P > kMaxWindows || !d->win_ptr || !d->win_feat || !d->N)
+    return set_error(AGP_EINVAL, "bad windows");
+  if (d->sigma_os != 2) return set_error(AGP_EINVAL, "sigma_os must be 2");
+  if (d->cutoff < 2 || d->cutoff > 6) return set_error(AGP_EINVAL, "cutoff must be in [2, 6]");
+  if (!(d->ell > 0) || !std::isfinite(d->ell) || !std::isfinite(d->sigma_f) ||
+      !std::isfinite(d->sigma_eps))
+    return set_error(AGP_EINVAL, "bad hyperparameters");
+  if (d->kernel != AGP_GAUSS && d->kernel != AGP_MATERN12) return set_error(AGP_EINVAL, "bad kernel");
+  if (d->prec != AGP_F32 && d->prec != AGP_F64) return set_error(AGP_EINVAL, "bad prec");
+  std::vector<int> used(d->p, 0);
+  if (d->win_ptr[0] != 0) return set_error(AGP_EINVAL, "win_ptr[0] must be 0");
+  for (int s = 0; s < d->P; ++s) {
+    const int a = d->win_ptr[s], b = d->win_ptr[s + 1];
+    if (b - a < 1 || b - a > kMaxDim) return set_error(AGP_EINVAL, "window dimension must be 1..3");
+    const int N = d->N[s];
+    if (N != 8 && N != 16 && N != 32 && N != 64) return set_error(AGP_EINVAL, "N must be 8, 16, 32 or 64");
+    if (d->cutoff > N / 2) return set_error(AGP_EINVAL, "cutoff must be <= N/2");
+    for (int q = a; q < b; ++q) {
+      const int f = d->win_feat[q];
+      if (f < 0 || f >= d->p) return set_error(AGP_EINVAL, "feature id out of range");
+      if (used[f]++) return set_error(AGP_EINVAL, "windows must be disjoint");
+    }
+  }
+  return AGP_OK;
+}
+
+template <typename T>
+agp_status compute_coeffs(agp_plan_s* pl, cudaStream_t st) {
+  for (auto& w : pl->win) {
+    double* tmp = nullptr;
+    AGP_CUDA(cudaMallocAsync(&tmp, sizeof(double) * w.cells * 2, st));
+    double* t0 = tmp;
+    double* t1 = tmp + w.cells;
+    for (int der = 0; der < 2; ++der) {
+      double* dst = der ? w.bder : w.b;
+      k_kernel_samples<<<nblk(w.cells, 256), 256, 0, st>>>(t0, w.N, w.d, pl->kernel, pl->ell, der);
+      double* src = t0;
+      for (int axis = 0; axis < w.d; ++axis) {
+        double* o = (axis == w.d - 1) ? dst : (src == t0 ? t1 : t0);
+        k_cos_axis<<<nblk(w.cells, 256), 256, 0, st>>>(src, o, w.N, w.d, axis);
+        src = o;
+      }
+      k_build_dmul<T><<<nblk(w.dmul_elems, 256), 256, 0, st>>>(
+          dst, reinterpret_cast<const double*>(w.winhat), w.N, w.d,
+          reinterpret_cast<T*>(der ? w.dmul_der : w.dmul));
+    }
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaFreeAsync(tmp, st));
+  }
+  return AGP_OK;
+}
+
+void free_plan(agp_plan_s* pl) {
+  if (!pl) return;
+  for (auto& w : pl->win) {
+    cudaFree(w.perm);
+    cudaFree(w.xs);
+    cudaFree(w.cell_start);
+    cudaFree(w.b);
+    cudaFree(w.bder);
+    cudaFree(w.dmul);
+    cudaFree(w.dmul_der);
+    cudaFree(w.winhat);
+    cudaFree(w.tw);
+    cudaFree(w.grid);
+    cudaFree(w.specA);
+    cudaFree(w.specB);
+  }
+  for (auto& e : pl->prof_ev) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  cudaFree(pl->items_all);
+  cudaFree(pl->wins_dev);
+  cudaFree(pl->err_dev);
+  delete pl;
+}
+
+template <typename T>
+agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
+  const int64_t n = pl->n;
+  const T* X = reinterpret_cast<const T*>(d->X);
+  AGP_CUDA(cudaMalloc(&pl->err_dev, sizeof(int) * 4));
+  AGP_CUDA(cudaMemsetAsync(pl->err_dev, 0, sizeof(int) * 4, st));
+
+  int32_t* cell_of = nullptr;
+  AGP_CUDA(cudaMallocAsync(&cell_of, sizeof(int32_t) * n, st));
+  std::vector<int32_t*> nchunk_start(pl->P, nullptr);
+  std::vector<int64_t> n_items(pl->P, 0);
+
+  for (int s = 0; s < pl->P; ++s) {
+    Window& w = pl->win[s];
+    int32_t *counts = nullptr, *fill = nullptr, *nch = nullptr;
+    AGP_CUDA(cudaMalloc(&w.perm, sizeof(int32_t) * n));
+    AGP_CUDA(cudaMalloc(&w.xs, sizeof(T) * n * w.d));
+    AGP_CUDA(cudaMalloc(&w.cell_start, sizeof(int32_t) * (w.cells + 1)));
+    AGP_CUDA(cudaMallocAsync(&counts, sizeof(int32_t) * w.cells, st));
+    AGP_CUDA(cudaMallocAsync(&fill, sizeof(int32_t) * w.cells, st));
+    AGP_CUDA(cudaMallocAsync(&nch, sizeof(int32_t) * w.cells, st));
+    AGP_CUDA(cudaMallocAsync(&nchunk_start[s], sizeof(int32_t) * (w.cells + 1), st));
+    AGP_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * w.cells, st));
+    AGP_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * w.cells, st));
+    k_bin_count<T><<<nblk(n, 256), 256, 0, st>>>(X, d->ldx, n, w.d, w.feat[0], w.feat[1],
+                                                 w.feat[2], w.N, w.n_os, cell_of, counts,
+                                                 pl->err_dev);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(counts, w.cell_start, w.cells);
+    k_scatter<T><<<nblk(n, 256), 256, 0, st>>>(X, d->ldx, n, w.d, w.feat[0], w.feat[1],
+                                               w.feat[2], cell_of, w.cell_start, fill, w.perm,
+                                               reinterpret_cast<T*>(w.xs));
+    k_chunks_per_cell<<<nblk(w.cells, 256), 256, 0, st>>>(w.cell_start, w.cells, nch);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(nch, nchunk_start[s], w.cells);
+    AGP_CUDA(cudaGetLastError());
+    int32_t tot = 0;
+    AGP_CUDA(cudaMemcpyAsync(&tot, nchunk_start[s] + w.cells, sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    n_items[s] = tot;
+    AGP_CUDA(cudaFreeAsync(counts, st));
+    AGP_CUDA(cudaFreeAsync(fill, st));
+    AGP_CUDA(cudaFreeAsync(nch, st));
+  }
+  int err = 0;
+  AGP_CUDA(cudaMemcpyAsync(&err, pl->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  if (err & kErrDomain) {
+    for (auto* p : nchunk_start) cudaFree(p);
+    cudaFree(cell_of);
+    return set_error(AGP_EDOMAIN, "a point lies outside [-1/4, 1/4)^d in some window");
+  }
+
+  // Work items, grouped by window dimension (all windows of one d share a launch).
+  int64_t total = 0;
+  for (int s = 0; s < pl->P; ++s) total += n_items[s];
+  AGP_CUDA(cudaMalloc(&pl->items_all, sizeof(int4) * (total > 0 ? total : 1)));
+  int64_t off = 0;
+  for (int dd = 1; dd <= kMaxDim; ++dd) {
+    pl->items_by_d[dd - 1] = off;
+    for (int s = 0; s < pl->P; ++s) {
+      Window& w = pl->win[s];
+      if (w.d != dd) continue;
+      w.items = pl->items_all + off;
+      w.n_items = n_items[s];
+      k_make_items<<<nblk(w.cells, 256), 256, 0, st>>>(w.cell_start, nchunk_start[s], w.cells, s,
+                                                       w.items);
+      off += n_items[s];
+    }
+  }
+  pl->items_by_d[kMaxDim] = off;
+  AGP_CUDA(cudaGetLastError());
+  for (auto* p : nchunk_start) AGP_CUDA(cudaFreeAsync(p, st));
+  AGP_CUDA(cudaFreeAsync(cell_of, st));
+
+  // Deconvolution factors, twiddles, coefficient buffers, grids.
+  std::vector<WinDev<T>> wd(pl->P);
+  for (int s = 0; s < pl->P; ++s) {
+    Window& w = pl->win[s];
+    const double b = pl->kb_b;
+    const double i0bs = bessel_i0(b * w.s);
+    w.winhat_h.resize(w.K);
+    for (int kk = 0; kk < w.K; ++kk) {
+      const double k = kk - w.N / 2;
+      const double om = 2.0 * M_PI * k / w.n_os;
+      w.winhat_h[kk] = bessel_i0(w.s * std::sqrt(b * b - om * om)) / i0bs;
+    }
+    AGP_CUDA(cudaMalloc(&w.winhat, sizeof(double) * w.K));
+    AGP_CUDA(cudaMemcpyAsync(w.winhat, w.winhat_h.data(), sizeof(double) * w.K,
+                             cudaMemcpyHostToDevice, st));
+    // twiddles exp(-2 pi i k (a + lo) / n_os), [K][W]
+    const int lo = -w.N / 2 - w.s + 1;
+    std::vector<T> tw(2 * (size_t)w.K * w.W);
+    for (int kk = 0; kk < w.K; ++kk) {
+      const int k = kk - w.N / 2;
+      for (int a = 0; a < w.W; ++a) {
+        // angle = -2 pi k l / n_os, reduced exactly modulo n_os in integers
+        long long kl = (long long)k * (a + lo);
+        kl %= w.n_os;
+        if (kl < 0) kl += w.n_os;
+        const double ang = -2.0 * M_PI * (double)kl / (double)w.n_os;
+        tw[2 * ((size_t)kk * w.W + a)] = (T)std::cos(ang);
+        tw[2 * ((size_t)kk * w.W + a) + 1] = (T)std::sin(ang);
+      }
+    }
+    AGP_CUDA(cudaMalloc(&w.tw, sizeof(T) * tw.size()));
+    AGP_CUDA(cudaMemcpyAsync(w.tw, tw.data(), sizeof(T) * tw.size(), cudaMemcpyHostToDevice, st));
+    AGP_CUDA(cudaStreamSynchronize(st));   // tw / winhat host vectors go out of scope
+    AGP_CUDA(cudaMalloc(&w.b, sizeof(double) * w.cells));
+    AGP_CUDA(cudaMalloc(&w.bder, sizeof(double) * w.cells));
+    AGP_CUDA(cudaMalloc(&w.dmul, sizeof(T) * w.dmul_elems));
+    AGP_CUDA(cudaMalloc(&w.dmul_der, sizeof(T) * w.dmul_elems));
+    AGP_CUDA(cudaMalloc(&w.grid, sizeof(T) * w.grid_elems * pl->rc_max));
+    AGP_CUDA(cudaMalloc(&w.specA, 2 * sizeof(T) * w.spec_elems * pl->rc_max));
+    AGP_CUDA(cudaMalloc(&w.specB, 2 * sizeof(T) * w.spec_elems * pl->rc_max));
+    wd[s].xs = reinterpret_cast<const T*>(w.xs);
+    wd[s].perm = w.perm;
+    wd[s].grid = reinterpret_cast<T*>(w.grid);
+    wd[s].n = n;
+    wd[s].N = w.N;
+    wd[s].n_os = w.n_os;
+    wd[s].W = w.W;
+  }
+  AGP_CUDA(cudaMalloc(&pl->wins_dev, sizeof(WinDev<T>) * pl->P));
+  AGP_CUDA(cudaMemcpyAsync(pl->wins_dev, wd.data(), sizeof(WinDev<T>) * pl->P,
+                           cudaMemcpyHostToDevice, st));
+  AGP_TRY(compute_coeffs<T>(pl, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  return AGP_OK;
+}
+
+int pick_rc(const agp_plan_s* pl, int R) {
+  if (pl->prec == AGP_F32) return R >= 9 ? 32 : (R >= 2 ? 8 : 1);
+  return R >= 2 ? 4 : 1;
+}
+
+// Stage timing: a pair of events around a group of launches on `st`.
+struct StageTimer {
+  agp_plan_s* pl;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageTimer(agp_plan_s* p, int s, cudaStream_t t) : pl(p), stage(s), st(t) {
+    if (pl->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+  }
+  ~StageTimer() {
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) == cudaSuccess && cudaEventRecord(b, st) == cudaSuccess)
+      pl->prof_ev.push_back({stage, a, b});
+    else
+      cudaEventDestroy(a);
+  }
+};
+
+// Sum over windows of scale * K_s V (coefficient set `der`), added into Out.
+template <typename T>
+agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_t ldo, int R,
+                         int der, T scale, cudaStream_t st) {
+  const int rc = pick_rc(pl, R);
+  for (int r0 = 0; r0 < R; r0 += rc) {
+    const int Rc = R - r0 < rc ? R - r0 : rc;
+    for (auto& w : pl->win)
+      AGP_CUDA(cudaMemsetAsync(w.grid, 0, sizeof(T) * w.grid_elems * rc, st));
+    for (int dd = 1; dd <= kMaxDim; ++dd)
+      if (pl->items_by_d[dd] > pl->items_by_d[dd - 1]) {
+        StageTimer tm(pl, 0, st);
+        AGP_CUDA(launch_spread<T>(pl, dd, rc, V + r0, ldv, Rc, st));
+        pl->launches[0] += 1;
+      }
+    {
+      StageTimer tm(pl, 1, st);
+      for (auto& w : pl->win) {
+        AGP_CUDA(fft_forward<T>(w, rc, st));
+        AGP_CUDA(spectral_multiply<T>(w, der ? w.dmul_der : w.dmul, rc, st));
+        AGP_CUDA(fft_inverse<T>(w, rc, st));
+        pl->launches[1] += 2 * w.d + 1;
+      }
+    }
+    for (int dd = 1; dd <= kMaxDim; ++dd)
+      if (pl->items_by_d[dd] > pl->items_by_d[dd - 1]) {
+        StageTimer tm(pl, 2, st);
+        AGP_CUDA(launch_interp<T>(pl, dd, rc, Out + r0, ldo, Rc, scale, st));
+        pl->launches[2] += 1;
+      }
+  }
+  return AGP_OK;
+}
+
+template <typename T>
+agp_status matvec_t(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_t ldo, int R,
+                    T noise, T scale, int der, bool windows, cudaStream_t st) {
+  {
+    StageTimer tm(pl, 3, st);
+    k_init_out<T><<<nblk(pl->n * R, 256), 256, 0, st>>>(Out, ldo, V, ldv, pl->n, R, noise);
+    pl->launches[3] += 1;
+  }
+  AGP_CUDA(cudaGetLastError());
+  if (windows) AGP_TRY(apply_windows<T>(pl, V, ldv, Out, ldo, R, der, scale, st));
+  return AGP_OK;
+}
+
+agp_status check_block(agp_plan pl, const void* V, int64_t ldv, const void* Out, int64_t ldo,
+                       int R) {
+  if (!pl) return set_error(AGP_EINVAL, "plan is NULL");
+  if (!V || !Out) return set_error(AGP_EINVAL, "V / Out is NULL");
+  if (R < 1 || ldv < R || ldo < R) return set_error(AGP_EINVAL, "need R >= 1, ldv >= R, ldo >= R");
+  const size_t es = elem_size(pl->prec);
+  const char* v0 = static_cast<const char*>(V);
+  const char* o0 = static_cast<const char*>(Out);
+  const char* v1 = v0 + es * (size_t)((pl->n - 1) * ldv + R);
+  const char* o1 = o0 + es * (size_t)((pl->n - 1) * ldo + R);
+  if (v0 < o1 && o0 < v1) return set_error(AGP_EINVAL, "Out overlaps V");
+  return AGP_OK;
+}
+
+}  // namespace
+}  // namespace agp
+
+using namespace agp;
+
+extern "C" {
+
+const char* agp_status_string(agp_status s) {
+  switch (s) {
+    case AGP_OK: return "AGP_OK";
+    case AGP_EINVAL: return "AGP_EINVAL";
+    case AGP_EDOMAIN: return "AGP_EDOMAIN";
+    case AGP_ECUDA: return "AGP_ECUDA";
+    case AGP_ENOMEM: return "AGP_ENOMEM";
+    case AGP_NOT_CONVERGED: return "AGP_NOT_CONVERGED";
+    case AGP_TIMEOUT: return "AGP_TIMEOUT";
+    case AGP_ENAN: return "AGP_ENAN";
+  }
+  return "AGP_UNKNOWN";
+}
+
+const char* agp_last_error(void) { return g_last_error.c_str(); }
+
+agp_status agp_plan_create(agp_plan* out, const agp_plan_desc* d, void* stream) {
+  if (!out) return set_error(AGP_EINVAL, "out is NULL");
+  *out = nullptr;
+  AGP_TRY(validate(d));
+  auto* pl = new (std::nothrow) agp_plan_s();
+  if (!pl) return set_error(AGP_ENOMEM, "host allocation");
+  pl->n = d->n;
+  pl->p = d->p;
+  pl->P = d->P;
+  pl->s = d->cutoff;
+  pl->sigma_os = d->sigma_os;
+  pl->kernel = d->kernel;
+  pl->prec = d->prec;
+  pl->ell = d->ell;
+  pl->sigma_f = d->sigma_f;
+  pl->sigma_eps = d->sigma_eps;
+  pl->kb_b = M_PI * (2.0 - 1.0 / d->sigma_os);
+  pl->kb_norm = 1.0 / (M_PI * bessel_i0(pl->kb_b * d->cutoff));
+  pl->rc_max = d->prec == AGP_F32 ? 32 : 4;
+  pl->win.resize(d->P);
+  for (int s = 0; s < d->P; ++s) {
+    Window& w = pl->win[s];
+    w.d = d->win_ptr[s + 1] - d->win_ptr[s];
+    for (int t = 0; t < w.d; ++t) w.feat[t] = d->win_feat[d->win_ptr[s] + t];
+    w.N = d->N[s];
+    w.n_os = d->sigma_os * w.N;
+    w.s = d->cutoff;
+    w.W = w.N + 2 * w.s - 1;
+    w.K = w.N + 1;
+    w.Kh = w.N / 2 + 1;
+    w.cells = 1;
+    w.grid_elems = 1;
+    w.spec_elems = w.Kh;
+    w.dmul_elems = w.Kh;
+    for (int t = 0; t < w.d; ++t) {
+      w.cells *= w.N;
+      w.grid_elems *= w.W;
+    }
+    for (int t = 0; t < w.d - 1; ++t) {
+      w.spec_elems *= w.W;
+      w.dmul_elems *= w.K;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  agp_status s = (d->prec == AGP_F32) ? plan_build<float>(pl, d, st) : plan_build<double>(pl, d, st);
+  if (s != AGP_OK) {
+    cudaStreamSynchronize(st);
+    free_plan(pl);
+    return s;
+  }
+  *out = pl;
+  return AGP_OK;
+}
+
+agp_status agp_plan_destroy(agp_plan pl) {
+  if (!pl) return AGP_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_plan(pl);
+  return cuda_status(e, "agp_plan_destroy");
+}
+
+agp_status agp_set_hyper(agp_plan pl, double ell, double sigma_f, double sigma_eps, void* stream) {
+  if (!pl) return set_error(AGP_EINVAL, "plan is NULL");
+  if (!(ell > 0) || !std::isfinite(ell) || !std::isfinite(sigma_f) || !std::isfinite(sigma_eps))
+    return set_error(AGP_EINVAL, "bad hyperparameters");
+  const bool new_ell = ell != pl->ell;
+  pl->ell = ell;
+  pl->sigma_f = sigma_f;
+  pl->sigma_eps = sigma_eps;
+  if (!new_ell) return AGP_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return pl->prec == AGP_F32 ? compute_coeffs<float>(pl, st) : compute_coeffs<double>(pl, st);
+}
+
+agp_status agp_matvec(agp_plan pl, const void* V, int64_t ldv, void* Out, int64_t ldo, int R,
+                      int add_noise, void* stream) {
+  AGP_TRY(check_block(pl, V, ldv, Out, ldo, R));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double noise = add_noise ? pl->sigma_eps * pl->sigma_eps : 0.0;
+  const double scale = pl->sigma_f * pl->sigma_f;
+  if (pl->prec == AGP_F32)
+    return matvec_t<float>(pl, (const float*)V, ldv, (float*)Out, ldo, R, (float)noise,
+                           (float)scale, 0, true, st);
+  return matvec_t<double>(pl, (const double*)V, ldv, (double*)Out, ldo, R, noise, scale, 0, true,
+                          st);
+}
+
+agp_status agp_deriv_matvec(agp_plan pl, agp_param which, const void* V, int64_t ldv, void* Out,
+                            int64_t ldo, int R, void* stream) {
+  AGP_TRY(check_block(pl, V, ldv, Out, ldo, R));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double noise = 0.0, scale = 0.0;
+  int der = 0;
+  bool windows = true;
+  switch (which) {
+    case AGP_D_ELL: scale = pl->sigma_f * pl->sigma_f; der = 1; break;
+    case AGP_D_SIGMA_F: scale = 2.0 * pl->sigma_f; break;
+    case AGP_D_SIGMA_EPS: noise = 2.0 * pl->sigma_eps; windows = false; break;
+    default: return set_error(AGP_EINVAL, "bad agp_param");
+  }
+  if (pl->prec == AGP_F32)
+    return matvec_t<float>(pl, (const float*)V, ldv, (float*)Out, ldo, R, (float)noise,
+                           (float)scale, der, windows, st);
+  return matvec_t<double>(pl, (const double*)V, ldv, (double*)Out, ldo, R, noise, scale, der,
+                          windows, st);
+}
+
+agp_status agp_adjoint_nfft(agp_plan pl, int window, const void* V, int64_t ldv, int R, void* chat,
+                            void* stream) {
+  if (!pl || window < 0 || window >= pl->P || !V || !chat || R < 1 || ldv < R)
+    return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Window& w = pl->win[window];
+  const int rc = pick_rc(pl, R);
+  for (int r0 = 0; r0 < R; r0 += rc) {
+    const int Rc = R - r0 < rc ? R - r0 : rc;
+    if (pl->prec == AGP_F32) {
+      AGP_CUDA(cudaMemsetAsync(w.grid, 0, sizeof(float) * w.grid_elems * rc, st));
+      AGP_CUDA(launch_spread_window<float>(pl, window, rc, (const float*)V + r0, ldv, Rc, st));
+      AGP_CUDA(fft_forward<float>(w, rc, st));
+      const float2* spec = (const float2*)((w.d % 2) ? w.specA : w.specB);
+      k_extract_spectrum<float, float2><<<nblk(w.cells * Rc, 256), 256, 0, st>>>(
+          spec, (const double*)w.winhat, w.N, w.d, rc, Rc, (float2*)chat + (int64_t)r0 * w.cells);
+    } else {
+      AGP_CUDA(cudaMemsetAsync(w.grid, 0, sizeof(double) * w.grid_elems * rc, st));
+      AGP_CUDA(launch_spread_window<double>(pl, window, rc, (const double*)V + r0, ldv, Rc, st));
+      AGP_CUDA(fft_forward<double>(w, rc, st));
+      const double2* spec = (const double2*)((w.d % 2) ? w.specA : w.specB);
+      k_extract_spectrum<double, double2><<<nblk(w.cells * Rc, 256), 256, 0, st>>>(
+          spec, (const double*)w.winhat, w.N, w.d, rc, Rc, (double2*)chat + (int64_t)r0 * w.cells);
+    }
+    AGP_CUDA(cudaGetLastError());
+  }
+  return AGP_OK;
+}
+
+agp_status agp_nfft_real(agp_plan pl, int window, const void* fhat, int R, void* Out, int64_t ldo,
+                         void* stream) {
+  if (!pl || window < 0 || window >= pl->P || !fhat || !Out || R < 1 || ldo < R)
+    return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Window& w = pl->win[window];
+  const int rc = pick_rc(pl, R);
+  const int64_t spec_total = w.dmul_elems * rc;
+  for (int r0 = 0; r0 < R; r0 += rc) {
+    const int Rc = R - r0 < rc ? R - r0 : rc;
+    if (pl->prec == AGP_F32) {
+      if (r0 == 0)
+        k_init_out<float><<<nblk(pl->n * R, 256), 256, 0, st>>>((float*)Out, ldo, nullptr, 0,
+                                                                 pl->n, R, 0.f);
+      float2* spec = (float2*)((w.d % 2) ? w.specA : w.specB);
+      k_insert_spectrum<float, float2><<<nblk(spec_total, 256), 256, 0, st>>>(
+          (const float2*)fhat + (int64_t)r0 * w.cells, (const double*)w.winhat, w.N, w.d, rc, Rc,
+          spec);
+      AGP_CUDA(fft_inverse<float>(w, rc, st));
+      AGP_CUDA(launch_interp_window<float>(pl, window, rc, (float*)Out + r0, ldo, Rc, 1.f, st));
+    } else {
+      if (r0 == 0)
+        k_init_out<double><<<nblk(pl->n * R, 256), 256, 0, st>>>((double*)Out, ldo, nullptr, 0,
+                                                                  pl->n, R, 0.0);
+      double2* spec = (double2*)((w.d % 2) ? w.specA : w.specB);
+      k_insert_spectrum<double, double2><<<nblk(spec_total, 256), 256, 0, st>>>(
+          (const double2*)fhat + (int64_t)r0 * w.cells, (const double*)w.winhat, w.N, w.d, rc, Rc,
+          spec);
+      AGP_CUDA(fft_inverse<double>(w, rc, st));
+      AGP_CUDA(launch_interp_window<double>(pl, window, rc, (double*)Out + r0, ldo, Rc, 1.0, st));
+    }
+    AGP_CUDA(cudaGetLastError());
+  }
+  return AGP_OK;
+}
+
+agp_status agp_plan_bins(agp_plan pl, int window, int32_t* bins, void* stream) {
+  if (!pl || window < 0 || window >= pl->P || !bins) return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Window& w = pl->win[window];
+  if (pl->prec == AGP_F32)
+    k_bins_out<float><<<nblk(pl->n, 256), 256, 0, st>>>((const float*)w.xs, w.perm, pl->n, w.d,
+                                                        w.n_os, bins);
+  else
+    k_bins_out<double><<<nblk(pl->n, 256), 256, 0, st>>>((const double*)w.xs, w.perm, pl->n, w.d,
+                                                         w.n_os, bins);
+  return cuda_status(cudaGetLastError(), "agp_plan_bins");
+}
+
+agp_status agp_plan_coeffs(agp_plan pl, int window, int deriv, double* b, void* stream) {
+  if (!pl || window < 0 || window >= pl->P || !b) return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Window& w = pl->win[window];
+  AGP_CUDA(cudaMemcpyAsync(b, deriv ? w.bder : w.b, sizeof(double) * w.cells,
+                           cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  return AGP_OK;
+}
+
+agp_status agp_profile_enable(agp_plan pl, int enable) {
+  if (!pl) return set_error(AGP_EINVAL, "plan is NULL");
+  pl->prof = enable != 0;
+  return AGP_OK;
+}
+
+agp_status agp_profile_read(agp_plan pl, agp_profile_t* out, int reset, void* stream) {
+  if (!pl || !out) return set_error(AGP_EINVAL, "bad arguments");
+  AGP_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  for (int k = 0; k < 4; ++k) {
+    out->ms[k] = 0.0;
+    out->launches[k] = pl->launches[k];
+  }
+  for (auto& e : pl->prof_ev) {
+    float ms = 0.f;
+    AGP_CUDA(cudaEventSynchronize(e.b));
+    AGP_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
+    out->ms[e.stage] += ms;
+  }
+  if (reset) {
+    for (auto& e : pl->prof_ev) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    pl->prof_ev.clear();
+    for (int k = 0; k < 4; ++k) pl->launches[k] = 0;
+  }
+  return AGP_OK;
+}
+
+agp_status agp_plan_query(agp_plan pl, int64_t* n, int* P, int window, int* d, int* N,
+                          int64_t* n_items) {
+  if (!pl) return set_error(AGP_EINVAL, "plan is NULL");
+  if (n) *n = pl->n;
+  if (P) *P = pl->P;
+  if (window >= 0 && window < pl->P) {
+    if (d) *d = pl->win[window].d;
+    if (N) *N = pl->win[window].N;
+    if (n_items) *n_items = pl->win[window].n_items;
+  }
+  return AGP_OK;
+}
+
+}  // extern "C"
