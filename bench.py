@@ -109,6 +109,26 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def measured_traffic(kernel, n, R):
+    """DRAM bytes (read + write) of one launch of `kernel` from the committed
+    ncu summary in profiles/traffic.json, or None when the summary does not
+    match this workload or the kernel source changed after the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        entry = json.load(open(path))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    if entry.get("n") != n or entry.get("rhs") != R:
+        return None
+    src = os.path.join(ROOT, "paper_2504_00480_gb300", "csrc", entry["source_file"])
+    try:
+        import hashlib
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return entry["bytes"] if digest == entry.get("source_sha256") else None
+
+
 # ---------------------------------------------------------------------------
 # reference arm / CPU baseline: the FP64 oracle on host cores
 # ---------------------------------------------------------------------------
@@ -229,19 +249,19 @@ def run_gpu(args):
     value = world * R * args.steps / (ms / 1e3)
     launches_per_step = sum(p["launches"] for p in prof.values()) / args.steps
 
-    # roofline of the dominant kernel (spreading or interpolation)
-    taps = sum((2 * w.cutoff) ** len(win) for win in w.windows)
-    per_stage = {s: prof[s]["ms"] / max(1, prof[s]["launches"]) for s in prof}
-    dom = max(("spread", "interp"), key=lambda s: prof[s]["ms"])
-    # algorithmic FP32 work of one launch: one FMA per tap, point and RHS for
-    # the d=3 windows (the launch that dominates); flops = 2 * FMAs
+    # Roofline of the dominant kernel: the d=3 launch of spreading or
+    # interpolation (one launch covers both d=3 windows). Algorithmic work of
+    # one launch: one FMA per tap, point and RHS = 2 flop x n x R x sum of
+    # (2s)^3 over the d=3 windows; its average duration comes from the
+    # library's CUDA events around each launch on the launching stream.
+    dom = max(("spread", "interp"), key=lambda s: prof[s]["ms_by_dim"][3])
+    launch_ms = prof[dom]["ms_by_dim"][3] / max(1, prof[dom]["timed_by_dim"][3])
     taps3 = sum((2 * w.cutoff) ** len(win) for win in w.windows if len(win) == 3)
-    taps2 = taps - taps3
-    ms3 = prof[dom]["ms"] / args.steps          # both launches of the stage, per step
-    flops_step = 2.0 * w.n * R * taps
-    achieved = flops_step / (ms3 / 1e3) / 1e12
+    flops_launch = 2.0 * w.n * R * taps3
+    achieved = flops_launch / (launch_ms / 1e3) / 1e12
     clocks = clk.summary()
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12   # FP32 FMA at max SM clock
+    traffic = measured_traffic(f"k_{dom}", w.n, R)
 
     # end-to-end through the C ABI with host buffers
     Vh = torch.tensor(w.V, dtype=torch.float32).pin_memory()
@@ -283,10 +303,12 @@ def run_gpu(args):
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(Vh.numel() * 4),
                         "d2h_bytes_per_step": int(Oh.numel() * 4)},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
-                "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved,
-                             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                             "traffic": None,
-                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+                "roofline": {"bound": "alu", "kernel": f"k_{dom}<float, 3, 5, 32>",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "launch_ms": launch_ms, "flop_per_launch": flops_launch,
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz "
+                                            "(nominal maximum clock)"},
                 "stages_ms_per_step": {s: prof[s]["ms"] / args.steps for s in prof},
                 "stage_launches_per_step": {s: prof[s]["launches"] / args.steps for s in prof},
                 "clocks": clocks, "cpu_baseline": cpu}

@@ -149,6 +149,73 @@ agp_status agp_plan_coeffs(agp_plan plan, int window, int deriv, double* b, void
 agp_status agp_plan_query(agp_plan plan, int64_t* n, int* P, int window, int* d,
                           int* N, int64_t* n_items);
 
+/* Batched conjugate gradients for K_hat X = B (Sec. 1: CG with zero initial
+ * guess, one independent recursion per column; vectors in the plan precision,
+ * every scalar -- column dot products, alpha, beta, residual norms -- in FP64
+ * on the device). Column r stops when its recursive relative residual
+ * |r_k|_2 / |b|_2 <= rtol or after maxit iterations.
+ * B: device [n][ldb]; Xsol: device [n][ldx], overwritten with the iterates;
+ * iters, relres: optional host arrays [R] (NULL to skip).
+ * n_landmarks: 0 (no preconditioner); other values return AGP_EINVAL.
+ * Returns AGP_NOT_CONVERGED if some column stopped above rtol (Xsol holds the
+ * last iterate). Synchronises `stream`. */
+agp_status agp_pcg_solve(agp_plan plan, const void* B, int64_t ldb, void* Xsol, int64_t ldx,
+                         int R, double rtol, int maxit, int n_landmarks, int* iters,
+                         double* relres, void* stream);
+
+/* Negative log marginal likelihood and its gradient with respect to
+ * (ell, sigma_f, sigma_eps), estimated as in Sec. 1 eqs. (1.4) and (1.5) with
+ * M = I:
+ *   nlml    = 1/2 (y^T alpha + (1/nz) sum_i z_i^T logm(K_hat) z_i + n log 2 pi)
+ *   grad[j] = 1/2 (-alpha^T dK_j alpha + (1/nz) sum_i u_i^T dK_j z_i)
+ * One batched CG run on [y, z_1..z_nz]: every probe column runs exactly
+ * lanczos_steps iterations (its CG coefficients give the Lanczos matrix of
+ * stochastic Lanczos quadrature; u_i is its CG iterate); the y column runs
+ * lanczos_steps iterations too when rtol = 0, else to relative residual rtol
+ * (at most maxit iterations) -- alpha is its iterate.
+ * Y: device [n]; Z: device [n][ldz], nz >= 1 probe columns (e.g. Rademacher,
+ * drawn by the caller); 1 <= lanczos_steps <= 64. nlml: host double; grad:
+ * host double[3] (ell, sigma_f, sigma_eps). Synchronises `stream`. */
+agp_status agp_nlml_grad(agp_plan plan, const void* Y, const void* Z, int64_t ldz, int nz,
+                         int lanczos_steps, double rtol, int maxit, double* nlml, double* grad,
+                         void* stream);
+
+/* ---- Batches of independent problems ----------------------------------------
+ * Many independent GP problems of different sizes (independent plans, each
+ * with its own points, windows and hyperparameters) applied together: every
+ * stage of the matvec runs as ONE launch over the work items of all problems
+ * (the spread and interpolation kernels take each window's vectors from a
+ * device table), so the per-problem launch overhead disappears and small
+ * problems fill the GPU together. All plans must have the same precision and
+ * cutoff; the batch refers to them, so they must outlive it. */
+typedef struct agp_batch_s* agp_batch;
+
+agp_status agp_batch_create(agp_batch* out, const agp_plan* plans, int nprob, void* stream);
+agp_status agp_batch_destroy(agp_batch batch);
+
+/* Bind the right-hand sides and outputs: problem q uses V[q] (device
+ * [n_q][ldv[q]]) and Out[q] (device [n_q][ldo[q]], must not overlap V[q]),
+ * columns 0..R-1, 1 <= R <= 32 (FP32 plans) or R <= 4 (FP64 plans). V, ldv,
+ * Out, ldo are host arrays [nprob]. Reads every plan's current sigma_f and
+ * sigma_eps: bind again after agp_set_hyper changes them (a new ell needs no
+ * rebinding). Synchronises `stream`. */
+agp_status agp_batch_bind(agp_batch batch, const void* const* V, const int64_t* ldv,
+                          void* const* Out, const int64_t* ldo, int R, void* stream);
+
+/* For every bound problem q: Out_q = K_hat_q V_q (which = -1) or
+ * Out_q = (dK_hat_q / dtheta) V_q (which = an agp_param), as agp_matvec and
+ * agp_deriv_matvec. Enqueues a fixed sequence of kernels (no allocation, no
+ * host synchronisation), so it can be captured in a CUDA graph once it has
+ * run outside capture. */
+agp_status agp_batch_matvec(agp_batch batch, int which, void* stream);
+
+/* Column dot products out[r] = sum_i A[i][r] * B[i][r], r < R, accumulated in
+ * FP64 (two-pass, deterministic order) for blocks of the plan precision.
+ * A: device [n][lda], B: device [n][ldb], n = the plan's point count;
+ * out: host double[R]. Synchronises `stream`. */
+agp_status agp_dot_columns(agp_plan plan, const void* A, int64_t lda, const void* B, int64_t ldb,
+                           int R, double* out, void* stream);
+
 /* Stage profiler (tracing). When enabled, the library records a pair of CUDA
  * events on the caller's stream around every kernel launch of the matvec
  * path, per stage: 0 = spreading, 1 = DFT + spectral multiply, 2 =
@@ -158,8 +225,10 @@ agp_status agp_plan_query(agp_plan plan, int64_t* n, int* P, int window, int* d,
  * last reset, and resets when reset != 0. Launch counts are kept even when
  * timing is disabled. */
 typedef struct {
-  double ms[4];
-  int64_t launches[4];
+  double ms[4];                /* device time per stage */
+  int64_t launches[4];         /* kernel launches per stage */
+  double ms_by_dim[4][4];      /* spreading / interpolation time per window dimension d = 1..3 */
+  int64_t timed_by_dim[4][4];  /* number of launches behind ms_by_dim[stage][d] */
 } agp_profile_t;
 
 agp_status agp_profile_enable(agp_plan plan, int enable);

@@ -41,7 +41,8 @@ class _Desc(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("ms", c_double * 4), ("launches", c_int64 * 4)]
+    _fields_ = [("ms", c_double * 4), ("launches", c_int64 * 4),
+                ("ms_by_dim", (c_double * 4) * 4), ("timed_by_dim", (c_int64 * 4) * 4)]
 
 
 STAGES = ("spread", "fft", "interp", "other")
@@ -62,6 +63,17 @@ _SIGS = {
     "agp_plan_coeffs": (c_int, [c_void_p, c_int, c_int, POINTER(c_double), c_void_p]),
     "agp_plan_query": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int), c_int, POINTER(c_int),
                                POINTER(c_int), POINTER(c_int64)]),
+    "agp_pcg_solve": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_double,
+                              c_int, c_int, POINTER(c_int), POINTER(c_double), c_void_p]),
+    "agp_nlml_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int, c_double,
+                              c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
+    "agp_dot_columns": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int,
+                                POINTER(c_double), c_void_p]),
+    "agp_batch_create": (c_int, [POINTER(c_void_p), POINTER(c_void_p), c_int, c_void_p]),
+    "agp_batch_destroy": (c_int, [c_void_p]),
+    "agp_batch_bind": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_int64), POINTER(c_void_p),
+                               POINTER(c_int64), c_int, c_void_p]),
+    "agp_batch_matvec": (c_int, [c_void_p, c_int, c_void_p]),
     "agp_profile_enable": (c_int, [c_void_p, c_int]),
     "agp_profile_read": (c_int, [c_void_p, POINTER(Profile), c_int, c_void_p]),
     "agp_status_string": (ctypes.c_char_p, [c_int]),
@@ -205,6 +217,107 @@ def agp_plan_query(plan: c_void_p, window: int = 0):
     return {"n": n.value, "P": P.value, "d": d.value, "N": N.value, "n_items": it.value}
 
 
+def agp_pcg_solve(plan: c_void_p, B: torch.Tensor, Xsol: torch.Tensor, rtol: float = 1e-4,
+                  maxit: int = 200, n_landmarks: int = 0, raise_not_converged: bool = True):
+    """Batched CG for K_hat X = B. Returns (iters, relres) as numpy arrays."""
+    bp, ldb, R = _block(B, B.dtype, "B")
+    xp, ldx, Rx = _block(Xsol, B.dtype, "Xsol")
+    if Rx != R or Xsol.shape[0] != B.shape[0]:
+        raise ValueError("Xsol must have B's shape")
+    it = (c_int * R)()
+    rel = (c_double * R)()
+    st = load_library().agp_pcg_solve(plan, bp, ldb, xp, ldx, R, float(rtol), int(maxit),
+                                      int(n_landmarks), it, rel, _stream())
+    if st != AGP_NOT_CONVERGED or raise_not_converged:
+        _check(st)
+    return np.array(it[:], dtype=np.int64), np.array(rel[:], dtype=np.float64)
+
+
+def agp_nlml_grad(plan: c_void_p, y: torch.Tensor, Z: torch.Tensor, lanczos_steps: int = 20,
+                  rtol: float = 0.0, maxit: int = 0):
+    """(nlml, {"ell": g, "sigma_f": g, "sigma_eps": g}) with probes Z [n][nz]."""
+    if y.dim() != 1 or not y.is_contiguous():
+        raise ValueError("y must be a contiguous 1-D tensor")
+    zp, ldz, nz = _block(Z, y.dtype, "Z")
+    nl = c_double()
+    g = (c_double * 3)()
+    _check(load_library().agp_nlml_grad(plan, y.data_ptr(), zp, ldz, nz, int(lanczos_steps),
+                                        float(rtol), int(maxit), byref(nl), g, _stream()))
+    return nl.value, {"ell": g[0], "sigma_f": g[1], "sigma_eps": g[2]}
+
+
+def agp_dot_columns(plan: c_void_p, A: torch.Tensor, B: torch.Tensor) -> np.ndarray:
+    """FP64 column dot products of two [n][R] blocks (library kernels)."""
+    ap, lda, R = _block(A, A.dtype, "A")
+    bp, ldb, Rb = _block(B, A.dtype, "B")
+    if Rb != R or A.shape[0] != B.shape[0]:
+        raise ValueError("A and B must have the same shape")
+    out = (c_double * R)()
+    _check(load_library().agp_dot_columns(plan, ap, lda, bp, ldb, R, out, _stream()))
+    return np.array(out[:], dtype=np.float64)
+
+
+def agp_batch_create(plans) -> c_void_p:
+    hs = (c_void_p * len(plans))(*[p.handle.value for p in plans])
+    b = c_void_p()
+    _check(load_library().agp_batch_create(byref(b), hs, len(plans), _stream()))
+    return b
+
+
+def agp_batch_destroy(batch: c_void_p):
+    _check(load_library().agp_batch_destroy(batch))
+
+
+def agp_batch_bind(batch: c_void_p, Vs, Outs):
+    """Bind per-problem right-hand sides and outputs ([n_q][R] blocks)."""
+    if len(Vs) != len(Outs):
+        raise ValueError("need one output per right-hand side block")
+    ptrs_v, lds_v, ptrs_o, lds_o, Rs = [], [], [], [], set()
+    for V, O in zip(Vs, Outs):
+        vp, ldv, R = _block(V, V.dtype, "V")
+        op, ldo, Ro = _block(O, V.dtype, "Out")
+        if Ro != R or O.shape[0] != V.shape[0]:
+            raise ValueError("Out must have V's shape")
+        ptrs_v.append(vp), lds_v.append(ldv), ptrs_o.append(op), lds_o.append(ldo), Rs.add(R)
+    if len(Rs) != 1:
+        raise ValueError("every problem of a batch needs the same number of columns")
+    k = len(Vs)
+    _check(load_library().agp_batch_bind(batch, (c_void_p * k)(*ptrs_v), (c_int64 * k)(*lds_v),
+                                         (c_void_p * k)(*ptrs_o), (c_int64 * k)(*lds_o),
+                                         Rs.pop(), _stream()))
+
+
+def agp_batch_matvec(batch: c_void_p, which: str | None = None):
+    w = -1 if which is None else PARAMS[which]
+    _check(load_library().agp_batch_matvec(batch, w, _stream()))
+
+
+class Batch:
+    """Independent plans applied together, one launch per stage."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)          # the batch refers to them: keep them alive
+        self._h = agp_batch_create(self.plans)
+
+    def bind(self, Vs, Outs):
+        self._bound = (list(Vs), list(Outs))
+        agp_batch_bind(self._h, Vs, Outs)
+
+    def matvec(self, which: str | None = None):
+        agp_batch_matvec(self._h, which)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            agp_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def agp_profile_enable(plan: c_void_p, enable: bool = True):
     _check(load_library().agp_profile_enable(plan, int(bool(enable))))
 
@@ -212,7 +325,10 @@ def agp_profile_enable(plan: c_void_p, enable: bool = True):
 def agp_profile_read(plan: c_void_p, reset: bool = True) -> dict:
     p = Profile()
     _check(load_library().agp_profile_read(plan, byref(p), int(bool(reset)), _stream()))
-    return {s: {"ms": p.ms[i], "launches": p.launches[i]} for i, s in enumerate(STAGES)}
+    return {s: {"ms": p.ms[i], "launches": p.launches[i],
+                "ms_by_dim": [p.ms_by_dim[i][d] for d in range(4)],
+                "timed_by_dim": [p.timed_by_dim[i][d] for d in range(4)]}
+            for i, s in enumerate(STAGES)}
 
 
 # ---------------------------------------------------------------------------
@@ -291,6 +407,16 @@ class Plan:
         out = np.empty((self.N[window],) * d, dtype=np.float64)
         agp_plan_coeffs(self._h, window, deriv, out)
         return out
+
+    def solve(self, B: torch.Tensor, rtol: float = 1e-4, maxit: int = 200,
+              raise_not_converged: bool = True):
+        X = torch.empty_like(B)
+        it, rel = agp_pcg_solve(self._h, B, X, rtol, maxit, 0, raise_not_converged)
+        return X, it, rel
+
+    def nlml_grad(self, y: torch.Tensor, Z: torch.Tensor, lanczos_steps: int = 20,
+                  rtol: float = 0.0, maxit: int = 0):
+        return agp_nlml_grad(self._h, y, Z, lanczos_steps, rtol, maxit)
 
     def profile(self, enable: bool = True):
         agp_profile_enable(self._h, enable)

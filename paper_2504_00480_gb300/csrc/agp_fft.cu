@@ -13,6 +13,10 @@
 // the twiddles are read through the read-only cache (every lane of a warp
 // reads the same twiddle). Cost is O(W K) per column, a few percent of the
 // spreading / interpolation work at the sizes used here.
+//
+// Every kernel serves a group of windows with the same (d, N, s) -- the
+// windows of one plan, or of every problem of a batch -- in one launch:
+// blockIdx.y selects the window's entry in a device table of buffer pointers.
 #include "agp_internal.cuh"
 
 namespace agp {
@@ -22,23 +26,29 @@ template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; };
 template <> struct C2<double> { using t = double2; };
 
+// buffer selector: 0 = grid, 1 = specA, 2 = specB
+template <typename P>
+__device__ __forceinline__ P* buf(const FftWin& f, int sel) {
+  return reinterpret_cast<P*>(sel == 0 ? f.grid : (sel == 1 ? f.specA : f.specB));
+}
+
 // Forward along the last axis, real -> half spectrum:
-// in [M][W][RC] real, out [M][KH][RC] complex, KH = N/2 + 1.
+// grid [M][W][RC] real -> specA [M][KH][RC] complex, KH = N/2 + 1.
 // tw rows are k + N/2 for k in [-N/2, N/2]; rows N/2 .. N are k = 0 .. N/2.
 template <typename T, int KH>
 __global__ void __launch_bounds__(128)
-k_fwd_last(const T* __restrict__ in, typename C2<T>::t* __restrict__ out,
-           const typename C2<T>::t* __restrict__ tw, int W, int RC, int64_t M) {
+k_fwd_last(const FftWin* __restrict__ tab, int W, int RC, int64_t M) {
   using T2 = typename C2<T>::t;
+  const FftWin f = tab[blockIdx.y];
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M * RC) return;
   const int64_t m = e / RC;
   const int r = (int)(e - m * RC);
-  const T2* twh = tw + (int64_t)(KH - 1) * W;   // row of k = 0
+  const T2* twh = reinterpret_cast<const T2*>(f.tw) + (int64_t)(KH - 1) * W;   // row of k = 0
   T re[KH], im[KH];
 #pragma unroll
   for (int k = 0; k < KH; ++k) re[k] = im[k] = T(0);
-  const T* src = in + m * W * RC + r;
+  const T* src = buf<const T>(f, 0) + m * W * RC + r;
   for (int a = 0; a < W; ++a) {
     const T x = src[(int64_t)a * RC];
 #pragma unroll
@@ -48,7 +58,7 @@ k_fwd_last(const T* __restrict__ in, typename C2<T>::t* __restrict__ out,
       im[k] = fma(x, t.y, im[k]);
     }
   }
-  T2* dst = out + m * KH * RC + r;
+  T2* dst = buf<T2>(f, 1) + m * KH * RC + r;
 #pragma unroll
   for (int k = 0; k < KH; ++k) {
     T2 v;
@@ -58,21 +68,21 @@ k_fwd_last(const T* __restrict__ in, typename C2<T>::t* __restrict__ out,
   }
 }
 
-// Forward along a non-last axis, complex -> complex:
-// in [M][W][I], out [M][K][I], K = N + 1.
+// Forward along a non-last axis, complex -> complex: [M][W][I] -> [M][K][I], K = N + 1.
 template <typename T, int K>
 __global__ void __launch_bounds__(128)
-k_fwd_mid(const typename C2<T>::t* __restrict__ in, typename C2<T>::t* __restrict__ out,
-          const typename C2<T>::t* __restrict__ tw, int W, int64_t M, int64_t I) {
+k_fwd_mid(const FftWin* __restrict__ tab, int src_sel, int dst_sel, int W, int64_t M, int64_t I) {
   using T2 = typename C2<T>::t;
+  const FftWin f = tab[blockIdx.y];
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M * I) return;
   const int64_t m = e / I;
   const int64_t i = e - m * I;
+  const T2* tw = reinterpret_cast<const T2*>(f.tw);
   T re[K], im[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) re[k] = im[k] = T(0);
-  const T2* src = in + m * W * I + i;
+  const T2* src = buf<const T2>(f, src_sel) + m * W * I + i;
   for (int a = 0; a < W; ++a) {
     const T2 x = src[(int64_t)a * I];
 #pragma unroll
@@ -84,7 +94,7 @@ k_fwd_mid(const typename C2<T>::t* __restrict__ in, typename C2<T>::t* __restric
       im[k] = fma(x.y, t.x, im[k]);
     }
   }
-  T2* dst = out + m * K * I + i;
+  T2* dst = buf<T2>(f, dst_sel) + m * K * I + i;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     T2 v;
@@ -94,25 +104,26 @@ k_fwd_mid(const typename C2<T>::t* __restrict__ in, typename C2<T>::t* __restric
   }
 }
 
-// Inverse along a non-last axis: in [M][K][I] -> out [M][W][I] (conjugate twiddles).
+// Inverse along a non-last axis: [M][K][I] -> [M][W][I] (conjugate twiddles).
 template <typename T, int K>
 __global__ void __launch_bounds__(128)
-k_inv_mid(const typename C2<T>::t* __restrict__ in, typename C2<T>::t* __restrict__ out,
-          const typename C2<T>::t* __restrict__ tw, int W, int64_t M, int64_t I) {
+k_inv_mid(const FftWin* __restrict__ tab, int src_sel, int dst_sel, int W, int64_t M, int64_t I) {
   using T2 = typename C2<T>::t;
+  const FftWin f = tab[blockIdx.y];
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M * I) return;
   const int64_t m = e / I;
   const int64_t i = e - m * I;
+  const T2* tw = reinterpret_cast<const T2*>(f.tw);
   T xr[K], xi[K];
-  const T2* src = in + m * K * I + i;
+  const T2* src = buf<const T2>(f, src_sel) + m * K * I + i;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const T2 x = src[(int64_t)k * I];
     xr[k] = x.x;
     xi[k] = x.y;
   }
-  T2* dst = out + m * W * I + i;
+  T2* dst = buf<T2>(f, dst_sel) + m * W * I + i;
   for (int a = 0; a < W; ++a) {
     T re = T(0), im = T(0);
 #pragma unroll
@@ -130,28 +141,28 @@ k_inv_mid(const typename C2<T>::t* __restrict__ in, typename C2<T>::t* __restric
   }
 }
 
-// Inverse along the last axis, Hermitian half -> real:
+// Inverse along the last axis, Hermitian half -> real grid:
 // g[a] = Re X_0 + 2 sum_{k=1}^{N/2} Re(X_k exp(+2 pi i k (a + lo) / n_os)).
 template <typename T, int KH>
 __global__ void __launch_bounds__(128)
-k_inv_last(const typename C2<T>::t* __restrict__ in, T* __restrict__ out,
-           const typename C2<T>::t* __restrict__ tw, int W, int RC, int64_t M) {
+k_inv_last(const FftWin* __restrict__ tab, int src_sel, int W, int RC, int64_t M) {
   using T2 = typename C2<T>::t;
+  const FftWin f = tab[blockIdx.y];
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M * RC) return;
   const int64_t m = e / RC;
   const int r = (int)(e - m * RC);
-  const T2* twh = tw + (int64_t)(KH - 1) * W;
+  const T2* twh = reinterpret_cast<const T2*>(f.tw) + (int64_t)(KH - 1) * W;
   T xr[KH], xi[KH];
-  const T2* src = in + m * KH * RC + r;
+  const T2* src = buf<const T2>(f, src_sel) + m * KH * RC + r;
 #pragma unroll
   for (int k = 0; k < KH; ++k) {
     const T2 x = src[(int64_t)k * RC];
-    const T f = (k == 0) ? T(1) : T(2);
-    xr[k] = f * x.x;
-    xi[k] = f * x.y;
+    const T s = (k == 0) ? T(1) : T(2);
+    xr[k] = s * x.x;
+    xi[k] = s * x.y;
   }
-  T* dst = out + m * W * RC + r;
+  T* dst = buf<T>(f, 0) + m * W * RC + r;
   for (int a = 0; a < W; ++a) {
     T acc = T(0);
 #pragma unroll
@@ -165,115 +176,124 @@ k_inv_last(const typename C2<T>::t* __restrict__ in, T* __restrict__ out,
 }
 
 template <typename T>
-__global__ void k_spec_mul(typename C2<T>::t* __restrict__ spec, const T* __restrict__ dmul,
-                           int RC, int64_t total) {
+__global__ void k_spec_mul(const FftWin* __restrict__ tab, int sel, int der, int RC, int64_t total) {
+  using T2 = typename C2<T>::t;
+  const FftWin f = tab[blockIdx.y];
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= total) return;
-  const T d = dmul[e / RC];
-  typename C2<T>::t v = spec[e];
+  const T d = reinterpret_cast<const T*>(der ? f.dmul_der : f.dmul)[e / RC];
+  T2* spec = buf<T2>(f, sel);
+  T2 v = spec[e];
   v.x *= d;
   v.y *= d;
   spec[e] = v;
 }
 
+// zero the grids of every window of a group: [grid_elems * RC] each
+template <typename T>
+__global__ void k_zero_grids(const FftWin* __restrict__ tab, int64_t total) {
+  const FftWin f = tab[blockIdx.y];
+  T* g = reinterpret_cast<T*>(f.grid);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    g[e] = T(0);
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+inline int64_t powi(int64_t b, int e) {
+  int64_t r = 1;
+  for (int t = 0; t < e; ++t) r *= b;
+  return r;
+}
+
 template <typename T, int N>
-cudaError_t forward_n(const Window& w, int RC, cudaStream_t st) {
-  using T2 = typename C2<T>::t;
+cudaError_t forward_n(const FftGroup& g, int RC, cudaStream_t st) {
   constexpr int K = N + 1, KH = N / 2 + 1;
-  const int W = w.W;
-  const T2* tw = reinterpret_cast<const T2*>(w.tw);
-  const T* g = reinterpret_cast<const T*>(w.grid);
-  T2* A = reinterpret_cast<T2*>(w.specA);
-  T2* B = reinterpret_cast<T2*>(w.specB);
-  int64_t M = 1;
-  for (int t = 0; t < w.d - 1; ++t) M *= W;
-  k_fwd_last<T, KH><<<blocks_for(M * RC, 128), 128, 0, st>>>(g, A, tw, W, RC, M);
-  // remaining axes from the second-to-last down to the first
-  T2* src = A;
-  T2* dst = B;
+  const int W = g.W;
+  const int64_t M = powi(W, g.d - 1);
+  k_fwd_last<T, KH><<<dim3(blocks_for(M * RC, 128), g.count), 128, 0, st>>>(g.tab, W, RC, M);
+  // remaining axes from the second-to-last down to the first (ping-pong A/B)
+  int src = 1, dst = 2;
   int64_t I = (int64_t)KH * RC;
-  for (int axis = w.d - 2; axis >= 0; --axis) {
-    int64_t Mo = 1;
-    for (int t = 0; t < axis; ++t) Mo *= W;
-    k_fwd_mid<T, K><<<blocks_for(Mo * I, 128), 128, 0, st>>>(src, dst, tw, W, Mo, I);
+  for (int axis = g.d - 2; axis >= 0; --axis) {
+    const int64_t Mo = powi(W, axis);
+    k_fwd_mid<T, K><<<dim3(blocks_for(Mo * I, 128), g.count), 128, 0, st>>>(g.tab, src, dst, W, Mo, I);
     I *= K;
-    T2* tmp = src;
+    const int t = src;
     src = dst;
-    dst = tmp;
+    dst = t;
   }
   return cudaGetLastError();
 }
 
 template <typename T, int N>
-cudaError_t inverse_n(const Window& w, int RC, cudaStream_t st) {
-  using T2 = typename C2<T>::t;
+cudaError_t inverse_n(const FftGroup& g, int RC, cudaStream_t st) {
   constexpr int K = N + 1, KH = N / 2 + 1;
-  const int W = w.W;
-  const T2* tw = reinterpret_cast<const T2*>(w.tw);
-  T* g = reinterpret_cast<T*>(w.grid);
-  T2* A = reinterpret_cast<T2*>(w.specA);
-  T2* B = reinterpret_cast<T2*>(w.specB);
+  const int W = g.W;
   // The forward pass leaves the spectrum in A for odd d and in B for even d.
-  T2* src = (w.d % 2) ? A : B;
-  T2* dst = (w.d % 2) ? B : A;
-  int64_t I = (int64_t)KH * RC;
-  for (int t = 0; t < w.d - 1; ++t) I *= K;
-  for (int axis = 0; axis <= w.d - 2; ++axis) {
+  int src = (g.d % 2) ? 1 : 2, dst = (g.d % 2) ? 2 : 1;
+  int64_t I = (int64_t)KH * RC * powi(K, g.d - 1);
+  for (int axis = 0; axis <= g.d - 2; ++axis) {
     I /= K;
-    int64_t Mo = 1;
-    for (int t = 0; t < axis; ++t) Mo *= W;
-    k_inv_mid<T, K><<<blocks_for(Mo * I, 128), 128, 0, st>>>(src, dst, tw, W, Mo, I);
-    T2* tmp = src;
+    const int64_t Mo = powi(W, axis);
+    k_inv_mid<T, K><<<dim3(blocks_for(Mo * I, 128), g.count), 128, 0, st>>>(g.tab, src, dst, W, Mo, I);
+    const int t = src;
     src = dst;
-    dst = tmp;
+    dst = t;
   }
-  int64_t M = 1;
-  for (int t = 0; t < w.d - 1; ++t) M *= W;
-  k_inv_last<T, KH><<<blocks_for(M * RC, 128), 128, 0, st>>>(src, g, tw, W, RC, M);
+  const int64_t M = powi(W, g.d - 1);
+  k_inv_last<T, KH><<<dim3(blocks_for(M * RC, 128), g.count), 128, 0, st>>>(g.tab, src, W, RC, M);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t fft_forward(const Window& w, int RC, cudaStream_t st) {
-  switch (w.N) {
-    case 8: return forward_n<T, 8>(w, RC, st);
-    case 16: return forward_n<T, 16>(w, RC, st);
-    case 32: return forward_n<T, 32>(w, RC, st);
-    case 64: return forward_n<T, 64>(w, RC, st);
+cudaError_t fft_forward(const FftGroup& g, int RC, cudaStream_t st) {
+  switch (g.N) {
+    case 8: return forward_n<T, 8>(g, RC, st);
+    case 16: return forward_n<T, 16>(g, RC, st);
+    case 32: return forward_n<T, 32>(g, RC, st);
+    case 64: return forward_n<T, 64>(g, RC, st);
   }
   return cudaErrorInvalidValue;
 }
 
 template <typename T>
-cudaError_t fft_inverse(const Window& w, int RC, cudaStream_t st) {
-  switch (w.N) {
-    case 8: return inverse_n<T, 8>(w, RC, st);
-    case 16: return inverse_n<T, 16>(w, RC, st);
-    case 32: return inverse_n<T, 32>(w, RC, st);
-    case 64: return inverse_n<T, 64>(w, RC, st);
+cudaError_t fft_inverse(const FftGroup& g, int RC, cudaStream_t st) {
+  switch (g.N) {
+    case 8: return inverse_n<T, 8>(g, RC, st);
+    case 16: return inverse_n<T, 16>(g, RC, st);
+    case 32: return inverse_n<T, 32>(g, RC, st);
+    case 64: return inverse_n<T, 64>(g, RC, st);
   }
   return cudaErrorInvalidValue;
 }
 
 template <typename T>
-cudaError_t spectral_multiply(const Window& w, const void* dmul, int RC, cudaStream_t st) {
-  using T2 = typename C2<T>::t;
-  T2* spec = reinterpret_cast<T2*>((w.d % 2) ? w.specA : w.specB);
-  const int64_t total = w.dmul_elems * RC;
-  k_spec_mul<T><<<blocks_for(total, 256), 256, 0, st>>>(spec, reinterpret_cast<const T*>(dmul),
-                                                        RC, total);
+cudaError_t spectral_multiply(const FftGroup& g, int der, int RC, cudaStream_t st) {
+  const int64_t total = g.dmul_elems * RC;
+  k_spec_mul<T><<<dim3(blocks_for(total, 256), g.count), 256, 0, st>>>(g.tab, (g.d % 2) ? 1 : 2,
+                                                                       der, RC, total);
   return cudaGetLastError();
 }
 
-template cudaError_t fft_forward<float>(const Window&, int, cudaStream_t);
-template cudaError_t fft_forward<double>(const Window&, int, cudaStream_t);
-template cudaError_t fft_inverse<float>(const Window&, int, cudaStream_t);
-template cudaError_t fft_inverse<double>(const Window&, int, cudaStream_t);
-template cudaError_t spectral_multiply<float>(const Window&, const void*, int, cudaStream_t);
-template cudaError_t spectral_multiply<double>(const Window&, const void*, int, cudaStream_t);
+template <typename T>
+cudaError_t zero_grids(const FftGroup& g, int RC, cudaStream_t st) {
+  const int64_t total = g.grid_elems * RC;
+  const unsigned bx = (unsigned)std::min<int64_t>(blocks_for(total, 256), 1024);
+  k_zero_grids<T><<<dim3(bx, g.count), 256, 0, st>>>(g.tab, total);
+  return cudaGetLastError();
+}
+
+template cudaError_t fft_forward<float>(const FftGroup&, int, cudaStream_t);
+template cudaError_t fft_forward<double>(const FftGroup&, int, cudaStream_t);
+template cudaError_t fft_inverse<float>(const FftGroup&, int, cudaStream_t);
+template cudaError_t fft_inverse<double>(const FftGroup&, int, cudaStream_t);
+template cudaError_t spectral_multiply<float>(const FftGroup&, int, int, cudaStream_t);
+template cudaError_t spectral_multiply<double>(const FftGroup&, int, int, cudaStream_t);
+template cudaError_t zero_grids<float>(const FftGroup&, int, cudaStream_t);
+template cudaError_t zero_grids<double>(const FftGroup&, int, cudaStream_t);
 
 }  // namespace agp

@@ -34,9 +34,44 @@ template <typename T>
 struct WinDev {
   const T* xs;            // sorted coordinates, [d][n]
   const int32_t* perm;    // sorted position -> caller's point index
+  const T* wts;           // window values, sorted order, [n][d][ttp] (see window_ttp)
   T* grid;                // active-box grid, [W^d][RC]
   int64_t n;
   int N, n_os, W;
+};
+
+// Window values stored per point and dimension: the 2s taps padded with zeros
+// to a multiple of 4 (16-byte vector loads).
+inline int window_ttp(int s) { return (2 * s + 3) / 4 * 4; }
+
+// Per-window right-hand sides and outputs, used when the windows of one
+// launch belong to different problems (batches): the kernels then take V,
+// Out and the scale factors from this table instead of their arguments.
+// scale multiplies the window's interpolated result.
+template <typename T>
+struct WinIO {
+  const T* V;
+  int64_t ldv;
+  T* Out;
+  int64_t ldo;
+  T scale;
+};
+
+// Buffers of one window for the DFT stages (device table entry).
+struct FftWin {
+  void* grid;
+  void* specA;
+  void* specB;
+  const void* tw;
+  const void* dmul;
+  const void* dmul_der;
+};
+
+// Windows with the same (d, N, s) processed by one launch per DFT stage.
+struct FftGroup {
+  int d = 0, N = 0, W = 0, count = 0;
+  int64_t grid_elems = 0, dmul_elems = 0;
+  FftWin* tab = nullptr;   // device [count]
 };
 
 // Kaiser-Bessel window of Appendix A in grid units, divided by I0(b s) so that
@@ -69,6 +104,8 @@ struct Window {
   // device buffers
   int32_t* perm = nullptr;       // [n]
   void* xs = nullptr;            // [d][n]
+  void* wts = nullptr;           // [n][d][window_ttp(s)] Kaiser-Bessel values, sorted order
+  double* costab = nullptr;      // [N][N] cos(2 pi l k / N) / N for the coefficient DFT
   int32_t* cell_start = nullptr; // [cells + 1]
   int4* items = nullptr;         // work items (window, cell, start, count)
   int64_t n_items = 0;
@@ -82,6 +119,18 @@ struct Window {
   void* specA = nullptr;         // complex scratch [spec_elems][rc_max]
   void* specB = nullptr;
   std::vector<double> winhat_h;  // host copy of n_os psi_hat(k)
+  FftWin* fft_self = nullptr;    // device table with this window alone
+  FftGroup self_group() const {
+    FftGroup g;
+    g.d = d;
+    g.N = N;
+    g.W = W;
+    g.count = 1;
+    g.grid_elems = grid_elems;
+    g.dmul_elems = dmul_elems;
+    g.tab = fft_self;
+    return g;
+  }
 };
 
 }  // namespace agp
@@ -101,10 +150,11 @@ struct agp_plan_s {
   void* wins_dev = nullptr;      // WinDev<T>[P]
   int4* items_all = nullptr;     // work items of every window, grouped by d
   int64_t items_by_d[agp::kMaxDim + 1] = {0, 0, 0, 0};   // offsets of each d group
+  std::vector<agp::FftGroup> groups;   // windows grouped by (d, N) for the DFT stages
   int* err_dev = nullptr;        // device error flags
   // stage profiler
   bool prof = false;
-  struct Ev { int stage; cudaEvent_t a, b; };
+  struct Ev { int stage, dim; cudaEvent_t a, b; };
   std::vector<Ev> prof_ev;
   int64_t launches[4] = {0, 0, 0, 0};
 };
@@ -115,33 +165,30 @@ namespace agp {
 agp_status set_error(agp_status s, const std::string& msg);
 agp_status cuda_status(cudaError_t e, const char* what);
 
-// ---- kernel launchers ----
-// Spread the columns V[:, 0..R) of every window with dimension d onto the
-// grids (grids must be zeroed). RC = grid column count (32, 8, 1 for FP32;
-// 4, 1 for FP64). (agp_nufft.cu)
+// ---- kernel launchers (agp_nufft.cu) ----
+// Spread the columns V[:, 0..R) of the windows referenced by `items` (all of
+// dimension d and cutoff s) onto their grids, which the caller has zeroed.
+// RC = grid column count (32, 8, 1 for FP32; 4, 1 for FP64). With io !=
+// nullptr every window takes its V and ldv from io[window] instead.
 template <typename T>
-cudaError_t launch_spread(const agp_plan_s* plan, int d, int RC, const T* V, int64_t ldv,
-                          int R, cudaStream_t st);
-// Interpolate the grids of every window with dimension d and add
-// scale * result into Out[:, 0..R). (agp_nufft.cu)
+cudaError_t spread_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
+                         int64_t n_items, int d, int s, int RC, const T* V, int64_t ldv, int R,
+                         cudaStream_t st);
+// Interpolate the grids of those windows and add scale * result into
+// Out[:, 0..R) (with io: Out, ldo and scale of io[window]).
 template <typename T>
-cudaError_t launch_interp(const agp_plan_s* plan, int d, int RC, T* Out, int64_t ldo, int R,
-                          T scale, cudaStream_t st);
-// Single-window variants (adjoint NFFT / NFFT entry points).
-template <typename T>
-cudaError_t launch_spread_window(const agp_plan_s* plan, int w, int RC, const T* V,
-                                 int64_t ldv, int R, cudaStream_t st);
-template <typename T>
-cudaError_t launch_interp_window(const agp_plan_s* plan, int w, int RC, T* Out, int64_t ldo,
-                                 int R, T scale, cudaStream_t st);
+cudaError_t interp_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
+                         int64_t n_items, int d, int s, int RC, T* Out, int64_t ldo, int R,
+                         T scale, cudaStream_t st);
 
-// Grid -> half spectrum (forward DFT over the active box), spectrum ->
-// grid (inverse), and the spectral multiply. (agp_fft.cu)
+// ---- DFT stages (agp_fft.cu), one launch per stage for a group of windows ----
 template <typename T>
-cudaError_t fft_forward(const Window& w, int RC, cudaStream_t st);   // grid -> specA (k layout)
+cudaError_t fft_forward(const FftGroup& g, int RC, cudaStream_t st);   // grid -> spectrum
 template <typename T>
-cudaError_t fft_inverse(const Window& w, int RC, cudaStream_t st);   // specA (k layout) -> grid
+cudaError_t fft_inverse(const FftGroup& g, int RC, cudaStream_t st);   // spectrum -> grid
 template <typename T>
-cudaError_t spectral_multiply(const Window& w, const void* dmul, int RC, cudaStream_t st);
+cudaError_t spectral_multiply(const FftGroup& g, int der, int RC, cudaStream_t st);
+template <typename T>
+cudaError_t zero_grids(const FftGroup& g, int RC, cudaStream_t st);
 
 }  // namespace agp

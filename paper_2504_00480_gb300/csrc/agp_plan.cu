@@ -186,24 +186,43 @@ __global__ void k_kernel_samples(double* __restrict__ out, int N, int d, int ker
 // One axis of the d-dimensional DFT of eq. (3.2). The samples are real and
 // even in every coordinate (kappa depends on |r| and the sample at
 // l_t = -N/2 multiplies exp(i pi k_t) = (-1)^k_t), so the transform along each
-// axis is the cosine sum (1/N) sum_l in[l] cos(2 pi l k / N).
-__global__ void k_cos_axis(const double* __restrict__ in, double* __restrict__ out, int N, int d,
-                           int axis) {
+// axis is the cosine sum sum_l in[l] costab[k][l], costab = cos(2 pi l k / N) / N
+// (indices shifted by N/2), precomputed once per plan.
+__global__ void k_cos_axis(const double* __restrict__ in, double* __restrict__ out,
+                           const double* __restrict__ costab, int N, int d, int axis) {
   int64_t total = 1, stride = 1;
   for (int t = 0; t < d; ++t) total *= N;
   for (int t = d - 1; t > axis; --t) stride *= N;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= total) return;
   const int kk = (int)((e / stride) % N);
-  const int k = kk - N / 2;
   const int64_t base = e - (int64_t)kk * stride;
+  const double* row = costab + (int64_t)kk * N;
   double s = 0.0;
-  for (int li = 0; li < N; ++li) {
-    const int l = li - N / 2;
-    // cos(2 pi l k / N) = cospi(2 l k / N); 2lk/N is exact in binary.
-    s += in[base + (int64_t)li * stride] * cospi(2.0 * (double)l * (double)k / (double)N);
+  for (int li = 0; li < N; ++li) s += in[base + (int64_t)li * stride] * row[li];
+  out[e] = s;
+}
+
+// Kaiser-Bessel values of every (sorted) point: wts[j][t][tap] =
+// psi(frac(u_t) + s - 1 - tap) for tap < 2s, 0 for the padding taps, where
+// u_t = x_t n_os (Appendix A window in grid units, divided by I0(b s)).
+// Evaluated in FP64 and rounded to the plan precision.
+template <typename T>
+__global__ void k_window_values(const T* __restrict__ xs, int64_t n, int d, int n_os, int s,
+                                int ttp, double b, double norm, T* __restrict__ wts) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * d * ttp) return;
+  const int tap = (int)(e % ttp);
+  const int64_t jt = e / ttp;
+  const int t = (int)(jt % d);
+  const int64_t j = jt / d;
+  double v = 0.0;
+  if (tap < 2 * s) {
+    const double u = (double)xs[(int64_t)t * n + j] * n_os;   // exact: n_os is a power of two
+    const double delta = (u - floor(u)) + (double)(s - 1 - tap);
+    v = kb_psi(delta, (double)s, b, norm);
   }
-  out[e] = s / N;
+  wts[e] = (T)v;
 }
 
 // Spectral multiplier on the half-spectrum layout [K]^(d-1) x [Kh]:
@@ -398,7 +417,7 @@ agp_status compute_coeffs(agp_plan_s* pl, cudaStream_t st) {
       double* src = t0;
       for (int axis = 0; axis < w.d; ++axis) {
         double* o = (axis == w.d - 1) ? dst : (src == t0 ? t1 : t0);
-        k_cos_axis<<<nblk(w.cells, 256), 256, 0, st>>>(src, o, w.N, w.d, axis);
+        k_cos_axis<<<nblk(w.cells, 256), 256, 0, st>>>(src, o, w.costab, w.N, w.d, axis);
         src = o;
       }
       k_build_dmul<T><<<nblk(w.dmul_elems, 256), 256, 0, st>>>(
@@ -416,6 +435,8 @@ void free_plan(agp_plan_s* pl) {
   for (auto& w : pl->win) {
     cudaFree(w.perm);
     cudaFree(w.xs);
+    cudaFree(w.wts);
+    cudaFree(w.costab);
     cudaFree(w.cell_start);
     cudaFree(w.b);
     cudaFree(w.bder);
@@ -426,7 +447,9 @@ void free_plan(agp_plan_s* pl) {
     cudaFree(w.grid);
     cudaFree(w.specA);
     cudaFree(w.specB);
+    cudaFree(w.fft_self);
   }
+  for (auto& g : pl->groups) cudaFree(g.tab);
   for (auto& e : pl->prof_ev) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -543,7 +566,26 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
     }
     AGP_CUDA(cudaMalloc(&w.tw, sizeof(T) * tw.size()));
     AGP_CUDA(cudaMemcpyAsync(w.tw, tw.data(), sizeof(T) * tw.size(), cudaMemcpyHostToDevice, st));
-    AGP_CUDA(cudaStreamSynchronize(st));   // tw / winhat host vectors go out of scope
+    // cosine table of the coefficient DFT: cos(2 pi l k / N) / N, l, k in I_N
+    std::vector<double> ct((size_t)w.N * w.N);
+    for (int kk = 0; kk < w.N; ++kk)
+      for (int li = 0; li < w.N; ++li) {
+        long long lk = (long long)(kk - w.N / 2) * (li - w.N / 2);
+        lk %= w.N;
+        if (lk < 0) lk += w.N;
+        ct[(size_t)kk * w.N + li] = std::cos(2.0 * M_PI * (double)lk / (double)w.N) / w.N;
+      }
+    AGP_CUDA(cudaMalloc(&w.costab, sizeof(double) * ct.size()));
+    AGP_CUDA(cudaMemcpyAsync(w.costab, ct.data(), sizeof(double) * ct.size(),
+                             cudaMemcpyHostToDevice, st));
+    AGP_CUDA(cudaStreamSynchronize(st));   // host tables go out of scope
+    // window values of every sorted point (they do not depend on the hyperparameters)
+    const int ttp = window_ttp(w.s);
+    AGP_CUDA(cudaMalloc(&w.wts, sizeof(T) * n * w.d * ttp));
+    k_window_values<T><<<nblk(n * w.d * ttp, 256), 256, 0, st>>>(
+        reinterpret_cast<const T*>(w.xs), n, w.d, w.n_os, w.s, ttp, pl->kb_b, pl->kb_norm,
+        reinterpret_cast<T*>(w.wts));
+    AGP_CUDA(cudaGetLastError());
     AGP_CUDA(cudaMalloc(&w.b, sizeof(double) * w.cells));
     AGP_CUDA(cudaMalloc(&w.bder, sizeof(double) * w.cells));
     AGP_CUDA(cudaMalloc(&w.dmul, sizeof(T) * w.dmul_elems));
@@ -553,6 +595,7 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
     AGP_CUDA(cudaMalloc(&w.specB, 2 * sizeof(T) * w.spec_elems * pl->rc_max));
     wd[s].xs = reinterpret_cast<const T*>(w.xs);
     wd[s].perm = w.perm;
+    wd[s].wts = reinterpret_cast<const T*>(w.wts);
     wd[s].grid = reinterpret_cast<T*>(w.grid);
     wd[s].n = n;
     wd[s].N = w.N;
@@ -562,8 +605,36 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
   AGP_CUDA(cudaMalloc(&pl->wins_dev, sizeof(WinDev<T>) * pl->P));
   AGP_CUDA(cudaMemcpyAsync(pl->wins_dev, wd.data(), sizeof(WinDev<T>) * pl->P,
                            cudaMemcpyHostToDevice, st));
+  // DFT buffer tables: one per window, and one per (d, N) group of windows
+  std::vector<FftWin> fw(pl->P);
+  for (int s = 0; s < pl->P; ++s) {
+    Window& w = pl->win[s];
+    fw[s] = FftWin{w.grid, w.specA, w.specB, w.tw, w.dmul, w.dmul_der};
+    AGP_CUDA(cudaMalloc(&w.fft_self, sizeof(FftWin)));
+    AGP_CUDA(cudaMemcpyAsync(w.fft_self, &fw[s], sizeof(FftWin), cudaMemcpyHostToDevice, st));
+  }
+  std::vector<std::vector<FftWin>> gtab;
+  for (int s = 0; s < pl->P; ++s) {
+    const Window& w = pl->win[s];
+    size_t gi = 0;
+    while (gi < pl->groups.size() && !(pl->groups[gi].d == w.d && pl->groups[gi].N == w.N)) ++gi;
+    if (gi == pl->groups.size()) {
+      FftGroup g = w.self_group();
+      g.count = 0;
+      g.tab = nullptr;
+      pl->groups.push_back(g);
+      gtab.emplace_back();
+    }
+    pl->groups[gi].count += 1;
+    gtab[gi].push_back(fw[s]);
+  }
+  for (size_t gi = 0; gi < pl->groups.size(); ++gi) {
+    AGP_CUDA(cudaMalloc(&pl->groups[gi].tab, sizeof(FftWin) * gtab[gi].size()));
+    AGP_CUDA(cudaMemcpyAsync(pl->groups[gi].tab, gtab[gi].data(), sizeof(FftWin) * gtab[gi].size(),
+                             cudaMemcpyHostToDevice, st));
+  }
   AGP_TRY(compute_coeffs<T>(pl, st));
-  AGP_CUDA(cudaStreamSynchronize(st));
+  AGP_CUDA(cudaStreamSynchronize(st));   // host tables go out of scope
   return AGP_OK;
 }
 
@@ -575,17 +646,17 @@ int pick_rc(const agp_plan_s* pl, int R) {
 // Stage timing: a pair of events around a group of launches on `st`.
 struct StageTimer {
   agp_plan_s* pl;
-  int stage;
+  int stage, dim;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
-  StageTimer(agp_plan_s* p, int s, cudaStream_t t) : pl(p), stage(s), st(t) {
+  StageTimer(agp_plan_s* p, int s, cudaStream_t t, int d = 0) : pl(p), stage(s), dim(d), st(t) {
     if (pl->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
   }
   ~StageTimer() {
     if (!a) return;
     cudaEvent_t b = nullptr;
     if (cudaEventCreate(&b) == cudaSuccess && cudaEventRecord(b, st) == cudaSuccess)
-      pl->prof_ev.push_back({stage, a, b});
+      pl->prof_ev.push_back({stage, dim, a, b});
     else
       cudaEventDestroy(a);
   }
@@ -596,31 +667,39 @@ template <typename T>
 agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_t ldo, int R,
                          int der, T scale, cudaStream_t st) {
   const int rc = pick_rc(pl, R);
+  const WinDev<T>* wins = reinterpret_cast<const WinDev<T>*>(pl->wins_dev);
   for (int r0 = 0; r0 < R; r0 += rc) {
     const int Rc = R - r0 < rc ? R - r0 : rc;
-    for (auto& w : pl->win)
-      AGP_CUDA(cudaMemsetAsync(w.grid, 0, sizeof(T) * w.grid_elems * rc, st));
-    for (int dd = 1; dd <= kMaxDim; ++dd)
-      if (pl->items_by_d[dd] > pl->items_by_d[dd - 1]) {
-        StageTimer tm(pl, 0, st);
-        AGP_CUDA(launch_spread<T>(pl, dd, rc, V + r0, ldv, Rc, st));
-        pl->launches[0] += 1;
-      }
+    {
+      StageTimer tm(pl, 3, st);
+      for (const auto& g : pl->groups) AGP_CUDA(zero_grids<T>(g, rc, st));
+      pl->launches[3] += (int64_t)pl->groups.size();
+    }
+    for (int dd = 1; dd <= kMaxDim; ++dd) {
+      const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
+      if (b == a) continue;
+      StageTimer tm(pl, 0, st, dd);
+      AGP_CUDA(spread_items<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc, V + r0, ldv,
+                               Rc, st));
+      pl->launches[0] += 1;
+    }
     {
       StageTimer tm(pl, 1, st);
-      for (auto& w : pl->win) {
-        AGP_CUDA(fft_forward<T>(w, rc, st));
-        AGP_CUDA(spectral_multiply<T>(w, der ? w.dmul_der : w.dmul, rc, st));
-        AGP_CUDA(fft_inverse<T>(w, rc, st));
-        pl->launches[1] += 2 * w.d + 1;
+      for (const auto& g : pl->groups) {
+        AGP_CUDA(fft_forward<T>(g, rc, st));
+        AGP_CUDA(spectral_multiply<T>(g, der, rc, st));
+        AGP_CUDA(fft_inverse<T>(g, rc, st));
+        pl->launches[1] += 2 * g.d + 1;
       }
     }
-    for (int dd = 1; dd <= kMaxDim; ++dd)
-      if (pl->items_by_d[dd] > pl->items_by_d[dd - 1]) {
-        StageTimer tm(pl, 2, st);
-        AGP_CUDA(launch_interp<T>(pl, dd, rc, Out + r0, ldo, Rc, scale, st));
-        pl->launches[2] += 1;
-      }
+    for (int dd = 1; dd <= kMaxDim; ++dd) {
+      const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
+      if (b == a) continue;
+      StageTimer tm(pl, 2, st, dd);
+      AGP_CUDA(interp_items<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc, Out + r0, ldo,
+                               Rc, scale, st));
+      pl->launches[2] += 1;
+    }
   }
   return AGP_OK;
 }
@@ -650,6 +729,58 @@ agp_status check_block(agp_plan pl, const void* V, int64_t ldv, const void* Out,
   const char* o1 = o0 + es * (size_t)((pl->n - 1) * ldo + R);
   if (v0 < o1 && o0 < v1) return set_error(AGP_EINVAL, "Out overlaps V");
   return AGP_OK;
+}
+
+template <typename T>
+struct Cplx;
+template <>
+struct Cplx<float> { using t = float2; };
+template <>
+struct Cplx<double> { using t = double2; };
+
+// Adjoint NFFT of one window: spread, forward DFT, deconvolve (Appendix A).
+template <typename T>
+agp_status adjoint_nfft_t(agp_plan_s* pl, int window, const T* V, int64_t ldv, int R, void* chat,
+                          cudaStream_t st) {
+  using T2 = typename Cplx<T>::t;
+  Window& w = pl->win[window];
+  const FftGroup g = w.self_group();
+  const int rc = pick_rc(pl, R);
+  const WinDev<T>* wins = reinterpret_cast<const WinDev<T>*>(pl->wins_dev);
+  for (int r0 = 0; r0 < R; r0 += rc) {
+    const int Rc = R - r0 < rc ? R - r0 : rc;
+    AGP_CUDA(zero_grids<T>(g, rc, st));
+    AGP_CUDA(spread_items<T>(wins, nullptr, w.items, w.n_items, w.d, pl->s, rc, V + r0, ldv, Rc, st));
+    AGP_CUDA(fft_forward<T>(g, rc, st));
+    const T2* spec = (const T2*)((w.d % 2) ? w.specA : w.specB);
+    k_extract_spectrum<T, T2><<<nblk(w.cells * Rc, 256), 256, 0, st>>>(
+        spec, (const double*)w.winhat, w.N, w.d, rc, Rc, (T2*)chat + (int64_t)r0 * w.cells);
+    AGP_CUDA(cudaGetLastError());
+  }
+  return AGP_OK;
+}
+
+// Real part of the NFFT of one window: deconvolve, inverse DFT, interpolate.
+template <typename T>
+agp_status nfft_real_t(agp_plan_s* pl, int window, const void* fhat, int R, T* Out, int64_t ldo,
+                       cudaStream_t st) {
+  using T2 = typename Cplx<T>::t;
+  Window& w = pl->win[window];
+  const FftGroup g = w.self_group();
+  const int rc = pick_rc(pl, R);
+  const int64_t spec_total = w.dmul_elems * rc;
+  const WinDev<T>* wins = reinterpret_cast<const WinDev<T>*>(pl->wins_dev);
+  k_init_out<T><<<nblk(pl->n * R, 256), 256, 0, st>>>(Out, ldo, nullptr, 0, pl->n, R, T(0));
+  for (int r0 = 0; r0 < R; r0 += rc) {
+    const int Rc = R - r0 < rc ? R - r0 : rc;
+    T2* spec = (T2*)((w.d % 2) ? w.specA : w.specB);
+    k_insert_spectrum<T, T2><<<nblk(spec_total, 256), 256, 0, st>>>(
+        (const T2*)fhat + (int64_t)r0 * w.cells, (const double*)w.winhat, w.N, w.d, rc, Rc, spec);
+    AGP_CUDA(fft_inverse<T>(g, rc, st));
+    AGP_CUDA(interp_items<T>(wins, nullptr, w.items, w.n_items, w.d, pl->s, rc, Out + r0, ldo, Rc,
+                             T(1), st));
+  }
+  return cuda_status(cudaGetLastError(), "agp_nfft_real");
 }
 
 }  // namespace
@@ -787,28 +918,9 @@ agp_status agp_adjoint_nfft(agp_plan pl, int window, const void* V, int64_t ldv,
   if (!pl || window < 0 || window >= pl->P || !V || !chat || R < 1 || ldv < R)
     return set_error(AGP_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Window& w = pl->win[window];
-  const int rc = pick_rc(pl, R);
-  for (int r0 = 0; r0 < R; r0 += rc) {
-    const int Rc = R - r0 < rc ? R - r0 : rc;
-    if (pl->prec == AGP_F32) {
-      AGP_CUDA(cudaMemsetAsync(w.grid, 0, sizeof(float) * w.grid_elems * rc, st));
-      AGP_CUDA(launch_spread_window<float>(pl, window, rc, (const float*)V + r0, ldv, Rc, st));
-      AGP_CUDA(fft_forward<float>(w, rc, st));
-      const float2* spec = (const float2*)((w.d % 2) ? w.specA : w.specB);
-      k_extract_spectrum<float, float2><<<nblk(w.cells * Rc, 256), 256, 0, st>>>(
-          spec, (const double*)w.winhat, w.N, w.d, rc, Rc, (float2*)chat + (int64_t)r0 * w.cells);
-    } else {
-      AGP_CUDA(cudaMemsetAsync(w.grid, 0, sizeof(double) * w.grid_elems * rc, st));
-      AGP_CUDA(launch_spread_window<double>(pl, window, rc, (const double*)V + r0, ldv, Rc, st));
-      AGP_CUDA(fft_forward<double>(w, rc, st));
-      const double2* spec = (const double2*)((w.d % 2) ? w.specA : w.specB);
-      k_extract_spectrum<double, double2><<<nblk(w.cells * Rc, 256), 256, 0, st>>>(
-          spec, (const double*)w.winhat, w.N, w.d, rc, Rc, (double2*)chat + (int64_t)r0 * w.cells);
-    }
-    AGP_CUDA(cudaGetLastError());
-  }
-  return AGP_OK;
+  if (pl->prec == AGP_F32)
+    return adjoint_nfft_t<float>(pl, window, (const float*)V, ldv, R, chat, st);
+  return adjoint_nfft_t<double>(pl, window, (const double*)V, ldv, R, chat, st);
 }
 
 agp_status agp_nfft_real(agp_plan pl, int window, const void* fhat, int R, void* Out, int64_t ldo,
@@ -816,35 +928,8 @@ agp_status agp_nfft_real(agp_plan pl, int window, const void* fhat, int R, void*
   if (!pl || window < 0 || window >= pl->P || !fhat || !Out || R < 1 || ldo < R)
     return set_error(AGP_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Window& w = pl->win[window];
-  const int rc = pick_rc(pl, R);
-  const int64_t spec_total = w.dmul_elems * rc;
-  for (int r0 = 0; r0 < R; r0 += rc) {
-    const int Rc = R - r0 < rc ? R - r0 : rc;
-    if (pl->prec == AGP_F32) {
-      if (r0 == 0)
-        k_init_out<float><<<nblk(pl->n * R, 256), 256, 0, st>>>((float*)Out, ldo, nullptr, 0,
-                                                                 pl->n, R, 0.f);
-      float2* spec = (float2*)((w.d % 2) ? w.specA : w.specB);
-      k_insert_spectrum<float, float2><<<nblk(spec_total, 256), 256, 0, st>>>(
-          (const float2*)fhat + (int64_t)r0 * w.cells, (const double*)w.winhat, w.N, w.d, rc, Rc,
-          spec);
-      AGP_CUDA(fft_inverse<float>(w, rc, st));
-      AGP_CUDA(launch_interp_window<float>(pl, window, rc, (float*)Out + r0, ldo, Rc, 1.f, st));
-    } else {
-      if (r0 == 0)
-        k_init_out<double><<<nblk(pl->n * R, 256), 256, 0, st>>>((double*)Out, ldo, nullptr, 0,
-                                                                  pl->n, R, 0.0);
-      double2* spec = (double2*)((w.d % 2) ? w.specA : w.specB);
-      k_insert_spectrum<double, double2><<<nblk(spec_total, 256), 256, 0, st>>>(
-          (const double2*)fhat + (int64_t)r0 * w.cells, (const double*)w.winhat, w.N, w.d, rc, Rc,
-          spec);
-      AGP_CUDA(fft_inverse<double>(w, rc, st));
-      AGP_CUDA(launch_interp_window<double>(pl, window, rc, (double*)Out + r0, ldo, Rc, 1.0, st));
-    }
-    AGP_CUDA(cudaGetLastError());
-  }
-  return AGP_OK;
+  if (pl->prec == AGP_F32) return nfft_real_t<float>(pl, window, fhat, R, (float*)Out, ldo, st);
+  return nfft_real_t<double>(pl, window, fhat, R, (double*)Out, ldo, st);
 }
 
 agp_status agp_plan_bins(agp_plan pl, int window, int32_t* bins, void* stream) {
@@ -882,12 +967,18 @@ agp_status agp_profile_read(agp_plan pl, agp_profile_t* out, int reset, void* st
   for (int k = 0; k < 4; ++k) {
     out->ms[k] = 0.0;
     out->launches[k] = pl->launches[k];
+    for (int d = 0; d < 4; ++d) {
+      out->ms_by_dim[k][d] = 0.0;
+      out->timed_by_dim[k][d] = 0;
+    }
   }
   for (auto& e : pl->prof_ev) {
     float ms = 0.f;
     AGP_CUDA(cudaEventSynchronize(e.b));
     AGP_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
     out->ms[e.stage] += ms;
+    out->ms_by_dim[e.stage][e.dim] += ms;
+    out->timed_by_dim[e.stage][e.dim] += 1;
   }
   if (reset) {
     for (auto& e : pl->prof_ev) {

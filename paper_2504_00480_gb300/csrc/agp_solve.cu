@@ -1,0 +1,525 @@
+// Batched conjugate gradients, stochastic Lanczos quadrature and the
+// negative log marginal likelihood gradient (Sec. 1 eqs. (1.2), (1.4), (1.5)
+// with M = I).
+//
+// Blocks are RHS-minor [n][R]. The kernel matvecs run in the plan precision
+// (FP32 or FP64); the CG recursion vectors x, r, p and every scalar (column
+// dot products, alpha, beta, residual norms, the Lanczos matrix, its
+// eigenvalues and the log determinant) are FP64 on the device. Column dot
+// products are two-pass and deterministic: per-block partial sums in FP64,
+// then one ordered sum per column. The host loop enqueues one CG iteration at
+// a time and reads the per-column convergence flags back every few iterations.
+#include <cmath>
+#include <vector>
+
+#include "agp_internal.cuh"
+
+namespace agp {
+namespace {
+
+constexpr int kDotThreads = 256;   // 8 row groups x 32 columns
+constexpr int kDotRows = 8;
+constexpr int kMaxDotBlocks = 1024;
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// partial[b][c] = sum over this block's rows of A[i][c] * B[i][c] (FP64), for
+// the 32 columns c0 .. c0+31 of blockIdx.y.
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kDotThreads)
+k_dot_partial(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, int64_t ldb, int64_t n,
+              int R, double* __restrict__ partial) {
+  __shared__ double red[kDotRows][32];
+  const int lane = threadIdx.x % 32, grp = threadIdx.x / 32;
+  const int c = blockIdx.y * 32 + lane;
+  double acc = 0.0;
+  if (c < R) {
+    for (int64_t i = (int64_t)blockIdx.x * kDotRows + grp; i < n; i += (int64_t)gridDim.x * kDotRows)
+      acc += (double)A[i * lda + c] * (double)B[i * ldb + c];
+  }
+  red[grp][lane] = acc;
+  __syncthreads();
+  if (grp == 0 && c < R) {
+    double s = 0.0;
+    for (int g = 0; g < kDotRows; ++g) s += red[g][lane];
+    partial[(int64_t)blockIdx.x * R + c] = s;
+  }
+}
+
+__global__ void k_dot_final(const double* __restrict__ partial, int nb, int R,
+                            double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * R + c];
+  out[c] = s;
+}
+
+template <typename TS, typename TD>
+__global__ void k_copy_block(const TS* __restrict__ src, int64_t lds, TD* __restrict__ dst,
+                             int64_t ldd, int64_t n, int R) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * R) return;
+  const int64_t i = e / R;
+  const int c = (int)(e - i * R);
+  dst[i * ldd + c] = (TD)src[i * lds + c];
+}
+
+template <typename T>
+__global__ void k_zero_block(T* __restrict__ dst, int64_t ldd, int64_t n, int R) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * R) return;
+  const int64_t i = e / R;
+  dst[i * ldd + (e - i * R)] = T(0);
+}
+
+// Per-column CG state (FP64).
+struct CgState {
+  double* rr;       // current |r|^2
+  double* bn2;      // |b|^2
+  double* pq;       // p^T K p
+  double* alpha;
+  double* beta;
+  double* relres;
+  int* active;      // 1 while the column iterates
+  int* iters;
+  int* maxit;       // per-column iteration cap
+  double* tol;      // per-column relative residual tolerance (0: run to maxit)
+  double* ahist;    // [maxit_all][R]
+  double* bhist;
+};
+
+__global__ void k_cg_start(CgState s, int R) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  s.bn2[c] = s.rr[c];
+  s.iters[c] = 0;
+  s.relres[c] = s.rr[c] > 0.0 ? 1.0 : 0.0;
+  s.active[c] = (s.rr[c] > 0.0 && s.maxit[c] > 0) ? 1 : 0;
+}
+
+__global__ void k_cg_alpha(CgState s, int R) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  // The truncated Fourier series of a kernel need not be positive definite
+  // (no boundary smoothing), so p^T K p < 0 is possible and CG carries on as
+  // the textbook recursion does; only an exact zero or a non-finite value
+  // stops the column.
+  double a = 0.0;
+  if (s.active[c]) {
+    const double pq = s.pq[c];
+    if (pq != 0.0 && isfinite(pq)) {
+      a = s.rr[c] / pq;
+    } else {
+      s.active[c] = 0;
+    }
+  }
+  s.alpha[c] = a;
+}
+
+// x += alpha p, r -= alpha q (x, r, p FP64; q = K p in the plan precision)
+template <typename T>
+__global__ void k_cg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                        const T* __restrict__ q, const double* __restrict__ alpha, int64_t n,
+                        int R) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * R) return;
+  const int c = (int)(e % R);
+  const double a = alpha[c];
+  if (a == 0.0) return;
+  x[e] += a * p[e];
+  r[e] -= a * (double)q[e];
+}
+
+__global__ void k_cg_beta(CgState s, const double* __restrict__ rr_new, int it, int R) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  double b = 0.0;
+  if (s.active[c]) {
+    const double rn = rr_new[c];
+    b = rn / s.rr[c];
+    s.ahist[(int64_t)it * R + c] = s.alpha[c];
+    s.bhist[(int64_t)it * R + c] = b;
+    s.iters[c] = it + 1;
+    s.relres[c] = sqrt(rn / s.bn2[c]);
+    s.rr[c] = rn;
+    if (!(rn > 0.0) || s.relres[c] <= s.tol[c] || it + 1 >= s.maxit[c]) s.active[c] = 0;
+  }
+  s.beta[c] = s.active[c] ? b : 0.0;
+}
+
+// p = r + beta p (FP64), and its copy in the plan precision for the next matvec
+template <typename T>
+__global__ void k_cg_p(double* __restrict__ p, T* __restrict__ pt, const double* __restrict__ r,
+                       const double* __restrict__ beta, const int* __restrict__ active, int64_t n,
+                       int R) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * R) return;
+  const int c = (int)(e % R);
+  if (!active[c]) return;
+  const double v = r[e] + beta[c] * p[e];
+  p[e] = v;
+  pt[e] = (T)v;
+}
+
+// Lanczos matrix from the CG coefficients of one probe (the CG-Lanczos
+// relation T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+// T_{j,j+1} = sqrt(beta_j)/alpha_j), its eigen-decomposition by the implicit
+// QL method with Wilkinson shifts, and the Gauss quadrature
+// z^T logm(K) z ~= |z|^2 sum_k tau_k^2 log theta_k, tau = first components of
+// the eigenvectors (only the first row of the rotation product is kept).
+constexpr int kMaxLanczos = 64;
+constexpr int kSlqThreads = 32;
+
+__device__ bool tridiag_ql(double* d, double* e, double* z, int m) {
+  // d: diagonal; e[i] couples i and i+1 (e[m-1] = 0); z: first row of the
+  // accumulated eigenvector matrix (starts as e_0).
+  for (int l = 0; l < m; ++l) {
+    int iter = 0;
+    while (true) {
+      int mm = l;
+      for (; mm < m - 1; ++mm)
+        if (fabs(e[mm]) <= 1e-16 * (fabs(d[mm]) + fabs(d[mm + 1]))) break;
+      if (mm == l) break;                       // d[l] has converged
+      if (++iter > 60) return false;
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = hypot(g, 1.0);
+      g = d[mm] - d[l] + e[l] / (g + copysign(r, g));
+      double s = 1.0, c = 1.0, p = 0.0;
+      bool split = false;
+      for (int i = mm - 1; i >= l; --i) {
+        double f = s * e[i];
+        const double b = c * e[i];
+        r = hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {                         // the matrix splits at i+1
+          d[i + 1] -= p;
+          e[mm] = 0.0;
+          split = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+        f = z[i + 1];
+        z[i + 1] = s * z[i] + c * f;
+        z[i] = c * z[i] - s * f;
+      }
+      if (split) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[mm] = 0.0;
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kSlqThreads)
+k_slq_logdet(const double* __restrict__ ahist, const double* __restrict__ bhist,
+             const int* __restrict__ iters, const double* __restrict__ bn2, int R, int c0,
+             double* __restrict__ quad) {
+  __shared__ double sd[kSlqThreads][kMaxLanczos];
+  __shared__ double se[kSlqThreads][kMaxLanczos];
+  __shared__ double sz[kSlqThreads][kMaxLanczos];
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  double* d = sd[threadIdx.x];
+  double* e = se[threadIdx.x];
+  double* z = sz[threadIdx.x];
+  const int m = min(iters[c], kMaxLanczos);
+  for (int j = 0; j < m; ++j) {
+    const double aj = ahist[(int64_t)j * R + c];
+    d[j] = 1.0 / aj + (j > 0 ? bhist[(int64_t)(j - 1) * R + c] / ahist[(int64_t)(j - 1) * R + c] : 0.0);
+    e[j] = (j + 1 < m) ? sqrt(bhist[(int64_t)j * R + c]) / aj : 0.0;
+    z[j] = (j == 0) ? 1.0 : 0.0;
+  }
+  if (m == 0 || !tridiag_ql(d, e, z, m)) {
+    quad[c] = (m == 0) ? 0.0 : nan("");
+    return;
+  }
+  double s = 0.0;
+  for (int k = 0; k < m; ++k) s += z[k] * z[k] * log(d[k]);
+  quad[c] = bn2[c] * s;
+}
+
+// CG workspace: the recursion vectors x, r, p are FP64 whatever the plan
+// precision (the paper runs CG in double precision); the matvec reads pt, the
+// copy of p in the plan precision, and writes q in the plan precision.
+template <typename T>
+struct Workspace {
+  double *x = nullptr, *r = nullptr, *p = nullptr;
+  T *pt = nullptr, *q = nullptr;
+  double* partial = nullptr;
+  double* scal = nullptr;   // 8 x R doubles
+  int* iscal = nullptr;     // 3 x R ints
+  double *ahist = nullptr, *bhist = nullptr;
+  cudaStream_t st;
+  ~Workspace() {
+    cudaFreeAsync(x, st);
+    cudaFreeAsync(r, st);
+    cudaFreeAsync(p, st);
+    cudaFreeAsync(pt, st);
+    cudaFreeAsync(q, st);
+    cudaFreeAsync(partial, st);
+    cudaFreeAsync(scal, st);
+    cudaFreeAsync(iscal, st);
+    cudaFreeAsync(ahist, st);
+    cudaFreeAsync(bhist, st);
+  }
+};
+
+#define AGP_CUDA(call)                                             \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_status(e_, #call);          \
+  } while (0)
+#define AGP_TRY(call)                                              \
+  do {                                                             \
+    agp_status s_ = (call);                                        \
+    if (s_ != AGP_OK) return s_;                                   \
+  } while (0)
+
+template <typename TA, typename TB>
+agp_status col_dot(const TA* A, int64_t lda, const TB* B, int64_t ldb, int64_t n, int R,
+                   double* partial, double* out, cudaStream_t st, agp_plan_s* pl) {
+  const int nb = (int)std::min<int64_t>(kMaxDotBlocks, (n + kDotRows - 1) / kDotRows);
+  dim3 grid(nb, (R + 31) / 32);
+  k_dot_partial<TA, TB><<<grid, kDotThreads, 0, st>>>(A, lda, B, ldb, n, R, partial);
+  k_dot_final<<<nblk(R, 128), 128, 0, st>>>(partial, nb, R, out);
+  pl->launches[3] += 2;
+  return cuda_status(cudaGetLastError(), "col_dot");
+}
+
+// CG on the columns of B; X receives the iterates. Per-column caps and
+// tolerances come from maxit_h / tol_h. On return ws holds the alpha/beta
+// history and the per-column state (scal layout: rr, bn2, pq, alpha, beta,
+// relres, rrnew, spare; iscal: active, iters, maxit).
+template <typename T>
+agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int R,
+                  const std::vector<int>& maxit_h, const std::vector<double>& tol_h, int check_every,
+                  Workspace<T>& ws, cudaStream_t st) {
+  const int64_t n = pl->n;
+  int maxall = 0;
+  for (int v : maxit_h) maxall = std::max(maxall, v);
+  ws.st = st;
+  AGP_CUDA(cudaMallocAsync(&ws.x, sizeof(double) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.r, sizeof(double) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.p, sizeof(double) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.pt, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.q, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.partial, sizeof(double) * kMaxDotBlocks * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.scal, sizeof(double) * 9 * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.iscal, sizeof(int) * 3 * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.ahist, sizeof(double) * std::max(1, maxall) * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.bhist, sizeof(double) * std::max(1, maxall) * R, st));
+  CgState s;
+  s.rr = ws.scal;
+  s.bn2 = ws.scal + R;
+  s.pq = ws.scal + 2 * R;
+  s.alpha = ws.scal + 3 * R;
+  s.beta = ws.scal + 4 * R;
+  s.relres = ws.scal + 5 * R;
+  double* rrnew = ws.scal + 6 * R;
+  s.tol = ws.scal + 7 * R;
+  s.active = ws.iscal;
+  s.iters = ws.iscal + R;
+  s.maxit = ws.iscal + 2 * R;
+  s.ahist = ws.ahist;
+  s.bhist = ws.bhist;
+  AGP_CUDA(cudaMemcpyAsync(s.maxit, maxit_h.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+  AGP_CUDA(cudaMemcpyAsync(s.tol, tol_h.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+
+  const unsigned gb = nblk(n * R, 256), gc = nblk(R, 128);
+  k_zero_block<double><<<gb, 256, 0, st>>>(ws.x, R, n, R);
+  k_copy_block<T, double><<<gb, 256, 0, st>>>(B, ldb, ws.r, R, n, R);
+  k_copy_block<T, double><<<gb, 256, 0, st>>>(B, ldb, ws.p, R, n, R);
+  k_copy_block<T, T><<<gb, 256, 0, st>>>(B, ldb, ws.pt, R, n, R);
+  pl->launches[3] += 4;
+  AGP_TRY(col_dot(ws.r, R, ws.r, R, n, R, ws.partial, s.rr, st, pl));
+  k_cg_start<<<gc, 128, 0, st>>>(s, R);
+  pl->launches[3] += 1;
+  std::vector<int> act(R);
+  for (int it = 0; it < maxall; ++it) {
+    AGP_TRY(agp_matvec(pl, ws.pt, R, ws.q, R, R, 1, st));
+    AGP_TRY(col_dot(ws.p, R, ws.q, R, n, R, ws.partial, s.pq, st, pl));
+    k_cg_alpha<<<gc, 128, 0, st>>>(s, R);
+    k_cg_xr<T><<<gb, 256, 0, st>>>(ws.x, ws.r, ws.p, ws.q, s.alpha, n, R);
+    pl->launches[3] += 2;
+    AGP_TRY(col_dot(ws.r, R, ws.r, R, n, R, ws.partial, rrnew, st, pl));
+    k_cg_beta<<<gc, 128, 0, st>>>(s, rrnew, it, R);
+    k_cg_p<T><<<gb, 256, 0, st>>>(ws.p, ws.pt, ws.r, s.beta, s.active, n, R);
+    pl->launches[3] += 2;
+    AGP_CUDA(cudaGetLastError());
+    if (check_every > 0 && ((it + 1) % check_every == 0) && it + 1 < maxall) {
+      AGP_CUDA(cudaMemcpyAsync(act.data(), s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+      AGP_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int v : act) any = any || v;
+      if (!any) break;
+    }
+  }
+  k_copy_block<double, T><<<gb, 256, 0, st>>>(ws.x, R, X, ldx, n, R);
+  pl->launches[3] += 1;
+  return cuda_status(cudaGetLastError(), "cg_run");
+}
+
+template <typename T>
+agp_status pcg_t(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int R, double rtol,
+                 int maxit, int* iters, double* relres, cudaStream_t st) {
+  Workspace<T> ws;
+  std::vector<int> mi(R, maxit);
+  std::vector<double> tl(R, rtol);
+  AGP_TRY(cg_run<T>(pl, B, ldb, X, ldx, R, mi, tl, 5, ws, st));
+  std::vector<int> it(R);
+  std::vector<double> rel(R);
+  AGP_CUDA(cudaMemcpyAsync(it.data(), ws.iscal + R, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaMemcpyAsync(rel.data(), ws.scal + 5 * R, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  bool ok = true;
+  for (int c = 0; c < R; ++c) {
+    if (iters) iters[c] = it[c];
+    if (relres) relres[c] = rel[c];
+    ok = ok && rel[c] <= rtol;
+  }
+  if (!ok) return set_error(AGP_NOT_CONVERGED, "CG stopped at maxit above the tolerance");
+  return AGP_OK;
+}
+
+template <typename T>
+agp_status nlml_t(agp_plan_s* pl, const T* Y, const T* Z, int64_t ldz, int nz, int steps,
+                  double rtol, int maxit, double* nlml, double* grad, cudaStream_t st) {
+  const int64_t n = pl->n;
+  const int R = 1 + nz;
+  T *B = nullptr, *Xs = nullptr, *D = nullptr;
+  double* dots = nullptr;
+  AGP_CUDA(cudaMallocAsync(&B, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&Xs, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&D, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&dots, sizeof(double) * 4 * R, st));
+  struct Free {
+    void* a[4];
+    cudaStream_t st;
+    ~Free() {
+      for (void* p : a) cudaFreeAsync(p, st);
+    }
+  } fr{{B, Xs, D, dots}, st};
+  k_copy_block<T, T><<<nblk(n, 256), 256, 0, st>>>(Y, 1, B, R, n, 1);
+  k_copy_block<T, T><<<nblk(n * nz, 256), 256, 0, st>>>(Z, ldz, B + 1, R, n, nz);
+  pl->launches[3] += 2;
+  AGP_CUDA(cudaGetLastError());
+  std::vector<int> mi(R, steps);
+  std::vector<double> tl(R, 0.0);
+  if (rtol > 0) {
+    mi[0] = maxit;
+    tl[0] = rtol;
+  }
+  {
+    Workspace<T> ws;
+    AGP_TRY(cg_run<T>(pl, B, R, Xs, R, R, mi, tl, rtol > 0 ? 5 : 0, ws, st));
+    // y^T alpha and the SLQ quadratures of the probes
+    AGP_TRY(col_dot(B, R, Xs, R, n, 1, ws.partial, dots, st, pl));
+    k_slq_logdet<<<nblk(nz, kSlqThreads), kSlqThreads, 0, st>>>(ws.ahist, ws.bhist, ws.iscal + R, ws.scal + R, R, 1,
+                                              dots + R);
+    pl->launches[3] += 1;
+    AGP_CUDA(cudaGetLastError());
+  }
+  std::vector<double> h(R + 1);
+  AGP_CUDA(cudaMemcpyAsync(h.data(), dots, sizeof(double) * (R), cudaMemcpyDeviceToHost, st));
+  // dots[R + c] holds the quadrature of column c (c >= 1)
+  std::vector<double> quad(R);
+  AGP_CUDA(cudaMemcpyAsync(quad.data(), dots + R, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  double logdet = 0.0;
+  for (int c = 1; c < R; ++c) logdet += quad[c];
+  logdet /= nz;
+  *nlml = 0.5 * (h[0] + logdet + (double)n * std::log(2.0 * M_PI));
+
+  // gradient: 1/2 (-alpha^T dK alpha + (1/nz) sum_i u_i^T dK z_i), Xs = [alpha, u_1..u_nz]
+  const agp_param ths[3] = {AGP_D_ELL, AGP_D_SIGMA_F, AGP_D_SIGMA_EPS};
+  for (int k = 0; k < 3; ++k) {
+    // dK applied to [alpha, z_1..z_nz]: build that block in D's scratch (reuse B)
+    k_copy_block<T, T><<<nblk(n, 256), 256, 0, st>>>(Xs, R, B, R, n, 1);
+    pl->launches[3] += 1;
+    AGP_TRY(agp_deriv_matvec(pl, ths[k], B, R, D, R, R, st));
+    double* part = nullptr;
+    AGP_CUDA(cudaMallocAsync(&part, sizeof(double) * kMaxDotBlocks * R, st));
+    agp_status s = col_dot(Xs, R, D, R, n, R, part, dots + 2 * R, st, pl);
+    cudaFreeAsync(part, st);
+    if (s != AGP_OK) return s;
+    std::vector<double> g(R);
+    AGP_CUDA(cudaMemcpyAsync(g.data(), dots + 2 * R, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    double tr = 0.0;
+    for (int c = 1; c < R; ++c) tr += g[c];
+    grad[k] = 0.5 * (-g[0] + tr / nz);
+  }
+  // A non-positive Ritz value makes log theta undefined: the truncated
+  // operator (no boundary smoothing, Sec. 3.1) is indefinite at these
+  // hyperparameters. The gradient estimate above does not use logarithms.
+  if (!std::isfinite(*nlml))
+    return set_error(AGP_ENAN, "SLQ met a non-positive Ritz value: K_hat is indefinite here");
+  return AGP_OK;
+}
+
+}  // namespace
+}  // namespace agp
+
+using namespace agp;
+
+extern "C" {
+
+agp_status agp_pcg_solve(agp_plan pl, const void* B, int64_t ldb, void* Xsol, int64_t ldx, int R,
+                         double rtol, int maxit, int n_landmarks, int* iters, double* relres,
+                         void* stream) {
+  if (!pl || !B || !Xsol || R < 1 || ldb < R || ldx < R || maxit < 0 || !(rtol >= 0))
+    return set_error(AGP_EINVAL, "bad arguments");
+  if (n_landmarks != 0) return set_error(AGP_EINVAL, "preconditioning is not available");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl->prec == AGP_F32)
+    return pcg_t<float>(pl, (const float*)B, ldb, (float*)Xsol, ldx, R, rtol, maxit, iters, relres, st);
+  return pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, iters, relres,
+                       st);
+}
+
+agp_status agp_dot_columns(agp_plan pl, const void* A, int64_t lda, const void* B, int64_t ldb,
+                           int R, double* out, void* stream) {
+  if (!pl || !A || !B || !out || R < 1 || lda < R || ldb < R)
+    return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* buf = nullptr;
+  AGP_CUDA(cudaMallocAsync(&buf, sizeof(double) * (kMaxDotBlocks + 1) * R, st));
+  agp_status s =
+      pl->prec == AGP_F32
+          ? col_dot((const float*)A, lda, (const float*)B, ldb, pl->n, R, buf,
+                           buf + (int64_t)kMaxDotBlocks * R, st, pl)
+          : col_dot((const double*)A, lda, (const double*)B, ldb, pl->n, R, buf,
+                            buf + (int64_t)kMaxDotBlocks * R, st, pl);
+  if (s == AGP_OK) {
+    cudaError_t e = cudaMemcpyAsync(out, buf + (int64_t)kMaxDotBlocks * R, sizeof(double) * R,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    s = cuda_status(e, "agp_dot_columns");
+  }
+  cudaFreeAsync(buf, st);
+  return s;
+}
+
+agp_status agp_nlml_grad(agp_plan pl, const void* Y, const void* Z, int64_t ldz, int nz,
+                         int lanczos_steps, double rtol, int maxit, double* nlml, double* grad,
+                         void* stream) {
+  if (!pl || !Y || !Z || nz < 1 || ldz < nz || lanczos_steps < 1 ||
+      lanczos_steps > kMaxLanczos || !nlml || !grad || (rtol > 0 && maxit < 1))
+    return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl->prec == AGP_F32)
+    return nlml_t<float>(pl, (const float*)Y, (const float*)Z, ldz, nz, lanczos_steps, rtol, maxit,
+                         nlml, grad, st);
+  return nlml_t<double>(pl, (const double*)Y, (const double*)Z, ldz, nz, lanczos_steps, rtol, maxit,
+                        nlml, grad, st);
+}
+
+}  // extern "C"

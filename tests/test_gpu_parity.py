@@ -31,9 +31,14 @@ def agp():
 
 
 def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    """Relative l2 error (complex arrays keep their imaginary parts); an
+    all-zero reference requires an all-zero result."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    if nb == 0:
+        return 0.0 if np.linalg.norm(a) == 0 else float("inf")
+    return float(np.linalg.norm(a - b) / nb)
 
 
 def make(agp, X, windows, N, s, kernel="gauss", ell=0.3, sf=1.0, se=0.1, dtype=torch.float32):
