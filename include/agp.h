@@ -216,6 +216,27 @@ agp_status agp_batch_matvec(agp_batch batch, int which, void* stream);
 agp_status agp_dot_columns(agp_plan plan, const void* A, int64_t lda, const void* B, int64_t ldb,
                            int R, double* out, void* stream);
 
+/* Column dot products like agp_dot_columns, for callers that may not allocate
+ * device memory: code that runs where cudaMalloc / cudaMallocAsync are not
+ * allowed or not wanted -- inside a framework or memory pool that owns all of
+ * the device's memory, or in a latency-critical loop that must not trigger an
+ * allocation (and the synchronisation or pool growth that can come with it).
+ * The paper has no counterpart: this is a property of the library, not of
+ * the method.
+ *  - Allocates nothing: the partial sums live in a fixed device array of the
+ *    library (512 blocks x 64 columns of doubles, 256 KB), held by every GPU
+ *    that loads the library until the process exits. Nothing in it needs to
+ *    start at zero: each call writes every partial sum it reads.
+ *  - The first call on a device looks the array up for that device (with it
+ *    current); make that first call before any stream capture.
+ *  - Every call shares the array: calls whose work overlaps on the GPU (two
+ *    streams, or two threads) race. Serialise them.
+ *  - prec: element type of A and B. A: device [n][lda], B: device [n][ldb];
+ *    out: device double[R], written with sum_i A[i][r] * B[i][r] (FP64).
+ *    R must be 1..64 (AGP_EINVAL otherwise). Asynchronous on `stream`. */
+agp_status agp_dot_columns_static(agp_prec prec, const void* A, int64_t lda, const void* B,
+                                  int64_t ldb, int64_t n, int R, double* out, void* stream);
+
 /* Stage profiler (tracing). When enabled, the library records a pair of CUDA
  * events on the caller's stream around every kernel launch of the matvec
  * path, per stage: 0 = spreading, 1 = DFT + spectral multiply, 2 =

@@ -69,6 +69,8 @@ _SIGS = {
                               c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
     "agp_dot_columns": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int,
                                 POINTER(c_double), c_void_p]),
+    "agp_dot_columns_static": (c_int, [c_int, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int,
+                                       c_void_p, c_void_p]),
     "agp_batch_create": (c_int, [POINTER(c_void_p), POINTER(c_void_p), c_int, c_void_p]),
     "agp_batch_destroy": (c_int, [c_void_p]),
     "agp_batch_bind": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_int64), POINTER(c_void_p),
@@ -255,6 +257,24 @@ def agp_dot_columns(plan: c_void_p, A: torch.Tensor, B: torch.Tensor) -> np.ndar
     out = (c_double * R)()
     _check(load_library().agp_dot_columns(plan, ap, lda, bp, ldb, R, out, _stream()))
     return np.array(out[:], dtype=np.float64)
+
+
+def agp_dot_columns_static(A: torch.Tensor, B: torch.Tensor, out: torch.Tensor):
+    """Column dot products into out (float64 CUDA tensor [R]) without any
+    device allocation by the library: for callers that must not allocate
+    (see include/agp.h). Calls that overlap on the GPU share one scratch
+    array and race; the first call on a device must precede stream capture."""
+    if A.dtype not in (torch.float32, torch.float64):
+        raise ValueError("A must be float32 or float64")
+    ap, lda, R = _block(A, A.dtype, "A")
+    bp, ldb, Rb = _block(B, A.dtype, "B")
+    if Rb != R or A.shape[0] != B.shape[0]:
+        raise ValueError("A and B must have the same shape")
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < R or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 CUDA tensor with R entries")
+    prec = 0 if A.dtype == torch.float32 else 1
+    _check(load_library().agp_dot_columns_static(prec, ap, lda, bp, ldb, A.shape[0], R,
+                                                 out.data_ptr(), _stream()))
 
 
 def agp_batch_create(plans) -> c_void_p:

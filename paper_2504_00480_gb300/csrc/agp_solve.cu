@@ -10,6 +10,7 @@
 // then one ordered sum per column. The host loop enqueues one CG iteration at
 // a time and reads the per-column convergence flags back every few iterations.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "agp_internal.cuh"
@@ -283,6 +284,37 @@ struct Workspace {
     if (s_ != AGP_OK) return s_;                                   \
   } while (0)
 
+// ---- Column dot products without allocation (agp_dot_columns_static) --------
+// The per-block FP64 partial sums of the two-pass reduction live in this
+// file-scope device array instead of memory allocated per call: at most
+// kStaticDotBlocks blocks x kStaticDotMaxR columns (256 KB). Every GPU that
+// loads the library holds it until the process exits. Host code must not use
+// the symbol as an address: static_dot_scratch() looks up its device address
+// once per device (with that device current) and caches it.
+constexpr int kStaticDotBlocks = 512;
+constexpr int kStaticDotMaxR = 64;
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) double g_static_dot_scratch[kStaticDotBlocks * kStaticDotMaxR];
+
+std::mutex g_static_dot_mu;
+double* g_static_dot_addr[kMaxDevices] = {};
+
+agp_status static_dot_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return set_error(AGP_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_static_dot_mu);
+  if (!g_static_dot_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_dot_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress");
+    g_static_dot_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_dot_addr[dev];
+  return AGP_OK;
+}
+
 template <typename TA, typename TB>
 agp_status col_dot(const TA* A, int64_t lda, const TB* B, int64_t ldb, int64_t n, int R,
                    double* partial, double* out, cudaStream_t st, agp_plan_s* pl) {
@@ -506,6 +538,28 @@ agp_status agp_dot_columns(agp_plan pl, const void* A, int64_t lda, const void* 
   }
   cudaFreeAsync(buf, st);
   return s;
+}
+
+agp_status agp_dot_columns_static(agp_prec prec, const void* A, int64_t lda, const void* B,
+                                  int64_t ldb, int64_t n, int R, double* out, void* stream) {
+  if (!A || !B || !out || n < 1 || lda < R || ldb < R)
+    return set_error(AGP_EINVAL, "bad arguments");
+  if (R < 1 || R > kStaticDotMaxR)
+    return set_error(AGP_EINVAL, "agp_dot_columns_static: R must be in [1, 64]");
+  if (prec != AGP_F32 && prec != AGP_F64) return set_error(AGP_EINVAL, "bad prec");
+  double* scratch = nullptr;
+  AGP_TRY(static_dot_scratch(&scratch));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nb = (int)std::min<int64_t>(kStaticDotBlocks, (n + kDotRows - 1) / kDotRows);
+  const dim3 grid(nb, (R + 31) / 32);
+  if (prec == AGP_F32)
+    k_dot_partial<float, float><<<grid, kDotThreads, 0, st>>>((const float*)A, lda, (const float*)B,
+                                                              ldb, n, R, scratch);
+  else
+    k_dot_partial<double, double><<<grid, kDotThreads, 0, st>>>((const double*)A, lda,
+                                                                (const double*)B, ldb, n, R, scratch);
+  k_dot_final<<<nblk(R, 128), 128, 0, st>>>(scratch, nb, R, out);
+  return cuda_status(cudaGetLastError(), "agp_dot_columns_static");
 }
 
 agp_status agp_nlml_grad(agp_plan pl, const void* Y, const void* Z, int64_t ldz, int nz,
