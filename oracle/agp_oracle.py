@@ -51,7 +51,8 @@ __all__ = [
     "truncated_matvec", "truncated_deriv_matvec",
     "bins", "kb_shape", "kb_window", "kb_window_hat",
     "nfft_adjoint", "nfft", "nfft_fastsum_matvec",
-    "cg", "lanczos_tridiag_from_cg", "slq_quadratic",
+    "cg", "pcg", "farthest_point_sampling", "additive_landmarks", "nystrom_preconditioner",
+    "lanczos_tridiag_from_cg", "slq_quadratic",
     "nlml_exact", "nlml_estimate",
 ]
 
@@ -496,6 +497,92 @@ def cg(apply_A, B, rtol=1e-4, maxit=200, fixed_iters=None):
             p = r + beta * p
         X[:, c] = x
     return X, iters, relres, alphas, betas
+
+
+def pcg(apply_A, apply_Minv, B, rtol=1e-4, maxit=200):
+    """Preconditioned conjugate gradients for A X = B, one recursion per
+    column, zero initial guess, stopping on the unpreconditioned relative
+    residual |b - A x|_2 / |b|_2 <= rtol (Sec. 1, Sec. 5.1). Returns X,
+    iterations, relative residuals."""
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    n, R = B.shape
+    X = np.zeros_like(B)
+    iters = np.zeros(R, dtype=np.int64)
+    relres = np.ones(R)
+    for c in range(R):
+        b = B[:, c]
+        bn = np.linalg.norm(b)
+        if bn == 0:
+            relres[c] = 0.0
+            continue
+        x = np.zeros(n)
+        r = b.copy()
+        z = apply_Minv(r[:, None])[:, 0]
+        p = z.copy()
+        rz = r @ z
+        for it in range(maxit):
+            q = apply_A(p[:, None])[:, 0]
+            a = rz / (p @ q)
+            x = x + a * p
+            r = r - a * q
+            iters[c] = it + 1
+            relres[c] = np.linalg.norm(r) / bn
+            if relres[c] <= rtol:
+                break
+            z = apply_Minv(r[:, None])[:, 0]
+            rz_new = r @ z
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+        X[:, c] = x
+    return X, iters, relres
+
+
+def farthest_point_sampling(x, k):
+    """Greedy farthest point sampling of k indices of the rows of x (Sec. 2.3,
+    the landmark choice of the additive AFN preconditioner): start at index 0,
+    then repeatedly take the point whose distance to the chosen set is
+    largest, the lowest index among equal distances. The squared distances
+    are compared after rounding to float32 (the precision in which the GPU
+    path takes this decision)."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    k = min(k, n)
+    chosen = [0]
+    dist = np.full(n, np.inf)
+    for _ in range(1, k):
+        last = x[chosen[-1]]
+        dist = np.minimum(dist, np.sum((x - last) ** 2, axis=1))
+        d32 = dist.astype(np.float32)
+        chosen.append(int(np.argmax(d32)))     # argmax returns the first maximum
+    return chosen
+
+
+def additive_landmarks(X, windows, k_total):
+    """Landmarks of every feature window (ceil(k_total / P) each by farthest
+    point sampling on that window's features), merged into one sorted set
+    without repeats (Sec. 2.3)."""
+    P = len(windows)
+    kw = max(1, -(-k_total // P))
+    s = set()
+    for w in windows:
+        s.update(farthest_point_sampling(window_points(X, w), kw))
+    return sorted(s)
+
+
+def nystrom_preconditioner(X, windows, kind, ell, sigma_f, sigma_eps, landmarks):
+    """M = K_{:,L} K_LL^{-1} K_{L,:} + sigma_eps^2 I with K = sigma_f^2 sum_s K_s
+    (the exact kernel of Sec. 2.1) and the landmark set L -- the (1,1)-block
+    Nystrom part of the additive AFN preconditioner (Sec. 2.3). Formed as a
+    dense n x n matrix; returns a function applying M^{-1}."""
+    n = X.shape[0]
+    L = list(landmarks)
+    KnL = dense_matvec(X, windows, kind, ell, sigma_f, 0.0, np.eye(n)[:, L], add_noise=False)
+    KLL = KnL[L, :]
+    M = KnL @ np.linalg.solve(KLL, KnL.T) + sigma_eps ** 2 * np.eye(n)
+    M = 0.5 * (M + M.T)
+    return lambda P: np.linalg.solve(M, P)
 
 
 def lanczos_tridiag_from_cg(alphas, betas):

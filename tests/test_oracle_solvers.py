@@ -36,6 +36,58 @@ def test_cg_zero_rhs_and_iteration_cap():
     assert it[1] == 3 and rel[1] > 1e-14
 
 
+def test_pcg_with_identity_is_cg_and_matches_solve():
+    X, W, th, rng = _problem(40)
+    K = O.dense_matrix(X, W, "gauss", th["ell"], th["sigma_f"], th["sigma_eps"])
+    B = rng.standard_normal((40, 2))
+    Xp, itp, _ = O.pcg(lambda P: K @ P, lambda P: P, B, rtol=1e-12, maxit=400)
+    Xc, itc, _, _, _ = O.cg(lambda P: K @ P, B, rtol=1e-12, maxit=400)
+    np.testing.assert_array_equal(itp, itc)
+    np.testing.assert_allclose(Xp, Xc, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(Xp, np.linalg.solve(K, B), rtol=1e-8, atol=1e-9)
+
+
+def test_farthest_point_sampling_brute_force():
+    # each chosen point has the largest distance to the points chosen before
+    # it (checked by enumeration), the first is index 0, and a duplicate of an
+    # earlier point is never chosen while a farther point exists
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-0.24, 0.24, size=(60, 2))
+    x[17] = x[0]
+    ch = O.farthest_point_sampling(x, 12)
+    assert ch[0] == 0 and len(set(ch)) == 12 and 17 not in ch
+    for t in range(1, 12):
+        prev = x[ch[:t]]
+        md = [min(np.sum((x[i] - p) ** 2) for p in prev) for i in range(60)]
+        assert md[ch[t]] == pytest.approx(max(md), rel=1e-6)
+    # three points on a line: 0, then the far end, then the middle
+    line = np.array([[0.0], [0.1], [0.2]])
+    assert O.farthest_point_sampling(line, 3) == [0, 2, 1]
+
+
+def test_nystrom_with_all_points_is_exact():
+    # L = every point: K_{:,L} K_LL^{-1} K_{L,:} = K, so M = K_hat and one PCG
+    # step solves the system
+    X, W, th, rng = _problem(30)
+    K = O.dense_matrix(X, W, "matern12", th["ell"], th["sigma_f"], th["sigma_eps"])
+    Minv = O.nystrom_preconditioner(X, W, "matern12", th["ell"], th["sigma_f"], th["sigma_eps"],
+                                    range(30))
+    B = rng.standard_normal((30, 2))
+    np.testing.assert_allclose(Minv(B), np.linalg.solve(K, B), rtol=1e-6, atol=1e-8)
+    Xs, it, _ = O.pcg(lambda P: K @ P, Minv, B, rtol=1e-8, maxit=5)
+    assert np.all(it == 1)
+
+
+def test_additive_landmarks_union_per_window():
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-0.24, 0.24, size=(80, 5))
+    W = [[0, 1, 2], [3, 4]]
+    L = O.additive_landmarks(X, W, 7)
+    want = sorted(set(O.farthest_point_sampling(X[:, [0, 1, 2]], 4)) |
+                  set(O.farthest_point_sampling(X[:, [3, 4]], 4)))
+    assert L == want and L[0] == 0
+
+
 def test_slq_exact_with_full_krylov_space():
     # With as many Lanczos steps as the dimension, Gauss quadrature is exact:
     # z^T logm(A) z = |z|^2 sum tau^2 log theta.
