@@ -2,8 +2,8 @@
 
 Workload (one GPU): n = 1,000,000 points, p = 8 standardized Gaussian features
 min-max scaled to [-0.24, 0.24], windows {0,1,2},{3,4,5},{6,7} (d = 3, 3, 2),
-Gaussian kernel, ell = sigma_f = sigma_eps = ln 2, N = 32 / 32 / 64, cutoff
-s = 5, FP32, 32 right-hand sides [y, 31 Rademacher probes].
+Gaussian kernel, ell = 0.1, sigma_f = sigma_eps = ln 2, N = 32 / 32 / 64,
+cutoff s = 5, FP32, 32 right-hand sides [y, 31 Rademacher probes].
 
 One step = new hyperparameters (Fourier coefficients of the kernel and its
 ell-derivative, recomputed on the device) + one application of K_hat to the
@@ -14,6 +14,10 @@ sum). The point set is fixed during hyperparameter training, so the plan
 Metric: additive-kernel MVMs/s (one MVM = K_hat applied to one vector, all
 windows). `e2e` times the same step through the C ABI with the right-hand
 sides in pinned host memory and the result copied back every step.
+Also reported: `nlml_grad`, NLML value + gradient evaluations per second on
+the same plan (y and 16 Rademacher probes, 20 Lanczos steps), and
+`plain_fp64`, the same library with an FP64 plan and one right-hand side per
+call, with the FP32 result's relative error against it.
 
 --impl reference times the FP64 CPU oracle (Fourier-truncated sum) on the
 host cores on a bounded sample of the same workload.
@@ -107,6 +111,13 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(r[0] for r in rows),
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
                 "samples": len(rows)}
+
+
+def measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def measured_traffic(kernel, n, R):
@@ -240,13 +251,9 @@ def run_gpu(args):
         dist.barrier()
     prof = plan.profile_read(reset=True)
     plan.profile(False)
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
+    ms = reduce_max(sum(a.elapsed_time(b) for a, b in evs), dist, dev)
     ms_step = ms / args.steps
-    value = world * R * args.steps / (ms / 1e3)
+    value = job_throughput(world, R, args.steps, ms)
     launches_per_step = sum(p["launches"] for p in prof.values()) / args.steps
 
     # Roofline of the dominant kernel: the d=3 launch of spreading or
@@ -261,32 +268,43 @@ def run_gpu(args):
     achieved = flops_launch / (launch_ms / 1e3) / 1e12
     clocks = clk.summary()
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12   # FP32 FMA at max SM clock
-    traffic = measured_traffic(f"k_{dom}", w.n, R)
+    kname = (f"k_spread<float, 3, {w.cutoff}, 32>" if dom == "spread"
+             else f"k_interp2<3, {w.cutoff}, 32>")
+    traffic = measured_traffic(kname, w.n, R)
+    # HBM view of the same launch: algorithmic bytes = per point and d=3
+    # window its 3 x 2s window values, its permutation index and its R-value
+    # row of V (spread) or Out (interp), plus the window's active grid box
+    # [W^3][R] once; measured bytes from the committed ncu summary
+    hbm_peak = measured_hbm_peak()
+    d3 = [k for k, win in enumerate(w.windows) if len(win) == 3]
+    grid_bytes = sum((w.N[k] + 2 * w.cutoff - 1) ** 3 * R * 4 for k in d3)
+    alg_bytes = len(d3) * w.n * (3 * 2 * w.cutoff * 4 + 4 + R * 4) + grid_bytes
+    hbm = {"unit": "GB/s", "peak": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+           "algorithmic_bytes": alg_bytes,
+           "algorithmic_gbs": alg_bytes / (launch_ms / 1e3) / 1e9,
+           "measured_gbs": None if traffic is None else traffic / (launch_ms / 1e3) / 1e9}
+    hbm["algorithmic_frac"] = None if hbm_peak is None else hbm["algorithmic_gbs"] / hbm_peak
 
-    # end-to-end through the C ABI with host buffers
-    Vh = torch.tensor(w.V, dtype=torch.float32).pin_memory()
-    Oh = torch.empty_like(Vh).pin_memory()
-    for k in range(2):
-        V.copy_(Vh, non_blocking=True)
-        step(k)
-        Oh.copy_(Out, non_blocking=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    e0.record(stream)
-    for k in range(args.steps):
-        V.copy_(Vh, non_blocking=True)
-        step(args.warmup + k)
-        Oh.copy_(Out, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t)
-    e2e = world * R * args.steps / (e2e_ms / 1e3)
+    # end-to-end through the C ABI with host buffers: every step copies its
+    # right-hand sides from pinned host memory and its result back. Steps are
+    # pipelined over double-buffered device blocks: the upload of step k+1
+    # and the download of step k-1 run on their own streams while step k
+    # computes (events order each buffer's reuse).
+    e2e_ms = time_e2e(agp, plan, w, ells, args, dev)
+    e2e = job_throughput(world, R, args.steps, reduce_max(e2e_ms, dist, dev))
+
+    # NLML value + gradient (Sec. 1 eqs. (1.4)-(1.5) with M = I) on the same
+    # plan: y and 16 Rademacher probes, 20 CG-Lanczos steps, then the three
+    # derivative matvecs; the call synchronises, so it is timed on the host
+    # around a device synchronisation.
+    plan.set_hyper(w.ell, w.sigma_f, w.sigma_eps)
+    nl = time_nlml(agp, plan, V, args.nlml_reps, dev)
+    agp.agp_matvec(plan.handle, V, Out, True)
+    # the plain FP64 path: the same library and workload with an FP64 plan,
+    # one right-hand side per call
+    plain = None
+    if not args.no_plain:
+        plain = time_plain_fp64(agp, w, V, Out, args.plain_reps, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -300,23 +318,133 @@ def run_gpu(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic", "config": workload_config(w.n),
-                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(Vh.numel() * 4),
-                        "d2h_bytes_per_step": int(Oh.numel() * 4)},
+                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(w.n * R * 4),
+                        "d2h_bytes_per_step": int(w.n * R * 4),
+                        "pipelined": "upload of step k+1 and download of step k-1 overlap "
+                                     "step k (double-buffered device blocks, three streams)"},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
-                "roofline": {"bound": "alu", "kernel": f"k_{dom}<float, 3, 5, 32>",
+                "roofline": {"bound": "alu", "kernel": kname,
                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": traffic,
                              "launch_ms": launch_ms, "flop_per_launch": flops_launch,
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz "
                                             "(nominal maximum clock)"},
+                "hbm": hbm,
                 "stages_ms_per_step": {s: prof[s]["ms"] / args.steps for s in prof},
                 "stage_launches_per_step": {s: prof[s]["launches"] / args.steps for s in prof},
-                "clocks": clocks, "cpu_baseline": cpu}
+                "clocks": clocks, "cpu_baseline": cpu,
+                "nlml_grad": nl, "plain_fp64": plain}
+        if plain is not None:
+            plain["batched_fp32_over_plain_fp64"] = value / plain["value"]
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def reduce_max(value, dist, device):
+    """Maximum of a per-rank float over all ranks (identity on one rank)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def job_throughput(world, rhs, steps, ms):
+    """Whole-job MVMs/s: every rank applies K_hat to `rhs` vectors per step
+    (independent replicas), timed by the slowest rank's `ms`."""
+    return world * rhs * steps / (ms / 1e3)
+
+
+def time_e2e(agp, plan, w, ells, args, dev):
+    import torch
+    Vh = torch.tensor(w.V, dtype=torch.float32).pin_memory()
+    Oh = [torch.empty_like(Vh).pin_memory() for _ in range(2)]
+    Vd = [torch.empty(Vh.shape, dtype=torch.float32, device=dev) for _ in range(2)]
+    Od = [torch.empty_like(Vd[0]) for _ in range(2)]
+    comp = torch.cuda.current_stream(dev)
+    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    uploaded, computed, downloaded = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    fresh = [True, True]
+
+    def run(k, nsteps):
+        for j in range(nsteps):
+            b = j % 2
+            with torch.cuda.stream(up):
+                if not fresh[b]:
+                    up.wait_event(computed[b])        # step j-2 is done reading Vd[b]
+                Vd[b].copy_(Vh, non_blocking=True)
+                uploaded[b].record(up)
+            comp.wait_event(uploaded[b])
+            if not fresh[b]:
+                comp.wait_event(downloaded[b])        # Od[b] of step j-2 is on the host
+            plan.set_hyper(ells[k + j], w.sigma_f, w.sigma_eps)
+            agp.agp_matvec(plan.handle, Vd[b], Od[b], True)
+            computed[b].record(comp)
+            with torch.cuda.stream(down):
+                down.wait_event(computed[b])
+                Oh[b].copy_(Od[b], non_blocking=True)
+                downloaded[b].record(down)
+            fresh[b] = False
+
+    run(0, 2)                                         # warm-up
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(comp)
+    up.wait_event(e0)
+    run(args.warmup, args.steps)
+    comp.wait_stream(down)
+    e1.record(comp)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1)
+
+
+def time_nlml(agp, plan, V, reps, dev):
+    import torch
+    y = V[:, 0].contiguous()
+    Z = V[:, 1:17]
+    res = {"unit": "NLML-grad/s", "probes": 16, "lanczos_steps": 20, "rhs": 17}
+    try:
+        plan.nlml_grad(y, Z, lanczos_steps=20)          # warm-up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            nl, g = plan.nlml_grad(y, Z, lanczos_steps=20)
+        torch.cuda.synchronize(dev)
+        dt = (time.perf_counter() - t0) / reps
+        res.update({"value": 1.0 / dt, "ms": 1e3 * dt, "reps": reps, "nlml": nl, "grad": g,
+                    "status": "ok"})
+    except agp.AgpError as e:
+        # the gradient is still computed when only the log-determinant fails
+        res.update({"value": None, "status": str(e)})
+    return res
+
+
+def time_plain_fp64(agp, w, V32, Out32, reps, dev):
+    import torch
+    X64 = torch.tensor(w.X, dtype=torch.float32, device=dev).double()
+    p64 = agp.Plan(X64, w.windows, w.N, w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
+    v = V32[:, :1].double().contiguous()
+    o = torch.empty_like(v)
+    for _ in range(2):
+        agp.agp_matvec(p64.handle, v, o, True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        agp.agp_matvec(p64.handle, v, o, True)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    # accuracy of the batched FP32 result against the FP64 one (column 0)
+    rel = float(torch.linalg.norm(Out32[:, 0].double() - o[:, 0]) / torch.linalg.norm(o[:, 0]))
+    p64.close()
+    return {"value": 1e3 / ms, "unit": "MVM/s", "ms_per_mvm": ms, "reps": reps, "rhs": 1,
+            "dtype": "f64", "fp32_rel_l2_vs_fp64": rel}
 
 
 def main():
@@ -327,6 +455,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nlml-reps", type=int, default=2)
+    ap.add_argument("--plain-reps", type=int, default=5)
+    ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

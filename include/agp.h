@@ -156,12 +156,30 @@ agp_status agp_plan_query(agp_plan plan, int64_t* n, int* P, int window, int* d,
  * |r_k|_2 / |b|_2 <= rtol or after maxit iterations.
  * B: device [n][ldb]; Xsol: device [n][ldx], overwritten with the iterates;
  * iters, relres: optional host arrays [R] (NULL to skip).
- * n_landmarks: 0 (no preconditioner); other values return AGP_EINVAL.
+ * n_landmarks: 0 for plain CG, or 1..480 for CG preconditioned with the
+ * landmark part of the paper's additive AFN preconditioner (Sec. 2.3):
+ * ceil(n_landmarks / P) landmarks per feature window by farthest point
+ * sampling (first landmark: point 0; ties: lowest index), merged, and
+ * M = K_{:,L} K_LL^{-1} K_{L,:} + sigma_eps^2 I (exact kernel) applied by the
+ * Woodbury identity with an FP64 Cholesky factor; needs sigma_eps > 0 and
+ * R <= 32. The stopping test stays on the unpreconditioned residual.
  * Returns AGP_NOT_CONVERGED if some column stopped above rtol (Xsol holds the
  * last iterate). Synchronises `stream`. */
 agp_status agp_pcg_solve(agp_plan plan, const void* B, int64_t ldb, void* Xsol, int64_t ldx,
                          int R, double rtol, int maxit, int n_landmarks, int* iters,
                          double* relres, void* stream);
+
+/* The landmark set that agp_pcg_solve uses for the same n_landmarks
+ * (1..480; Sec. 2.3): ceil(n_landmarks / P) indices per feature window by
+ * farthest point sampling on that window's coordinates (in the plan
+ * precision; first landmark point 0; each next one maximises the squared
+ * distance to those already chosen, compared after rounding to float32,
+ * ties to the lowest index), merged into increasing order without repeats.
+ * idx: host int32 array with room for cap entries; count: host int, set to
+ * the size of the set (at most P * ceil(n_landmarks / P)). Returns AGP_EINVAL
+ * if cap is smaller (count is still set). Synchronises `stream`. */
+agp_status agp_plan_landmarks(agp_plan plan, int n_landmarks, int32_t* idx, int cap, int* count,
+                              void* stream);
 
 /* Negative log marginal likelihood and its gradient with respect to
  * (ell, sigma_f, sigma_eps), estimated as in Sec. 1 eqs. (1.4) and (1.5) with

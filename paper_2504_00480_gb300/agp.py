@@ -67,6 +67,7 @@ _SIGS = {
                               c_int, c_int, POINTER(c_int), POINTER(c_double), c_void_p]),
     "agp_nlml_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int, c_double,
                               c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
+    "agp_plan_landmarks": (c_int, [c_void_p, c_int, c_void_p, c_int, POINTER(c_int), c_void_p]),
     "agp_dot_columns": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int,
                                 POINTER(c_double), c_void_p]),
     "agp_dot_columns_static": (c_int, [c_int, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int,
@@ -233,6 +234,18 @@ def agp_pcg_solve(plan: c_void_p, B: torch.Tensor, Xsol: torch.Tensor, rtol: flo
     if st != AGP_NOT_CONVERGED or raise_not_converged:
         _check(st)
     return np.array(it[:], dtype=np.int64), np.array(rel[:], dtype=np.float64)
+
+
+def agp_plan_landmarks(plan: c_void_p, n_landmarks: int) -> np.ndarray:
+    """The landmark indices agp_pcg_solve uses for n_landmarks (sorted)."""
+    P = c_int()
+    _check(load_library().agp_plan_query(plan, None, byref(P), 0, None, None, None))
+    cap = P.value * (-(-int(n_landmarks) // P.value))
+    idx = (c_int32 * max(cap, 1))()
+    cnt = c_int()
+    _check(load_library().agp_plan_landmarks(plan, int(n_landmarks), idx, cap, byref(cnt),
+                                             _stream()))
+    return np.array(idx[:cnt.value], dtype=np.int64)
 
 
 def agp_nlml_grad(plan: c_void_p, y: torch.Tensor, Z: torch.Tensor, lanczos_steps: int = 20,
@@ -429,10 +442,13 @@ class Plan:
         return out
 
     def solve(self, B: torch.Tensor, rtol: float = 1e-4, maxit: int = 200,
-              raise_not_converged: bool = True):
+              raise_not_converged: bool = True, n_landmarks: int = 0):
         X = torch.empty_like(B)
-        it, rel = agp_pcg_solve(self._h, B, X, rtol, maxit, 0, raise_not_converged)
+        it, rel = agp_pcg_solve(self._h, B, X, rtol, maxit, n_landmarks, raise_not_converged)
         return X, it, rel
+
+    def landmarks(self, n_landmarks: int) -> np.ndarray:
+        return agp_plan_landmarks(self._h, n_landmarks)
 
     def nlml_grad(self, y: torch.Tensor, Z: torch.Tensor, lanczos_steps: int = 20,
                   rtol: float = 0.0, maxit: int = 0):

@@ -276,7 +276,7 @@ agp_status agp_batch_bind(agp_batch b, const void* const* V, const int64_t* ldv,
       return set_error(AGP_EINVAL, "Out overlaps V in a batched problem");
   }
   b->R = R;
-  b->rc = b->prec == AGP_F32 ? (R >= 9 ? 32 : (R >= 2 ? 8 : 1)) : (R >= 2 ? 4 : 1);
+  b->rc = rhs_block_width(b->prec, R);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   agp_status s = b->prec == AGP_F32 ? batch_bind<float>(b, V, ldv, Out, ldo, R, st)
                                     : batch_bind<double>(b, V, ldv, Out, ldo, R, st);

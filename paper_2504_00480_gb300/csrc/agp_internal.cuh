@@ -34,7 +34,7 @@ template <typename T>
 struct WinDev {
   const T* xs;            // sorted coordinates, [d][n]
   const int32_t* perm;    // sorted position -> caller's point index
-  const T* wts;           // window values, sorted order, [n][d][ttp] (see window_ttp)
+  const T* wts;           // window values, sorted order, [n][window_wpp(d, s)]
   T* grid;                // active-box grid, [W^d][RC]
   int64_t n;
   int N, n_os, W;
@@ -43,6 +43,10 @@ struct WinDev {
 // Window values stored per point and dimension: the 2s taps padded with zeros
 // to a multiple of 4 (16-byte vector loads).
 inline int window_ttp(int s) { return (2 * s + 3) / 4 * 4; }
+// Window values stored per point: the first d-1 dimensions as window_ttp(s)
+// values each (2s taps, zero padded), then the last dimension's 2s taps each
+// written twice (v, v), so that packed FP32 pairs load them directly.
+inline int window_wpp(int d, int s) { return (d - 1) * window_ttp(s) + 4 * s; }
 
 // Per-window right-hand sides and outputs, used when the windows of one
 // launch belong to different problems (batches): the kernels then take V,
@@ -104,7 +108,7 @@ struct Window {
   // device buffers
   int32_t* perm = nullptr;       // [n]
   void* xs = nullptr;            // [d][n]
-  void* wts = nullptr;           // [n][d][window_ttp(s)] Kaiser-Bessel values, sorted order
+  void* wts = nullptr;           // [n][window_wpp(d, s)] Kaiser-Bessel values, sorted order
   double* costab = nullptr;      // [N][N] cos(2 pi l k / N) / N for the coefficient DFT
   int32_t* cell_start = nullptr; // [cells + 1]
   int4* items = nullptr;         // work items (window, cell, start, count)
@@ -170,6 +174,10 @@ agp_status cuda_status(cudaError_t e, const char* what);
 // dimension d and cutoff s) onto their grids, which the caller has zeroed.
 // RC = grid column count (32, 8, 1 for FP32; 4, 1 for FP64). With io !=
 // nullptr every window takes its V and ldv from io[window] instead.
+// Right-hand sides processed per pass of spreading / DFT / interpolation for
+// R requested columns (the grid holds that many columns per point).
+int rhs_block_width(agp_prec prec, int R);
+
 template <typename T>
 cudaError_t spread_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
                          int64_t n_items, int d, int s, int RC, const T* V, int64_t ldv, int R,
@@ -180,6 +188,35 @@ template <typename T>
 cudaError_t interp_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
                          int64_t n_items, int d, int s, int RC, T* Out, int64_t ldo, int R,
                          T scale, cudaStream_t st);
+
+// ---- landmark (Nystrom) preconditioner (agp_precond.cu) ----
+// M^{-1} = sigma_eps^{-2} (I - B Ginv B^T), B = K_{:,L} [n][k] stored in the
+// plan precision, Ginv = (sigma_eps^2 K_LL + B^T B)^{-1} [k][k] in FP64. The
+// products with B are accumulated to about FP64 accuracy in both precisions
+// (FP32 plans: compensated FP32 arithmetic on hi/lo splits).
+constexpr int kMaxLandmarks = 480;      // requested landmarks
+constexpr int kMaxLandmarkSet = 512;    // after merging the windows' sets
+struct Precond {
+  int k = 0, rmax = 0, slices = 0;
+  int64_t n = 0, rows_per_slice = 0;
+  double inv_s2 = 0;
+  void* B = nullptr;
+  double* Ginv = nullptr;
+  double* partial = nullptr;   // [slices][k][rmax]
+  double* t1 = nullptr;        // [k][rmax]
+  void* t2 = nullptr;          // FP64 plans: [k][rmax] double; FP32: hi, lo [2][k][rmax] float
+  float* xsplit = nullptr;     // FP32 plans: hi, lo parts of the input [2][n][rmax]
+};
+void precond_free(Precond* pc);
+template <typename T>
+agp_status precond_build(agp_plan_s* pl, int k, int rmax, Precond* pc, cudaStream_t st);
+// The landmark set the preconditioner uses for a request of k landmarks
+// (sorted, no repeats; host vector).
+template <typename T>
+agp_status precond_landmarks(agp_plan_s* pl, int k, std::vector<int32_t>& out, cudaStream_t st);
+// Y = M^{-1} X for X, Y FP64 [n][R] with leading dimension R (R <= 32).
+template <typename T>
+agp_status precond_apply(const Precond& pc, const double* X, double* Y, int R, cudaStream_t st);
 
 // ---- DFT stages (agp_fft.cu), one launch per stage for a group of windows ----
 template <typename T>

@@ -1,0 +1,7 @@
+// Spreading and interpolation kernels instantiated for a block of 24
+// right-hand sides (see agp_nufft_kernels.cuh).
+#include "agp_nufft_kernels.cuh"
+
+namespace agp {
+AGP_NUFFT_RC_DEFINE(float, 24)
+}  // namespace agp

@@ -1,0 +1,8 @@
+// Spreading and interpolation kernels instantiated for a block of 8
+// right-hand sides (see agp_nufft_kernels.cuh).
+#include "agp_nufft_kernels.cuh"
+
+namespace agp {
+AGP_NUFFT_RC_DEFINE(float, 8)
+AGP_NUFFT_RC_DEFINE(double, 4)
+}  // namespace agp

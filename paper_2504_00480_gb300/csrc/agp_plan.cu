@@ -203,19 +203,27 @@ __global__ void k_cos_axis(const double* __restrict__ in, double* __restrict__ o
   out[e] = s;
 }
 
-// Kaiser-Bessel values of every (sorted) point: wts[j][t][tap] =
-// psi(frac(u_t) + s - 1 - tap) for tap < 2s, 0 for the padding taps, where
-// u_t = x_t n_os (Appendix A window in grid units, divided by I0(b s)).
-// Evaluated in FP64 and rounded to the plan precision.
+// Kaiser-Bessel values of every (sorted) point, psi(frac(u_t) + s - 1 - tap)
+// for tap < 2s, where u_t = x_t n_os (Appendix A window in grid units,
+// divided by I0(b s)); evaluated in FP64 and rounded to the plan precision.
+// Layout per point (window_wpp values): dimensions 0..d-2 as ttp values each
+// (zero padded), then the last dimension's taps each written twice.
 template <typename T>
 __global__ void k_window_values(const T* __restrict__ xs, int64_t n, int d, int n_os, int s,
                                 int ttp, double b, double norm, T* __restrict__ wts) {
+  const int wpp = (d - 1) * ttp + 4 * s;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= n * d * ttp) return;
-  const int tap = (int)(e % ttp);
-  const int64_t jt = e / ttp;
-  const int t = (int)(jt % d);
-  const int64_t j = jt / d;
+  if (e >= n * wpp) return;
+  const int64_t j = e / wpp;
+  const int o = (int)(e - j * wpp);
+  int t, tap;
+  if (o < (d - 1) * ttp) {
+    t = o / ttp;
+    tap = o - t * ttp;
+  } else {
+    t = d - 1;
+    tap = (o - (d - 1) * ttp) / 2;
+  }
   double v = 0.0;
   if (tap < 2 * s) {
     const double u = (double)xs[(int64_t)t * n + j] * n_os;   // exact: n_os is a power of two
@@ -581,8 +589,9 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
     AGP_CUDA(cudaStreamSynchronize(st));   // host tables go out of scope
     // window values of every sorted point (they do not depend on the hyperparameters)
     const int ttp = window_ttp(w.s);
-    AGP_CUDA(cudaMalloc(&w.wts, sizeof(T) * n * w.d * ttp));
-    k_window_values<T><<<nblk(n * w.d * ttp, 256), 256, 0, st>>>(
+    const int wpp = window_wpp(w.d, w.s);
+    AGP_CUDA(cudaMalloc(&w.wts, sizeof(T) * n * wpp));
+    k_window_values<T><<<nblk(n * wpp, 256), 256, 0, st>>>(
         reinterpret_cast<const T*>(w.xs), n, w.d, w.n_os, w.s, ttp, pl->kb_b, pl->kb_norm,
         reinterpret_cast<T*>(w.wts));
     AGP_CUDA(cudaGetLastError());
@@ -638,10 +647,7 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
   return AGP_OK;
 }
 
-int pick_rc(const agp_plan_s* pl, int R) {
-  if (pl->prec == AGP_F32) return R >= 9 ? 32 : (R >= 2 ? 8 : 1);
-  return R >= 2 ? 4 : 1;
-}
+int pick_rc(const agp_plan_s* pl, int R) { return rhs_block_width(pl->prec, R); }
 
 // Stage timing: a pair of events around a group of launches on `st`.
 struct StageTimer {

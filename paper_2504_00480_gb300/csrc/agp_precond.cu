@@ -1,0 +1,525 @@
+// Landmark (Nystrom) preconditioner for batched PCG -- the (1,1)-block part of
+// the paper's additive AFN preconditioner (Sec. 2.3): landmarks are chosen by
+// farthest point sampling (FPS) in every feature window and merged; with
+// B = K_{:,L} (the kernel part sigma_f^2 sum_s K_s, exact kernel) and
+// K_LL = B_L,
+//     M = B K_LL^{-1} B^T + sigma_eps^2 I,
+//     M^{-1} = sigma_eps^{-2} (I - B G^{-1} B^T),  G = sigma_eps^2 K_LL + B^T B
+// (Woodbury identity). G is k x k (k <= 512) and inverted once in FP64 by a
+// Cholesky factorisation; applying M^{-1} to an [n][R] block costs two skinny
+// products with B.
+//
+// Accuracy: M^{-1} r = sigma_eps^{-2} (r - B t2) cancels heavily where r lies
+// in the landmark space, so relative errors of B t2 are amplified by up to
+// kappa(M) ~ |K| / sigma_eps^2; with plain FP32 sums the preconditioned CG
+// stalls. FP32 plans therefore split the FP64 inputs into hi + lo FP32 parts
+// and accumulate every product with B, and the Gram matrix B^T B, with the
+// compensated dot product of Ogita, Rump and Oishi ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26(6), 2005, Algorithm Dot2): about twice
+// the FP32 precision at ~10 FP32 operations per term, instead of FP64
+// arithmetic, which runs at a small fraction of the FP32 rate on this part.
+//
+// FPS: the first landmark of a window is the caller's point 0; each next one
+// maximises the distance to the landmarks chosen so far (ties: lowest index),
+// found with a packed (distance, index) atomic maximum.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "agp_internal.cuh"
+
+namespace agp {
+namespace {
+
+#define AGP_CUDA(call)                                             \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_status(e_, #call);          \
+  } while (0)
+#define AGP_TRY(call)                                              \
+  do {                                                             \
+    agp_status s_ = (call);                                        \
+    if (s_ != AGP_OK) return s_;                                   \
+  } while (0)
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// One step of Dot2: (s, c) += a * b with the product split exactly into
+// p + e and an error-free two-sum of s and p; the rounding errors collect in
+// c. The value is s + c. The _rn intrinsics are never fused or reordered.
+__device__ __forceinline__ void dot2_add(float& s, float& c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  c = __fadd_rn(c, __fadd_rn(q, e));
+  s = t;
+}
+
+// x (FP64) -> hi = fl32(x), lo = fl32(x - hi)
+__global__ void k_split(const double* __restrict__ x, int64_t m, float* __restrict__ hi,
+                        float* __restrict__ lo) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const double v = x[e];
+  const float h = __double2float_rn(v);
+  hi[e] = h;
+  lo[e] = __double2float_rn(v - (double)h);
+}
+
+// sorted [d][n] coordinates -> caller order [d][n]
+template <typename T>
+__global__ void k_unsort(const T* __restrict__ xs, const int32_t* __restrict__ perm, int64_t n,
+                         int d, T* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * d) return;
+  const int t = (int)(e / n);
+  const int64_t q = e - (int64_t)t * n;
+  out[(int64_t)t * n + perm[q]] = xs[e];
+}
+
+__global__ void k_fill_double(double* __restrict__ p, int64_t n, double v) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < n) p[e] = v;
+}
+
+// One FPS step: fold the previous landmark into the running minimum distances
+// and record the argmax as key (distance bits << 32 | ~index).
+template <typename T>
+__global__ void k_fps_step(const T* __restrict__ x, int64_t n, int d, int step,
+                           unsigned long long* __restrict__ keys, double* __restrict__ dist) {
+  const unsigned last = (step == 1) ? 0u : 0xFFFFFFFFu - (unsigned)(keys[step - 1] & 0xFFFFFFFFull);
+  double xl[3] = {0, 0, 0};
+  for (int t = 0; t < d; ++t) xl[t] = (double)x[(int64_t)t * n + last];
+  unsigned long long best = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    // explicit rounding (no fused multiply-add): the squared distance is the
+    // plainly rounded sum ((u_0^2 + u_1^2) + u_2^2), so the choice does not
+    // depend on how the compiler contracts it
+    double d2 = 0.0;
+    for (int t = 0; t < d; ++t) {
+      const double u = (double)x[(int64_t)t * n + i] - xl[t];
+      d2 = __dadd_rn(d2, __dmul_rn(u, u));
+    }
+    const double m = fmin(dist[i], d2);
+    dist[i] = m;
+    const unsigned long long key =
+        ((unsigned long long)__float_as_uint((float)m) << 32) | (0xFFFFFFFFull - (unsigned long long)i);
+    best = key > best ? key : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+    best = other > best ? other : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(keys + step, best);
+}
+
+// B[i][j] = sigma_f^2 sum_s kappa_s(|x_i^s - x_{L_j}^s|) (exact kernel, Sec. 2.1)
+template <typename T>
+struct WinPts {
+  const T* x;   // caller order [d][n]
+  int d;
+};
+
+template <typename T>
+__global__ void k_kernel_cols(const WinPts<T>* __restrict__ wp, int P, int64_t n,
+                              const int32_t* __restrict__ lm, int k, int kernel, double ell,
+                              double sf2, T* __restrict__ B) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t i = e / k;
+  const int j = (int)(e - i * k);
+  const int64_t l = lm[j];
+  double s = 0.0;
+  for (int w = 0; w < P; ++w) {
+    const WinPts<T> p = wp[w];
+    double r2 = 0.0;
+    for (int t = 0; t < p.d; ++t) {
+      const double u = (double)p.x[(int64_t)t * n + i] - (double)p.x[(int64_t)t * n + l];
+      r2 += u * u;
+    }
+    s += (kernel == AGP_GAUSS) ? exp(-r2 / (2.0 * ell * ell)) : exp(-sqrt(r2) / ell);
+  }
+  B[e] = (T)(sf2 * s);
+}
+
+// G[a][b] = s2 * B[L_a][b]  (then += B^T B)
+template <typename T>
+__global__ void k_gram_init(const T* __restrict__ B, const int32_t* __restrict__ lm, int k,
+                            double s2, double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  const int a = e / k, b = e - a * k;
+  G[e] = s2 * (double)B[(int64_t)lm[a] * k + b];
+}
+
+// G += B^T B over a slice of rows: 32 x 32 output tile per CTA (blockIdx.x, y),
+// row slices over blockIdx.z, added to G with FP64 atomics. FP64 plans: FP64
+// FMAs; FP32 plans: Dot2 over the whole slice (the products of FP32 entries
+// are split exactly).
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_gram(const T* __restrict__ B, int64_t n, int k, int64_t rows_per_slice, double* __restrict__ G) {
+  __shared__ T sa[64][33];
+  __shared__ T sb[64][33];
+  const int ta = threadIdx.x / 32, tb = threadIdx.x % 32;
+  const int a = blockIdx.x * 32 + ta, b = blockIdx.y * 32 + tb;
+  const int64_t r0 = (int64_t)blockIdx.z * rows_per_slice;
+  const int64_t r1 = min(n, r0 + rows_per_slice);
+  double acc = 0.0;
+  float s = 0.0f, c = 0.0f;
+  for (int64_t rb = r0; rb < r1; rb += 64) {
+    for (int e = threadIdx.x; e < 64 * 32; e += 1024) {
+      const int rr = e / 32, cc = e % 32;
+      const int64_t row = rb + rr;
+      const int ca = blockIdx.x * 32 + cc, cb = blockIdx.y * 32 + cc;
+      sa[rr][cc] = (row < r1 && ca < k) ? B[row * k + ca] : T(0);
+      sb[rr][cc] = (row < r1 && cb < k) ? B[row * k + cb] : T(0);
+    }
+    __syncthreads();
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll 8
+      for (int rr = 0; rr < 64; ++rr) dot2_add(s, c, sa[rr][ta], sb[rr][tb]);
+    } else {
+#pragma unroll 8
+      for (int rr = 0; rr < 64; ++rr) acc = fma((double)sa[rr][ta], (double)sb[rr][tb], acc);
+    }
+    __syncthreads();
+  }
+  if constexpr (sizeof(T) == 4) acc = (double)s + (double)c;
+  if (a < k && b < k) atomicAdd(G + (int64_t)a * k + b, acc);
+}
+
+// In-place lower Cholesky factor of G (k x k, FP64) by one CTA; flag = 1 on a
+// non-positive pivot.
+__global__ void __launch_bounds__(1024) k_cholesky(double* __restrict__ G, int k, int* flag) {
+  for (int j = 0; j < k; ++j) {
+    __syncthreads();
+    const double piv = G[(int64_t)j * k + j];
+    if (!(piv > 0.0)) {
+      if (threadIdx.x == 0) *flag = 1;
+      return;
+    }
+    const double lj = sqrt(piv);
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(int64_t)i * k + j] /= lj;
+    if (threadIdx.x == 0) G[(int64_t)j * k + j] = lj;
+    __syncthreads();
+    const int m = k - j - 1;   // trailing lower triangle, rows/cols j+1 .. k-1
+    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+      const int ii = j + 1 + (int)(e / m), ll = j + 1 + (int)(e % m);
+      if (ll <= ii) G[(int64_t)ii * k + ll] -= G[(int64_t)ii * k + j] * G[(int64_t)ll * k + j];
+    }
+  }
+}
+
+// Column j of L^{-1} by forward substitution (thread per column).
+__global__ void k_tri_inverse(const double* __restrict__ L, int k, double* __restrict__ Li) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  for (int i = 0; i < j; ++i) Li[(int64_t)i * k + j] = 0.0;
+  for (int i = j; i < k; ++i) {
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int m = j; m < i; ++m) s -= L[(int64_t)i * k + m] * Li[(int64_t)m * k + j];
+    Li[(int64_t)i * k + j] = s / L[(int64_t)i * k + i];
+  }
+}
+
+// Ginv = L^{-T} L^{-1}
+__global__ void k_gram_inverse(const double* __restrict__ Li, int k, double* __restrict__ Gi) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  const int a = e / k, b = e - a * k;
+  double s = 0.0;
+  for (int m = max(a, b); m < k; ++m) s += Li[(int64_t)m * k + a] * Li[(int64_t)m * k + b];
+  Gi[e] = s;
+}
+
+// Apply step 1: partial[z][j][r] = sum over row slice z of B[i][j] * X[i][r].
+// CTA: 32 landmark columns (4 per warp) x 32 right-hand sides (lanes), so each
+// block of X rows is read once per 32 landmarks. FP64 plans: FP64 FMAs; FP32
+// plans: Dot2 on X's hi part plus plain FMAs on its lo part.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_pc_bt(const T* __restrict__ B, const double* __restrict__ X, const float* __restrict__ Xh,
+        const float* __restrict__ Xl, int64_t n, int k, int R, int64_t rows_per_slice,
+        double* __restrict__ partial) {
+  const int r = threadIdx.x % 32;
+  const int j0 = blockIdx.x * 32 + (threadIdx.x / 32) * 4;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_slice;
+  const int64_t r1 = min(n, r0 + rows_per_slice);
+  if (r >= R) return;
+  int nq = k - j0;
+  nq = nq < 0 ? 0 : (nq > 4 ? 4 : nq);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if constexpr (sizeof(T) == 4) {
+    float s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
+    for (int64_t i = r0; i < r1; ++i) {
+      const float xh = Xh[i * R + r], xl = Xl[i * R + r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nq) {
+          const float b = __ldg(B + i * k + j0 + q);
+          dot2_add(s[q], c[q], b, xh);
+          sl[q] = __fmaf_rn(b, xl, sl[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = (double)s[q] + (double)c[q] + (double)sl[q];
+  } else {
+    for (int64_t i = r0; i < r1; ++i) {
+      const double x = X[i * R + r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nq) acc[q] = fma((double)__ldg(B + i * k + j0 + q), x, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q < nq) partial[((int64_t)blockIdx.y * k + j0 + q) * R + r] = acc[q];
+}
+
+// Apply step 2 (two launches): phase 0 sums the slices, t1 = sum_z partial[z];
+// phase 1 multiplies, t2 = Ginv t1 (k x R, FP64), stored as FP64 (FP64 plans)
+// or as hi and lo FP32 parts (FP32 plans).
+template <typename T>
+__global__ void k_pc_mid(const double* __restrict__ partial, int nz, const double* __restrict__ Gi,
+                         int k, int R, int phase, double* __restrict__ t1, void* __restrict__ t2) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * R) return;
+  if (phase == 0) {   // reduce the slices
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += partial[(int64_t)z * k * R + e];
+    t1[e] = s;
+  } else {            // multiply by Ginv
+    const int a = e / R, r = e - a * R;
+    double s = 0.0;
+    for (int b = 0; b < k; ++b) s += Gi[(int64_t)a * k + b] * t1[(int64_t)b * R + r];
+    if constexpr (sizeof(T) == 4) {
+      float* t2f = static_cast<float*>(t2);
+      const float h = __double2float_rn(s);
+      t2f[e] = h;
+      t2f[(int64_t)k * R + e] = __double2float_rn(s - (double)h);
+    } else {
+      static_cast<double*>(t2)[e] = s;
+    }
+  }
+}
+
+// Apply step 3: Y[i][r] = inv_s2 (X[i][r] - sum_j B[i][j] t2[j][r]); a warp per
+// row, lanes = right-hand sides, t2 staged in shared memory. FP32 plans: Dot2
+// on t2's hi part plus FMAs on its lo part, the subtraction in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_pc_out(const T* __restrict__ B, const double* __restrict__ X, const void* __restrict__ t2,
+         int64_t n, int k, int R, double inv_s2, double* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NP = sizeof(T) == 4 ? 2 : 1;   // hi, lo parts (FP32) or the FP64 values
+  T* st2 = reinterpret_cast<T*>(smem_raw);     // [NP][k][R]
+  for (int e = threadIdx.x; e < NP * k * R; e += blockDim.x) st2[e] = static_cast<const T*>(t2)[e];
+  __syncthreads();
+  const int lane = threadIdx.x % 32;
+  if (lane >= R) return;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; i < n; i += (int64_t)gridDim.x * 8) {
+    const T* brow = B + i * k;
+    double bt;
+    if constexpr (sizeof(T) == 4) {
+      float s = 0.0f, c = 0.0f, sl = 0.0f;
+      const float* th = st2;
+      const float* tl = st2 + k * R;
+      for (int j = 0; j < k; ++j) {
+        const float b = __ldg(brow + j);
+        dot2_add(s, c, b, th[j * R + lane]);
+        sl = __fmaf_rn(b, tl[j * R + lane], sl);
+      }
+      bt = (double)s + (double)c + (double)sl;
+    } else {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s = fma(__ldg(brow + j), st2[j * R + lane], s);
+      bt = s;
+    }
+    Y[i * R + lane] = inv_s2 * (X[i * R + lane] - bt);
+  }
+}
+
+}  // namespace
+
+void precond_free(Precond* pc) {
+  if (!pc) return;
+  cudaFree(pc->B);
+  cudaFree(pc->Ginv);
+  cudaFree(pc->partial);
+  cudaFree(pc->t1);
+  cudaFree(pc->t2);
+  cudaFree(pc->xsplit);
+  *pc = Precond();
+}
+
+// Caller-order coordinates of every window (freed with the object).
+template <typename T>
+struct CallerPoints {
+  std::vector<T*> xo;
+  std::vector<WinPts<T>> wp;
+  cudaStream_t st = nullptr;
+  ~CallerPoints() {
+    for (T* p : xo)
+      if (p) cudaFreeAsync(p, st);
+  }
+};
+
+template <typename T>
+agp_status caller_points(agp_plan_s* pl, CallerPoints<T>& cp, cudaStream_t st) {
+  const int64_t n = pl->n;
+  cp.st = st;
+  cp.xo.assign(pl->P, nullptr);
+  cp.wp.resize(pl->P);
+  for (int s = 0; s < pl->P; ++s) {
+    const Window& w = pl->win[s];
+    AGP_CUDA(cudaMallocAsync(&cp.xo[s], sizeof(T) * n * w.d, st));
+    k_unsort<T><<<nblk(n * w.d, 256), 256, 0, st>>>(reinterpret_cast<const T*>(w.xs), w.perm, n,
+                                                    w.d, cp.xo[s]);
+    cp.wp[s] = WinPts<T>{cp.xo[s], w.d};
+  }
+  return cuda_status(cudaGetLastError(), "caller_points");
+}
+
+// Landmarks: ceil(k_req / P) per window by farthest point sampling, merged
+// into a sorted set without repeats (host vector).
+template <typename T>
+agp_status select_landmarks(agp_plan_s* pl, const CallerPoints<T>& cp, int k_req,
+                            std::vector<int32_t>& all, cudaStream_t st) {
+  const int64_t n = pl->n;
+  const int P = pl->P;
+  const int kw = std::max(1, (int)std::min<int64_t>(n, (k_req + P - 1) / P));
+  unsigned long long* keys = nullptr;
+  double* dist = nullptr;
+  AGP_CUDA(cudaMallocAsync(&keys, sizeof(unsigned long long) * kw, st));
+  AGP_CUDA(cudaMallocAsync(&dist, sizeof(double) * n, st));
+  all.clear();
+  for (int s = 0; s < P; ++s) {
+    AGP_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * kw, st));
+    k_fill_double<<<nblk(n, 256), 256, 0, st>>>(dist, n, INFINITY);
+    const unsigned blocks = (unsigned)std::min<int64_t>(nblk(n, 256), 1024);
+    for (int step = 1; step < kw; ++step)
+      k_fps_step<T><<<blocks, 256, 0, st>>>(cp.xo[s], n, pl->win[s].d, step, keys, dist);
+    std::vector<unsigned long long> hk(kw);
+    AGP_CUDA(cudaMemcpyAsync(hk.data(), keys, sizeof(unsigned long long) * kw, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    all.push_back(0);
+    for (int step = 1; step < kw; ++step) all.push_back((int32_t)(0xFFFFFFFFull - (hk[step] & 0xFFFFFFFFull)));
+  }
+  cudaFreeAsync(keys, st);
+  cudaFreeAsync(dist, st);
+  std::sort(all.begin(), all.end());
+  all.erase(std::unique(all.begin(), all.end()), all.end());
+  return AGP_OK;
+}
+
+template <typename T>
+agp_status precond_build(agp_plan_s* pl, int k_req, int rmax, Precond* pc, cudaStream_t st) {
+  const int64_t n = pl->n;
+  const int P = pl->P;
+  if (!(pl->sigma_eps > 0)) return set_error(AGP_EINVAL, "the preconditioner needs sigma_eps > 0");
+  CallerPoints<T> cp;
+  AGP_TRY(caller_points<T>(pl, cp, st));
+  std::vector<int32_t> all;
+  AGP_TRY(select_landmarks<T>(pl, cp, k_req, all, st));
+  const std::vector<WinPts<T>>& wp = cp.wp;
+  const int k = (int)all.size();
+  if (k > kMaxLandmarkSet)
+    return set_error(AGP_EINVAL, "preconditioner: more than 512 landmarks after merging windows");
+  int32_t* lm = nullptr;
+  WinPts<T>* wpd = nullptr;
+  AGP_CUDA(cudaMallocAsync(&lm, sizeof(int32_t) * k, st));
+  AGP_CUDA(cudaMallocAsync(&wpd, sizeof(WinPts<T>) * P, st));
+  AGP_CUDA(cudaMemcpyAsync(lm, all.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
+  AGP_CUDA(cudaMemcpyAsync(wpd, wp.data(), sizeof(WinPts<T>) * P, cudaMemcpyHostToDevice, st));
+  // B = K_{:,L}
+  pc->k = k;
+  pc->n = n;
+  pc->rmax = rmax;
+  pc->inv_s2 = 1.0 / (pl->sigma_eps * pl->sigma_eps);
+  AGP_CUDA(cudaMalloc(&pc->B, sizeof(T) * n * k));
+  k_kernel_cols<T><<<nblk(n * k, 256), 256, 0, st>>>(wpd, P, n, lm, k, pl->kernel, pl->ell,
+                                                     pl->sigma_f * pl->sigma_f, (T*)pc->B);
+  // G = sigma_eps^2 K_LL + B^T B, then Ginv by Cholesky
+  double *G = nullptr, *Li = nullptr;
+  int* flag = nullptr;
+  AGP_CUDA(cudaMallocAsync(&G, sizeof(double) * k * k, st));
+  AGP_CUDA(cudaMallocAsync(&Li, sizeof(double) * k * k, st));
+  AGP_CUDA(cudaMallocAsync(&flag, sizeof(int), st));
+  AGP_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  k_gram_init<T><<<nblk((int64_t)k * k, 256), 256, 0, st>>>((const T*)pc->B, lm, k,
+                                                           pl->sigma_eps * pl->sigma_eps, G);
+  const int64_t slices = std::min<int64_t>(64, (n + 4095) / 4096);
+  const int64_t rps = (n + slices - 1) / slices;
+  k_gram<T><<<dim3((k + 31) / 32, (k + 31) / 32, (unsigned)slices), 1024, 0, st>>>((const T*)pc->B,
+                                                                                   n, k, rps, G);
+  k_cholesky<<<1, 1024, 0, st>>>(G, k, flag);
+  k_tri_inverse<<<nblk(k, 128), 128, 0, st>>>(G, k, Li);
+  AGP_CUDA(cudaMalloc(&pc->Ginv, sizeof(double) * k * k));
+  k_gram_inverse<<<nblk((int64_t)k * k, 256), 256, 0, st>>>(Li, k, pc->Ginv);
+  AGP_CUDA(cudaGetLastError());
+  int hflag = 0;
+  AGP_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  cudaFreeAsync(G, st);
+  cudaFreeAsync(Li, st);
+  cudaFreeAsync(flag, st);
+  cudaFreeAsync(lm, st);
+  cudaFreeAsync(wpd, st);
+  if (hflag) return set_error(AGP_ENAN, "preconditioner: non-positive pivot in the Cholesky factor");
+  // apply workspace
+  pc->slices = (int)std::min<int64_t>(256, (n + 2047) / 2048);
+  pc->rows_per_slice = (n + pc->slices - 1) / pc->slices;
+  AGP_CUDA(cudaMalloc(&pc->partial, sizeof(double) * pc->slices * k * rmax));
+  AGP_CUDA(cudaMalloc(&pc->t1, sizeof(double) * k * rmax));
+  AGP_CUDA(cudaMalloc(&pc->t2, sizeof(T) * k * rmax * (sizeof(T) == 4 ? 2 : 1)));
+  if (sizeof(T) == 4) AGP_CUDA(cudaMalloc(&pc->xsplit, sizeof(float) * 2 * n * rmax));
+  return AGP_OK;
+}
+
+template <typename T>
+agp_status precond_apply(const Precond& pc, const double* X, double* Y, int R, cudaStream_t st) {
+  if (R > pc.rmax || R > 32) return set_error(AGP_EINVAL, "preconditioner: too many columns");
+  const int k = pc.k;
+  const float *xh = nullptr, *xl = nullptr;
+  if (sizeof(T) == 4) {
+    float* h = pc.xsplit;
+    float* l = pc.xsplit + pc.n * R;
+    k_split<<<nblk(pc.n * R, 256), 256, 0, st>>>(X, pc.n * R, h, l);
+    xh = h;
+    xl = l;
+  }
+  k_pc_bt<T><<<dim3((k + 31) / 32, pc.slices), 256, 0, st>>>((const T*)pc.B, X, xh, xl, pc.n, k, R,
+                                                             pc.rows_per_slice, pc.partial);
+  k_pc_mid<T><<<nblk((int64_t)k * R, 128), 128, 0, st>>>(pc.partial, pc.slices, pc.Ginv, k, R, 0,
+                                                         pc.t1, pc.t2);
+  k_pc_mid<T><<<nblk((int64_t)k * R, 128), 128, 0, st>>>(pc.partial, pc.slices, pc.Ginv, k, R, 1,
+                                                         pc.t1, pc.t2);
+  constexpr int NP = sizeof(T) == 4 ? 2 : 1;
+  const size_t smem = sizeof(T) * NP * (size_t)k * R;
+  AGP_CUDA(cudaFuncSetAttribute(k_pc_out<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(T) * NP * kMaxLandmarkSet * 32)));
+  const unsigned blocks = (unsigned)std::min<int64_t>(nblk(pc.n, 8), 152 * 8);
+  k_pc_out<T><<<blocks, 256, smem, st>>>((const T*)pc.B, X, pc.t2, pc.n, k, R, pc.inv_s2, Y);
+  return cuda_status(cudaGetLastError(), "precond_apply");
+}
+
+template <typename T>
+agp_status precond_landmarks(agp_plan_s* pl, int k, std::vector<int32_t>& out, cudaStream_t st) {
+  CallerPoints<T> cp;
+  AGP_TRY(caller_points<T>(pl, cp, st));
+  return select_landmarks<T>(pl, cp, k, out, st);
+}
+
+template agp_status precond_landmarks<float>(agp_plan_s*, int, std::vector<int32_t>&, cudaStream_t);
+template agp_status precond_landmarks<double>(agp_plan_s*, int, std::vector<int32_t>&, cudaStream_t);
+template agp_status precond_build<float>(agp_plan_s*, int, int, Precond*, cudaStream_t);
+template agp_status precond_build<double>(agp_plan_s*, int, int, Precond*, cudaStream_t);
+template agp_status precond_apply<float>(const Precond&, const double*, double*, int, cudaStream_t);
+template agp_status precond_apply<double>(const Precond&, const double*, double*, int, cudaStream_t);
+
+}  // namespace agp

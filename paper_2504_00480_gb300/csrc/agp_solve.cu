@@ -88,6 +88,9 @@ struct CgState {
   double* tol;      // per-column relative residual tolerance (0: run to maxit)
   double* ahist;    // [maxit_all][R]
   double* bhist;
+  double* rz;       // r^T M^{-1} r (preconditioned runs)
+  double* rznew;
+  int pc;           // 1: preconditioned recursion
 };
 
 __global__ void k_cg_start(CgState s, int R) {
@@ -110,7 +113,7 @@ __global__ void k_cg_alpha(CgState s, int R) {
   if (s.active[c]) {
     const double pq = s.pq[c];
     if (pq != 0.0 && isfinite(pq)) {
-      a = s.rr[c] / pq;
+      a = (s.pc ? s.rz[c] : s.rr[c]) / pq;
     } else {
       s.active[c] = 0;
     }
@@ -138,7 +141,12 @@ __global__ void k_cg_beta(CgState s, const double* __restrict__ rr_new, int it, 
   double b = 0.0;
   if (s.active[c]) {
     const double rn = rr_new[c];
-    b = rn / s.rr[c];
+    if (s.pc) {
+      b = s.rznew[c] / s.rz[c];
+      s.rz[c] = s.rznew[c];
+    } else {
+      b = rn / s.rr[c];
+    }
     s.ahist[(int64_t)it * R + c] = s.alpha[c];
     s.bhist[(int64_t)it * R + c] = b;
     s.iters[c] = it + 1;
@@ -252,24 +260,17 @@ k_slq_logdet(const double* __restrict__ ahist, const double* __restrict__ bhist,
 // copy of p in the plan precision, and writes q in the plan precision.
 template <typename T>
 struct Workspace {
-  double *x = nullptr, *r = nullptr, *p = nullptr;
+  double *x = nullptr, *r = nullptr, *p = nullptr, *z = nullptr;
   T *pt = nullptr, *q = nullptr;
   double* partial = nullptr;
-  double* scal = nullptr;   // 8 x R doubles
+  double* scal = nullptr;   // 11 x R doubles
   int* iscal = nullptr;     // 3 x R ints
   double *ahist = nullptr, *bhist = nullptr;
   cudaStream_t st;
   ~Workspace() {
-    cudaFreeAsync(x, st);
-    cudaFreeAsync(r, st);
-    cudaFreeAsync(p, st);
-    cudaFreeAsync(pt, st);
-    cudaFreeAsync(q, st);
-    cudaFreeAsync(partial, st);
-    cudaFreeAsync(scal, st);
-    cudaFreeAsync(iscal, st);
-    cudaFreeAsync(ahist, st);
-    cudaFreeAsync(bhist, st);
+    void* bufs[] = {x, z, r, p, pt, q, partial, scal, iscal, ahist, bhist};
+    for (void* b : bufs)
+      if (b) cudaFreeAsync(b, st);
   }
 };
 
@@ -330,10 +331,13 @@ agp_status col_dot(const TA* A, int64_t lda, const TB* B, int64_t ldb, int64_t n
 // tolerances come from maxit_h / tol_h. On return ws holds the alpha/beta
 // history and the per-column state (scal layout: rr, bn2, pq, alpha, beta,
 // relres, rrnew, spare; iscal: active, iters, maxit).
+// With pc != nullptr the recursion is preconditioned CG: z = M^{-1} r,
+// alpha = r^T z / p^T K p, beta = r_new^T z_new / r^T z, p = z + beta p; the
+// stopping test stays on the unpreconditioned relative residual.
 template <typename T>
 agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int R,
                   const std::vector<int>& maxit_h, const std::vector<double>& tol_h, int check_every,
-                  Workspace<T>& ws, cudaStream_t st) {
+                  Workspace<T>& ws, cudaStream_t st, const Precond* pc = nullptr) {
   const int64_t n = pl->n;
   int maxall = 0;
   for (int v : maxit_h) maxall = std::max(maxall, v);
@@ -343,8 +347,9 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   AGP_CUDA(cudaMallocAsync(&ws.p, sizeof(double) * n * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.pt, sizeof(T) * n * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.q, sizeof(T) * n * R, st));
+  if (pc) AGP_CUDA(cudaMallocAsync(&ws.z, sizeof(double) * n * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.partial, sizeof(double) * kMaxDotBlocks * R, st));
-  AGP_CUDA(cudaMallocAsync(&ws.scal, sizeof(double) * 9 * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.scal, sizeof(double) * 11 * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.iscal, sizeof(int) * 3 * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.ahist, sizeof(double) * std::max(1, maxall) * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.bhist, sizeof(double) * std::max(1, maxall) * R, st));
@@ -362,15 +367,26 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   s.maxit = ws.iscal + 2 * R;
   s.ahist = ws.ahist;
   s.bhist = ws.bhist;
+  s.rz = ws.scal + 9 * R;
+  s.rznew = ws.scal + 10 * R;
+  s.pc = pc ? 1 : 0;
   AGP_CUDA(cudaMemcpyAsync(s.maxit, maxit_h.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
   AGP_CUDA(cudaMemcpyAsync(s.tol, tol_h.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
 
   const unsigned gb = nblk(n * R, 256), gc = nblk(R, 128);
   k_zero_block<double><<<gb, 256, 0, st>>>(ws.x, R, n, R);
   k_copy_block<T, double><<<gb, 256, 0, st>>>(B, ldb, ws.r, R, n, R);
-  k_copy_block<T, double><<<gb, 256, 0, st>>>(B, ldb, ws.p, R, n, R);
-  k_copy_block<T, T><<<gb, 256, 0, st>>>(B, ldb, ws.pt, R, n, R);
-  pl->launches[3] += 4;
+  pl->launches[3] += 2;
+  if (pc) {   // p = z = M^{-1} r, rz = r^T z
+    AGP_TRY(precond_apply<T>(*pc, ws.r, ws.z, R, st));
+    k_copy_block<double, double><<<gb, 256, 0, st>>>(ws.z, R, ws.p, R, n, R);
+    k_copy_block<double, T><<<gb, 256, 0, st>>>(ws.z, R, ws.pt, R, n, R);
+    AGP_TRY(col_dot(ws.r, R, ws.z, R, n, R, ws.partial, s.rz, st, pl));
+  } else {
+    k_copy_block<T, double><<<gb, 256, 0, st>>>(B, ldb, ws.p, R, n, R);
+    k_copy_block<T, T><<<gb, 256, 0, st>>>(B, ldb, ws.pt, R, n, R);
+  }
+  pl->launches[3] += 2;
   AGP_TRY(col_dot(ws.r, R, ws.r, R, n, R, ws.partial, s.rr, st, pl));
   k_cg_start<<<gc, 128, 0, st>>>(s, R);
   pl->launches[3] += 1;
@@ -382,8 +398,12 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
     k_cg_xr<T><<<gb, 256, 0, st>>>(ws.x, ws.r, ws.p, ws.q, s.alpha, n, R);
     pl->launches[3] += 2;
     AGP_TRY(col_dot(ws.r, R, ws.r, R, n, R, ws.partial, rrnew, st, pl));
+    if (pc) {
+      AGP_TRY(precond_apply<T>(*pc, ws.r, ws.z, R, st));
+      AGP_TRY(col_dot(ws.r, R, ws.z, R, n, R, ws.partial, s.rznew, st, pl));
+    }
     k_cg_beta<<<gc, 128, 0, st>>>(s, rrnew, it, R);
-    k_cg_p<T><<<gb, 256, 0, st>>>(ws.p, ws.pt, ws.r, s.beta, s.active, n, R);
+    k_cg_p<T><<<gb, 256, 0, st>>>(ws.p, ws.pt, pc ? ws.z : ws.r, s.beta, s.active, n, R);
     pl->launches[3] += 2;
     AGP_CUDA(cudaGetLastError());
     if (check_every > 0 && ((it + 1) % check_every == 0) && it + 1 < maxall) {
@@ -401,11 +421,17 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
 
 template <typename T>
 agp_status pcg_t(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int R, double rtol,
-                 int maxit, int* iters, double* relres, cudaStream_t st) {
+                 int maxit, int n_landmarks, int* iters, double* relres, cudaStream_t st) {
+  Precond pc;
+  struct Release {
+    Precond* p;
+    ~Release() { precond_free(p); }
+  } release{&pc};
+  if (n_landmarks > 0) AGP_TRY(precond_build<T>(pl, n_landmarks, R, &pc, st));
   Workspace<T> ws;
   std::vector<int> mi(R, maxit);
   std::vector<double> tl(R, rtol);
-  AGP_TRY(cg_run<T>(pl, B, ldb, X, ldx, R, mi, tl, 5, ws, st));
+  AGP_TRY(cg_run<T>(pl, B, ldb, X, ldx, R, mi, tl, 5, ws, st, n_landmarks > 0 ? &pc : nullptr));
   std::vector<int> it(R);
   std::vector<double> rel(R);
   AGP_CUDA(cudaMemcpyAsync(it.data(), ws.iscal + R, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
@@ -509,12 +535,30 @@ agp_status agp_pcg_solve(agp_plan pl, const void* B, int64_t ldb, void* Xsol, in
                          void* stream) {
   if (!pl || !B || !Xsol || R < 1 || ldb < R || ldx < R || maxit < 0 || !(rtol >= 0))
     return set_error(AGP_EINVAL, "bad arguments");
-  if (n_landmarks != 0) return set_error(AGP_EINVAL, "preconditioning is not available");
+  if (n_landmarks < 0 || n_landmarks > kMaxLandmarks || (n_landmarks > 0 && R > 32))
+    return set_error(AGP_EINVAL, "n_landmarks must be in [0, 480] (and R <= 32 when > 0)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (pl->prec == AGP_F32)
-    return pcg_t<float>(pl, (const float*)B, ldb, (float*)Xsol, ldx, R, rtol, maxit, iters, relres, st);
-  return pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, iters, relres,
-                       st);
+    return pcg_t<float>(pl, (const float*)B, ldb, (float*)Xsol, ldx, R, rtol, maxit, n_landmarks,
+                        iters, relres, st);
+  return pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, n_landmarks,
+                       iters, relres, st);
+}
+
+agp_status agp_plan_landmarks(agp_plan pl, int n_landmarks, int32_t* idx, int cap, int* count,
+                              void* stream) {
+  if (!pl || !count || n_landmarks < 1 || n_landmarks > kMaxLandmarks || cap < 0 ||
+      (cap > 0 && !idx))
+    return set_error(AGP_EINVAL, "bad arguments (n_landmarks must be in [1, 480])");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<int32_t> L;
+  const agp_status s = pl->prec == AGP_F32 ? precond_landmarks<float>(pl, n_landmarks, L, st)
+                                           : precond_landmarks<double>(pl, n_landmarks, L, st);
+  if (s != AGP_OK) return s;
+  *count = (int)L.size();
+  if ((int)L.size() > cap) return set_error(AGP_EINVAL, "idx holds fewer entries than the landmark set");
+  std::copy(L.begin(), L.end(), idx);
+  return AGP_OK;
 }
 
 agp_status agp_dot_columns(agp_plan pl, const void* A, int64_t lda, const void* B, int64_t ldb,

@@ -190,7 +190,7 @@ def test_batched_pcg_workload_subset_matern(agp, R):
     check_matvec(agp, w, torch.float32, R=R)
 
 
-@pytest.mark.parametrize("R", [17, 32, 40])
+@pytest.mark.parametrize("R", [12, 17, 24, 32, 40])
 def test_nlml_workload_subset_mixed_d(agp, R):
     w = inputs.subset(inputs.nlml_grad(n=3000, R=40), 3000)
     check_matvec(agp, w, torch.float32, R=R)
