@@ -54,6 +54,8 @@ __all__ = [
     "cg", "pcg", "farthest_point_sampling", "additive_landmarks", "nystrom_preconditioner",
     "lanczos_tridiag_from_cg", "slq_quadratic",
     "nlml_exact", "nlml_estimate",
+    "nystrom_blocks", "nystrom_matrix", "nystrom_logdet", "nystrom_probes", "pcg_lanczos",
+    "nystrom_dM_quadratic", "nystrom_trace_Minv_dM", "nlml_estimate_preconditioned",
 ]
 
 TWO_PI = 2.0 * math.pi
@@ -647,3 +649,157 @@ def nlml_estimate(apply_K, apply_dK, y, Z, lanczos_steps, rtol=1e-10, maxit=None
         tr = float(np.sum(U * dz)) / nz
         grads[th] = 0.5 * (-(alpha @ da) + tr)
     return nlml, grads
+
+
+# ---------------------------------------------------------------------------
+# Preconditioned NLML estimate with the landmark (Nystrom) preconditioner
+# (Sec. 1 eqs. (1.3)-(1.5); M from the (1,1) block of Sec. 2.3)
+# ---------------------------------------------------------------------------
+
+def nystrom_blocks(X, windows, kind, ell, sigma_f, landmarks, which=None):
+    """B = K_{:,L}, the columns of sigma_f^2 sum_s K_s (exact kernel, Sec. 2.1)
+    at the landmarks L, and K_LL = B[L, :]. With which = "ell" or "sigma_f"
+    the derivative of B with respect to that hyperparameter (sigma_eps does
+    not enter B)."""
+    n = X.shape[0]
+    L = list(landmarks)
+    E = np.zeros((n, len(L)))
+    E[L, np.arange(len(L))] = 1.0
+    if which is None:
+        B = dense_matvec(X, windows, kind, ell, sigma_f, 0.0, E, add_noise=False)
+    else:
+        B = dense_deriv_matvec(X, windows, kind, ell, sigma_f, 0.0, E, which)
+    return B, B[L, :]
+
+
+def nystrom_matrix(B, KLL, s2):
+    """M = B K_LL^{-1} B^T + s2 I as an explicit n x n array."""
+    M = B @ np.linalg.solve(KLL, B.T) + s2 * np.eye(B.shape[0])
+    return 0.5 * (M + M.T)
+
+
+def nystrom_logdet(B, KLL, s2):
+    """log det M for M = B K_LL^{-1} B^T + s2 I by the matrix determinant
+    lemma: (n - k) log s2 + log det(s2 K_LL + B^T B) - log det K_LL."""
+    n, k = B.shape
+    _, ld_g = np.linalg.slogdet(s2 * KLL + B.T @ B)
+    _, ld_k = np.linalg.slogdet(KLL)
+    return (n - k) * math.log(s2) + ld_g - ld_k
+
+
+def nystrom_probes(B, KLL, sigma_eps, Wn, Wk):
+    """Probes with covariance M: z_i = sigma_eps Wn[:, i] + B C^{-T} Wk[:, i],
+    C the lower Cholesky factor of K_LL, for given vectors w_i = [Wn; Wk][:, i]
+    (n + k entries, E[w w^T] = I): cov(z) = sigma_eps^2 I + B K_LL^{-1} B^T."""
+    C = np.linalg.cholesky(KLL)
+    T = np.linalg.solve(C.T, np.asarray(Wk, dtype=np.float64))
+    return sigma_eps * np.asarray(Wn, dtype=np.float64) + B @ T
+
+
+def pcg_lanczos(apply_A, apply_Minv, B, steps):
+    """PCG with zero initial guess and exactly ``steps`` steps per column,
+    recording the alpha and beta sequences (which give the Lanczos matrix of
+    M^{-1/2} A M^{-1/2} started at M^{-1/2} b, by the same CG-Lanczos relation
+    as in lanczos_tridiag_from_cg) and r_0^T M^{-1} r_0 = b^T M^{-1} b.
+    Returns X, alphas, betas, rz0."""
+    B = np.asarray(B, dtype=np.float64)
+    n, R = B.shape
+    X = np.zeros_like(B)
+    alphas, betas, rz0 = [[] for _ in range(R)], [[] for _ in range(R)], np.zeros(R)
+    for c in range(R):
+        x = np.zeros(n)
+        r = B[:, c].copy()
+        z = apply_Minv(r[:, None])[:, 0]
+        p = z.copy()
+        rz = r @ z
+        rz0[c] = rz
+        for _ in range(steps):
+            q = apply_A(p[:, None])[:, 0]
+            a = rz / (p @ q)
+            x = x + a * p
+            r = r - a * q
+            z = apply_Minv(r[:, None])[:, 0]
+            rz_new = r @ z
+            b = rz_new / rz
+            alphas[c].append(a)
+            betas[c].append(b)
+            p = z + b * p
+            rz = rz_new
+        X[:, c] = x
+    return X, alphas, betas, rz0
+
+
+def nystrom_dM_quadratic(B, KLL, dB, dKLL, P):
+    """p_i^T (dM/dtheta) p_i for the columns p_i of P, theta in {ell,
+    sigma_f}: dM = dB K^{-1} B^T + B K^{-1} dB^T - B K^{-1} dK_LL K^{-1} B^T
+    (K = K_LL), so p^T dM p = 2 a^T K^{-1} e - a^T K^{-1} dK_LL K^{-1} a with
+    a = B^T p, e = dB^T p."""
+    A = B.T @ P
+    Ed = dB.T @ P
+    KiA = np.linalg.solve(KLL, A)
+    return 2.0 * np.sum(KiA * Ed, axis=0) - np.sum(KiA * (dKLL @ KiA), axis=0)
+
+
+def nystrom_trace_Minv_dM(B, KLL, dB, dKLL, s2):
+    """tr(M^{-1} dM/dtheta) for theta in {ell, sigma_f} (dense: the oracle)."""
+    M = nystrom_matrix(B, KLL, s2)
+    dM = dB @ np.linalg.solve(KLL, B.T)
+    dM = dM + dM.T - B @ np.linalg.solve(KLL, dKLL) @ np.linalg.solve(KLL, B.T)
+    return float(np.trace(np.linalg.solve(M, dM)))
+
+
+def nlml_estimate_preconditioned(apply_K, apply_dK, y, Wn, Wk, lanczos_steps, B, KLL, dB,
+                                 landmarks, sigma_eps, rtol=1e-10, maxit=None):
+    """Estimate of the NLML and its gradient with the landmark preconditioner
+    M = B K_LL^{-1} B^T + sigma_eps^2 I (Sec. 2.3).
+
+    Sec. 1 eq. (1.4): Z~ = 1/2 (y^T alpha + log det M + (1/n_z) sum_i q_i +
+    n log 2 pi), log det M exact (eq. (1.3)), q_i the SLQ estimate of
+    z~_i^T logm(M^{-1/2} K_hat M^{-1/2}) z~_i from ``lanczos_steps`` PCG steps on
+    K_hat x = z_i, with z~_i = M^{-1/2} z_i (|z~_i|^2 = z_i^T M^{-1} z_i). The
+    probes z_i = sigma_eps wn_i + B C^{-T} wk_i have covariance M, so the z~_i
+    have covariance I and the mean of the q_i estimates tr(Delta log).
+
+    Eq. (1.5): dZ~/dtheta = 1/2 (-alpha^T dK alpha + tr(M^{-1} dM) + (1/n_z)
+    sum_i s_i), s_i = u_i^T dK p_i - p_i^T dM p_i with u_i = K_hat^{-1} z_i
+    (the PCG iterate) and p_i = M^{-1} z_i: for cov(z) = M its mean is
+    tr(K_hat^{-1} dK) - tr(M^{-1} dM), the trace of (M^{-1}K_hat)^{-1}
+    d(M^{-1} K_hat). dB: {"ell": dB/dell, "sigma_f": dB/dsigma_f} (from
+    nystrom_blocks), landmarks: the rows L of B; for sigma_eps, dM = 2 sigma_eps I.
+    alpha solves K_hat alpha = y by PCG to ``rtol``. Returns (nlml, {theta: grad})."""
+    y = np.asarray(y, dtype=np.float64).reshape(-1)
+    n = y.shape[0]
+    s2 = sigma_eps ** 2
+    M = nystrom_matrix(B, KLL, s2)
+
+    def Minv(P):
+        return np.linalg.solve(M, P)
+
+    alpha, _, _ = pcg(apply_K, Minv, y[:, None], rtol=rtol,
+                      maxit=maxit if maxit is not None else 10 * n)
+    alpha = alpha[:, 0]
+    Z = nystrom_probes(B, KLL, sigma_eps, Wn, Wk)
+    U, al, be, rz0 = pcg_lanczos(apply_K, Minv, Z, lanczos_steps)
+    nz = Z.shape[1]
+    quad = 0.0
+    for i in range(nz):
+        quad += slq_quadratic(lanczos_tridiag_from_cg(al[i], be[i]), float(rz0[i]))
+    logdet = nystrom_logdet(B, KLL, s2) + quad / nz
+    nlml = 0.5 * (y @ alpha + logdet + n * math.log(TWO_PI))
+    P = Minv(Z)
+    L = list(landmarks)
+    grads = {}
+    for th, f in apply_dK.items():
+        da = f(alpha[:, None])[:, 0]
+        dz = f(P)
+        if th == "sigma_eps":
+            tr_m = 2.0 * sigma_eps * float(np.trace(np.linalg.inv(M)))
+            pdp = 2.0 * sigma_eps * np.sum(P * P, axis=0)
+        else:
+            dKLL = dB[th][L]
+            tr_m = nystrom_trace_Minv_dM(B, KLL, dB[th], dKLL, s2)
+            pdp = nystrom_dM_quadratic(B, KLL, dB[th], dKLL, P)
+        s = np.sum(U * dz, axis=0) - pdp
+        grads[th] = 0.5 * (-(alpha @ da) + tr_m + float(np.mean(s)))
+    return nlml, grads
+

@@ -139,3 +139,96 @@ def test_nlml_estimate_exact_with_orthogonal_probes(kind):
     for w in ["ell", "sigma_f", "sigma_eps"]:
         fd = (Zexact(**{w: th[w] + h}) - Zexact(**{w: th[w] - h})) / (2 * h)
         assert g[w] == pytest.approx(fd, rel=1e-5, abs=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# preconditioned estimator (Sec. 1 eqs. (1.3)-(1.5) with the landmark M)
+# ---------------------------------------------------------------------------
+def _nystrom_problem(n=12, k_total=4, kind="matern12", seed=60):
+    X, W, th, rng = _problem(n, seed)
+    L = O.additive_landmarks(X, W, k_total)
+    return X, W, th, rng, L
+
+
+@pytest.mark.parametrize("kind", ["gauss", "matern12"])
+def test_nystrom_logdet_matches_dense(kind):
+    X, W, th, _, L = _nystrom_problem(kind=kind)
+    B, KLL = O.nystrom_blocks(X, W, kind, th["ell"], th["sigma_f"], L)
+    s2 = th["sigma_eps"] ** 2
+    _, want = np.linalg.slogdet(O.nystrom_matrix(B, KLL, s2))
+    assert O.nystrom_logdet(B, KLL, s2) == pytest.approx(want, rel=1e-11)
+
+
+def test_nystrom_probes_have_covariance_M():
+    # with w_i = sqrt(n+k) q_i over an orthogonal basis of R^{n+k}, the mean
+    # of z_i z_i^T is F F^T = M exactly
+    X, W, th, rng, L = _nystrom_problem()
+    B, KLL = O.nystrom_blocks(X, W, "matern12", th["ell"], th["sigma_f"], L)
+    n, k = B.shape
+    Q, _ = np.linalg.qr(rng.standard_normal((n + k, n + k)))
+    Wf = math.sqrt(n + k) * Q
+    Z = O.nystrom_probes(B, KLL, th["sigma_eps"], Wf[:n], Wf[n:])
+    M = O.nystrom_matrix(B, KLL, th["sigma_eps"] ** 2)
+    np.testing.assert_allclose(Z @ Z.T / (n + k), M, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("which", ["ell", "sigma_f"])
+def test_nystrom_dM_terms_match_finite_differences(which):
+    # tr(M^{-1} dM) = d/dtheta log det M and p^T dM p = d/dtheta p^T M p,
+    # each against central differences of M(theta) built from scratch
+    X, W, th, rng, L = _nystrom_problem(kind="gauss")
+    s2 = th["sigma_eps"] ** 2
+    B, KLL = O.nystrom_blocks(X, W, "gauss", th["ell"], th["sigma_f"], L)
+    dB, _ = O.nystrom_blocks(X, W, "gauss", th["ell"], th["sigma_f"], L, which=which)
+    dKLL = dB[L]
+    h = 1e-5
+
+    def at(delta):
+        t = dict(th)
+        t[which] += delta
+        Bh, Kh = O.nystrom_blocks(X, W, "gauss", t["ell"], t["sigma_f"], L)
+        return O.nystrom_matrix(Bh, Kh, s2), O.nystrom_logdet(Bh, Kh, s2)
+
+    (Mp, lp), (Mm, lm) = at(h), at(-h)
+    assert O.nystrom_trace_Minv_dM(B, KLL, dB, dKLL, s2) == pytest.approx((lp - lm) / (2 * h),
+                                                                           rel=1e-6)
+    P = rng.standard_normal((X.shape[0], 3))
+    fd = np.sum(P * ((Mp - Mm) / (2 * h) @ P), axis=0)
+    np.testing.assert_allclose(O.nystrom_dM_quadratic(B, KLL, dB, dKLL, P), fd, rtol=1e-6)
+
+
+@pytest.mark.parametrize("kind", ["gauss", "matern12"])
+def test_nlml_preconditioned_exact_with_orthogonal_probes(kind):
+    # probes over a scaled orthogonal basis of R^{n+k} (so mean z z^T = M) and
+    # n-k+1 PCG steps (M^{-1} K_hat has eigenvalue 1 with multiplicity >= k,
+    # hence at most n-k+1 distinct eigenvalues) make the estimator exact: it
+    # must return scipy's NLML and its finite-difference gradient
+    n = 12
+    X, W, th, rng, L = _nystrom_problem(n, 4, kind)
+    k = len(L)
+    y = rng.standard_normal(n)
+    B, KLL = O.nystrom_blocks(X, W, kind, th["ell"], th["sigma_f"], L)
+    dB = {w: O.nystrom_blocks(X, W, kind, th["ell"], th["sigma_f"], L, which=w)[0]
+          for w in ["ell", "sigma_f"]}
+    Q, _ = np.linalg.qr(rng.standard_normal((n + k, n + k)))
+    Wf = math.sqrt(n + k) * Q
+
+    def Kmat(**kw):
+        t = dict(th, **kw)
+        return O.dense_matrix(X, W, kind, t["ell"], t["sigma_f"], t["sigma_eps"])
+
+    K = Kmat()
+    dK = {w: O.dense_matrix(X, W, kind, th["ell"], th["sigma_f"], th["sigma_eps"], which=w)
+          for w in ["ell", "sigma_f", "sigma_eps"]}
+    nl, g = O.nlml_estimate_preconditioned(
+        lambda P: K @ P, {w: (lambda P, M=M: M @ P) for w, M in dK.items()}, y, Wf[:n], Wf[n:],
+        n - k + 1, B, KLL, dB, L, th["sigma_eps"])
+
+    def Zexact(**kw):
+        return -scipy.stats.multivariate_normal(mean=np.zeros(n), cov=Kmat(**kw)).logpdf(y)
+
+    assert nl == pytest.approx(Zexact(), rel=1e-8)
+    h = 1e-6
+    for w in ["ell", "sigma_f", "sigma_eps"]:
+        fd = (Zexact(**{w: th[w] + h}) - Zexact(**{w: th[w] - h})) / (2 * h)
+        assert g[w] == pytest.approx(fd, rel=1e-5, abs=1e-7), w
