@@ -54,7 +54,7 @@ __all__ = [
     "cg", "pcg", "farthest_point_sampling", "additive_landmarks", "nystrom_preconditioner",
     "lanczos_tridiag_from_cg", "slq_quadratic",
     "nlml_exact", "nlml_estimate",
-    "nystrom_blocks", "nystrom_matrix", "nystrom_logdet", "nystrom_probes", "pcg_lanczos",
+    "landmark_jitter", "nystrom_blocks", "nystrom_matrix", "nystrom_logdet", "nystrom_probes", "pcg_lanczos",
     "nystrom_dM_quadratic", "nystrom_trace_Minv_dM", "nlml_estimate_preconditioned",
 ]
 
@@ -69,23 +69,30 @@ def kernel(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
     """Windowed sub-kernel kappa_s as a function of the distance r = |x - y|_2.
 
     Sec. 2.1, eq. (2.2): Gaussian exp(-r^2 / (2 ell^2)) and Matern(1/2)
-    exp(-r / ell); neither carries sigma_f (it multiplies the sum)."""
+    exp(-r / ell); the Matern(3/2) kernel of the remark in Sec. 4,
+    (1 + sqrt(3) r / l) exp(-sqrt(3) r / l) with l = sqrt(3) ell, i.e.
+    (1 + r / ell) exp(-r / ell). None carries sigma_f (it multiplies the sum)."""
     r = np.asarray(r, dtype=np.float64)
     if kind == "gauss":
         return np.exp(-(r * r) / (2.0 * ell * ell))
     if kind == "matern12":
         return np.exp(-r / ell)
+    if kind == "matern32":
+        return (1.0 + r / ell) * np.exp(-r / ell)
     raise ValueError(kind)
 
 
 def kernel_der_ell(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
     """Derivative of kappa_s with respect to ell, Sec. 2.1 eq. (2.3):
-    Gaussian r^2/ell^3 kappa^G, Matern(1/2) r/ell^2 kappa^M."""
+    Gaussian r^2/ell^3 kappa^G, Matern(1/2) r/ell^2 kappa^M; Matern(3/2):
+    d/dell (1 + r/ell) e^{-r/ell} = r^2/ell^3 e^{-r/ell}."""
     r = np.asarray(r, dtype=np.float64)
     if kind == "gauss":
         return (r * r) / ell ** 3 * kernel(kind, r, ell)
     if kind == "matern12":
         return r / ell ** 2 * kernel(kind, r, ell)
+    if kind == "matern32":
+        return (r * r) / ell ** 3 * np.exp(-r / ell)
     raise ValueError(kind)
 
 
@@ -573,15 +580,26 @@ def additive_landmarks(X, windows, k_total):
     return sorted(s)
 
 
-def nystrom_preconditioner(X, windows, kind, ell, sigma_f, sigma_eps, landmarks):
-    """M = K_{:,L} K_LL^{-1} K_{L,:} + sigma_eps^2 I with K = sigma_f^2 sum_s K_s
-    (the exact kernel of Sec. 2.1) and the landmark set L -- the (1,1)-block
-    Nystrom part of the additive AFN preconditioner (Sec. 2.3). Formed as a
-    dense n x n matrix; returns a function applying M^{-1}."""
+def landmark_jitter(sigma_f, P):
+    """delta added to the diagonal of K_LL: 1e-6 times the kernel's diagonal
+    value sigma_f^2 P. Not in the paper: it keeps K_LL and G = sigma_eps^2
+    K_LL + B^T B factorisable when more landmarks are requested than the
+    kernel's numerical rank (smooth kernels, large n). It is held fixed when
+    differentiating M."""
+    return 1e-6 * sigma_f ** 2 * P
+
+
+def nystrom_preconditioner(X, windows, kind, ell, sigma_f, sigma_eps, landmarks, jitter=None):
+    """M = K_{:,L} (K_LL + delta I)^{-1} K_{L,:} + sigma_eps^2 I with K =
+    sigma_f^2 sum_s K_s (the exact kernel of Sec. 2.1), the landmark set L and
+    delta = landmark_jitter unless given -- the (1,1)-block Nystrom part of the
+    additive AFN preconditioner (Sec. 2.3). Formed as a dense n x n matrix;
+    returns a function applying M^{-1}."""
     n = X.shape[0]
     L = list(landmarks)
     KnL = dense_matvec(X, windows, kind, ell, sigma_f, 0.0, np.eye(n)[:, L], add_noise=False)
-    KLL = KnL[L, :]
+    delta = landmark_jitter(sigma_f, len(windows)) if jitter is None else jitter
+    KLL = KnL[L, :] + delta * np.eye(len(L))
     M = KnL @ np.linalg.solve(KLL, KnL.T) + sigma_eps ** 2 * np.eye(n)
     M = 0.5 * (M + M.T)
     return lambda P: np.linalg.solve(M, P)
@@ -656,20 +674,22 @@ def nlml_estimate(apply_K, apply_dK, y, Z, lanczos_steps, rtol=1e-10, maxit=None
 # (Sec. 1 eqs. (1.3)-(1.5); M from the (1,1) block of Sec. 2.3)
 # ---------------------------------------------------------------------------
 
-def nystrom_blocks(X, windows, kind, ell, sigma_f, landmarks, which=None):
+def nystrom_blocks(X, windows, kind, ell, sigma_f, landmarks, which=None, jitter=None):
     """B = K_{:,L}, the columns of sigma_f^2 sum_s K_s (exact kernel, Sec. 2.1)
-    at the landmarks L, and K_LL = B[L, :]. With which = "ell" or "sigma_f"
-    the derivative of B with respect to that hyperparameter (sigma_eps does
-    not enter B)."""
+    at the landmarks L, and K_LL = B[L, :] + delta I (delta = landmark_jitter
+    unless given). With which = "ell" or "sigma_f" the derivative of B with
+    respect to that hyperparameter and its landmark rows (sigma_eps does not
+    enter B; delta is held fixed)."""
     n = X.shape[0]
     L = list(landmarks)
     E = np.zeros((n, len(L)))
     E[L, np.arange(len(L))] = 1.0
-    if which is None:
-        B = dense_matvec(X, windows, kind, ell, sigma_f, 0.0, E, add_noise=False)
-    else:
-        B = dense_deriv_matvec(X, windows, kind, ell, sigma_f, 0.0, E, which)
-    return B, B[L, :]
+    if which is not None:
+        dB = dense_deriv_matvec(X, windows, kind, ell, sigma_f, 0.0, E, which)
+        return dB, dB[L, :]
+    B = dense_matvec(X, windows, kind, ell, sigma_f, 0.0, E, add_noise=False)
+    delta = landmark_jitter(sigma_f, len(windows)) if jitter is None else jitter
+    return B, B[L, :] + delta * np.eye(len(L))
 
 
 def nystrom_matrix(B, KLL, s2):

@@ -11,7 +11,7 @@ import pytest
 import oracle as O
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-KINDS = ["gauss", "matern12"]
+KINDS = ["gauss", "matern12", "matern32"]
 
 
 def _read_golden(name):
@@ -185,3 +185,20 @@ def test_ndft_pair_single_point():
     C[1 + 4, -4 + 4, 0] = 1.0
     f = O.ndft(x, C, 8)
     assert f[0, 0] == pytest.approx(cmath.exp(2j * math.pi * (1 * 0.1 - 4 * -0.2)))
+
+
+def test_matern32_coeffs_equal_fourier_transform_3d():
+    # Small ell: the kernel has decayed at the cell boundary ((1 + 17) e^-17
+    # ~ 7e-7 at r = 1/2) and b_k approximates the continuous Fourier transform
+    # of the remark in Sec. 4 (d = 3, nu = 3/2, l = sqrt(3) ell):
+    #   kappa_hat(w) = 2^3 pi^{3/2} Gamma(3) 3^{3/2} / (Gamma(3/2) l^3)
+    #                  * (3 / l^2 + 4 pi^2 |w|^2)^{-3}.
+    N, ell = 64, 0.03
+    l = math.sqrt(3.0) * ell
+    b = O.fourier_coeffs("matern32", ell, N, 3)
+    c = 2 ** 3 * math.pi ** 1.5 * math.gamma(3) * 3 ** 1.5 / (math.gamma(1.5) * l ** 3)
+    for k in [(0, 0, 0), (1, 0, 0), (1, 2, 0), (3, 1, 2), (4, 4, 4)]:
+        w2 = sum(t * t for t in k)
+        want = c * (3.0 / l ** 2 + 4 * math.pi ** 2 * w2) ** -3
+        got = b[tuple(t + N // 2 for t in k)].real
+        assert got == pytest.approx(want, rel=2e-4), k

@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 
-KINDS = ["gauss", "matern12"]
+KINDS = ["gauss", "matern12", "matern32"]
 
 
 def test_kernel_textbook_values():
@@ -39,7 +39,13 @@ def _brute(X, windows, kind, ell, sf, se, v):
                 for f in w:
                     d2 += (X[i][f] - X[j][f]) ** 2
                 r = math.sqrt(d2)
-                k = math.exp(-d2 / (2 * ell * ell)) if kind == "gauss" else math.exp(-r / ell)
+                if kind == "gauss":
+                    k = math.exp(-d2 / (2 * ell * ell))
+                elif kind == "matern12":
+                    k = math.exp(-r / ell)
+                else:   # Matern(3/2) in the form of Sec. 4 with l = sqrt(3) ell
+                    l = math.sqrt(3.0) * ell
+                    k = (1 + math.sqrt(3.0) * r / l) * math.exp(-math.sqrt(3.0) * r / l)
                 acc += k * v[j]
         out[i] = sf * sf * acc + se * se * v[i]
     return np.array(out)
@@ -138,3 +144,14 @@ def test_dense_rows_subset():
     rows = [0, 17, 59]
     np.testing.assert_allclose(O.dense_matvec(X, [[0, 1, 2]], "gauss", 0.2, 1.0, 0.1, v,
                                               rows=rows), full[rows], rtol=1e-14)
+
+
+def test_matern32_textbook_values():
+    # (1 + sqrt(3) r / l) exp(-sqrt(3) r / l) with l = sqrt(3) ell (the remark
+    # of Sec. 4): at r = ell this is 2 / e.
+    assert O.kernel("matern32", 0.4, 0.4) == pytest.approx(2.0 / math.e, rel=1e-15)
+    assert O.kernel("matern32", 0.0, 0.3) == 1.0
+    l = math.sqrt(3.0) * 0.25
+    r = 0.6
+    assert O.kernel("matern32", r, 0.25) == pytest.approx(
+        (1 + math.sqrt(3.0) * r / l) * math.exp(-math.sqrt(3.0) * r / l), rel=1e-14)

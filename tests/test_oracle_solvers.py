@@ -71,7 +71,7 @@ def test_nystrom_with_all_points_is_exact():
     X, W, th, rng = _problem(30)
     K = O.dense_matrix(X, W, "matern12", th["ell"], th["sigma_f"], th["sigma_eps"])
     Minv = O.nystrom_preconditioner(X, W, "matern12", th["ell"], th["sigma_f"], th["sigma_eps"],
-                                    range(30))
+                                    range(30), jitter=0.0)
     B = rng.standard_normal((30, 2))
     np.testing.assert_allclose(Minv(B), np.linalg.solve(K, B), rtol=1e-6, atol=1e-8)
     Xs, it, _ = O.pcg(lambda P: K @ P, Minv, B, rtol=1e-8, maxit=5)
@@ -183,10 +183,12 @@ def test_nystrom_dM_terms_match_finite_differences(which):
     dKLL = dB[L]
     h = 1e-5
 
+    jit = O.landmark_jitter(th["sigma_f"], len(W))   # held fixed, as in dM
+
     def at(delta):
         t = dict(th)
         t[which] += delta
-        Bh, Kh = O.nystrom_blocks(X, W, "gauss", t["ell"], t["sigma_f"], L)
+        Bh, Kh = O.nystrom_blocks(X, W, "gauss", t["ell"], t["sigma_f"], L, jitter=jit)
         return O.nystrom_matrix(Bh, Kh, s2), O.nystrom_logdet(Bh, Kh, s2)
 
     (Mp, lp), (Mm, lm) = at(h), at(-h)
