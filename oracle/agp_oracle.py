@@ -580,13 +580,23 @@ def additive_landmarks(X, windows, k_total):
     return sorted(s)
 
 
-def landmark_jitter(sigma_f, P):
-    """delta added to the diagonal of K_LL: 1e-6 times the kernel's diagonal
-    value sigma_f^2 P. Not in the paper: it keeps K_LL and G = sigma_eps^2
-    K_LL + B^T B factorisable when more landmarks are requested than the
-    kernel's numerical rank (smooth kernels, large n). It is held fixed when
-    differentiating M."""
-    return 1e-6 * sigma_f ** 2 * P
+def landmark_jitter(B, KLL0, sigma_f, P, sigma_eps):
+    """delta added to the diagonal of K_LL (not in the paper): 1e-6 sigma_f^2 P
+    (1e-6 of the kernel's diagonal value), grown 100-fold, at most four
+    times, while the Cholesky factorisation of G = sigma_eps^2 (K_LL + delta I)
+    + B^T B fails in FP64 -- when more landmarks are requested than the
+    kernel's numerical rank the landmark columns B are numerically dependent.
+    KLL0 = B[L] without jitter. It is held fixed when M is differentiated."""
+    BtB = np.asarray(B, dtype=np.float64).T @ np.asarray(B, dtype=np.float64)
+    k = KLL0.shape[0]
+    delta = 1e-6 * sigma_f ** 2 * P
+    for _ in range(5):
+        try:
+            np.linalg.cholesky(sigma_eps ** 2 * (KLL0 + delta * np.eye(k)) + BtB)
+            return delta
+        except np.linalg.LinAlgError:
+            delta *= 100.0
+    raise np.linalg.LinAlgError("G is not positive definite for any jitter tried")
 
 
 def nystrom_preconditioner(X, windows, kind, ell, sigma_f, sigma_eps, landmarks, jitter=None):
@@ -598,7 +608,8 @@ def nystrom_preconditioner(X, windows, kind, ell, sigma_f, sigma_eps, landmarks,
     n = X.shape[0]
     L = list(landmarks)
     KnL = dense_matvec(X, windows, kind, ell, sigma_f, 0.0, np.eye(n)[:, L], add_noise=False)
-    delta = landmark_jitter(sigma_f, len(windows)) if jitter is None else jitter
+    delta = (landmark_jitter(KnL, KnL[L, :], sigma_f, len(windows), sigma_eps)
+             if jitter is None else jitter)
     KLL = KnL[L, :] + delta * np.eye(len(L))
     M = KnL @ np.linalg.solve(KLL, KnL.T) + sigma_eps ** 2 * np.eye(n)
     M = 0.5 * (M + M.T)
@@ -674,12 +685,13 @@ def nlml_estimate(apply_K, apply_dK, y, Z, lanczos_steps, rtol=1e-10, maxit=None
 # (Sec. 1 eqs. (1.3)-(1.5); M from the (1,1) block of Sec. 2.3)
 # ---------------------------------------------------------------------------
 
-def nystrom_blocks(X, windows, kind, ell, sigma_f, landmarks, which=None, jitter=None):
+def nystrom_blocks(X, windows, kind, ell, sigma_f, landmarks, which=None, jitter=None,
+                   sigma_eps=None):
     """B = K_{:,L}, the columns of sigma_f^2 sum_s K_s (exact kernel, Sec. 2.1)
-    at the landmarks L, and K_LL = B[L, :] + delta I (delta = landmark_jitter
-    unless given). With which = "ell" or "sigma_f" the derivative of B with
-    respect to that hyperparameter and its landmark rows (sigma_eps does not
-    enter B; delta is held fixed)."""
+    at the landmarks L, and K_LL = B[L, :] + delta I (delta = landmark_jitter,
+    which needs sigma_eps, unless given). With which = "ell" or "sigma_f" the
+    derivative of B with respect to that hyperparameter and its landmark rows
+    (sigma_eps does not enter B; delta is held fixed)."""
     n = X.shape[0]
     L = list(landmarks)
     E = np.zeros((n, len(L)))
@@ -688,7 +700,8 @@ def nystrom_blocks(X, windows, kind, ell, sigma_f, landmarks, which=None, jitter
         dB = dense_deriv_matvec(X, windows, kind, ell, sigma_f, 0.0, E, which)
         return dB, dB[L, :]
     B = dense_matvec(X, windows, kind, ell, sigma_f, 0.0, E, add_noise=False)
-    delta = landmark_jitter(sigma_f, len(windows)) if jitter is None else jitter
+    delta = (landmark_jitter(B, B[L, :], sigma_f, len(windows), sigma_eps)
+             if jitter is None else jitter)
     return B, B[L, :] + delta * np.eye(len(L))
 
 

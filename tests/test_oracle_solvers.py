@@ -153,7 +153,7 @@ def _nystrom_problem(n=12, k_total=4, kind="matern12", seed=60):
 @pytest.mark.parametrize("kind", ["gauss", "matern12"])
 def test_nystrom_logdet_matches_dense(kind):
     X, W, th, _, L = _nystrom_problem(kind=kind)
-    B, KLL = O.nystrom_blocks(X, W, kind, th["ell"], th["sigma_f"], L)
+    B, KLL = O.nystrom_blocks(X, W, kind, th["ell"], th["sigma_f"], L, sigma_eps=th["sigma_eps"])
     s2 = th["sigma_eps"] ** 2
     _, want = np.linalg.slogdet(O.nystrom_matrix(B, KLL, s2))
     assert O.nystrom_logdet(B, KLL, s2) == pytest.approx(want, rel=1e-11)
@@ -163,7 +163,8 @@ def test_nystrom_probes_have_covariance_M():
     # with w_i = sqrt(n+k) q_i over an orthogonal basis of R^{n+k}, the mean
     # of z_i z_i^T is F F^T = M exactly
     X, W, th, rng, L = _nystrom_problem()
-    B, KLL = O.nystrom_blocks(X, W, "matern12", th["ell"], th["sigma_f"], L)
+    B, KLL = O.nystrom_blocks(X, W, "matern12", th["ell"], th["sigma_f"], L,
+                              sigma_eps=th["sigma_eps"])
     n, k = B.shape
     Q, _ = np.linalg.qr(rng.standard_normal((n + k, n + k)))
     Wf = math.sqrt(n + k) * Q
@@ -178,12 +179,12 @@ def test_nystrom_dM_terms_match_finite_differences(which):
     # each against central differences of M(theta) built from scratch
     X, W, th, rng, L = _nystrom_problem(kind="gauss")
     s2 = th["sigma_eps"] ** 2
-    B, KLL = O.nystrom_blocks(X, W, "gauss", th["ell"], th["sigma_f"], L)
+    B, KLL = O.nystrom_blocks(X, W, "gauss", th["ell"], th["sigma_f"], L, sigma_eps=th["sigma_eps"])
     dB, _ = O.nystrom_blocks(X, W, "gauss", th["ell"], th["sigma_f"], L, which=which)
     dKLL = dB[L]
     h = 1e-5
 
-    jit = O.landmark_jitter(th["sigma_f"], len(W))   # held fixed, as in dM
+    jit = O.landmark_jitter(B, B[L], th["sigma_f"], len(W), th["sigma_eps"])   # fixed, as in dM
 
     def at(delta):
         t = dict(th)
@@ -209,7 +210,7 @@ def test_nlml_preconditioned_exact_with_orthogonal_probes(kind):
     X, W, th, rng, L = _nystrom_problem(n, 4, kind)
     k = len(L)
     y = rng.standard_normal(n)
-    B, KLL = O.nystrom_blocks(X, W, kind, th["ell"], th["sigma_f"], L)
+    B, KLL = O.nystrom_blocks(X, W, kind, th["ell"], th["sigma_f"], L, sigma_eps=th["sigma_eps"])
     dB = {w: O.nystrom_blocks(X, W, kind, th["ell"], th["sigma_f"], L, which=w)[0]
           for w in ["ell", "sigma_f"]}
     Q, _ = np.linalg.qr(rng.standard_normal((n + k, n + k)))
