@@ -299,6 +299,8 @@ def run_gpu(args):
     # around a device synchronisation.
     plan.set_hyper(w.ell, w.sigma_f, w.sigma_eps)
     nl = time_nlml(agp, plan, V, args.nlml_reps, dev)
+    nl_pc = None if args.no_nlml_pc else time_nlml_pc(agp, plan, V, dev,
+                                                      n_landmarks=10 * len(w.windows))
     agp.agp_matvec(plan.handle, V, Out, True)
     # the plain FP64 path: the same library and workload with an FP64 plan,
     # one right-hand side per call
@@ -333,7 +335,7 @@ def run_gpu(args):
                 "stages_ms_per_step": {s: prof[s]["ms"] / args.steps for s in prof},
                 "stage_launches_per_step": {s: prof[s]["launches"] / args.steps for s in prof},
                 "clocks": clocks, "cpu_baseline": cpu,
-                "nlml_grad": nl, "plain_fp64": plain}
+                "nlml_grad": nl, "nlml_grad_pc": nl_pc, "plain_fp64": plain}
         if plain is not None:
             plain["batched_fp32_over_plain_fp64"] = value / plain["value"]
         print(json.dumps(line), flush=True)
@@ -424,6 +426,30 @@ def time_nlml(agp, plan, V, reps, dev):
     return res
 
 
+def time_nlml_pc(agp, plan, V, dev, n_landmarks=30, nz=16, steps=20):
+    """The preconditioned estimate (landmark preconditioner built inside the
+    call) on the same plan: y, 16 probes with covariance M, 20 PCG steps, 10
+    landmarks per feature window (the paper's default, Sec. 5)."""
+    import torch
+    y = V[:, 0].contiguous()
+    k = len(plan.landmarks(n_landmarks))
+    Wn = torch.tensor(inputs.gaussian(V.shape[0], nz, 7), dtype=V.dtype, device=dev)
+    Wk = inputs.gaussian(k, nz, 8)
+    res = {"unit": "NLML-grad/s", "probes": nz, "lanczos_steps": steps, "landmarks": k,
+           "includes": "landmark selection, B = K_{:,L} and its ell-derivative, the k x k "
+                       "factorisations, PCG and the derivative matvecs"}
+    try:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        nl, g = plan.nlml_grad_pc(y, Wn, Wk, n_landmarks, lanczos_steps=steps)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        res.update({"value": 1.0 / dt, "ms": 1e3 * dt, "nlml": nl, "grad": g, "status": "ok"})
+    except agp.AgpError as e:
+        res.update({"value": None, "status": str(e)})
+    return res
+
+
 def time_plain_fp64(agp, w, V32, Out32, reps, dev):
     import torch
     X64 = torch.tensor(w.X, dtype=torch.float32, device=dev).double()
@@ -458,6 +484,7 @@ def main():
     ap.add_argument("--nlml-reps", type=int, default=2)
     ap.add_argument("--plain-reps", type=int, default=5)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-nlml-pc", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -54,7 +54,9 @@ typedef enum {
   AGP_ENAN = 7           /* a non-finite value was met */
 } agp_status;
 
-typedef enum { AGP_GAUSS = 0, AGP_MATERN12 = 1 } agp_kernel;   /* Sec. 2.1 eq. (2.2) */
+/* Sec. 2.1 eq. (2.2): Gaussian exp(-r^2/(2 ell^2)), Matern(1/2) exp(-r/ell);
+ * Matern(3/2) of the remark in Sec. 4, (1 + r/ell) exp(-r/ell) (its l = sqrt(3) ell). */
+typedef enum { AGP_GAUSS = 0, AGP_MATERN12 = 1, AGP_MATERN32 = 2 } agp_kernel;
 typedef enum { AGP_F32 = 0, AGP_F64 = 1 } agp_prec;
 typedef enum { AGP_D_ELL = 0, AGP_D_SIGMA_F = 1, AGP_D_SIGMA_EPS = 2 } agp_param;
 
@@ -144,6 +146,23 @@ agp_status agp_plan_bins(agp_plan plan, int window, int32_t* bins, void* stream)
  * Synchronises `stream`. */
 agp_status agp_plan_coeffs(agp_plan plan, int window, int deriv, double* b, void* stream);
 
+/* Work items ("bins"): the points of each window are sorted by grid cell and
+ * cut into work items of at most `points` points of one cell (default 256);
+ * one work item is one CTA of spreading and interpolation. Rebuilds the work
+ * items (16 <= points <= 4096, else AGP_EINVAL). Batches created on the plan
+ * before the call keep the old items: create them again. Synchronises
+ * `stream`. (Not from the paper: a property of the GPU layout.) */
+agp_status agp_plan_set_item_points(agp_plan plan, int points, void* stream);
+
+/* Autotuner for the work-item size: for each candidate in {64, 128, 256,
+ * 512, 1024} rebuilds the work items and times `reps` applications of K_hat
+ * to R columns (device scratch allocated and freed here, CUDA events on
+ * `stream`), then keeps the fastest. points, ms: optional host outputs, the
+ * chosen size and its mean time per call in milliseconds. Batches must be
+ * created after this call. Synchronises `stream`. */
+agp_status agp_plan_autotune(agp_plan plan, int R, int reps, int* points, double* ms,
+                             void* stream);
+
 /* Size queries: n, number of windows, and the number of work items (point
  * chunks) of one window. */
 agp_status agp_plan_query(agp_plan plan, int64_t* n, int* P, int window, int* d,
@@ -160,9 +179,12 @@ agp_status agp_plan_query(agp_plan plan, int64_t* n, int* P, int window, int* d,
  * landmark part of the paper's additive AFN preconditioner (Sec. 2.3):
  * ceil(n_landmarks / P) landmarks per feature window by farthest point
  * sampling (first landmark: point 0; ties: lowest index), merged, and
- * M = K_{:,L} K_LL^{-1} K_{L,:} + sigma_eps^2 I (exact kernel) applied by the
- * Woodbury identity with an FP64 Cholesky factor; needs sigma_eps > 0 and
- * R <= 32. The stopping test stays on the unpreconditioned residual.
+ * M = K_{:,L} (K_LL + delta I)^{-1} K_{L,:} + sigma_eps^2 I (exact kernel;
+ * delta starts at 1e-6 sigma_f^2 P and grows 100-fold, at most four times,
+ * while the FP64 Cholesky of G = sigma_eps^2 (K_LL + delta I) + B^T B,
+ * B = K_{:,L}, meets a non-positive pivot, which happens when the landmarks
+ * outnumber the kernel's numerical rank) applied by the Woodbury identity with
+ * an FP64 Cholesky factor; needs sigma_eps > 0 and R <= 32. The stopping test stays on the unpreconditioned residual.
  * Returns AGP_NOT_CONVERGED if some column stopped above rtol (Xsol holds the
  * last iterate). Synchronises `stream`. */
 agp_status agp_pcg_solve(agp_plan plan, const void* B, int64_t ldb, void* Xsol, int64_t ldx,
@@ -197,6 +219,30 @@ agp_status agp_plan_landmarks(agp_plan plan, int n_landmarks, int32_t* idx, int 
 agp_status agp_nlml_grad(agp_plan plan, const void* Y, const void* Z, int64_t ldz, int nz,
                          int lanczos_steps, double rtol, int maxit, double* nlml, double* grad,
                          void* stream);
+
+/* The same estimate with the landmark preconditioner M = B K_LL^{-1} B^T +
+ * sigma_eps^2 I of agp_pcg_solve (Sec. 2.3), as in Sec. 1 eqs. (1.3)-(1.5):
+ *   nlml    = 1/2 (y^T alpha + log det M + (1/nz) sum_i q_i + n log 2 pi)
+ *   grad[j] = 1/2 (-alpha^T dK_j alpha + tr(M^{-1} dM_j)
+ *                  + (1/nz) sum_i (u_i^T dK_j p_i - p_i^T dM_j p_i))
+ * log det M and tr(M^{-1} dM_j) are exact (FP64, through the k x k Cholesky
+ * factors); the probes z_i = sigma_eps wn_i + B C^{-T} wk_i (C C^T = K_LL)
+ * have covariance M for caller-drawn vectors w_i = [wn_i; wk_i] with
+ * covariance I; q_i is the SLQ estimate of z~_i^T logm(M^{-1/2} K_hat
+ * M^{-1/2}) z~_i, z~_i = M^{-1/2} z_i, from exactly lanczos_steps PCG steps
+ * on K_hat x = z_i (u_i is the iterate, p_i = M^{-1} z_i). The y column runs
+ * lanczos_steps PCG steps when rtol = 0, else to relative residual rtol (at
+ * most maxit steps).
+ * Y: device [n]; Wn: device [n][ldwn] in the plan precision, 1 <= nz <= 31
+ * columns; Wk: host double [k][nz] with k the size of the landmark set for
+ * n_landmarks (agp_plan_landmarks); 1 <= n_landmarks <= 480; needs
+ * sigma_eps > 0. nlml: host double; grad: host double[3] (ell, sigma_f,
+ * sigma_eps). Returns AGP_ENAN (gradient still written) when SLQ meets a
+ * non-positive Ritz value or K_LL is not positive definite. Synchronises
+ * `stream`. */
+agp_status agp_nlml_grad_pc(agp_plan plan, const void* Y, const void* Wn, int64_t ldwn,
+                            const double* Wk, int nz, int n_landmarks, int lanczos_steps,
+                            double rtol, int maxit, double* nlml, double* grad, void* stream);
 
 /* ---- Batches of independent problems ----------------------------------------
  * Many independent GP problems of different sizes (independent plans, each

@@ -21,7 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libagp.so")
 
 AGP_OK, AGP_EINVAL, AGP_EDOMAIN, AGP_ECUDA, AGP_ENOMEM, AGP_NOT_CONVERGED, AGP_TIMEOUT, AGP_ENAN = range(8)
-KERNELS = {"gauss": 0, "matern12": 1}
+KERNELS = {"gauss": 0, "matern12": 1, "matern32": 2}
 PARAMS = {"ell": 0, "sigma_f": 1, "sigma_eps": 2}
 
 
@@ -68,6 +68,12 @@ _SIGS = {
     "agp_nlml_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int, c_double,
                               c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
     "agp_plan_landmarks": (c_int, [c_void_p, c_int, c_void_p, c_int, POINTER(c_int), c_void_p]),
+    "agp_plan_set_item_points": (c_int, [c_void_p, c_int, c_void_p]),
+    "agp_plan_autotune": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_double),
+                                  c_void_p]),
+    "agp_nlml_grad_pc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, POINTER(c_double), c_int,
+                                 c_int, c_int, c_double, c_int, POINTER(c_double),
+                                 POINTER(c_double), c_void_p]),
     "agp_dot_columns": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int,
                                 POINTER(c_double), c_void_p]),
     "agp_dot_columns_static": (c_int, [c_int, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int,
@@ -234,6 +240,38 @@ def agp_pcg_solve(plan: c_void_p, B: torch.Tensor, Xsol: torch.Tensor, rtol: flo
     if st != AGP_NOT_CONVERGED or raise_not_converged:
         _check(st)
     return np.array(it[:], dtype=np.int64), np.array(rel[:], dtype=np.float64)
+
+
+def agp_nlml_grad_pc(plan: c_void_p, y: torch.Tensor, Wn: torch.Tensor, Wk: np.ndarray,
+                     n_landmarks: int, lanczos_steps: int = 20, rtol: float = 0.0, maxit: int = 0):
+    """Preconditioned (nlml, grads) with probe vectors Wn (device [n][nz]) and
+    Wk (host [k][nz], k = len(landmarks(n_landmarks)))."""
+    if y.dim() != 1 or not y.is_contiguous():
+        raise ValueError("y must be a contiguous 1-D tensor")
+    wp, ldw, nz = _block(Wn, y.dtype, "Wn")
+    wk = np.ascontiguousarray(np.asarray(Wk, dtype=np.float64))
+    if wk.ndim != 2 or wk.shape[1] != nz:
+        raise ValueError("Wk must be [k][nz]")
+    nl = c_double()
+    g = (c_double * 3)()
+    _check(load_library().agp_nlml_grad_pc(plan, y.data_ptr(), wp, ldw,
+                                           wk.ctypes.data_as(POINTER(c_double)), nz,
+                                           int(n_landmarks), int(lanczos_steps), float(rtol),
+                                           int(maxit), byref(nl), g, _stream()))
+    return nl.value, {"ell": g[0], "sigma_f": g[1], "sigma_eps": g[2]}
+
+
+def agp_plan_set_item_points(plan: c_void_p, points: int):
+    _check(load_library().agp_plan_set_item_points(plan, int(points), _stream()))
+
+
+def agp_plan_autotune(plan: c_void_p, R: int = 32, reps: int = 3):
+    """(chosen points per work item, mean ms per matvec at that size)."""
+    pts = c_int()
+    ms = c_double()
+    _check(load_library().agp_plan_autotune(plan, int(R), int(reps), byref(pts), byref(ms),
+                                            _stream()))
+    return pts.value, ms.value
 
 
 def agp_plan_landmarks(plan: c_void_p, n_landmarks: int) -> np.ndarray:
@@ -446,6 +484,16 @@ class Plan:
         X = torch.empty_like(B)
         it, rel = agp_pcg_solve(self._h, B, X, rtol, maxit, n_landmarks, raise_not_converged)
         return X, it, rel
+
+    def nlml_grad_pc(self, y: torch.Tensor, Wn: torch.Tensor, Wk, n_landmarks: int,
+                     lanczos_steps: int = 20, rtol: float = 0.0, maxit: int = 0):
+        return agp_nlml_grad_pc(self._h, y, Wn, Wk, n_landmarks, lanczos_steps, rtol, maxit)
+
+    def autotune(self, R: int = 32, reps: int = 3):
+        return agp_plan_autotune(self._h, R, reps)
+
+    def set_item_points(self, points: int):
+        agp_plan_set_item_points(self._h, points)
 
     def landmarks(self, n_landmarks: int) -> np.ndarray:
         return agp_plan_landmarks(self._h, n_landmarks)

@@ -150,6 +150,7 @@ struct agp_plan_s {
   double ell = 1, sigma_f = 1, sigma_eps = 0;
   double kb_b = 0, kb_norm = 0;
   int rc_max = 32;
+  int item_points = agp::kItemPoints;   // points per work item (bin size), see agp_plan_autotune
   std::vector<agp::Window> win;
   void* wins_dev = nullptr;      // WinDev<T>[P]
   int4* items_all = nullptr;     // work items of every window, grouped by d
@@ -206,10 +207,30 @@ struct Precond {
   double* t1 = nullptr;        // [k][rmax]
   void* t2 = nullptr;          // FP64 plans: [k][rmax] double; FP32: hi, lo [2][k][rmax] float
   float* xsplit = nullptr;     // FP32 plans: hi, lo parts of the input [2][n][rmax]
+  void* Bd = nullptr;          // dB/dell [n][k] (only with PrecondNlml)
+};
+// What the preconditioned likelihood needs besides M^{-1} (host FP64, k x k
+// row-major): G^{-1}, K_LL^{-1}, the lower Cholesky factor of K_LL, the
+// ell-derivative of K_LL and B^T dB/dell, and the log-determinants of G and K_LL.
+struct PrecondNlml {
+  std::vector<double> Ginv, K, Kinv, Kchol, Kder, BtBder;   // K includes delta I
+  double logdet_G = 0.0, logdet_K = 0.0;
+  double delta = 0.0;                                        // jitter on K_LL
 };
 void precond_free(Precond* pc);
 template <typename T>
-agp_status precond_build(agp_plan_s* pl, int k, int rmax, Precond* pc, cudaStream_t st);
+agp_status precond_build(agp_plan_s* pl, int k, int rmax, Precond* pc, cudaStream_t st,
+                         PrecondNlml* ex = nullptr);
+// out[j][r] = sum_i Bsel[i][j] X[i][r] (Bsel = B, or dB/dell when der), X FP64
+// [n][R] with leading dimension R, out host [k][R]; accumulated like M^{-1}.
+template <typename T>
+agp_status precond_bt(const Precond& pc, int der, const double* X, int R, double* out,
+                      cudaStream_t st);
+// Z[i][r] = a W[i][r] + sum_j B[i][j] Tk[j][r] for r < nz: W in the plan
+// precision [n][ldw], Tk device FP64 [k][nz], Z [n][ldz] in the plan precision.
+template <typename T>
+agp_status precond_affine(const Precond& pc, double a, const T* W, int64_t ldw, const double* Tk,
+                          int nz, T* Z, int64_t ldz, cudaStream_t st);
 // The landmark set the preconditioner uses for a request of k landmarks
 // (sorted, no repeats; host vector).
 template <typename T>

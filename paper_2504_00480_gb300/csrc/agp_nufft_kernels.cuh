@@ -26,6 +26,29 @@
 // dispatches.
 #include "agp_internal.cuh"
 
+// Compile-time tuning knobs (defaults are the measured best on GB300).
+#ifndef AGP_SPREAD_SUB
+#define AGP_SPREAD_SUB 128          // points per shared-memory stage of k_spread
+#endif
+#ifndef AGP_INTERP_T2_UNROLL
+#define AGP_INTERP_T2_UNROLL 5      // rows of the block contracted together in k_interp2
+#endif
+#ifndef AGP_SPREAD_STAGES
+#define AGP_SPREAD_STAGES 2         // shared-memory stages in flight in k_spread (2 or 3)
+#endif
+#ifndef AGP_SPREAD_POINT_UNROLL
+#define AGP_SPREAD_POINT_UNROLL 1   // points of a stage processed together in k_spread
+#endif
+#ifndef AGP_INTERP_RS
+#define AGP_INTERP_RS 16            // right-hand sides per CTA of k_interp2 (8 or 16)
+#endif
+#ifndef AGP_INTERP_ASYNC_W
+#define AGP_INTERP_ASYNC_W 1        // stage k_interp2's window values with cp.async
+#endif
+#ifndef AGP_INTERP_WPS_PAD
+#define AGP_INTERP_WPS_PAD 1        // padding of a point's values in k_interp2's shared memory
+#endif
+
 namespace agp {
 namespace {
 
@@ -92,6 +115,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
                "r"(src_bytes));
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
@@ -147,13 +174,14 @@ struct SpreadShape {
   static constexpr int RPC = ROWS / PARTS;                     // rows per CTA
   static constexpr int LANES = RPC * NG;
   static constexpr int THREADS = (LANES + 31) / 32 * 32;
-  static constexpr int SUB = 64;                               // points per stage
+  static constexpr int SUB = AGP_SPREAD_SUB;                   // points per stage
   static constexpr int WPP = wpp_of(D, S);                     // window values per point
   static constexpr int VROW = (RC * sizeof(T) + 15) / 16 * 16 / sizeof(T);   // padded row
   static constexpr int VCH = (int)(VROW * sizeof(T) / 16);     // 16-byte chunks per V row
   static constexpr int PFN = (SUB * VCH + THREADS - 1) / THREADS;   // chunks per thread
   static constexpr int STAGE = SUB * (WPP + VROW);             // elements per stage
-  static constexpr size_t SMEM = 2 * STAGE * sizeof(T);
+  static constexpr int NST = AGP_SPREAD_STAGES;                // stages in flight
+  static constexpr size_t SMEM = NST * STAGE * sizeof(T);
   // CTAs per SM the register budget is sized for (accumulators + ~56 others)
   static constexpr int EST_REGS = (int)(TT * RG * sizeof(T) / 4) + 56;
   static constexpr int MINB_RAW = 65536 / (THREADS * EST_REGS);
@@ -248,22 +276,48 @@ k_spread(const WinDev<T>* __restrict__ wins, const WinIO<T>* __restrict__ io,
     for (int q = 0; q < B3; ++q) acc2[t][q] = 0ull;
 
   const int nchunk = (m + SUB - 1) / SUB;
-  if (vec_ok) load_perm(0);
-  stage(0, 0);
-  if (vec_ok && nchunk > 1) load_perm(1);
-  for (int c = 0; c < nchunk; ++c) {
-    if (c + 1 < nchunk) {
-      stage(c + 1, (c + 1) & 1);
-      if (vec_ok && c + 2 < nchunk) load_perm(c + 2);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+  constexpr int NST = Sh::NST;
+  static_assert(NST == 2 || NST == 3, "two or three stages");
+  if constexpr (NST == 2) {
+    if (vec_ok) load_perm(0);
+    stage(0, 0);
+    if (vec_ok && nchunk > 1) load_perm(1);
+  } else {
+    // prologue: chunks 0 and 1 in flight, perm of chunk 2 in registers
+    if (vec_ok) load_perm(0);
+    stage(0, 0);
+    if (nchunk > 1) {
+      if (vec_ok) load_perm(1);
+      stage(1, 1);
     }
-    __syncthreads();
-    const T* ws = sm + (c & 1) * Sh::STAGE;
+    if (vec_ok && nchunk > 2) load_perm(2);
+  }
+  for (int c = 0; c < nchunk; ++c) {
+    if constexpr (NST == 2) {
+      if (c + 1 < nchunk) {
+        stage(c + 1, (c + 1) & 1);
+        if (vec_ok && c + 2 < nchunk) load_perm(c + 2);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+    } else {
+      // chunk c landed (chunk c+1 may still be in flight); after the barrier
+      // every thread is done with chunk c-1, whose buffer takes chunk c+2
+      if (c + 1 < nchunk) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      __syncthreads();
+      if (c + 2 < nchunk) {
+        stage(c + 2, (c + 2) % 3);
+        if (vec_ok && c + 3 < nchunk) load_perm(c + 3);
+      }
+    }
+    const T* ws = sm + (c % NST) * Sh::STAGE;
     const T* vs = ws + SUB * WPP;
     const int ns = min(SUB, m - c * SUB);
-#pragma unroll 1
+    constexpr int kPointUnroll = AGP_SPREAD_POINT_UNROLL;
+#pragma unroll kPointUnroll
     for (int q = 0; q < ns; ++q) {
       const T* pw = ws + q * WPP;
       T wr;
@@ -298,7 +352,7 @@ k_spread(const WinDev<T>* __restrict__ wins, const WinIO<T>* __restrict__ io,
         }
       }
     }
-    __syncthreads();   // the buffer of chunk c is refilled at iteration c + 1
+    if constexpr (NST == 2) __syncthreads();   // the buffer of chunk c is refilled at c + 1
   }
   if (!active || col >= R) return;   // padding lanes / padding columns
   int cc[3] = {0, 0, 0};
@@ -559,7 +613,7 @@ template <int D, int S, int RC>
 struct Interp2Shape {
   static constexpr int TT = 2 * S;
   static constexpr int TTP = ttp_of(S);
-  static constexpr int RS = (RC % 16 == 0) ? 16 : 8;             // right-hand sides per CTA
+  static constexpr int RS = (RC % 16 == 0) ? AGP_INTERP_RS : 8;  // right-hand sides per CTA
   static constexpr int RP = RS / 2;                             // pairs per point group
   static constexpr int THREADS = 128;
   static constexpr int PP = 4;                                  // points per lane
@@ -568,9 +622,10 @@ struct Interp2Shape {
   static constexpr int PTS = NGRP * PP;                         // points per pass
   static constexpr int BLK = (D == 1) ? TT : ((D == 2) ? TT * TT : TT * TT * TT);
   static constexpr int WPP = wpp_of(D, S);
-  // stride of a point's values in shared memory: even (8-byte pairs) and
-  // 2 mod 4, so the point groups of a warp (PP points apart) hit different banks
-  static constexpr int WPS = WPP + 2;
+  // stride of a point's values in shared memory (WPP is a multiple of 4; an
+  // odd stride puts the point groups of a warp, PP points apart, on
+  // different banks)
+  static constexpr int WPS = WPP + AGP_INTERP_WPS_PAD;
   static constexpr int CPC = RS * 4 / 16;                      // 16-byte chunks per staged cell
   static constexpr size_t SMEM = sizeof(float) * ((size_t)BLK * RS + (size_t)PTS * WPS);
 };
@@ -625,11 +680,17 @@ k_interp2(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict
   for (int p0 = 0; p0 < m; p0 += PTS) {
     const int np = min(PTS, m - p0);
     __syncthreads();                          // previous pass done with ws
+    // window values of this pass by asynchronous 4-byte copies: in the first
+    // pass they travel together with the block
     for (int e = tid; e < np * WPP; e += Sh::THREADS) {
       const int q = e / WPP;
-      ws[q * WPS + (e - q * WPP)] = __ldg(w.wts + (int64_t)(j0 + p0) * WPP + e);
+      if constexpr (AGP_INTERP_ASYNC_W)
+        cp_async4(ws + q * WPS + (e - q * WPP), w.wts + (int64_t)(j0 + p0) * WPP + e);
+      else
+        ws[q * WPS + (e - q * WPP)] = __ldg(w.wts + (int64_t)(j0 + p0) * WPP + e);
     }
-    cp_async_wait<0>();                       // the staged block has landed (first pass)
+    cp_async_commit();
+    cp_async_wait<0>();                       // block (first pass) and window values landed
     __syncthreads();
     if (warp_first_grp * PP >= np) continue;  // no point of this pass in this warp
 
@@ -638,9 +699,10 @@ k_interp2(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict
     for (int k = 0; k < PP; ++k) {
       const int q = grp * PP + k;
 #pragma unroll
-      for (int t = 0; t < TT; ++t)
-        wl[k][t] = (q < np) ? *reinterpret_cast<const f32x2*>(ws + q * WPS + (D - 1) * TTP + 2 * t)
-                            : 0ull;
+      for (int t = 0; t < TT; ++t) {
+        const float v = (q < np) ? ws[q * WPS + (D - 1) * TTP + 2 * t] : 0.0f;
+        wl[k][t] = x2_pack(v, v);
+      }
     }
     auto wdup = [&](int k, int dim, int t) {
       const float v = ws[min(grp * PP + k, PTS - 1) * WPS + dim * TTP + t];
@@ -663,6 +725,8 @@ k_interp2(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict
         f32x2 u1[PP];
 #pragma unroll
         for (int k = 0; k < PP; ++k) u1[k] = 0ull;
+        constexpr int kT2Unroll = AGP_INTERP_T2_UNROLL;
+#pragma unroll kT2Unroll
         for (int t2 = 0; t2 < TT; ++t2) {
           f32x2 u2[PP];
 #pragma unroll

@@ -125,22 +125,22 @@ __global__ void k_scatter(const T* __restrict__ X, int64_t ldx, int64_t n, int d
   for (int t = 0; t < d; ++t) xs[t * n + pos] = X[i * ldx + f[t]];
 }
 
-__global__ void k_chunks_per_cell(const int32_t* __restrict__ cell_start, int64_t cells,
+__global__ void k_chunks_per_cell(const int32_t* __restrict__ cell_start, int64_t cells, int cap,
                                   int32_t* __restrict__ nchunks) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= cells) return;
   const int cnt = cell_start[c + 1] - cell_start[c];
-  nchunks[c] = (cnt + kItemPoints - 1) / kItemPoints;
+  nchunks[c] = (cnt + cap - 1) / cap;
 }
 
 __global__ void k_make_items(const int32_t* __restrict__ cell_start,
                              const int32_t* __restrict__ chunk_start, int64_t cells, int window,
-                             int4* __restrict__ items) {
+                             int cap, int4* __restrict__ items) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= cells) return;
   const int a = cell_start[c], b = cell_start[c + 1];
   int o = chunk_start[c];
-  for (int s = a; s < b; s += kItemPoints) items[o++] = make_int4(window, (int)c, s, min(kItemPoints, b - s));
+  for (int s = a; s < b; s += cap) items[o++] = make_int4(window, (int)c, s, min(cap, b - s));
 }
 
 // bins of every point in the caller's order: floor(x_t n_os) (a signed index)
@@ -175,10 +175,14 @@ __global__ void k_kernel_samples(double* __restrict__ out, int N, int d, int ker
   if (kernel == AGP_GAUSS) {
     v = exp(-r2 / (2.0 * ell * ell));
     if (der) v *= r2 / (ell * ell * ell);
-  } else {
+  } else if (kernel == AGP_MATERN12) {
     const double r = sqrt(r2);
     v = exp(-r / ell);
     if (der) v *= r / (ell * ell);
+  } else {   // Matern(3/2): (1 + r/ell) e^{-r/ell}, derivative r^2/ell^3 e^{-r/ell}
+    const double r = sqrt(r2);
+    const double ex = exp(-r / ell);
+    v = der ? r2 / (ell * ell * ell) * ex : (1.0 + r / ell) * ex;
   }
   out[e] = v;
 }
@@ -393,7 +397,8 @@ agp_status validate(const agp_plan_desc* d) {
   if (!(d->ell > 0) || !std::isfinite(d->ell) || !std::isfinite(d->sigma_f) ||
       !std::isfinite(d->sigma_eps))
     return set_error(AGP_EINVAL, "bad hyperparameters");
-  if (d->kernel != AGP_GAUSS && d->kernel != AGP_MATERN12) return set_error(AGP_EINVAL, "bad kernel");
+  if (d->kernel != AGP_GAUSS && d->kernel != AGP_MATERN12 && d->kernel != AGP_MATERN32)
+    return set_error(AGP_EINVAL, "bad kernel");
   if (d->prec != AGP_F32 && d->prec != AGP_F64) return set_error(AGP_EINVAL, "bad prec");
   std::vector<int> used(d->p, 0);
   if (d->win_ptr[0] != 0) return set_error(AGP_EINVAL, "win_ptr[0] must be 0");
@@ -468,6 +473,60 @@ void free_plan(agp_plan_s* pl) {
   delete pl;
 }
 
+// (Re)build the work items of every window with at most `cap` points each,
+// grouped by window dimension (all windows of one d share a launch).
+agp_status build_items(agp_plan_s* pl, int cap, cudaStream_t st) {
+  std::vector<int64_t> n_items(pl->P, 0);
+  std::vector<int32_t*> chunk_start(pl->P, nullptr);
+  struct Free {
+    std::vector<int32_t*>& v;
+    cudaStream_t st;
+    ~Free() {
+      for (auto* p : v)
+        if (p) cudaFreeAsync(p, st);
+    }
+  } fr{chunk_start, st};
+  for (int s = 0; s < pl->P; ++s) {
+    Window& w = pl->win[s];
+    int32_t* nch = nullptr;
+    AGP_CUDA(cudaMallocAsync(&nch, sizeof(int32_t) * w.cells, st));
+    AGP_CUDA(cudaMallocAsync(&chunk_start[s], sizeof(int32_t) * (w.cells + 1), st));
+    k_chunks_per_cell<<<nblk(w.cells, 256), 256, 0, st>>>(w.cell_start, w.cells, cap, nch);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(nch, chunk_start[s], w.cells);
+    AGP_CUDA(cudaGetLastError());
+    int32_t tot = 0;
+    AGP_CUDA(cudaMemcpyAsync(&tot, chunk_start[s] + w.cells, sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    AGP_CUDA(cudaFreeAsync(nch, st));
+    n_items[s] = tot;
+  }
+  int64_t total = 0;
+  for (int s = 0; s < pl->P; ++s) total += n_items[s];
+  int4* items = nullptr;
+  AGP_CUDA(cudaMalloc(&items, sizeof(int4) * (total > 0 ? total : 1)));
+  int64_t off = 0;
+  for (int dd = 1; dd <= kMaxDim; ++dd) {
+    pl->items_by_d[dd - 1] = off;
+    for (int s = 0; s < pl->P; ++s) {
+      Window& w = pl->win[s];
+      if (w.d != dd) continue;
+      w.items = items + off;
+      w.n_items = n_items[s];
+      k_make_items<<<nblk(w.cells, 256), 256, 0, st>>>(w.cell_start, chunk_start[s], w.cells, s,
+                                                       cap, w.items);
+      off += n_items[s];
+    }
+  }
+  pl->items_by_d[kMaxDim] = off;
+  AGP_CUDA(cudaGetLastError());
+  AGP_CUDA(cudaStreamSynchronize(st));
+  if (pl->items_all) cudaFree(pl->items_all);
+  pl->items_all = items;
+  pl->item_points = cap;
+  return AGP_OK;
+}
+
 template <typename T>
 agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
   const int64_t n = pl->n;
@@ -477,19 +536,15 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
 
   int32_t* cell_of = nullptr;
   AGP_CUDA(cudaMallocAsync(&cell_of, sizeof(int32_t) * n, st));
-  std::vector<int32_t*> nchunk_start(pl->P, nullptr);
-  std::vector<int64_t> n_items(pl->P, 0);
 
   for (int s = 0; s < pl->P; ++s) {
     Window& w = pl->win[s];
-    int32_t *counts = nullptr, *fill = nullptr, *nch = nullptr;
+    int32_t *counts = nullptr, *fill = nullptr;
     AGP_CUDA(cudaMalloc(&w.perm, sizeof(int32_t) * n));
     AGP_CUDA(cudaMalloc(&w.xs, sizeof(T) * n * w.d));
     AGP_CUDA(cudaMalloc(&w.cell_start, sizeof(int32_t) * (w.cells + 1)));
     AGP_CUDA(cudaMallocAsync(&counts, sizeof(int32_t) * w.cells, st));
     AGP_CUDA(cudaMallocAsync(&fill, sizeof(int32_t) * w.cells, st));
-    AGP_CUDA(cudaMallocAsync(&nch, sizeof(int32_t) * w.cells, st));
-    AGP_CUDA(cudaMallocAsync(&nchunk_start[s], sizeof(int32_t) * (w.cells + 1), st));
     AGP_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * w.cells, st));
     AGP_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * w.cells, st));
     k_bin_count<T><<<nblk(n, 256), 256, 0, st>>>(X, d->ldx, n, w.d, w.feat[0], w.feat[1],
@@ -499,48 +554,20 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
     k_scatter<T><<<nblk(n, 256), 256, 0, st>>>(X, d->ldx, n, w.d, w.feat[0], w.feat[1],
                                                w.feat[2], cell_of, w.cell_start, fill, w.perm,
                                                reinterpret_cast<T*>(w.xs));
-    k_chunks_per_cell<<<nblk(w.cells, 256), 256, 0, st>>>(w.cell_start, w.cells, nch);
-    k_scan_exclusive<<<1, 1024, 0, st>>>(nch, nchunk_start[s], w.cells);
     AGP_CUDA(cudaGetLastError());
-    int32_t tot = 0;
-    AGP_CUDA(cudaMemcpyAsync(&tot, nchunk_start[s] + w.cells, sizeof(int32_t),
-                             cudaMemcpyDeviceToHost, st));
-    AGP_CUDA(cudaStreamSynchronize(st));
-    n_items[s] = tot;
     AGP_CUDA(cudaFreeAsync(counts, st));
     AGP_CUDA(cudaFreeAsync(fill, st));
-    AGP_CUDA(cudaFreeAsync(nch, st));
   }
   int err = 0;
   AGP_CUDA(cudaMemcpyAsync(&err, pl->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   AGP_CUDA(cudaStreamSynchronize(st));
   if (err & kErrDomain) {
-    for (auto* p : nchunk_start) cudaFree(p);
     cudaFree(cell_of);
     return set_error(AGP_EDOMAIN, "a point lies outside [-1/4, 1/4)^d in some window");
   }
 
-  // Work items, grouped by window dimension (all windows of one d share a launch).
-  int64_t total = 0;
-  for (int s = 0; s < pl->P; ++s) total += n_items[s];
-  AGP_CUDA(cudaMalloc(&pl->items_all, sizeof(int4) * (total > 0 ? total : 1)));
-  int64_t off = 0;
-  for (int dd = 1; dd <= kMaxDim; ++dd) {
-    pl->items_by_d[dd - 1] = off;
-    for (int s = 0; s < pl->P; ++s) {
-      Window& w = pl->win[s];
-      if (w.d != dd) continue;
-      w.items = pl->items_all + off;
-      w.n_items = n_items[s];
-      k_make_items<<<nblk(w.cells, 256), 256, 0, st>>>(w.cell_start, nchunk_start[s], w.cells, s,
-                                                       w.items);
-      off += n_items[s];
-    }
-  }
-  pl->items_by_d[kMaxDim] = off;
-  AGP_CUDA(cudaGetLastError());
-  for (auto* p : nchunk_start) AGP_CUDA(cudaFreeAsync(p, st));
   AGP_CUDA(cudaFreeAsync(cell_of, st));
+  AGP_TRY(build_items(pl, kItemPoints, st));
 
   // Deconvolution factors, twiddles, coefficient buffers, grids.
   std::vector<WinDev<T>> wd(pl->P);
@@ -994,6 +1021,58 @@ agp_status agp_profile_read(agp_plan pl, agp_profile_t* out, int reset, void* st
     pl->prof_ev.clear();
     for (int k = 0; k < 4; ++k) pl->launches[k] = 0;
   }
+  return AGP_OK;
+}
+
+agp_status agp_plan_set_item_points(agp_plan pl, int points, void* stream) {
+  if (!pl || points < 16 || points > 4096)
+    return set_error(AGP_EINVAL, "points per work item must be in [16, 4096]");
+  return build_items(pl, points, static_cast<cudaStream_t>(stream));
+}
+
+agp_status agp_plan_autotune(agp_plan pl, int R, int reps, int* points, double* ms, void* stream) {
+  if (!pl || R < 1 || reps < 1) return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)pl->n * R * (pl->prec == AGP_F32 ? 4 : 8);
+  void *V = nullptr, *Out = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  struct Free {
+    void **v, **o;
+    cudaEvent_t *a, *b;
+    cudaStream_t st;
+    ~Free() {
+      if (*v) cudaFreeAsync(*v, st);
+      if (*o) cudaFreeAsync(*o, st);
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } fr{&V, &Out, &a, &b, st};
+  AGP_CUDA(cudaMallocAsync(&V, bytes, st));
+  AGP_CUDA(cudaMallocAsync(&Out, bytes, st));
+  AGP_CUDA(cudaMemsetAsync(V, 0, bytes, st));
+  AGP_CUDA(cudaEventCreate(&a));
+  AGP_CUDA(cudaEventCreate(&b));
+  const int cands[] = {64, 128, 256, 512, 1024};
+  int best = pl->item_points;
+  float best_ms = 0.0f;
+  for (int c : cands) {
+    AGP_TRY(build_items(pl, c, st));
+    AGP_TRY(agp_matvec(pl, V, R, Out, R, R, 1, st));   // warm-up
+    AGP_CUDA(cudaEventRecord(a, st));
+    for (int k = 0; k < reps; ++k) AGP_TRY(agp_matvec(pl, V, R, Out, R, R, 1, st));
+    AGP_CUDA(cudaEventRecord(b, st));
+    AGP_CUDA(cudaEventSynchronize(b));
+    float t = 0.0f;
+    AGP_CUDA(cudaEventElapsedTime(&t, a, b));
+    t /= reps;
+    if (best_ms == 0.0f || t < best_ms) {
+      best_ms = t;
+      best = c;
+    }
+  }
+  AGP_TRY(build_items(pl, best, st));
+  if (points) *points = best;
+  if (ms) *ms = best_ms;
   return AGP_OK;
 }
 

@@ -1,8 +1,9 @@
 // Landmark (Nystrom) preconditioner for batched PCG -- the (1,1)-block part of
 // the paper's additive AFN preconditioner (Sec. 2.3): landmarks are chosen by
 // farthest point sampling (FPS) in every feature window and merged; with
-// B = K_{:,L} (the kernel part sigma_f^2 sum_s K_s, exact kernel) and
-// K_LL = B_L,
+// B = K_{:,L} (the kernel part sigma_f^2 sum_s K_s, exact kernel) and K_LL
+// its landmark rows, evaluated in FP64, plus delta I (a safeguard when the
+// landmarks outnumber the kernel's numerical rank, see precond_build),
 //     M = B K_LL^{-1} B^T + sigma_eps^2 I,
 //     M^{-1} = sigma_eps^{-2} (I - B G^{-1} B^T),  G = sigma_eps^2 K_LL + B^T B
 // (Woodbury identity). G is k x k (k <= 512) and inverted once in FP64 by a
@@ -123,15 +124,13 @@ struct WinPts {
   int d;
 };
 
+// sum_s kappa_s(|x_i^s - x_l^s|) (der = 0) or its ell-derivative (der = 1;
+// Sec. 2.1 eq. (2.3): Gaussian kappa r^2 / ell^3, Matern(1/2) kappa r / ell^2,
+// Matern(3/2) r^2 / ell^3 e^{-r/ell}),
+// exact kernel in FP64 from the plan-precision coordinates
 template <typename T>
-__global__ void k_kernel_cols(const WinPts<T>* __restrict__ wp, int P, int64_t n,
-                              const int32_t* __restrict__ lm, int k, int kernel, double ell,
-                              double sf2, T* __restrict__ B) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= n * k) return;
-  const int64_t i = e / k;
-  const int j = (int)(e - i * k);
-  const int64_t l = lm[j];
+__device__ double kernel_sum(const WinPts<T>* __restrict__ wp, int P, int64_t n, int64_t i,
+                             int64_t l, int kernel, double ell, int der) {
   double s = 0.0;
   for (int w = 0; w < P; ++w) {
     const WinPts<T> p = wp[w];
@@ -140,28 +139,55 @@ __global__ void k_kernel_cols(const WinPts<T>* __restrict__ wp, int P, int64_t n
       const double u = (double)p.x[(int64_t)t * n + i] - (double)p.x[(int64_t)t * n + l];
       r2 += u * u;
     }
-    s += (kernel == AGP_GAUSS) ? exp(-r2 / (2.0 * ell * ell)) : exp(-sqrt(r2) / ell);
+    if (kernel == AGP_GAUSS) {
+      const double kv = exp(-r2 / (2.0 * ell * ell));
+      s += der ? kv * r2 / (ell * ell * ell) : kv;
+    } else if (kernel == AGP_MATERN12) {
+      const double r = sqrt(r2);
+      const double kv = exp(-r / ell);
+      s += der ? kv * r / (ell * ell) : kv;
+    } else {   // Matern(3/2)
+      const double r = sqrt(r2);
+      const double ex = exp(-r / ell);
+      s += der ? r2 / (ell * ell * ell) * ex : (1.0 + r / ell) * ex;
+    }
   }
-  B[e] = (T)(sf2 * s);
+  return s;
 }
 
-// G[a][b] = s2 * B[L_a][b]  (then += B^T B)
+// B[i][j] = sigma_f^2 kernel_sum(i, L_j) (or its ell-derivative), [n][k]
 template <typename T>
-__global__ void k_gram_init(const T* __restrict__ B, const int32_t* __restrict__ lm, int k,
-                            double s2, double* __restrict__ G) {
+__global__ void k_kernel_cols(const WinPts<T>* __restrict__ wp, int P, int64_t n,
+                              const int32_t* __restrict__ lm, int k, int kernel, double ell,
+                              double sf2, int der, T* __restrict__ B) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t i = e / k;
+  const int j = (int)(e - i * k);
+  B[e] = (T)(sf2 * kernel_sum<T>(wp, P, n, i, lm[j], kernel, ell, der));
+}
+
+// K_LL[a][b] = sigma_f^2 kernel_sum(L_a, L_b) + delta [a == b] in FP64 (or the
+// ell-derivative block with delta = 0)
+template <typename T>
+__global__ void k_kernel_block(const WinPts<T>* __restrict__ wp, int P, int64_t n,
+                               const int32_t* __restrict__ lm, int k, int kernel, double ell,
+                               double sf2, int der, double delta, double* __restrict__ K) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= k * k) return;
   const int a = e / k, b = e - a * k;
-  G[e] = s2 * (double)B[(int64_t)lm[a] * k + b];
+  K[e] = sf2 * kernel_sum<T>(wp, P, n, lm[a], lm[b], kernel, ell, der) + (a == b ? delta : 0.0);
 }
 
-// G += B^T B over a slice of rows: 32 x 32 output tile per CTA (blockIdx.x, y),
+// G += B^T C over a slice of rows (C = B for the Gram matrix): 32 x 32 output
+// tile per CTA (blockIdx.x, y),
 // row slices over blockIdx.z, added to G with FP64 atomics. FP64 plans: FP64
 // FMAs; FP32 plans: Dot2 over the whole slice (the products of FP32 entries
 // are split exactly).
 template <typename T>
 __global__ void __launch_bounds__(1024)
-k_gram(const T* __restrict__ B, int64_t n, int k, int64_t rows_per_slice, double* __restrict__ G) {
+k_gram(const T* __restrict__ B, const T* __restrict__ C, int64_t n, int k, int64_t rows_per_slice,
+       double* __restrict__ G) {
   __shared__ T sa[64][33];
   __shared__ T sb[64][33];
   const int ta = threadIdx.x / 32, tb = threadIdx.x % 32;
@@ -176,7 +202,7 @@ k_gram(const T* __restrict__ B, int64_t n, int k, int64_t rows_per_slice, double
       const int64_t row = rb + rr;
       const int ca = blockIdx.x * 32 + cc, cb = blockIdx.y * 32 + cc;
       sa[rr][cc] = (row < r1 && ca < k) ? B[row * k + ca] : T(0);
-      sb[rr][cc] = (row < r1 && cb < k) ? B[row * k + cb] : T(0);
+      sb[rr][cc] = (row < r1 && cb < k) ? C[row * k + cb] : T(0);
     }
     __syncthreads();
     if constexpr (sizeof(T) == 4) {
@@ -190,6 +216,24 @@ k_gram(const T* __restrict__ B, int64_t n, int k, int64_t rows_per_slice, double
   }
   if constexpr (sizeof(T) == 4) acc = (double)s + (double)c;
   if (a < k && b < k) atomicAdd(G + (int64_t)a * k + b, acc);
+}
+
+// out = s a + b (m values)
+__global__ void k_axpy(const double* __restrict__ a, double s, const double* __restrict__ b,
+                       int64_t m, double* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < m) out[e] = s * a[e] + b[e];
+}
+
+// A[j][j] += delta
+__global__ void k_shift_diag(double* __restrict__ A, int k, double delta) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) A[(int64_t)j * k + j] += delta;
+}
+
+__global__ void k_diag(const double* __restrict__ A, int k, double* __restrict__ d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) d[j] = A[(int64_t)j * k + j];
 }
 
 // In-place lower Cholesky factor of G (k x k, FP64) by one CTA; flag = 1 on a
@@ -344,6 +388,27 @@ k_pc_out(const T* __restrict__ B, const double* __restrict__ X, const void* __re
   }
 }
 
+// Z[i][r] = a W[i][r] + sum_j B[i][j] Tk[j][r]: a warp per row, lanes = columns,
+// Tk staged in shared memory, FP64 accumulation
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_pc_affine(const T* __restrict__ B, const T* __restrict__ W, int64_t ldw,
+            const double* __restrict__ Tk, int64_t n, int k, int nz, double a, T* __restrict__ Z,
+            int64_t ldz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* st = reinterpret_cast<double*>(smem_raw);   // [k][nz]
+  for (int e = threadIdx.x; e < k * nz; e += blockDim.x) st[e] = Tk[e];
+  __syncthreads();
+  const int lane = threadIdx.x % 32;
+  if (lane >= nz) return;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; i < n; i += (int64_t)gridDim.x * 8) {
+    const T* brow = B + i * k;
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s = fma((double)__ldg(brow + j), st[j * nz + lane], s);
+    Z[i * ldz + lane] = (T)(a * (double)W[i * ldw + lane] + s);
+  }
+}
+
 }  // namespace
 
 void precond_free(Precond* pc) {
@@ -354,6 +419,7 @@ void precond_free(Precond* pc) {
   cudaFree(pc->t1);
   cudaFree(pc->t2);
   cudaFree(pc->xsplit);
+  cudaFree(pc->Bd);
   *pc = Precond();
 }
 
@@ -418,7 +484,8 @@ agp_status select_landmarks(agp_plan_s* pl, const CallerPoints<T>& cp, int k_req
 }
 
 template <typename T>
-agp_status precond_build(agp_plan_s* pl, int k_req, int rmax, Precond* pc, cudaStream_t st) {
+agp_status precond_build(agp_plan_s* pl, int k_req, int rmax, Precond* pc, cudaStream_t st,
+                         PrecondNlml* ex) {
   const int64_t n = pl->n;
   const int P = pl->P;
   if (!(pl->sigma_eps > 0)) return set_error(AGP_EINVAL, "the preconditioner needs sigma_eps > 0");
@@ -443,28 +510,115 @@ agp_status precond_build(agp_plan_s* pl, int k_req, int rmax, Precond* pc, cudaS
   pc->inv_s2 = 1.0 / (pl->sigma_eps * pl->sigma_eps);
   AGP_CUDA(cudaMalloc(&pc->B, sizeof(T) * n * k));
   k_kernel_cols<T><<<nblk(n * k, 256), 256, 0, st>>>(wpd, P, n, lm, k, pl->kernel, pl->ell,
-                                                     pl->sigma_f * pl->sigma_f, (T*)pc->B);
-  // G = sigma_eps^2 K_LL + B^T B, then Ginv by Cholesky
-  double *G = nullptr, *Li = nullptr;
+                                                     pl->sigma_f * pl->sigma_f, 0, (T*)pc->B);
+  // K_LL (FP64, exact kernel) + delta I and G = sigma_eps^2 K_LL + B^T B, then
+  // Ginv by Cholesky. delta starts at 1e-6 sigma_f^2 P (1e-6 of the kernel's
+  // diagonal value); when the FP64 Cholesky of G meets a non-positive pivot
+  // (the landmarks outnumber the kernel's numerical rank and the columns of B
+  // are numerically dependent) delta grows 100-fold and G is factorised
+  // again, at most four times. delta is held fixed when M is differentiated.
+  const double s2 = pl->sigma_eps * pl->sigma_eps;
+  double *G = nullptr, *Li = nullptr, *KLL = nullptr, *KLL0 = nullptr, *BtB = nullptr;
   int* flag = nullptr;
   AGP_CUDA(cudaMallocAsync(&G, sizeof(double) * k * k, st));
   AGP_CUDA(cudaMallocAsync(&Li, sizeof(double) * k * k, st));
+  AGP_CUDA(cudaMallocAsync(&KLL, sizeof(double) * k * k, st));
+  AGP_CUDA(cudaMallocAsync(&KLL0, sizeof(double) * k * k, st));
+  AGP_CUDA(cudaMallocAsync(&BtB, sizeof(double) * k * k, st));
   AGP_CUDA(cudaMallocAsync(&flag, sizeof(int), st));
-  AGP_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  k_gram_init<T><<<nblk((int64_t)k * k, 256), 256, 0, st>>>((const T*)pc->B, lm, k,
-                                                           pl->sigma_eps * pl->sigma_eps, G);
+  k_kernel_block<T><<<nblk((int64_t)k * k, 256), 256, 0, st>>>(
+      wpd, P, n, lm, k, pl->kernel, pl->ell, pl->sigma_f * pl->sigma_f, 0, 0.0, KLL0);
+  AGP_CUDA(cudaMemsetAsync(BtB, 0, sizeof(double) * k * k, st));
   const int64_t slices = std::min<int64_t>(64, (n + 4095) / 4096);
   const int64_t rps = (n + slices - 1) / slices;
-  k_gram<T><<<dim3((k + 31) / 32, (k + 31) / 32, (unsigned)slices), 1024, 0, st>>>((const T*)pc->B,
-                                                                                   n, k, rps, G);
-  k_cholesky<<<1, 1024, 0, st>>>(G, k, flag);
+  k_gram<T><<<dim3((k + 31) / 32, (k + 31) / 32, (unsigned)slices), 1024, 0, st>>>(
+      (const T*)pc->B, (const T*)pc->B, n, k, rps, BtB);
+  double delta = 1e-6 * pl->sigma_f * pl->sigma_f * P;
+  int hflag = 1;
+  for (int attempt = 0; attempt < 5 && hflag; ++attempt, delta *= 100.0) {
+    AGP_CUDA(cudaMemcpyAsync(KLL, KLL0, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, st));
+    k_shift_diag<<<nblk(k, 128), 128, 0, st>>>(KLL, k, delta);
+    k_axpy<<<nblk((int64_t)k * k, 256), 256, 0, st>>>(KLL, s2, BtB, (int64_t)k * k, G);
+    AGP_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    k_cholesky<<<1, 1024, 0, st>>>(G, k, flag);
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    if (!hflag) break;
+  }
+  cudaFreeAsync(BtB, st);
+  cudaFreeAsync(KLL0, st);
   k_tri_inverse<<<nblk(k, 128), 128, 0, st>>>(G, k, Li);
   AGP_CUDA(cudaMalloc(&pc->Ginv, sizeof(double) * k * k));
   k_gram_inverse<<<nblk((int64_t)k * k, 256), 256, 0, st>>>(Li, k, pc->Ginv);
   AGP_CUDA(cudaGetLastError());
-  int hflag = 0;
-  AGP_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   AGP_CUDA(cudaStreamSynchronize(st));
+  if (ex && !hflag) {
+    const size_t kk = (size_t)k * k;
+    ex->delta = delta;
+    std::vector<double> diag(k);
+    double *dg = nullptr, *Kd = nullptr, *KLi = nullptr, *Kinv = nullptr, *W = nullptr;
+    AGP_CUDA(cudaMallocAsync(&dg, sizeof(double) * k, st));
+    AGP_CUDA(cudaMallocAsync(&Kd, sizeof(double) * kk, st));
+    AGP_CUDA(cudaMallocAsync(&KLi, sizeof(double) * kk, st));
+    AGP_CUDA(cudaMallocAsync(&Kinv, sizeof(double) * kk, st));
+    AGP_CUDA(cudaMallocAsync(&W, sizeof(double) * kk, st));
+    // log det G from its Cholesky factor (G now holds L)
+    k_diag<<<nblk(k, 128), 128, 0, st>>>(G, k, dg);
+    AGP_CUDA(cudaMemcpyAsync(diag.data(), dg, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    ex->Ginv.resize(kk);
+    AGP_CUDA(cudaMemcpyAsync(ex->Ginv.data(), pc->Ginv, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    ex->logdet_G = 0.0;
+    for (int j = 0; j < k; ++j) ex->logdet_G += 2.0 * std::log(diag[j]);
+    // K_LL: Cholesky factor, inverse, log det
+    AGP_CUDA(cudaMemcpyAsync(Kd, KLL, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st));
+    ex->K.resize(kk);
+    AGP_CUDA(cudaMemcpyAsync(ex->K.data(), Kd, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    k_cholesky<<<1, 1024, 0, st>>>(Kd, k, flag);
+    k_tri_inverse<<<nblk(k, 128), 128, 0, st>>>(Kd, k, KLi);
+    k_gram_inverse<<<nblk((int64_t)kk, 256), 256, 0, st>>>(KLi, k, Kinv);
+    k_diag<<<nblk(k, 128), 128, 0, st>>>(Kd, k, dg);
+    ex->Kchol.resize(kk);
+    ex->Kinv.resize(kk);
+    AGP_CUDA(cudaMemcpyAsync(ex->Kchol.data(), Kd, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaMemcpyAsync(ex->Kinv.data(), Kinv, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaMemcpyAsync(diag.data(), dg, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    // dB/dell, its landmark rows and B^T dB/dell
+    AGP_CUDA(cudaMalloc(&pc->Bd, sizeof(T) * n * k));
+    k_kernel_cols<T><<<nblk(n * k, 256), 256, 0, st>>>(wpd, P, n, lm, k, pl->kernel, pl->ell,
+                                                       pl->sigma_f * pl->sigma_f, 1, (T*)pc->Bd);
+    k_kernel_block<T><<<nblk((int64_t)kk, 256), 256, 0, st>>>(
+        wpd, P, n, lm, k, pl->kernel, pl->ell, pl->sigma_f * pl->sigma_f, 1, 0.0, Kd);
+    ex->Kder.resize(kk);
+    AGP_CUDA(cudaMemcpyAsync(ex->Kder.data(), Kd, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * kk, st));
+    k_gram<T><<<dim3((k + 31) / 32, (k + 31) / 32, (unsigned)slices), 1024, 0, st>>>(
+        (const T*)pc->B, (const T*)pc->Bd, n, k, rps, W);
+    ex->BtBder.resize(kk);
+    AGP_CUDA(cudaMemcpyAsync(ex->BtBder.data(), W, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+    int kflag = 0;
+    AGP_CUDA(cudaMemcpyAsync(&kflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaStreamSynchronize(st));
+    for (void* q : {(void*)dg, (void*)Kd, (void*)KLi, (void*)Kinv, (void*)W}) cudaFreeAsync(q, st);
+    if (kflag) {
+      cudaFreeAsync(KLL, st);
+      cudaFreeAsync(G, st);
+      cudaFreeAsync(Li, st);
+      cudaFreeAsync(flag, st);
+      cudaFreeAsync(lm, st);
+      cudaFreeAsync(wpd, st);
+      return set_error(AGP_ENAN, "preconditioner: K_LL is not positive definite");
+    }
+    ex->logdet_K = 0.0;
+    for (int j = 0; j < k; ++j) {
+      ex->logdet_K += 2.0 * std::log(diag[j]);
+      for (int b = j + 1; b < k; ++b) ex->Kchol[(size_t)j * k + b] = 0.0;   // keep the lower factor
+    }
+  }
+  cudaFreeAsync(KLL, st);
   cudaFreeAsync(G, st);
   cudaFreeAsync(Li, st);
   cudaFreeAsync(flag, st);
@@ -509,6 +663,42 @@ agp_status precond_apply(const Precond& pc, const double* X, double* Y, int R, c
 }
 
 template <typename T>
+agp_status precond_bt(const Precond& pc, int der, const double* X, int R, double* out,
+                      cudaStream_t st) {
+  if (R > pc.rmax || R > 32) return set_error(AGP_EINVAL, "preconditioner: too many columns");
+  if (der && !pc.Bd) return set_error(AGP_EINVAL, "preconditioner: no derivative columns");
+  const int k = pc.k;
+  const float *xh = nullptr, *xl = nullptr;
+  if (sizeof(T) == 4) {
+    float* h = pc.xsplit;
+    float* l = pc.xsplit + pc.n * R;
+    k_split<<<nblk(pc.n * R, 256), 256, 0, st>>>(X, pc.n * R, h, l);
+    xh = h;
+    xl = l;
+  }
+  k_pc_bt<T><<<dim3((k + 31) / 32, pc.slices), 256, 0, st>>>(
+      (const T*)(der ? pc.Bd : pc.B), X, xh, xl, pc.n, k, R, pc.rows_per_slice, pc.partial);
+  k_pc_mid<T><<<nblk((int64_t)k * R, 128), 128, 0, st>>>(pc.partial, pc.slices, pc.Ginv, k, R, 0,
+                                                         pc.t1, pc.t2);
+  AGP_CUDA(cudaGetLastError());
+  AGP_CUDA(cudaMemcpyAsync(out, pc.t1, sizeof(double) * k * R, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  return AGP_OK;
+}
+
+template <typename T>
+agp_status precond_affine(const Precond& pc, double a, const T* W, int64_t ldw, const double* Tk,
+                          int nz, T* Z, int64_t ldz, cudaStream_t st) {
+  if (nz < 1 || nz > 32) return set_error(AGP_EINVAL, "preconditioner: 1..32 columns");
+  const size_t smem = sizeof(double) * (size_t)pc.k * nz;
+  AGP_CUDA(cudaFuncSetAttribute(k_pc_affine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double) * kMaxLandmarkSet * 32)));
+  const unsigned blocks = (unsigned)std::min<int64_t>(nblk(pc.n, 8), 152 * 8);
+  k_pc_affine<T><<<blocks, 256, smem, st>>>((const T*)pc.B, W, ldw, Tk, pc.n, pc.k, nz, a, Z, ldz);
+  return cuda_status(cudaGetLastError(), "precond_affine");
+}
+
+template <typename T>
 agp_status precond_landmarks(agp_plan_s* pl, int k, std::vector<int32_t>& out, cudaStream_t st) {
   CallerPoints<T> cp;
   AGP_TRY(caller_points<T>(pl, cp, st));
@@ -517,8 +707,18 @@ agp_status precond_landmarks(agp_plan_s* pl, int k, std::vector<int32_t>& out, c
 
 template agp_status precond_landmarks<float>(agp_plan_s*, int, std::vector<int32_t>&, cudaStream_t);
 template agp_status precond_landmarks<double>(agp_plan_s*, int, std::vector<int32_t>&, cudaStream_t);
-template agp_status precond_build<float>(agp_plan_s*, int, int, Precond*, cudaStream_t);
-template agp_status precond_build<double>(agp_plan_s*, int, int, Precond*, cudaStream_t);
+template agp_status precond_build<float>(agp_plan_s*, int, int, Precond*, cudaStream_t,
+                                         PrecondNlml*);
+template agp_status precond_build<double>(agp_plan_s*, int, int, Precond*, cudaStream_t,
+                                          PrecondNlml*);
+template agp_status precond_affine<float>(const Precond&, double, const float*, int64_t,
+                                          const double*, int, float*, int64_t, cudaStream_t);
+template agp_status precond_affine<double>(const Precond&, double, const double*, int64_t,
+                                           const double*, int, double*, int64_t, cudaStream_t);
+template agp_status precond_bt<float>(const Precond&, int, const double*, int, double*,
+                                      cudaStream_t);
+template agp_status precond_bt<double>(const Precond&, int, const double*, int, double*,
+                                       cudaStream_t);
 template agp_status precond_apply<float>(const Precond&, const double*, double*, int, cudaStream_t);
 template agp_status precond_apply<double>(const Precond&, const double*, double*, int, cudaStream_t);
 

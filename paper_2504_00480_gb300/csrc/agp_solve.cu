@@ -266,9 +266,10 @@ struct Workspace {
   double* scal = nullptr;   // 11 x R doubles
   int* iscal = nullptr;     // 3 x R ints
   double *ahist = nullptr, *bhist = nullptr;
+  double* rz0 = nullptr;    // preconditioned runs: r_0^T M^{-1} r_0 per column
   cudaStream_t st;
   ~Workspace() {
-    void* bufs[] = {x, z, r, p, pt, q, partial, scal, iscal, ahist, bhist};
+    void* bufs[] = {x, z, r, p, pt, q, partial, scal, iscal, ahist, bhist, rz0};
     for (void* b : bufs)
       if (b) cudaFreeAsync(b, st);
   }
@@ -348,6 +349,7 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   AGP_CUDA(cudaMallocAsync(&ws.pt, sizeof(T) * n * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.q, sizeof(T) * n * R, st));
   if (pc) AGP_CUDA(cudaMallocAsync(&ws.z, sizeof(double) * n * R, st));
+  if (pc) AGP_CUDA(cudaMallocAsync(&ws.rz0, sizeof(double) * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.partial, sizeof(double) * kMaxDotBlocks * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.scal, sizeof(double) * 11 * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.iscal, sizeof(int) * 3 * R, st));
@@ -382,6 +384,7 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
     k_copy_block<double, double><<<gb, 256, 0, st>>>(ws.z, R, ws.p, R, n, R);
     k_copy_block<double, T><<<gb, 256, 0, st>>>(ws.z, R, ws.pt, R, n, R);
     AGP_TRY(col_dot(ws.r, R, ws.z, R, n, R, ws.partial, s.rz, st, pl));
+    AGP_CUDA(cudaMemcpyAsync(ws.rz0, s.rz, sizeof(double) * R, cudaMemcpyDeviceToDevice, st));
   } else {
     k_copy_block<T, double><<<gb, 256, 0, st>>>(B, ldb, ws.p, R, n, R);
     k_copy_block<T, T><<<gb, 256, 0, st>>>(B, ldb, ws.pt, R, n, R);
@@ -523,6 +526,161 @@ agp_status nlml_t(agp_plan_s* pl, const T* Y, const T* Z, int64_t ldz, int nz, i
   return AGP_OK;
 }
 
+// Preconditioned NLML estimate and gradient, Sec. 1 eqs. (1.3)-(1.5), with the
+// landmark preconditioner M = B K_LL^{-1} B^T + sigma_eps^2 I of Sec. 2.3:
+//   nlml = 1/2 (y^T alpha + log det M + (1/nz) sum_i q_i + n log 2 pi),
+//   q_i  = (z_i^T M^{-1} z_i) e_1^T log(T_i) e_1  (SLQ of M^{-1/2} K_hat M^{-1/2}),
+//   grad = 1/2 (-alpha^T dK alpha + tr(M^{-1} dM) + (1/nz) sum_i (u_i^T dK p_i - p_i^T dM p_i)),
+// z_i = sigma_eps wn_i + B C^{-T} wk_i (covariance M, C C^T = K_LL), T_i from
+// `steps` PCG steps on K_hat x = z_i, u_i the PCG iterate, p_i = M^{-1} z_i.
+// The k x k algebra runs on the host in FP64: with G = sigma^2 K_LL + B^T B,
+//   log det M = (n - k) log sigma^2 + log det G - log det K_LL,
+//   tr(M^{-1}) = (n - k + sigma^2 tr(G^{-1} K_LL)) / sigma^2,
+//   tr(M^{-1} dM/dell) = 2 tr(G^{-1} B^T B') - tr(K'_LL K_LL^{-1}) + sigma^2 tr(K'_LL G^{-1}),
+// (B' = dB/dell; for sigma_f, B' = (2/sigma_f) B and K'_LL = (2/sigma_f)(K_LL - delta I)
+// with the jitter delta held fixed), dM/dsigma_eps = 2 sigma_eps I.
+template <typename T>
+agp_status nlml_pc_t(agp_plan_s* pl, const T* Y, const T* Wn, int64_t ldwn, const double* Wk_h,
+                     int nz, int n_landmarks, int steps, double rtol, int maxit, double* nlml,
+                     double* grad, cudaStream_t st) {
+  const int64_t n = pl->n;
+  const int R = 1 + nz;
+  const double sig = pl->sigma_eps, s2 = sig * sig, sf = pl->sigma_f;
+  Precond pc;
+  struct Release {
+    Precond* p;
+    ~Release() { precond_free(p); }
+  } release{&pc};
+  PrecondNlml ex;
+  AGP_TRY(precond_build<T>(pl, n_landmarks, R, &pc, st, &ex));
+  const int k = pc.k;
+  auto tr_prod = [&](const std::vector<double>& A, const std::vector<double>& Bm) {
+    double t = 0.0;   // tr(A Bm) = sum_ij A_ij Bm_ji
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) t += A[(size_t)i * k + j] * Bm[(size_t)j * k + i];
+    return t;
+  };
+  // probes: Tk = C^{-T} Wk (back substitution with the lower factor C)
+  std::vector<double> Tk((size_t)k * nz);
+  for (int r = 0; r < nz; ++r)
+    for (int j = k - 1; j >= 0; --j) {
+      double v = Wk_h[(size_t)j * nz + r];
+      for (int i = j + 1; i < k; ++i) v -= ex.Kchol[(size_t)i * k + j] * Tk[(size_t)i * nz + r];
+      Tk[(size_t)j * nz + r] = v / ex.Kchol[(size_t)j * k + j];
+    }
+  T *Bblk = nullptr, *Xs = nullptr, *Din = nullptr, *Dout = nullptr;
+  double *Tk_d = nullptr, *Zd = nullptr, *Pd = nullptr, *dots = nullptr, *part = nullptr;
+  AGP_CUDA(cudaMallocAsync(&Bblk, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&Xs, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&Din, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&Dout, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&Tk_d, sizeof(double) * k * nz, st));
+  AGP_CUDA(cudaMallocAsync(&Zd, sizeof(double) * n * nz, st));
+  AGP_CUDA(cudaMallocAsync(&Pd, sizeof(double) * n * nz, st));
+  AGP_CUDA(cudaMallocAsync(&dots, sizeof(double) * 4 * R, st));
+  AGP_CUDA(cudaMallocAsync(&part, sizeof(double) * kMaxDotBlocks * R, st));
+  struct Free {
+    void* a[9];
+    cudaStream_t st;
+    ~Free() {
+      for (void* p : a) cudaFreeAsync(p, st);
+    }
+  } fr{{Bblk, Xs, Din, Dout, Tk_d, Zd, Pd, dots, part}, st};
+  AGP_CUDA(cudaMemcpyAsync(Tk_d, Tk.data(), sizeof(double) * k * nz, cudaMemcpyHostToDevice, st));
+  k_copy_block<T, T><<<nblk(n, 256), 256, 0, st>>>(Y, 1, Bblk, R, n, 1);
+  pl->launches[3] += 1;
+  AGP_TRY(precond_affine<T>(pc, sig, Wn, ldwn, Tk_d, nz, Bblk + 1, R, st));
+  // PCG on [y, z_1..z_nz]: probes run exactly `steps` steps (their coefficients
+  // give the Lanczos matrices), y to rtol when rtol > 0
+  std::vector<int> mi(R, steps);
+  std::vector<double> tl(R, 0.0);
+  if (rtol > 0) {
+    mi[0] = maxit;
+    tl[0] = rtol;
+  }
+  std::vector<double> h(2 * R);
+  {
+    Workspace<T> ws;
+    AGP_TRY(cg_run<T>(pl, Bblk, R, Xs, R, R, mi, tl, rtol > 0 ? 5 : 0, ws, st, &pc));
+    AGP_TRY(col_dot(Bblk, R, Xs, R, n, 1, ws.partial, dots, st, pl));
+    k_slq_logdet<<<nblk(nz, kSlqThreads), kSlqThreads, 0, st>>>(ws.ahist, ws.bhist, ws.iscal + R,
+                                                                 ws.rz0, R, 1, dots + R);
+    pl->launches[3] += 1;
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaMemcpyAsync(h.data(), dots, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+  }
+  double quad = 0.0;
+  for (int c = 1; c < R; ++c) quad += h[R + c];
+  const double logdet_M = (double)(n - k) * std::log(s2) + ex.logdet_G - ex.logdet_K;
+  *nlml = 0.5 * (h[0] + logdet_M + quad / nz + (double)n * std::log(2.0 * M_PI));
+
+  // p_i = M^{-1} z_i and the small-dimensional terms
+  k_copy_block<T, double><<<nblk(n * nz, 256), 256, 0, st>>>(Bblk + 1, R, Zd, nz, n, nz);
+  pl->launches[3] += 1;
+  AGP_TRY(precond_apply<T>(pc, Zd, Pd, nz, st));
+  std::vector<double> A((size_t)k * nz), E((size_t)k * nz), pp(nz);
+  AGP_TRY(precond_bt<T>(pc, 0, Pd, nz, A.data(), st));
+  AGP_TRY(precond_bt<T>(pc, 1, Pd, nz, E.data(), st));
+  AGP_TRY(col_dot(Pd, nz, Pd, nz, n, nz, part, dots, st, pl));
+  AGP_CUDA(cudaMemcpyAsync(pp.data(), dots, sizeof(double) * nz, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  const double tr_gk = tr_prod(ex.Ginv, ex.K);
+  const double tr_minv = ((double)(n - k) + s2 * tr_gk) / s2;
+  double tr_kinv = 0.0, tr_ginv = 0.0;
+  for (int i = 0; i < k; ++i) {
+    tr_kinv += ex.Kinv[(size_t)i * k + i];
+    tr_ginv += ex.Ginv[(size_t)i * k + i];
+  }
+  // sigma_f: dB = (2/sigma_f) B and dK_LL = (2/sigma_f)(K - delta I) with the
+  // jitter delta held fixed
+  const double tr_dm[3] = {
+      2.0 * tr_prod(ex.Ginv, ex.BtBder) - tr_prod(ex.Kder, ex.Kinv) + s2 * tr_prod(ex.Kder, ex.Ginv),
+      (2.0 / sf) * ((double)k - s2 * tr_gk + ex.delta * tr_kinv - s2 * ex.delta * tr_ginv),
+      2.0 * sig * tr_minv};
+  // p_i^T dM p_i with a = B^T p_i, e = B'^T p_i, v = K_LL^{-1} a
+  std::vector<double> pdp[3] = {std::vector<double>(nz), std::vector<double>(nz),
+                                std::vector<double>(nz)};
+  std::vector<double> v(k);
+  for (int r = 0; r < nz; ++r) {
+    for (int i = 0; i < k; ++i) {
+      double t = 0.0;
+      for (int j = 0; j < k; ++j) t += ex.Kinv[(size_t)i * k + j] * A[(size_t)j * nz + r];
+      v[i] = t;
+    }
+    double va = 0.0, ve = 0.0, vkv = 0.0, vv = 0.0;
+    for (int i = 0; i < k; ++i) {
+      va += v[i] * A[(size_t)i * nz + r];
+      vv += v[i] * v[i];
+      ve += v[i] * E[(size_t)i * nz + r];
+      double t = 0.0;
+      for (int j = 0; j < k; ++j) t += ex.Kder[(size_t)i * k + j] * v[j];
+      vkv += v[i] * t;
+    }
+    pdp[0][r] = 2.0 * ve - vkv;
+    pdp[1][r] = (2.0 / sf) * (va + ex.delta * vv);
+    pdp[2][r] = 2.0 * sig * pp[r];
+  }
+  // dK applied to [alpha, p_1..p_nz], dotted with [alpha, u_1..u_nz]
+  k_copy_block<T, T><<<nblk(n, 256), 256, 0, st>>>(Xs, R, Din, R, n, 1);
+  k_copy_block<double, T><<<nblk(n * nz, 256), 256, 0, st>>>(Pd, nz, Din + 1, R, n, nz);
+  pl->launches[3] += 2;
+  const agp_param ths[3] = {AGP_D_ELL, AGP_D_SIGMA_F, AGP_D_SIGMA_EPS};
+  for (int t = 0; t < 3; ++t) {
+    AGP_TRY(agp_deriv_matvec(pl, ths[t], Din, R, Dout, R, R, st));
+    AGP_TRY(col_dot(Xs, R, Dout, R, n, R, part, dots, st, pl));
+    std::vector<double> g(R);
+    AGP_CUDA(cudaMemcpyAsync(g.data(), dots, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    double smean = 0.0;
+    for (int r = 0; r < nz; ++r) smean += g[1 + r] - pdp[t][r];
+    grad[t] = 0.5 * (-g[0] + tr_dm[t] + smean / nz);
+  }
+  if (!std::isfinite(*nlml))
+    return set_error(AGP_ENAN, "SLQ met a non-positive Ritz value: K_hat is indefinite here");
+  return AGP_OK;
+}
+
 }  // namespace
 }  // namespace agp
 
@@ -559,6 +717,22 @@ agp_status agp_plan_landmarks(agp_plan pl, int n_landmarks, int32_t* idx, int ca
   if ((int)L.size() > cap) return set_error(AGP_EINVAL, "idx holds fewer entries than the landmark set");
   std::copy(L.begin(), L.end(), idx);
   return AGP_OK;
+}
+
+agp_status agp_nlml_grad_pc(agp_plan pl, const void* Y, const void* Wn, int64_t ldwn,
+                            const double* Wk, int nz, int n_landmarks, int lanczos_steps,
+                            double rtol, int maxit, double* nlml, double* grad, void* stream) {
+  if (!pl || !Y || !Wn || !Wk || !nlml || !grad || nz < 1 || nz > 31 || ldwn < nz ||
+      lanczos_steps < 1 || lanczos_steps > kMaxLanczos || (rtol > 0 && maxit < 1) || !(rtol >= 0))
+    return set_error(AGP_EINVAL, "bad arguments");
+  if (n_landmarks < 1 || n_landmarks > kMaxLandmarks)
+    return set_error(AGP_EINVAL, "n_landmarks must be in [1, 480]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl->prec == AGP_F32)
+    return nlml_pc_t<float>(pl, (const float*)Y, (const float*)Wn, ldwn, Wk, nz, n_landmarks,
+                            lanczos_steps, rtol, maxit, nlml, grad, st);
+  return nlml_pc_t<double>(pl, (const double*)Y, (const double*)Wn, ldwn, Wk, nz, n_landmarks,
+                           lanczos_steps, rtol, maxit, nlml, grad, st);
 }
 
 agp_status agp_dot_columns(agp_plan pl, const void* A, int64_t lda, const void* B, int64_t ldb,

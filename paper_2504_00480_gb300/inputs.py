@@ -61,12 +61,18 @@ def rademacher(n: int, R: int, seed: int) -> np.ndarray:
     return rng.integers(0, 2, size=(n, R)).astype(np.float64) * 2.0 - 1.0
 
 
+def gaussian(m: int, R: int, seed: int) -> np.ndarray:
+    """m x R matrix of independent standard normal entries (the vectors w
+    from which the preconditioned likelihood builds its probes)."""
+    return np.random.default_rng(seed).standard_normal((m, R))
+
+
 @dataclass
 class Workload:
     name: str
     X: np.ndarray                 # (n, p) scaled points, float64 holding `dtype` values
     windows: list                 # list of lists of 0-based feature ids
-    kernel: str                   # "gauss" | "matern12"
+    kernel: str                   # "gauss" | "matern12" | "matern32"
     ell: float
     sigma_f: float
     sigma_eps: float

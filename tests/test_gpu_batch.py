@@ -95,3 +95,48 @@ def test_batch_rejects_mixed_cutoff(agp, problems):
     with pytest.raises(agp.AgpError) as ei:
         agp.Batch([plans[0], other])
     assert ei.value.status == agp.AGP_EINVAL
+
+
+def test_uneven_batch_full_size_sampled(agp):
+    # The full uneven-batch workload: 64 problems, n log-uniform in
+    # [1e4, 2e5] (~4e6 points), per-problem lengthscale, matvec and
+    # ell-derivative matvec in one batched launch per stage, captured in a
+    # CUDA graph. Checked on sampled rows of the three smallest problems and
+    # the largest one against the oracle's truncated sum (all n points).
+    ws = inputs.uneven_batch()
+    assert len(ws) == 64 and sum(w.X.shape[0] for w in ws) > 3_000_000
+    plans = [agp.Plan(torch.tensor(w.X, dtype=torch.float32, device=DEV), w.windows, w.N,
+                      w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps) for w in ws]
+    Vs = [torch.tensor(w.V, dtype=torch.float32, device=DEV) for w in ws]
+    Outs = [torch.zeros_like(v) for v in Vs]
+    Ders = [torch.zeros_like(v) for v in Vs]
+    b_mv, b_der = agp.Batch(plans), agp.Batch(plans)
+    b_mv.bind(Vs, Outs)
+    b_der.bind(Vs, Ders)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b_mv.matvec()
+        b_der.matvec("ell")
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(g):
+        b_mv.matvec()
+        b_der.matvec("ell")
+    for o in Outs + Ders:
+        o.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    order = np.argsort([w.X.shape[0] for w in ws])
+    rng = np.random.default_rng(11)
+    for q in list(order[:3]) + [order[-1]]:
+        w = ws[q]
+        rows = np.sort(rng.choice(w.X.shape[0], 16, replace=False))
+        ref = O.truncated_matvec(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps, w.V,
+                                 w.N, rows=rows)
+        assert rel(Outs[q].cpu().numpy()[rows], ref) <= 1e-4, w.name
+        dref = O.truncated_deriv_matvec(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps,
+                                        w.V, w.N, "ell", rows=rows)
+        assert rel(Ders[q].cpu().numpy()[rows], dref) <= 1e-4, w.name
+    b_mv.close()
+    b_der.close()
