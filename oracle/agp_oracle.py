@@ -33,6 +33,10 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
 * ``kb_window_hat``: numerical quadrature of the truncated window.
 * ``nfft``/``nfft_adjoint``: error against the exact NDFT below the window
   error bound of Appendix A.
+* ``afn_*``/``fsai_pattern``: the FSAI factor with a full pattern equals the
+  inverse Cholesky factor of the Schur complement and M equals K_hat; the
+  FSAI defining equations; M's landmark rows equal K_hat's; fill 1 keeps
+  K_hat's diagonal; dense solve and slogdet; finite differences of log det M.
 * ``cg``: dense Cholesky solve; ``slq_quadratic``: eigendecomposition-based
   matrix logarithm with full Krylov space; ``nlml_exact``: scipy's
   multivariate normal log density.
@@ -56,6 +60,8 @@ __all__ = [
     "nlml_exact", "nlml_estimate",
     "landmark_jitter", "nystrom_blocks", "nystrom_matrix", "nystrom_logdet", "nystrom_probes", "pcg_lanczos",
     "nystrom_dM_quadratic", "nystrom_trace_Minv_dM", "nlml_estimate_preconditioned",
+    "afn_split", "fsai_pattern", "afn_factors", "afn_matrix", "afn_apply_inverse",
+    "afn_logdet", "afn_logdet_grad",
 ]
 
 TWO_PI = 2.0 * math.pi
@@ -836,3 +842,128 @@ def nlml_estimate_preconditioned(apply_K, apply_dK, y, Wn, Wk, lanczos_steps, B,
         grads[th] = 0.5 * (-(alpha @ da) + tr_m + float(np.mean(s)))
     return nlml, grads
 
+
+
+# ---------------------------------------------------------------------------
+# Additive AFN preconditioner (Sec. 2.3): Cholesky of the landmark block and
+# a factorised sparse approximate inverse (FSAI) of the Schur complement
+# ---------------------------------------------------------------------------
+
+def afn_split(n, landmarks):
+    """(L, F): the landmark indices (ascending) and the remaining indices
+    (ascending) -- the 2 x 2 block structure of the AFN preconditioner."""
+    L = sorted(set(int(i) for i in landmarks))
+    mask = np.ones(n, dtype=bool)
+    mask[L] = False
+    return L, [int(i) for i in np.nonzero(mask)[0]]
+
+
+def fsai_pattern(X, windows, landmarks, fill):
+    """Sparsity pattern of the lower-triangular FSAI factor of the Schur
+    complement (Sec. 2.3: 'fill level'). Rows and columns are the positions
+    t = 0 .. |F|-1 of the non-landmark points F in ascending index order.
+    Row t holds t and its min(fill - 1, t) nearest earlier positions u < t,
+    by the squared Euclidean distance over the window features (every
+    window's features in window order), evaluated in float32 with one
+    rounding per subtraction, product and sum, in feature order; ties go to
+    the lower position. Returns one ascending position list per row (t last)."""
+    n = X.shape[0]
+    _, F = afn_split(n, landmarks)
+    cols = [c for w in windows for c in w]
+    x = np.asarray(X, dtype=np.float64)[F][:, cols].astype(np.float32)
+    J = []
+    for t in range(len(F)):
+        if t == 0 or fill <= 1:
+            J.append([t])
+            continue
+        acc = np.zeros(t, dtype=np.float32)
+        for c in range(len(cols)):
+            dd = (x[:t, c] - x[t, c]).astype(np.float32)
+            acc = (acc + (dd * dd).astype(np.float32)).astype(np.float32)
+        order = np.lexsort((np.arange(t), acc))     # by distance, then position
+        J.append(sorted(int(u) for u in order[:fill - 1]) + [t])
+    return J
+
+
+def afn_factors(X, windows, kind, ell, sigma_f, sigma_eps, landmarks, fill):
+    """The factors of the AFN preconditioner for K_hat = sigma_f^2 sum_s K_s +
+    sigma_eps^2 I (exact kernel, Sec. 2.1). With the landmarks L first and
+    the rest F after them,
+
+        K_hat = [K_LL  K_LF]   S = K_FF - K_FL K_LL^{-1} K_LF (Schur complement)
+                [K_FL  K_FF],
+
+    (all blocks of K_hat, noise included). Row t of the FSAI factor G is
+    g / sqrt(g_t), g solving S[J_t, J_t] g = e_t on the pattern J_t of
+    fsai_pattern, so that G S G^T has unit diagonal and G^T G approximates
+    S^{-1}. Returns (L, F, K_LL, K_FL, S, G, J) as dense arrays."""
+    n = X.shape[0]
+    L, F = afn_split(n, landmarks)
+    K = dense_matrix(X, windows, kind, ell, sigma_f, sigma_eps)
+    KLL = K[np.ix_(L, L)]
+    KFL = K[np.ix_(F, L)]
+    S = K[np.ix_(F, F)] - KFL @ np.linalg.solve(KLL, KFL.T)
+    S = 0.5 * (S + S.T)
+    J = fsai_pattern(X, windows, landmarks, fill)
+    G = np.zeros((len(F), len(F)))
+    for t, Jt in enumerate(J):
+        e = np.zeros(len(Jt))
+        e[-1] = 1.0
+        g = np.linalg.solve(S[np.ix_(Jt, Jt)], e)
+        G[t, Jt] = g / math.sqrt(g[-1])
+    return L, F, KLL, KFL, S, G, J
+
+
+def afn_matrix(L, F, KLL, KFL, G):
+    """M = Phi diag(K_LL, (G^T G)^{-1}) Phi^T, Phi = [I 0; K_FL K_LL^{-1} I],
+    as an explicit n x n array in the original point order."""
+    n = len(L) + len(F)
+    k = len(L)
+    Phi = np.eye(n)
+    Phi[k:, :k] = np.linalg.solve(KLL, KFL.T).T
+    D = np.zeros((n, n))
+    D[:k, :k] = KLL
+    D[k:, k:] = np.linalg.inv(G.T @ G)
+    Mp = Phi @ D @ Phi.T
+    order = list(L) + list(F)
+    M = np.zeros((n, n))
+    M[np.ix_(order, order)] = 0.5 * (Mp + Mp.T)
+    return M
+
+
+def afn_apply_inverse(L, F, KLL, KFL, G, V):
+    """M^{-1} V in the three block steps of the factorised form:
+    t = V_F - K_FL K_LL^{-1} V_L; w = G^T G t;
+    out_L = K_LL^{-1} (V_L - K_FL^T w), out_F = w."""
+    V = np.asarray(V, dtype=np.float64)
+    VL, VF = V[L], V[F]
+    y = np.linalg.solve(KLL, VL)
+    t = VF - KFL @ y
+    w = G.T @ (G @ t)
+    out = np.zeros_like(V)
+    out[F] = w
+    out[L] = np.linalg.solve(KLL, VL - KFL.T @ w)
+    return out
+
+
+def afn_logdet(KLL, G):
+    """log det M = log det K_LL - 2 sum_t log G_tt (block triangular factors)."""
+    _, ld = np.linalg.slogdet(KLL)
+    return ld - 2.0 * float(np.sum(np.log(np.diag(G))))
+
+
+def afn_logdet_grad(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, G, J, which):
+    """d log det M / dtheta with the landmarks and the pattern held fixed:
+    tr(K_LL^{-1} dK_LL) + sum_t G_t^T dS[J_t, J_t] G_t, because
+    d log G_tt = -1/2 G_t^T dS[J_t, J_t] G_t for G_tt^2 = e_t^T S_JJ^{-1} e_t,
+    and dS = dK_FF - dK_FL A - A^T dK_LF + A^T dK_LL A with A = K_LL^{-1} K_LF."""
+    dK = dense_matrix(X, windows, kind, ell, sigma_f, sigma_eps, which=which)
+    dLL = dK[np.ix_(L, L)]
+    dFL = dK[np.ix_(F, L)]
+    A = np.linalg.solve(KLL, KFL.T)
+    dS = dK[np.ix_(F, F)] - dFL @ A - A.T @ dFL.T + A.T @ dLL @ A
+    out = float(np.trace(np.linalg.solve(KLL, dLL)))
+    for t, Jt in enumerate(J):
+        g = G[t, Jt]
+        out += float(g @ dS[np.ix_(Jt, Jt)] @ g)
+    return out
