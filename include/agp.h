@@ -244,6 +244,52 @@ agp_status agp_nlml_grad_pc(agp_plan plan, const void* Y, const void* Wn, int64_
                             const double* Wk, int nz, int n_landmarks, int lanczos_steps,
                             double rtol, int maxit, double* nlml, double* grad, void* stream);
 
+/* ---- Additive AFN preconditioner (Sec. 2.3) ----------------------------------
+ * The adaptive factorised Nystrom preconditioner for additive kernels: the
+ * landmark block of K_hat is factorised exactly and the Schur complement of
+ * the remaining points is approximated by a factorised sparse approximate
+ * inverse (FSAI) with at most `fill` entries per row. With the landmarks L
+ * first and the other points F (increasing index) after them,
+ *   S = K_FF - K_FL K_LL^{-1} K_LF     (blocks of K_hat, noise included),
+ *   M = Phi diag(K_LL, (G^T G)^{-1}) Phi^T,   Phi = [I 0; K_FL K_LL^{-1} I],
+ * with the exact kernel in FP64. G is lower triangular: row t (the t-th point
+ * of F) holds t and its min(fill - 1, t) nearest earlier points of F, by the
+ * squared Euclidean distance over all window features (in window order)
+ * computed in float32 with one rounding per subtraction, product and sum,
+ * ties to the lower index; on that pattern J_t, G[t, J_t] = g / sqrt(g_t)
+ * with S[J_t, J_t] g = e_t. M's landmark rows equal those of K_hat; with a
+ * full pattern M = K_hat; with fill = 1 G is the inverse square root of S's
+ * diagonal. log det M = log det K_LL - 2 sum_t log G_tt.
+ * The landmark count is the caller's (the paper's adaptive rank estimate is
+ * not made). The object keeps the hyperparameters of the plan at creation;
+ * build a new one after agp_set_hyper. Memory: about (12 fill + 8 k) bytes per
+ * point plus 24 * 32 bytes per point of apply workspace. */
+typedef struct agp_afn_s* agp_afn;
+
+/* Build M for the plan's current hyperparameters. n_landmarks: 1..480,
+ * landmarks chosen as in agp_pcg_solve (agp_plan_landmarks); fill: 1..128.
+ * Needs sigma_eps > 0. Returns AGP_ENAN if a factorisation meets a
+ * non-positive pivot (*out stays NULL). Synchronises `stream`. */
+agp_status agp_afn_create(agp_afn* out, agp_plan plan, int n_landmarks, int fill, void* stream);
+agp_status agp_afn_destroy(agp_afn afn);
+/* Y = M^{-1} V for FP64 device blocks V [n][ldv] and Y [n][ldy] (row-major,
+ * 1 <= R <= 32 columns; Y must not alias V). Asynchronous on `stream`. */
+agp_status agp_afn_apply(agp_afn afn, const double* V, int64_t ldv, double* Y, int64_t ldy, int R,
+                         void* stream);
+/* Size of the landmark set, nonzeros of G and log det M (each may be NULL). */
+agp_status agp_afn_info(agp_afn afn, int* n_landmarks, int64_t* nnz, double* logdet);
+/* Host copies of the landmark indices (int32 [k]) and the pattern (int32
+ * [n - k][fill]: positions in F, increasing, the row's own position last,
+ * -1 after). Either pointer may be NULL. Synchronises `stream`. */
+agp_status agp_afn_pattern(agp_afn afn, int32_t* landmarks, int32_t* J, void* stream);
+/* Preconditioned CG on K_hat Xsol = B with the AFN preconditioner, as
+ * agp_pcg_solve otherwise (R <= 32; stopping test on the unpreconditioned
+ * relative residual). AGP_EINVAL if `afn` was built for other hyperparameters
+ * or another point count. Synchronises `stream`. */
+agp_status agp_pcg_solve_afn(agp_plan plan, agp_afn afn, const void* B, int64_t ldb, void* Xsol,
+                             int64_t ldx, int R, double rtol, int maxit, int* iters,
+                             double* relres, void* stream);
+
 /* ---- Batches of independent problems ----------------------------------------
  * Many independent GP problems of different sizes (independent plans, each
  * with its own points, windows and hyperparameters) applied together: every

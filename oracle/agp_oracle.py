@@ -858,7 +858,7 @@ def afn_split(n, landmarks):
     return L, [int(i) for i in np.nonzero(mask)[0]]
 
 
-def fsai_pattern(X, windows, landmarks, fill):
+def fsai_pattern(X, windows, landmarks, fill, rows=None):
     """Sparsity pattern of the lower-triangular FSAI factor of the Schur
     complement (Sec. 2.3: 'fill level'). Rows and columns are the positions
     t = 0 .. |F|-1 of the non-landmark points F in ascending index order.
@@ -866,13 +866,14 @@ def fsai_pattern(X, windows, landmarks, fill):
     by the squared Euclidean distance over the window features (every
     window's features in window order), evaluated in float32 with one
     rounding per subtraction, product and sum, in feature order; ties go to
-    the lower position. Returns one ascending position list per row (t last)."""
+    the lower position. Returns one ascending position list per row (t last),
+    for every row or for the positions listed in ``rows``."""
     n = X.shape[0]
     _, F = afn_split(n, landmarks)
     cols = [c for w in windows for c in w]
     x = np.asarray(X, dtype=np.float64)[F][:, cols].astype(np.float32)
     J = []
-    for t in range(len(F)):
+    for t in (range(len(F)) if rows is None else rows):
         if t == 0 or fill <= 1:
             J.append([t])
             continue

@@ -74,6 +74,13 @@ _SIGS = {
     "agp_nlml_grad_pc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, POINTER(c_double), c_int,
                                  c_int, c_int, c_double, c_int, POINTER(c_double),
                                  POINTER(c_double), c_void_p]),
+    "agp_afn_create": (c_int, [POINTER(c_void_p), c_void_p, c_int, c_int, c_void_p]),
+    "agp_afn_destroy": (c_int, [c_void_p]),
+    "agp_afn_apply": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p]),
+    "agp_afn_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int64), POINTER(c_double)]),
+    "agp_afn_pattern": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "agp_pcg_solve_afn": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int,
+                                  c_double, c_int, POINTER(c_int), POINTER(c_double), c_void_p]),
     "agp_dot_columns": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int,
                                 POINTER(c_double), c_void_p]),
     "agp_dot_columns_static": (c_int, [c_int, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int,
@@ -286,6 +293,102 @@ def agp_plan_landmarks(plan: c_void_p, n_landmarks: int) -> np.ndarray:
     return np.array(idx[:cnt.value], dtype=np.int64)
 
 
+def agp_afn_create(plan: c_void_p, n_landmarks: int, fill: int) -> c_void_p:
+    h = c_void_p()
+    _check(load_library().agp_afn_create(byref(h), plan, int(n_landmarks), int(fill), _stream()))
+    return h
+
+
+def agp_afn_destroy(afn: c_void_p):
+    _check(load_library().agp_afn_destroy(afn))
+
+
+def agp_afn_apply(afn: c_void_p, V: torch.Tensor, Y: torch.Tensor):
+    """Y = M^{-1} V (float64 CUDA blocks [n][R])."""
+    vp, ldv, R = _block(V, torch.float64, "V")
+    yp, ldy, Ry = _block(Y, torch.float64, "Y")
+    if Ry != R or Y.shape[0] != V.shape[0]:
+        raise ValueError("Y must have V's shape")
+    _check(load_library().agp_afn_apply(afn, vp, ldv, yp, ldy, R, _stream()))
+
+
+def agp_afn_info(afn: c_void_p):
+    """(landmark count, nonzeros of G, log det M)."""
+    k = c_int()
+    nnz = c_int64()
+    ld = c_double()
+    _check(load_library().agp_afn_info(afn, byref(k), byref(nnz), byref(ld)))
+    return k.value, nnz.value, ld.value
+
+
+def agp_afn_pattern(afn: c_void_p, n: int, fill: int):
+    """(landmarks [k], pattern [n - k][fill]) as numpy int arrays."""
+    k, _, _ = agp_afn_info(afn)
+    lm = np.zeros(max(k, 1), dtype=np.int32)
+    J = np.zeros((max(n - k, 1), fill), dtype=np.int32)
+    _check(load_library().agp_afn_pattern(afn, lm.ctypes.data_as(c_void_p),
+                                          J.ctypes.data_as(c_void_p), _stream()))
+    return lm[:k].astype(np.int64), J[:n - k].astype(np.int64)
+
+
+def agp_pcg_solve_afn(plan: c_void_p, afn: c_void_p, B: torch.Tensor, Xsol: torch.Tensor,
+                      rtol: float = 1e-4, maxit: int = 200, raise_not_converged: bool = True):
+    """CG for K_hat X = B preconditioned by the AFN object. Returns (iters, relres)."""
+    bp, ldb, R = _block(B, B.dtype, "B")
+    xp, ldx, Rx = _block(Xsol, B.dtype, "Xsol")
+    if Rx != R or Xsol.shape[0] != B.shape[0]:
+        raise ValueError("Xsol must have B's shape")
+    it = (c_int * R)()
+    rel = (c_double * R)()
+    st = load_library().agp_pcg_solve_afn(plan, afn, bp, ldb, xp, ldx, R, float(rtol), int(maxit),
+                                          it, rel, _stream())
+    if st != AGP_NOT_CONVERGED or raise_not_converged:
+        _check(st)
+    return np.array(it[:], dtype=np.int64), np.array(rel[:], dtype=np.float64)
+
+
+class Afn:
+    """The additive AFN preconditioner of a plan at its current hyperparameters."""
+
+    def __init__(self, plan: "Plan", n_landmarks: int, fill: int):
+        self.plan = plan
+        self.fill = int(fill)
+        self._h = agp_afn_create(plan.handle, n_landmarks, fill)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            agp_afn_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, V: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = torch.empty_like(V) if out is None else out
+        agp_afn_apply(self._h, V, out)
+        return out
+
+    def info(self):
+        return agp_afn_info(self._h)
+
+    def pattern(self):
+        return agp_afn_pattern(self._h, self.plan.n, self.fill)
+
+    def solve(self, B: torch.Tensor, rtol: float = 1e-4, maxit: int = 200,
+              raise_not_converged: bool = True):
+        X = torch.empty_like(B)
+        it, rel = agp_pcg_solve_afn(self.plan.handle, self._h, B, X, rtol, maxit,
+                                    raise_not_converged)
+        return X, it, rel
+
+
 def agp_nlml_grad(plan: c_void_p, y: torch.Tensor, Z: torch.Tensor, lanczos_steps: int = 20,
                   rtol: float = 0.0, maxit: int = 0):
     """(nlml, {"ell": g, "sigma_f": g, "sigma_eps": g}) with probes Z [n][nz]."""
@@ -488,6 +591,9 @@ class Plan:
     def nlml_grad_pc(self, y: torch.Tensor, Wn: torch.Tensor, Wk, n_landmarks: int,
                      lanczos_steps: int = 20, rtol: float = 0.0, maxit: int = 0):
         return agp_nlml_grad_pc(self._h, y, Wn, Wk, n_landmarks, lanczos_steps, rtol, maxit)
+
+    def afn(self, n_landmarks: int, fill: int) -> Afn:
+        return Afn(self, n_landmarks, fill)
 
     def autotune(self, R: int = 32, reps: int = 3):
         return agp_plan_autotune(self._h, R, reps)

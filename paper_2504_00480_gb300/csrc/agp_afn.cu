@@ -1,0 +1,598 @@
+// Additive AFN preconditioner (Sec. 2.3): the landmark block of K_hat is
+// factorised exactly, the Schur complement of the remaining points gets a
+// factorised sparse approximate inverse (FSAI) with a fixed fill level.
+//
+// With the landmarks L (farthest point sampling per window, merged) first
+// and the remaining points F (ascending index) after them,
+//     K_hat = [K_LL K_LF; K_FL K_FF]   (noise sigma_eps^2 on every diagonal),
+//     S = K_FF - K_FL K_LL^{-1} K_LF   (Schur complement, m = n - k rows),
+//     M = Phi diag(K_LL, (G^T G)^{-1}) Phi^T,  Phi = [I 0; K_FL K_LL^{-1} I],
+// where G is lower triangular with at most `fill` entries per row: row t
+// holds t and its fill-1 nearest earlier positions u < t of F (squared
+// Euclidean distance over the window features in float32, rounded after
+// every subtraction, product and sum, in feature order; ties to the lower
+// position), and G[t, J_t] = g / sqrt(g_t) with S[J_t, J_t] g = e_t, so that
+// G S G^T has unit diagonal. With C the lower Cholesky factor of K_LL and
+// W = K_FL C^{-T} ([m][k]),
+//     M^{-1} r:  v = C^{-1} r_L;  t = r_F - W v;  w = G^T G t;
+//                out_F = w;  out_L = C^{-T} (v - W^T w),
+//     log det M = log det K_LL - 2 sum_t log G_tt.
+// Everything is FP64: the exact kernel entries, S[J, J] and its Cholesky
+// factor (one CTA per row of G, in shared memory), and the apply's vectors.
+//
+// Device layout: J and Gval [m][fill] (row-major, positions ascending with
+// t last, -1 / 0 padding), and G^T as compressed columns (colptr [m + 1],
+// colrow, colval) filled once at build time so that the apply gathers
+// instead of scattering.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "agp_exact.cuh"
+
+namespace agp {
+namespace {
+
+constexpr int kKnnWarps = 8;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// out[a][j] = sf2 kernel_sum(rows_a, L_j), FP64 [m][k]
+template <typename T>
+__global__ void k_kernel_rows(const WinPts<T>* __restrict__ wp, int P, int64_t n,
+                              const int32_t* __restrict__ rows, int64_t m,
+                              const int32_t* __restrict__ lm, int k, int kernel, double ell,
+                              double sf2, double* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * k) return;
+  const int64_t a = e / k;
+  const int j = (int)(e - a * k);
+  out[e] = sf2 * kernel_sum<T>(wp, P, n, rows[a], lm[j], kernel, ell, 0);
+}
+
+// W[a][j] = sum_{i <= j} Ci[j][i] Bf[a][i]   (W = Bf C^{-T}, Ci = C^{-1} lower)
+__global__ void k_times_lower_t(const double* __restrict__ Bf, int64_t m, int k,
+                                const double* __restrict__ Ci, double* __restrict__ W) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * k) return;
+  const int64_t a = e / k;
+  const int j = (int)(e - a * k);
+  double s = 0.0;
+  for (int i = 0; i <= j; ++i) s = fma(Ci[(int64_t)j * k + i], Bf[a * k + i], s);
+  W[e] = s;
+}
+
+// xf[c0 + t][a] = float32 of coordinate t of point F_a (one window, caller order [d][n])
+template <typename T>
+__global__ void k_gather_feat(const T* __restrict__ x, int d, int64_t n,
+                              const int32_t* __restrict__ F, int64_t m, int c0,
+                              float* __restrict__ xf) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * d) return;
+  const int t = (int)(e / m);
+  const int64_t a = e - (int64_t)t * m;
+  xf[(int64_t)(c0 + t) * m + a] = (float)x[(int64_t)t * n + F[a]];
+}
+
+// Pattern of row a (one warp per row): the fill-1 nearest earlier positions
+// kept in a list sorted by (distance, position) in shared memory; candidates
+// u = 0 .. a-1 are scanned 32 at a time and inserted one by one. Writes
+// J[a][0 .. len) ascending with a last, -1 after, and len[a].
+__global__ void __launch_bounds__(kKnnWarps * 32)
+k_knn_lower(const float* __restrict__ xf, int pf, int64_t m, int fill, int32_t* __restrict__ J,
+            int32_t* __restrict__ len) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t a = (int64_t)blockIdx.x * kKnnWarps + warp;
+  if (a >= m) return;   // the whole warp leaves together
+  float* ld = reinterpret_cast<float*>(smem_raw) + (size_t)warp * (2 * kAfnMaxFill + pf);
+  int* lp = reinterpret_cast<int*>(ld + kAfnMaxFill);
+  float* q = ld + 2 * kAfnMaxFill;
+  for (int c = lane; c < pf; c += 32) q[c] = xf[(int64_t)c * m + a];
+  __syncwarp();
+  const int cap = fill - 1;
+  int cnt = 0;
+  float thr_d = 0.0f;
+  int thr_p = 0;
+  for (int64_t u0 = 0; u0 < a && cap > 0; u0 += 32) {
+    const int64_t u = u0 + lane;
+    const bool valid = u < a;
+    float dist = 0.0f;
+    if (valid)
+      for (int c = 0; c < pf; ++c) {
+        const float dd = __fsub_rn(xf[(int64_t)c * m + u], q[c]);
+        dist = __fadd_rn(dist, __fmul_rn(dd, dd));
+      }
+    const bool pass =
+        valid && (cnt < cap || dist < thr_d || (dist == thr_d && (int)u < thr_p));
+    unsigned mask = __ballot_sync(kFull, pass);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const float dc = __shfl_sync(kFull, dist, src);
+      const int uc = (int)(u0 + src);
+      if (cnt == cap && !(dc < thr_d || (dc == thr_d && uc < thr_p))) continue;
+      int below = 0;
+      for (int e0 = 0; e0 < cnt; e0 += 32) {
+        const int e = e0 + lane;
+        const bool lt = e < cnt && (ld[e] < dc || (ld[e] == dc && lp[e] < uc));
+        below += __popc(__ballot_sync(kFull, lt));
+      }
+      const int newcnt = min(cnt + 1, cap);
+      float rd[kAfnMaxFill / 32];
+      int rp[kAfnMaxFill / 32];
+#pragma unroll
+      for (int qq = 0; qq < kAfnMaxFill / 32; ++qq) {
+        const int e = lane + 32 * qq;
+        if (e > below && e < newcnt) {
+          rd[qq] = ld[e - 1];
+          rp[qq] = lp[e - 1];
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int qq = 0; qq < kAfnMaxFill / 32; ++qq) {
+        const int e = lane + 32 * qq;
+        if (e > below && e < newcnt) {
+          ld[e] = rd[qq];
+          lp[e] = rp[qq];
+        }
+      }
+      if (lane == 0) {
+        ld[below] = dc;
+        lp[below] = uc;
+      }
+      __syncwarp();
+      cnt = newcnt;
+      if (cnt == cap) {
+        thr_d = ld[cap - 1];
+        thr_p = lp[cap - 1];
+      }
+    }
+  }
+  // ascending positions: the rank of each entry among the chosen positions
+  int32_t* row = J + a * fill;
+  for (int e = lane; e < cnt; e += 32) {
+    const int pe = lp[e];
+    int rank = 0;
+    for (int f = 0; f < cnt; ++f) rank += lp[f] < pe;
+    row[rank] = pe;
+  }
+  for (int e = cnt + lane; e < fill; e += 32) row[e] = e == cnt ? (int32_t)a : -1;
+  if (lane == 0) len[a] = cnt + 1;
+}
+
+// Row a of G (one CTA): S[J, J] in shared memory (lower triangle, stride
+// fill + 1), its Cholesky factor R in place, then R^T g = e_last by columns.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_fsai_rows(const WinPts<T>* __restrict__ wp, int P, int64_t n, const int32_t* __restrict__ F,
+            const double* __restrict__ W, int k, const int32_t* __restrict__ J,
+            const int32_t* __restrict__ len, int fill, int kernel, double ell, double sf2,
+            double s2, double* __restrict__ Gval, double* __restrict__ logdiag,
+            int* __restrict__ flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* S = reinterpret_cast<double*>(smem_raw);
+  __shared__ int pos[kAfnMaxFill], idx[kAfnMaxFill];
+  __shared__ double acc[kAfnMaxFill], g[kAfnMaxFill];
+  const int tid = threadIdx.x, bs = blockDim.x;
+  const int64_t a = blockIdx.x;
+  const int L = len[a];
+  const int ldS = fill + 1;
+  for (int q = tid; q < L; q += bs) {
+    pos[q] = J[a * fill + q];
+    idx[q] = F[pos[q]];
+    acc[q] = 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < L * L; e += bs) {
+    const int i = e / L, j = e - i * L;
+    if (j > i) continue;
+    const double* wi = W + (int64_t)pos[i] * k;
+    const double* wj = W + (int64_t)pos[j] * k;
+    double c = 0.0;
+    for (int q = 0; q < k; ++q) c = fma(wi[q], wj[q], c);
+    S[i * ldS + j] = sf2 * kernel_sum<T>(wp, P, n, idx[i], idx[j], kernel, ell, 0) +
+                     (i == j ? s2 : 0.0) - c;
+  }
+  __syncthreads();
+  for (int j = 0; j < L; ++j) {
+    const double piv = S[j * ldS + j];
+    if (!(piv > 0.0)) {   // the same value for every thread: all leave together
+      if (tid == 0) atomicExch(flag, 1);
+      return;
+    }
+    const double rj = sqrt(piv);
+    __syncthreads();
+    for (int i = j + 1 + tid; i < L; i += bs) S[i * ldS + j] /= rj;
+    if (tid == 0) S[j * ldS + j] = rj;
+    __syncthreads();
+    const int mm = L - j - 1;
+    for (int e = tid; e < mm * mm; e += bs) {
+      const int ii = j + 1 + e / mm, ll = j + 1 + e % mm;
+      if (ll <= ii) S[ii * ldS + ll] -= S[ii * ldS + j] * S[ll * ldS + j];
+    }
+    __syncthreads();
+  }
+  for (int i = L - 1; i >= 0; --i) {
+    if (tid == 0) g[i] = ((i == L - 1 ? 1.0 : 0.0) - acc[i]) / S[i * ldS + i];
+    __syncthreads();
+    for (int j = tid; j < i; j += bs) acc[j] = fma(S[i * ldS + j], g[i], acc[j]);
+    __syncthreads();
+  }
+  for (int q = tid; q < fill; q += bs) Gval[a * fill + q] = q < L ? g[q] : 0.0;
+  if (tid == 0) logdiag[a] = log(g[L - 1]);
+}
+
+__global__ void k_col_count(const int32_t* __restrict__ J, const int32_t* __restrict__ len,
+                            int64_t m, int fill, int32_t* __restrict__ cnt) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * fill) return;
+  const int64_t a = e / fill;
+  if ((int)(e - a * fill) < len[a]) atomicAdd(cnt + J[e], 1);
+}
+
+// exclusive prefix sum of in[0 .. m) into out[0 .. m], one CTA
+__global__ void __launch_bounds__(1024) k_scan(const int32_t* __restrict__ in,
+                                               int32_t* __restrict__ out, int64_t m) {
+  __shared__ int64_t part[1024];
+  const int tid = threadIdx.x;
+  const int64_t per = (m + 1023) / 1024;
+  const int64_t lo = tid * per, hi = min(m, lo + per);
+  int64_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += in[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    int64_t run = 0;
+    for (int q = 0; q < 1024; ++q) {
+      const int64_t v = part[q];
+      part[q] = run;
+      run += v;
+    }
+    out[m] = (int32_t)run;
+  }
+  __syncthreads();
+  int64_t run = part[tid];
+  for (int64_t i = lo; i < hi; ++i) {
+    out[i] = (int32_t)run;
+    run += in[i];
+  }
+}
+
+__global__ void k_col_fill(const int32_t* __restrict__ J, const int32_t* __restrict__ len,
+                           const double* __restrict__ Gval, int64_t m, int fill,
+                           const int32_t* __restrict__ colptr, int32_t* __restrict__ cursor,
+                           int32_t* __restrict__ colrow, double* __restrict__ colval) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * fill) return;
+  const int64_t a = e / fill;
+  if ((int)(e - a * fill) >= len[a]) return;
+  const int v = J[e];
+  const int slot = colptr[v] + atomicAdd(cursor + v, 1);
+  colrow[slot] = (int32_t)a;
+  colval[slot] = Gval[e];
+}
+
+// ---- apply ----
+
+// v[j][r] = sum_{i <= j} Ci[j][i] X[L_i][r]
+__global__ void k_afn_lm_in(const double* __restrict__ X, int64_t ldx,
+                            const int32_t* __restrict__ L, int k, int R,
+                            const double* __restrict__ Ci, double* __restrict__ v) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * R) return;
+  const int j = e / R, r = e - j * R;
+  double s = 0.0;
+  for (int i = 0; i <= j; ++i) s = fma(Ci[(int64_t)j * k + i], X[(int64_t)L[i] * ldx + r], s);
+  v[e] = s;
+}
+
+// t[a][r] = X[F_a][r] - sum_j W[a][j] v[j][r]: a warp per row, lanes = columns,
+// v staged in shared memory
+__global__ void __launch_bounds__(256)
+k_afn_schur_in(const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ F,
+               int64_t m, const double* __restrict__ W, int k, int R,
+               const double* __restrict__ v, double* __restrict__ t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sv = reinterpret_cast<double*>(smem_raw);
+  for (int e = threadIdx.x; e < k * R; e += blockDim.x) sv[e] = v[e];
+  __syncthreads();
+  const int lane = threadIdx.x % 32;
+  if (lane >= R) return;
+  for (int64_t a = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; a < m; a += (int64_t)gridDim.x * 8) {
+    const double* wr = W + a * k;
+    double s = X[(int64_t)F[a] * ldx + lane];
+    for (int j = 0; j < k; ++j) s = fma(-wr[j], sv[j * R + lane], s);
+    t[a * R + lane] = s;
+  }
+}
+
+// u[a][r] = sum_q G[a][q] t[J[a][q]][r]: a warp per row
+__global__ void __launch_bounds__(256)
+k_afn_g(const double* __restrict__ Gval, const int32_t* __restrict__ J,
+        const int32_t* __restrict__ len, int fill, int64_t m, int R, const double* __restrict__ t,
+        double* __restrict__ u) {
+  const int lane = threadIdx.x % 32;
+  if (lane >= R) return;
+  for (int64_t a = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; a < m; a += (int64_t)gridDim.x * 8) {
+    const int L = len[a];
+    double s = 0.0;
+    for (int q = 0; q < L; ++q)
+      s = fma(Gval[a * fill + q], t[(int64_t)J[a * fill + q] * R + lane], s);
+    u[a * R + lane] = s;
+  }
+}
+
+// w[a][r] = sum over column a of G of G[b][a] u[b][r]; also Y[F_a][r] = w
+__global__ void __launch_bounds__(256)
+k_afn_gt(const int32_t* __restrict__ colptr, const int32_t* __restrict__ colrow,
+         const double* __restrict__ colval, int64_t m, int R, const double* __restrict__ u,
+         double* __restrict__ w, const int32_t* __restrict__ F, double* __restrict__ Y,
+         int64_t ldy) {
+  const int lane = threadIdx.x % 32;
+  if (lane >= R) return;
+  for (int64_t a = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; a < m; a += (int64_t)gridDim.x * 8) {
+    double s = 0.0;
+    for (int e = colptr[a]; e < colptr[a + 1]; ++e)
+      s = fma(colval[e], u[(int64_t)colrow[e] * R + lane], s);
+    w[a * R + lane] = s;
+    Y[(int64_t)F[a] * ldy + lane] = s;
+  }
+}
+
+// partial[z][j][r] = sum over the rows a of slice z of W[a][j] w[a][r]
+__global__ void __launch_bounds__(256)
+k_afn_wt(const double* __restrict__ W, const double* __restrict__ w, int64_t m, int k, int R,
+         int64_t rows_per_slice, double* __restrict__ partial) {
+  const int r = threadIdx.x % 32;
+  const int j0 = blockIdx.x * 32 + (threadIdx.x / 32) * 4;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_slice;
+  const int64_t r1 = min(m, r0 + rows_per_slice);
+  if (r >= R) return;
+  int nq = k - j0;
+  nq = nq < 0 ? 0 : (nq > 4 ? 4 : nq);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t a = r0; a < r1; ++a) {
+    const double x = w[a * R + r];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nq) acc[q] = fma(W[a * k + j0 + q], x, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q < nq) partial[((int64_t)blockIdx.y * k + j0 + q) * R + r] = acc[q];
+}
+
+// h[i][r] = v[i][r] - sum_z partial[z][i][r]
+__global__ void k_afn_lm_mid(const double* __restrict__ partial, int nz,
+                             const double* __restrict__ v, int k, int R, double* __restrict__ h) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * R) return;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += partial[(int64_t)z * k * R + e];
+  h[e] = v[e] - s;
+}
+
+// Y[L_j][r] = sum_{i >= j} Ci[i][j] h[i][r]
+__global__ void k_afn_lm_out(const double* __restrict__ h, const int32_t* __restrict__ L, int k,
+                             int R, const double* __restrict__ Ci, double* __restrict__ Y,
+                             int64_t ldy) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * R) return;
+  const int j = e / R, r = e - j * R;
+  double s = 0.0;
+  for (int i = j; i < k; ++i) s = fma(Ci[(int64_t)i * k + j], h[(int64_t)i * R + r], s);
+  Y[(int64_t)L[j] * ldy + r] = s;
+}
+
+}  // namespace
+
+void afn_free(Afn* af) {
+  if (!af) return;
+  for (void* p : {(void*)af->L, (void*)af->F, (void*)af->Ci, (void*)af->W, (void*)af->J,
+                  (void*)af->len, (void*)af->Gval, (void*)af->colptr, (void*)af->colrow,
+                  (void*)af->colval, (void*)af->v, (void*)af->t, (void*)af->u, (void*)af->w,
+                  (void*)af->partial, (void*)af->h})
+    cudaFree(p);
+  *af = Afn();
+}
+
+template <typename T>
+agp_status afn_build(agp_plan_s* pl, int k_req, int fill, int rmax, Afn* af, cudaStream_t st) {
+  const int64_t n = pl->n;
+  const int P = pl->P;
+  if (!(pl->sigma_eps > 0)) return set_error(AGP_EINVAL, "the AFN preconditioner needs sigma_eps > 0");
+  if (fill < 1 || fill > kAfnMaxFill) return set_error(AGP_EINVAL, "AFN fill must be in 1..128");
+  if (k_req < 1 || k_req > kMaxLandmarks)
+    return set_error(AGP_EINVAL, "AFN landmarks must be in 1..480");
+  if (rmax < 1 || rmax > 32) return set_error(AGP_EINVAL, "AFN: 1..32 right-hand sides");
+  CallerPoints<T> cp;
+  AGP_TRY(caller_points<T>(pl, cp, st));
+  std::vector<int32_t> lms;
+  AGP_TRY(select_landmarks<T>(pl, cp, k_req, lms, st));
+  const int k = (int)lms.size();
+  if (k > kMaxLandmarkSet) return set_error(AGP_EINVAL, "AFN: more than 512 landmarks after merging");
+  std::vector<int32_t> fh;
+  fh.reserve(n - k);
+  {
+    size_t q = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (q < lms.size() && lms[q] == i) {
+        ++q;
+        continue;
+      }
+      fh.push_back((int32_t)i);
+    }
+  }
+  const int64_t m = (int64_t)fh.size();
+  af->n = n;
+  af->m = m;
+  af->k = k;
+  af->fill = fill;
+  af->rmax = rmax;
+  af->ell = pl->ell;
+  af->sigma_f = pl->sigma_f;
+  af->sigma_eps = pl->sigma_eps;
+  af->kernel = pl->kernel;
+  af->landmarks = lms;
+  const double sf2 = pl->sigma_f * pl->sigma_f;
+  const double s2 = pl->sigma_eps * pl->sigma_eps;
+  WinPts<T>* wpd = nullptr;
+  AGP_CUDA(cudaMallocAsync(&wpd, sizeof(WinPts<T>) * P, st));
+  AGP_CUDA(cudaMemcpyAsync(wpd, cp.wp.data(), sizeof(WinPts<T>) * P, cudaMemcpyHostToDevice, st));
+  AGP_CUDA(cudaMalloc(&af->L, sizeof(int32_t) * k));
+  AGP_CUDA(cudaMemcpyAsync(af->L, lms.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
+  // K_LL (noise included) -> C -> Ci = C^{-1}, log det K_LL
+  double *KLL = nullptr, *dg = nullptr;
+  int* flag = nullptr;
+  AGP_CUDA(cudaMallocAsync(&KLL, sizeof(double) * k * k, st));
+  AGP_CUDA(cudaMallocAsync(&dg, sizeof(double) * k, st));
+  AGP_CUDA(cudaMallocAsync(&flag, sizeof(int), st));
+  AGP_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  AGP_CUDA(cudaMalloc(&af->Ci, sizeof(double) * k * k));
+  k_kernel_block<T><<<nblk((int64_t)k * k, 256), 256, 0, st>>>(wpd, P, n, af->L, k, pl->kernel,
+                                                               pl->ell, sf2, 0, s2, KLL);
+  k_cholesky<<<1, 1024, 0, st>>>(KLL, k, flag);
+  k_tri_inverse<<<nblk(k, 128), 128, 0, st>>>(KLL, k, af->Ci);
+  k_diag<<<nblk(k, 128), 128, 0, st>>>(KLL, k, dg);
+  std::vector<double> diag(k);
+  int hflag = 0;
+  AGP_CUDA(cudaGetLastError());
+  AGP_CUDA(cudaMemcpyAsync(diag.data(), dg, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  cudaFreeAsync(KLL, st);
+  cudaFreeAsync(dg, st);
+  if (hflag) {
+    cudaFreeAsync(flag, st);
+    cudaFreeAsync(wpd, st);
+    return set_error(AGP_ENAN, "AFN: the landmark block is not positive definite");
+  }
+  double logdet = 0.0;
+  for (int j = 0; j < k; ++j) logdet += 2.0 * std::log(diag[j]);
+  if (m > 0) {
+    AGP_CUDA(cudaMalloc(&af->F, sizeof(int32_t) * m));
+    AGP_CUDA(cudaMemcpyAsync(af->F, fh.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    // W = K_FL C^{-T}
+    double* Bf = nullptr;
+    AGP_CUDA(cudaMallocAsync(&Bf, sizeof(double) * m * k, st));
+    AGP_CUDA(cudaMalloc(&af->W, sizeof(double) * m * k));
+    k_kernel_rows<T><<<nblk(m * k, 256), 256, 0, st>>>(wpd, P, n, af->F, m, af->L, k, pl->kernel,
+                                                       pl->ell, sf2, Bf);
+    k_times_lower_t<<<nblk(m * k, 256), 256, 0, st>>>(Bf, m, k, af->Ci, af->W);
+    cudaFreeAsync(Bf, st);
+    // pattern: float32 window features of F, nearest earlier positions
+    int pf = 0;
+    for (int s = 0; s < P; ++s) pf += pl->win[s].d;
+    float* xf = nullptr;
+    AGP_CUDA(cudaMallocAsync(&xf, sizeof(float) * pf * m, st));
+    for (int s = 0, c0 = 0; s < P; c0 += pl->win[s].d, ++s)
+      k_gather_feat<T><<<nblk(m * pl->win[s].d, 256), 256, 0, st>>>(
+          cp.xo[s], pl->win[s].d, n, af->F, m, c0, xf);
+    AGP_CUDA(cudaMalloc(&af->J, sizeof(int32_t) * m * fill));
+    AGP_CUDA(cudaMalloc(&af->len, sizeof(int32_t) * m));
+    const size_t ksmem = sizeof(float) * kKnnWarps * (2 * kAfnMaxFill + pf);
+    AGP_CUDA(cudaFuncSetAttribute(k_knn_lower, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ksmem));
+    k_knn_lower<<<nblk(m, kKnnWarps), kKnnWarps * 32, ksmem, st>>>(xf, pf, m, fill, af->J,
+                                                                   af->len);
+    cudaFreeAsync(xf, st);
+    // FSAI rows
+    double* logdiag = nullptr;
+    AGP_CUDA(cudaMallocAsync(&logdiag, sizeof(double) * m, st));
+    AGP_CUDA(cudaMalloc(&af->Gval, sizeof(double) * m * fill));
+    const size_t fsmem = sizeof(double) * (size_t)fill * (fill + 1);
+    AGP_CUDA(cudaFuncSetAttribute(k_fsai_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fsmem));
+    const int fthreads = fill <= 32 ? 64 : (fill <= 64 ? 128 : 256);
+    k_fsai_rows<T><<<(unsigned)m, fthreads, fsmem, st>>>(wpd, P, n, af->F, af->W, k, af->J,
+                                                         af->len, fill, pl->kernel, pl->ell, sf2,
+                                                         s2, af->Gval, logdiag, flag);
+    // G^T as compressed columns
+    int32_t *cnt = nullptr, *cursor = nullptr;
+    AGP_CUDA(cudaMallocAsync(&cnt, sizeof(int32_t) * m, st));
+    AGP_CUDA(cudaMallocAsync(&cursor, sizeof(int32_t) * m, st));
+    AGP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * m, st));
+    AGP_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * m, st));
+    AGP_CUDA(cudaMalloc(&af->colptr, sizeof(int32_t) * (m + 1)));
+    k_col_count<<<nblk(m * fill, 256), 256, 0, st>>>(af->J, af->len, m, fill, cnt);
+    k_scan<<<1, 1024, 0, st>>>(cnt, af->colptr, m);
+    int32_t nnz = 0;
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaMemcpyAsync(&nnz, af->colptr + m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    af->nnz = nnz;
+    AGP_CUDA(cudaMalloc(&af->colrow, sizeof(int32_t) * std::max<int64_t>(1, nnz)));
+    AGP_CUDA(cudaMalloc(&af->colval, sizeof(double) * std::max<int64_t>(1, nnz)));
+    k_col_fill<<<nblk(m * fill, 256), 256, 0, st>>>(af->J, af->len, af->Gval, m, fill, af->colptr,
+                                                    cursor, af->colrow, af->colval);
+    std::vector<double> ld(m);
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaMemcpyAsync(ld.data(), logdiag, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    cudaFreeAsync(cnt, st);
+    cudaFreeAsync(cursor, st);
+    cudaFreeAsync(logdiag, st);
+    if (hflag) {
+      cudaFreeAsync(flag, st);
+      cudaFreeAsync(wpd, st);
+      return set_error(AGP_ENAN, "AFN: a Schur complement block is not positive definite");
+    }
+    for (int64_t a = 0; a < m; ++a) logdet -= 2.0 * ld[a];
+  }
+  af->logdet = logdet;
+  cudaFreeAsync(flag, st);
+  cudaFreeAsync(wpd, st);
+  // apply workspace
+  af->slices = (int)std::min<int64_t>(256, std::max<int64_t>(1, (m + 2047) / 2048));
+  af->rows_per_slice = std::max<int64_t>(1, (m + af->slices - 1) / af->slices);
+  AGP_CUDA(cudaMalloc(&af->v, sizeof(double) * k * rmax));
+  AGP_CUDA(cudaMalloc(&af->h, sizeof(double) * k * rmax));
+  AGP_CUDA(cudaMalloc(&af->partial, sizeof(double) * af->slices * k * rmax));
+  if (m > 0) {
+    AGP_CUDA(cudaMalloc(&af->t, sizeof(double) * m * rmax));
+    AGP_CUDA(cudaMalloc(&af->u, sizeof(double) * m * rmax));
+    AGP_CUDA(cudaMalloc(&af->w, sizeof(double) * m * rmax));
+  }
+  AGP_CUDA(cudaMemsetAsync(af->partial, 0, sizeof(double) * af->slices * k * rmax, st));
+  return cuda_status(cudaGetLastError(), "afn_build");
+}
+
+agp_status afn_apply(const Afn& af, const double* X, int64_t ldx, double* Y, int64_t ldy, int R,
+                     cudaStream_t st) {
+  if (R < 1 || R > af.rmax) return set_error(AGP_EINVAL, "AFN apply: too many columns");
+  const int k = af.k;
+  const int64_t m = af.m;
+  k_afn_lm_in<<<nblk((int64_t)k * R, 128), 128, 0, st>>>(X, ldx, af.L, k, R, af.Ci, af.v);
+  if (m > 0) {
+    const unsigned blocks = (unsigned)std::min<int64_t>(nblk(m, 8), 152 * 16);
+    const size_t smem = sizeof(double) * (size_t)k * R;
+    AGP_CUDA(cudaFuncSetAttribute(k_afn_schur_in, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(double) * kMaxLandmarkSet * 32)));
+    k_afn_schur_in<<<blocks, 256, smem, st>>>(X, ldx, af.F, m, af.W, k, R, af.v, af.t);
+    k_afn_g<<<blocks, 256, 0, st>>>(af.Gval, af.J, af.len, af.fill, m, R, af.t, af.u);
+    k_afn_gt<<<blocks, 256, 0, st>>>(af.colptr, af.colrow, af.colval, m, R, af.u, af.w, af.F, Y,
+                                     ldy);
+    k_afn_wt<<<dim3((k + 31) / 32, af.slices), 256, 0, st>>>(af.W, af.w, m, k, R,
+                                                            af.rows_per_slice, af.partial);
+  }
+  k_afn_lm_mid<<<nblk((int64_t)k * R, 128), 128, 0, st>>>(af.partial, m > 0 ? af.slices : 0, af.v,
+                                                         k, R, af.h);
+  k_afn_lm_out<<<nblk((int64_t)k * R, 128), 128, 0, st>>>(af.h, af.L, k, R, af.Ci, Y, ldy);
+  return cuda_status(cudaGetLastError(), "afn_apply");
+}
+
+agp_status afn_pattern(const Afn& af, int32_t* landmarks, int32_t* J, cudaStream_t st) {
+  if (landmarks) std::copy(af.landmarks.begin(), af.landmarks.end(), landmarks);
+  if (J && af.m > 0) {
+    AGP_CUDA(cudaMemcpyAsync(J, af.J, sizeof(int32_t) * af.m * af.fill, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+  }
+  return AGP_OK;
+}
+
+template agp_status afn_build<float>(agp_plan_s*, int, int, int, Afn*, cudaStream_t);
+template agp_status afn_build<double>(agp_plan_s*, int, int, int, Afn*, cudaStream_t);
+
+}  // namespace agp

@@ -239,6 +239,38 @@ agp_status precond_landmarks(agp_plan_s* pl, int k, std::vector<int32_t>& out, c
 template <typename T>
 agp_status precond_apply(const Precond& pc, const double* X, double* Y, int R, cudaStream_t st);
 
+// ---- additive AFN preconditioner (agp_afn.cu) ----
+// M = Phi diag(K_LL, (G^T G)^{-1}) Phi^T with the landmark block factorised
+// exactly and G the FSAI factor of the Schur complement (FP64 throughout).
+constexpr int kAfnMaxFill = 128;
+struct Afn {
+  int64_t n = 0, m = 0, nnz = 0, rows_per_slice = 0;
+  int k = 0, fill = 0, rmax = 0, slices = 0, kernel = 0;
+  double ell = 0, sigma_f = 0, sigma_eps = 0;   // hyperparameters it was built for
+  double logdet = 0;                            // log det M
+  std::vector<int32_t> landmarks;               // host copy of L
+  int32_t* L = nullptr;       // [k] landmark indices (ascending)
+  int32_t* F = nullptr;       // [m] the other indices (ascending)
+  double* Ci = nullptr;       // [k][k] C^{-1}, C the lower Cholesky factor of K_LL
+  double* W = nullptr;        // [m][k] K_FL C^{-T}
+  int32_t* J = nullptr;       // [m][fill] pattern positions, ascending, row's own last
+  int32_t* len = nullptr;     // [m] entries per row
+  double* Gval = nullptr;     // [m][fill]
+  int32_t* colptr = nullptr;  // G^T: [m + 1]
+  int32_t* colrow = nullptr;  // [nnz]
+  double* colval = nullptr;   // [nnz]
+  double *v = nullptr, *h = nullptr, *partial = nullptr;   // apply workspace
+  double *t = nullptr, *u = nullptr, *w = nullptr;
+};
+void afn_free(Afn* af);
+template <typename T>
+agp_status afn_build(agp_plan_s* pl, int k, int fill, int rmax, Afn* af, cudaStream_t st);
+// Y = M^{-1} X for FP64 blocks X [n][ldx], Y [n][ldy], R <= rmax columns.
+agp_status afn_apply(const Afn& af, const double* X, int64_t ldx, double* Y, int64_t ldy, int R,
+                     cudaStream_t st);
+// Host copies of the landmarks [k] and the pattern [m][fill] (either may be null).
+agp_status afn_pattern(const Afn& af, int32_t* landmarks, int32_t* J, cudaStream_t st);
+
 // ---- DFT stages (agp_fft.cu), one launch per stage for a group of windows ----
 template <typename T>
 cudaError_t fft_forward(const FftGroup& g, int RC, cudaStream_t st);   // grid -> spectrum

@@ -27,23 +27,10 @@
 #include <cmath>
 #include <vector>
 
-#include "agp_internal.cuh"
+#include "agp_exact.cuh"
 
 namespace agp {
 namespace {
-
-#define AGP_CUDA(call)                                             \
-  do {                                                             \
-    cudaError_t e_ = (call);                                       \
-    if (e_ != cudaSuccess) return cuda_status(e_, #call);          \
-  } while (0)
-#define AGP_TRY(call)                                              \
-  do {                                                             \
-    agp_status s_ = (call);                                        \
-    if (s_ != AGP_OK) return s_;                                   \
-  } while (0)
-
-inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // One step of Dot2: (s, c) += a * b with the product split exactly into
 // p + e and an error-free two-sum of s and p; the rounding errors collect in
@@ -67,116 +54,6 @@ __global__ void k_split(const double* __restrict__ x, int64_t m, float* __restri
   const float h = __double2float_rn(v);
   hi[e] = h;
   lo[e] = __double2float_rn(v - (double)h);
-}
-
-// sorted [d][n] coordinates -> caller order [d][n]
-template <typename T>
-__global__ void k_unsort(const T* __restrict__ xs, const int32_t* __restrict__ perm, int64_t n,
-                         int d, T* __restrict__ out) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= n * d) return;
-  const int t = (int)(e / n);
-  const int64_t q = e - (int64_t)t * n;
-  out[(int64_t)t * n + perm[q]] = xs[e];
-}
-
-__global__ void k_fill_double(double* __restrict__ p, int64_t n, double v) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < n) p[e] = v;
-}
-
-// One FPS step: fold the previous landmark into the running minimum distances
-// and record the argmax as key (distance bits << 32 | ~index).
-template <typename T>
-__global__ void k_fps_step(const T* __restrict__ x, int64_t n, int d, int step,
-                           unsigned long long* __restrict__ keys, double* __restrict__ dist) {
-  const unsigned last = (step == 1) ? 0u : 0xFFFFFFFFu - (unsigned)(keys[step - 1] & 0xFFFFFFFFull);
-  double xl[3] = {0, 0, 0};
-  for (int t = 0; t < d; ++t) xl[t] = (double)x[(int64_t)t * n + last];
-  unsigned long long best = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    // explicit rounding (no fused multiply-add): the squared distance is the
-    // plainly rounded sum ((u_0^2 + u_1^2) + u_2^2), so the choice does not
-    // depend on how the compiler contracts it
-    double d2 = 0.0;
-    for (int t = 0; t < d; ++t) {
-      const double u = (double)x[(int64_t)t * n + i] - xl[t];
-      d2 = __dadd_rn(d2, __dmul_rn(u, u));
-    }
-    const double m = fmin(dist[i], d2);
-    dist[i] = m;
-    const unsigned long long key =
-        ((unsigned long long)__float_as_uint((float)m) << 32) | (0xFFFFFFFFull - (unsigned long long)i);
-    best = key > best ? key : best;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-    best = other > best ? other : best;
-  }
-  if ((threadIdx.x & 31) == 0) atomicMax(keys + step, best);
-}
-
-// B[i][j] = sigma_f^2 sum_s kappa_s(|x_i^s - x_{L_j}^s|) (exact kernel, Sec. 2.1)
-template <typename T>
-struct WinPts {
-  const T* x;   // caller order [d][n]
-  int d;
-};
-
-// sum_s kappa_s(|x_i^s - x_l^s|) (der = 0) or its ell-derivative (der = 1;
-// Sec. 2.1 eq. (2.3): Gaussian kappa r^2 / ell^3, Matern(1/2) kappa r / ell^2,
-// Matern(3/2) r^2 / ell^3 e^{-r/ell}),
-// exact kernel in FP64 from the plan-precision coordinates
-template <typename T>
-__device__ double kernel_sum(const WinPts<T>* __restrict__ wp, int P, int64_t n, int64_t i,
-                             int64_t l, int kernel, double ell, int der) {
-  double s = 0.0;
-  for (int w = 0; w < P; ++w) {
-    const WinPts<T> p = wp[w];
-    double r2 = 0.0;
-    for (int t = 0; t < p.d; ++t) {
-      const double u = (double)p.x[(int64_t)t * n + i] - (double)p.x[(int64_t)t * n + l];
-      r2 += u * u;
-    }
-    if (kernel == AGP_GAUSS) {
-      const double kv = exp(-r2 / (2.0 * ell * ell));
-      s += der ? kv * r2 / (ell * ell * ell) : kv;
-    } else if (kernel == AGP_MATERN12) {
-      const double r = sqrt(r2);
-      const double kv = exp(-r / ell);
-      s += der ? kv * r / (ell * ell) : kv;
-    } else {   // Matern(3/2)
-      const double r = sqrt(r2);
-      const double ex = exp(-r / ell);
-      s += der ? r2 / (ell * ell * ell) * ex : (1.0 + r / ell) * ex;
-    }
-  }
-  return s;
-}
-
-// B[i][j] = sigma_f^2 kernel_sum(i, L_j) (or its ell-derivative), [n][k]
-template <typename T>
-__global__ void k_kernel_cols(const WinPts<T>* __restrict__ wp, int P, int64_t n,
-                              const int32_t* __restrict__ lm, int k, int kernel, double ell,
-                              double sf2, int der, T* __restrict__ B) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= n * k) return;
-  const int64_t i = e / k;
-  const int j = (int)(e - i * k);
-  B[e] = (T)(sf2 * kernel_sum<T>(wp, P, n, i, lm[j], kernel, ell, der));
-}
-
-// K_LL[a][b] = sigma_f^2 kernel_sum(L_a, L_b) + delta [a == b] in FP64 (or the
-// ell-derivative block with delta = 0)
-template <typename T>
-__global__ void k_kernel_block(const WinPts<T>* __restrict__ wp, int P, int64_t n,
-                               const int32_t* __restrict__ lm, int k, int kernel, double ell,
-                               double sf2, int der, double delta, double* __restrict__ K) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= k * k) return;
-  const int a = e / k, b = e - a * k;
-  K[e] = sf2 * kernel_sum<T>(wp, P, n, lm[a], lm[b], kernel, ell, der) + (a == b ? delta : 0.0);
 }
 
 // G += B^T C over a slice of rows (C = B for the Gram matrix): 32 x 32 output
@@ -223,62 +100,6 @@ __global__ void k_axpy(const double* __restrict__ a, double s, const double* __r
                        int64_t m, double* __restrict__ out) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e < m) out[e] = s * a[e] + b[e];
-}
-
-// A[j][j] += delta
-__global__ void k_shift_diag(double* __restrict__ A, int k, double delta) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < k) A[(int64_t)j * k + j] += delta;
-}
-
-__global__ void k_diag(const double* __restrict__ A, int k, double* __restrict__ d) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < k) d[j] = A[(int64_t)j * k + j];
-}
-
-// In-place lower Cholesky factor of G (k x k, FP64) by one CTA; flag = 1 on a
-// non-positive pivot.
-__global__ void __launch_bounds__(1024) k_cholesky(double* __restrict__ G, int k, int* flag) {
-  for (int j = 0; j < k; ++j) {
-    __syncthreads();
-    const double piv = G[(int64_t)j * k + j];
-    if (!(piv > 0.0)) {
-      if (threadIdx.x == 0) *flag = 1;
-      return;
-    }
-    const double lj = sqrt(piv);
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(int64_t)i * k + j] /= lj;
-    if (threadIdx.x == 0) G[(int64_t)j * k + j] = lj;
-    __syncthreads();
-    const int m = k - j - 1;   // trailing lower triangle, rows/cols j+1 .. k-1
-    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-      const int ii = j + 1 + (int)(e / m), ll = j + 1 + (int)(e % m);
-      if (ll <= ii) G[(int64_t)ii * k + ll] -= G[(int64_t)ii * k + j] * G[(int64_t)ll * k + j];
-    }
-  }
-}
-
-// Column j of L^{-1} by forward substitution (thread per column).
-__global__ void k_tri_inverse(const double* __restrict__ L, int k, double* __restrict__ Li) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= k) return;
-  for (int i = 0; i < j; ++i) Li[(int64_t)i * k + j] = 0.0;
-  for (int i = j; i < k; ++i) {
-    double s = (i == j) ? 1.0 : 0.0;
-    for (int m = j; m < i; ++m) s -= L[(int64_t)i * k + m] * Li[(int64_t)m * k + j];
-    Li[(int64_t)i * k + j] = s / L[(int64_t)i * k + i];
-  }
-}
-
-// Ginv = L^{-T} L^{-1}
-__global__ void k_gram_inverse(const double* __restrict__ Li, int k, double* __restrict__ Gi) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= k * k) return;
-  const int a = e / k, b = e - a * k;
-  double s = 0.0;
-  for (int m = max(a, b); m < k; ++m) s += Li[(int64_t)m * k + a] * Li[(int64_t)m * k + b];
-  Gi[e] = s;
 }
 
 // Apply step 1: partial[z][j][r] = sum over row slice z of B[i][j] * X[i][r].
@@ -423,18 +244,6 @@ void precond_free(Precond* pc) {
   *pc = Precond();
 }
 
-// Caller-order coordinates of every window (freed with the object).
-template <typename T>
-struct CallerPoints {
-  std::vector<T*> xo;
-  std::vector<WinPts<T>> wp;
-  cudaStream_t st = nullptr;
-  ~CallerPoints() {
-    for (T* p : xo)
-      if (p) cudaFreeAsync(p, st);
-  }
-};
-
 template <typename T>
 agp_status caller_points(agp_plan_s* pl, CallerPoints<T>& cp, cudaStream_t st) {
   const int64_t n = pl->n;
@@ -451,8 +260,6 @@ agp_status caller_points(agp_plan_s* pl, CallerPoints<T>& cp, cudaStream_t st) {
   return cuda_status(cudaGetLastError(), "caller_points");
 }
 
-// Landmarks: ceil(k_req / P) per window by farthest point sampling, merged
-// into a sorted set without repeats (host vector).
 template <typename T>
 agp_status select_landmarks(agp_plan_s* pl, const CallerPoints<T>& cp, int k_req,
                             std::vector<int32_t>& all, cudaStream_t st) {
@@ -705,6 +512,12 @@ agp_status precond_landmarks(agp_plan_s* pl, int k, std::vector<int32_t>& out, c
   return select_landmarks<T>(pl, cp, k, out, st);
 }
 
+template agp_status caller_points<float>(agp_plan_s*, CallerPoints<float>&, cudaStream_t);
+template agp_status caller_points<double>(agp_plan_s*, CallerPoints<double>&, cudaStream_t);
+template agp_status select_landmarks<float>(agp_plan_s*, const CallerPoints<float>&, int,
+                                            std::vector<int32_t>&, cudaStream_t);
+template agp_status select_landmarks<double>(agp_plan_s*, const CallerPoints<double>&, int,
+                                             std::vector<int32_t>&, cudaStream_t);
 template agp_status precond_landmarks<float>(agp_plan_s*, int, std::vector<int32_t>&, cudaStream_t);
 template agp_status precond_landmarks<double>(agp_plan_s*, int, std::vector<int32_t>&, cudaStream_t);
 template agp_status precond_build<float>(agp_plan_s*, int, int, Precond*, cudaStream_t,

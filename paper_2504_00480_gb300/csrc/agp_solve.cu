@@ -332,14 +332,21 @@ agp_status col_dot(const TA* A, int64_t lda, const TB* B, int64_t ldb, int64_t n
 // tolerances come from maxit_h / tol_h. On return ws holds the alpha/beta
 // history and the per-column state (scal layout: rr, bn2, pq, alpha, beta,
 // relres, rrnew, spare; iscal: active, iters, maxit).
-// With pc != nullptr the recursion is preconditioned CG: z = M^{-1} r,
+// With pc != nullptr (landmark preconditioner) or afn != nullptr (AFN) the
+// recursion is preconditioned CG: z = M^{-1} r,
 // alpha = r^T z / p^T K p, beta = r_new^T z_new / r^T z, p = z + beta p; the
 // stopping test stays on the unpreconditioned relative residual.
 template <typename T>
 agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int R,
                   const std::vector<int>& maxit_h, const std::vector<double>& tol_h, int check_every,
-                  Workspace<T>& ws, cudaStream_t st, const Precond* pc = nullptr) {
+                  Workspace<T>& ws, cudaStream_t st, const Precond* pc = nullptr,
+                  const Afn* afn = nullptr) {
   const int64_t n = pl->n;
+  const bool pcon = pc || afn;
+  auto apply_pc = [&]() -> agp_status {
+    pl->launches[3] += 1;
+    return afn ? afn_apply(*afn, ws.r, R, ws.z, R, R, st) : precond_apply<T>(*pc, ws.r, ws.z, R, st);
+  };
   int maxall = 0;
   for (int v : maxit_h) maxall = std::max(maxall, v);
   ws.st = st;
@@ -348,8 +355,8 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   AGP_CUDA(cudaMallocAsync(&ws.p, sizeof(double) * n * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.pt, sizeof(T) * n * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.q, sizeof(T) * n * R, st));
-  if (pc) AGP_CUDA(cudaMallocAsync(&ws.z, sizeof(double) * n * R, st));
-  if (pc) AGP_CUDA(cudaMallocAsync(&ws.rz0, sizeof(double) * R, st));
+  if (pcon) AGP_CUDA(cudaMallocAsync(&ws.z, sizeof(double) * n * R, st));
+  if (pcon) AGP_CUDA(cudaMallocAsync(&ws.rz0, sizeof(double) * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.partial, sizeof(double) * kMaxDotBlocks * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.scal, sizeof(double) * 11 * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.iscal, sizeof(int) * 3 * R, st));
@@ -371,7 +378,7 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   s.bhist = ws.bhist;
   s.rz = ws.scal + 9 * R;
   s.rznew = ws.scal + 10 * R;
-  s.pc = pc ? 1 : 0;
+  s.pc = pcon ? 1 : 0;
   AGP_CUDA(cudaMemcpyAsync(s.maxit, maxit_h.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
   AGP_CUDA(cudaMemcpyAsync(s.tol, tol_h.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
 
@@ -379,8 +386,8 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   k_zero_block<double><<<gb, 256, 0, st>>>(ws.x, R, n, R);
   k_copy_block<T, double><<<gb, 256, 0, st>>>(B, ldb, ws.r, R, n, R);
   pl->launches[3] += 2;
-  if (pc) {   // p = z = M^{-1} r, rz = r^T z
-    AGP_TRY(precond_apply<T>(*pc, ws.r, ws.z, R, st));
+  if (pcon) {   // p = z = M^{-1} r, rz = r^T z
+    AGP_TRY(apply_pc());
     k_copy_block<double, double><<<gb, 256, 0, st>>>(ws.z, R, ws.p, R, n, R);
     k_copy_block<double, T><<<gb, 256, 0, st>>>(ws.z, R, ws.pt, R, n, R);
     AGP_TRY(col_dot(ws.r, R, ws.z, R, n, R, ws.partial, s.rz, st, pl));
@@ -401,12 +408,12 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
     k_cg_xr<T><<<gb, 256, 0, st>>>(ws.x, ws.r, ws.p, ws.q, s.alpha, n, R);
     pl->launches[3] += 2;
     AGP_TRY(col_dot(ws.r, R, ws.r, R, n, R, ws.partial, rrnew, st, pl));
-    if (pc) {
-      AGP_TRY(precond_apply<T>(*pc, ws.r, ws.z, R, st));
+    if (pcon) {
+      AGP_TRY(apply_pc());
       AGP_TRY(col_dot(ws.r, R, ws.z, R, n, R, ws.partial, s.rznew, st, pl));
     }
     k_cg_beta<<<gc, 128, 0, st>>>(s, rrnew, it, R);
-    k_cg_p<T><<<gb, 256, 0, st>>>(ws.p, ws.pt, pc ? ws.z : ws.r, s.beta, s.active, n, R);
+    k_cg_p<T><<<gb, 256, 0, st>>>(ws.p, ws.pt, pcon ? ws.z : ws.r, s.beta, s.active, n, R);
     pl->launches[3] += 2;
     AGP_CUDA(cudaGetLastError());
     if (check_every > 0 && ((it + 1) % check_every == 0) && it + 1 < maxall) {
@@ -424,7 +431,8 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
 
 template <typename T>
 agp_status pcg_t(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int R, double rtol,
-                 int maxit, int n_landmarks, int* iters, double* relres, cudaStream_t st) {
+                 int maxit, int n_landmarks, int* iters, double* relres, cudaStream_t st,
+                 const Afn* afn = nullptr) {
   Precond pc;
   struct Release {
     Precond* p;
@@ -434,7 +442,8 @@ agp_status pcg_t(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int
   Workspace<T> ws;
   std::vector<int> mi(R, maxit);
   std::vector<double> tl(R, rtol);
-  AGP_TRY(cg_run<T>(pl, B, ldb, X, ldx, R, mi, tl, 5, ws, st, n_landmarks > 0 ? &pc : nullptr));
+  AGP_TRY(cg_run<T>(pl, B, ldb, X, ldx, R, mi, tl, 5, ws, st, n_landmarks > 0 ? &pc : nullptr,
+                    afn));
   std::vector<int> it(R);
   std::vector<double> rel(R);
   AGP_CUDA(cudaMemcpyAsync(it.data(), ws.iscal + R, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
@@ -701,6 +710,74 @@ agp_status agp_pcg_solve(agp_plan pl, const void* B, int64_t ldb, void* Xsol, in
                         iters, relres, st);
   return pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, n_landmarks,
                        iters, relres, st);
+}
+
+agp_status agp_afn_create(agp_afn* out, agp_plan pl, int n_landmarks, int fill, void* stream) {
+  if (!out) return set_error(AGP_EINVAL, "bad arguments");
+  *out = nullptr;
+  if (!pl || n_landmarks < 1 || n_landmarks > kMaxLandmarks || fill < 1 || fill > kAfnMaxFill)
+    return set_error(AGP_EINVAL, "n_landmarks must be in [1, 480] and fill in [1, 128]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Afn* af = new Afn();
+  const agp_status s = pl->prec == AGP_F32 ? afn_build<float>(pl, n_landmarks, fill, 32, af, st)
+                                           : afn_build<double>(pl, n_landmarks, fill, 32, af, st);
+  if (s != AGP_OK) {
+    cudaStreamSynchronize(st);
+    afn_free(af);
+    delete af;
+    return s;
+  }
+  *out = reinterpret_cast<agp_afn>(af);
+  return AGP_OK;
+}
+
+agp_status agp_afn_destroy(agp_afn afn) {
+  if (!afn) return AGP_OK;
+  Afn* af = reinterpret_cast<Afn*>(afn);
+  afn_free(af);   // cudaFree waits for the device
+  delete af;
+  return AGP_OK;
+}
+
+agp_status agp_afn_apply(agp_afn afn, const double* V, int64_t ldv, double* Y, int64_t ldy, int R,
+                         void* stream) {
+  if (!afn || !V || !Y || R < 1 || R > 32 || ldv < R || ldy < R)
+    return set_error(AGP_EINVAL, "bad arguments");
+  return afn_apply(*reinterpret_cast<const Afn*>(afn), V, ldv, Y, ldy, R,
+                   static_cast<cudaStream_t>(stream));
+}
+
+agp_status agp_afn_info(agp_afn afn, int* n_landmarks, int64_t* nnz, double* logdet) {
+  if (!afn) return set_error(AGP_EINVAL, "bad arguments");
+  const Afn* af = reinterpret_cast<const Afn*>(afn);
+  if (n_landmarks) *n_landmarks = af->k;
+  if (nnz) *nnz = af->nnz;
+  if (logdet) *logdet = af->logdet;
+  return AGP_OK;
+}
+
+agp_status agp_afn_pattern(agp_afn afn, int32_t* landmarks, int32_t* J, void* stream) {
+  if (!afn) return set_error(AGP_EINVAL, "bad arguments");
+  return afn_pattern(*reinterpret_cast<const Afn*>(afn), landmarks, J,
+                     static_cast<cudaStream_t>(stream));
+}
+
+agp_status agp_pcg_solve_afn(agp_plan pl, agp_afn afn, const void* B, int64_t ldb, void* Xsol,
+                             int64_t ldx, int R, double rtol, int maxit, int* iters,
+                             double* relres, void* stream) {
+  if (!pl || !afn || !B || !Xsol || R < 1 || R > 32 || ldb < R || ldx < R || maxit < 0 ||
+      !(rtol >= 0))
+    return set_error(AGP_EINVAL, "bad arguments");
+  const Afn* af = reinterpret_cast<const Afn*>(afn);
+  if (af->n != pl->n || af->ell != pl->ell || af->sigma_f != pl->sigma_f ||
+      af->sigma_eps != pl->sigma_eps || af->kernel != (int)pl->kernel)
+    return set_error(AGP_EINVAL, "the AFN preconditioner was built for other hyperparameters");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl->prec == AGP_F32)
+    return pcg_t<float>(pl, (const float*)B, ldb, (float*)Xsol, ldx, R, rtol, maxit, 0, iters,
+                        relres, st, af);
+  return pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, 0, iters,
+                       relres, st, af);
 }
 
 agp_status agp_plan_landmarks(agp_plan pl, int n_landmarks, int32_t* idx, int cap, int* count,
