@@ -36,7 +36,10 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
 * ``afn_*``/``fsai_pattern``: the FSAI factor with a full pattern equals the
   inverse Cholesky factor of the Schur complement and M equals K_hat; the
   FSAI defining equations; M's landmark rows equal K_hat's; fill 1 keeps
-  K_hat's diagonal; dense solve and slogdet; finite differences of log det M.
+  K_hat's diagonal; dense solve and slogdet; finite differences of log det M,
+  of G and of M; Z Z^T = M for the probes of the identity; the AFN likelihood
+  estimate is exact with a full pattern and equals the dense Hutchinson
+  average with a full Krylov space.
 * ``cg``: dense Cholesky solve; ``slq_quadratic``: eigendecomposition-based
   matrix logarithm with full Krylov space; ``nlml_exact``: scipy's
   multivariate normal log density.
@@ -61,7 +64,7 @@ __all__ = [
     "landmark_jitter", "nystrom_blocks", "nystrom_matrix", "nystrom_logdet", "nystrom_probes", "pcg_lanczos",
     "nystrom_dM_quadratic", "nystrom_trace_Minv_dM", "nlml_estimate_preconditioned",
     "afn_split", "fsai_pattern", "afn_factors", "afn_matrix", "afn_apply_inverse",
-    "afn_logdet", "afn_logdet_grad",
+    "afn_logdet", "afn_logdet_grad", "afn_dG", "afn_dM", "afn_probes", "nlml_estimate_afn",
 ]
 
 TWO_PI = 2.0 * math.pi
@@ -968,3 +971,107 @@ def afn_logdet_grad(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, G
         g = G[t, Jt]
         out += float(g @ dS[np.ix_(Jt, Jt)] @ g)
     return out
+
+
+def _afn_dblocks(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, which):
+    """dK_LL, dK_FL and dS (derivatives of the blocks of K_hat and of the
+    Schur complement S with respect to ``which``)."""
+    dK = dense_matrix(X, windows, kind, ell, sigma_f, sigma_eps, which=which)
+    dLL = dK[np.ix_(L, L)]
+    dFL = dK[np.ix_(F, L)]
+    A = np.linalg.solve(KLL, KFL.T)
+    dS = dK[np.ix_(F, F)] - dFL @ A - A.T @ dFL.T + A.T @ dLL @ A
+    return dLL, dFL, 0.5 * (dS + dS.T)
+
+
+def afn_dG(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, S, G, J, which):
+    """dG/dtheta with the landmarks and the pattern held fixed. Row t,
+    g = G[t, J_t]: differentiating S_JJ u = e_t and g = u / sqrt(u_t) gives
+    dg = -S_JJ^{-1} dS_JJ g + g (g^T dS_JJ g) / 2."""
+    _, _, dS = _afn_dblocks(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, which)
+    dG = np.zeros_like(G)
+    for t, Jt in enumerate(J):
+        g = G[t, Jt]
+        v = dS[np.ix_(Jt, Jt)] @ g
+        dG[t, Jt] = -np.linalg.solve(S[np.ix_(Jt, Jt)], v) + 0.5 * g * float(g @ v)
+    return dG
+
+
+def afn_dM(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, S, G, J, which):
+    """dM/dtheta (dense, original point order) for M = Phi D Phi^T with
+    Phi = [I 0; Xm I], Xm = K_FL K_LL^{-1}, D = diag(K_LL, (G^T G)^{-1}):
+    dXm = (dK_FL - Xm dK_LL) K_LL^{-1},
+    d(G^T G)^{-1} = -(G^T G)^{-1} (dG^T G + G^T dG) (G^T G)^{-1}."""
+    dLL, dFL, _ = _afn_dblocks(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, which)
+    dG = afn_dG(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, S, G, J, which)
+    n, k = len(L) + len(F), len(L)
+    Xm = np.linalg.solve(KLL, KFL.T).T
+    dXm = np.linalg.solve(KLL, (dFL - Xm @ dLL).T).T
+    Phi = np.eye(n)
+    Phi[k:, :k] = Xm
+    dPhi = np.zeros((n, n))
+    dPhi[k:, :k] = dXm
+    St = np.linalg.inv(G.T @ G)
+    D = np.zeros((n, n))
+    D[:k, :k] = KLL
+    D[k:, k:] = St
+    dD = np.zeros((n, n))
+    dD[:k, :k] = dLL
+    dD[k:, k:] = -St @ (dG.T @ G + G.T @ dG) @ St
+    dMp = dPhi @ D @ Phi.T + Phi @ dD @ Phi.T + Phi @ D @ dPhi.T
+    order = list(L) + list(F)
+    dM = np.zeros((n, n))
+    dM[np.ix_(order, order)] = 0.5 * (dMp + dMp.T)
+    return dM
+
+
+def afn_probes(L, F, KLL, KFL, G, Wn):
+    """Probes with covariance M: z = Phi [C w_L; G^{-1} w_F] (C C^T = K_LL),
+    i.e. z_L = C w_L and z_F = K_FL K_LL^{-1} z_L + G^{-1} w_F, for given
+    vectors w (the columns of Wn, rows in the original point order)."""
+    Wn = np.asarray(Wn, dtype=np.float64)
+    C = np.linalg.cholesky(KLL)
+    Z = np.zeros_like(Wn)
+    zL = C @ Wn[L]
+    Z[L] = zL
+    Z[F] = KFL @ np.linalg.solve(KLL, zL) + np.linalg.solve(G, Wn[F])
+    return Z
+
+
+def nlml_estimate_afn(apply_K, apply_dK, y, Wn, lanczos_steps, X, windows, kind, ell, sigma_f,
+                      sigma_eps, landmarks, fill, rtol=1e-10, maxit=None):
+    """Estimate of the NLML and its gradient (Sec. 1 eqs. (1.3)-(1.5)) with the
+    additive AFN preconditioner M of afn_factors (Sec. 2.3): the same
+    estimator as nlml_estimate_preconditioned, with log det M = log det K_LL -
+    2 sum log G_tt, tr(M^{-1} dM) = d log det M / dtheta (afn_logdet_grad),
+    probes z_i = afn_probes(w_i) and p^T dM p from afn_dM. Returns (nlml,
+    {theta: grad})."""
+    y = np.asarray(y, dtype=np.float64).reshape(-1)
+    n = y.shape[0]
+    L, F, KLL, KFL, S, G, J = afn_factors(X, windows, kind, ell, sigma_f, sigma_eps,
+                                          landmarks, fill)
+
+    def Minv(P):
+        return afn_apply_inverse(L, F, KLL, KFL, G, P)
+
+    alpha, _, _ = pcg(apply_K, Minv, y[:, None], rtol=rtol,
+                      maxit=maxit if maxit is not None else 10 * n)
+    alpha = alpha[:, 0]
+    Z = afn_probes(L, F, KLL, KFL, G, Wn)
+    U, al, be, rz0 = pcg_lanczos(apply_K, Minv, Z, lanczos_steps)
+    nz = Z.shape[1]
+    quad = 0.0
+    for i in range(nz):
+        quad += slq_quadratic(lanczos_tridiag_from_cg(al[i], be[i]), float(rz0[i]))
+    logdet = afn_logdet(KLL, G) + quad / nz
+    nlml = 0.5 * (y @ alpha + logdet + n * math.log(TWO_PI))
+    P = Minv(Z)
+    grads = {}
+    for th, f in apply_dK.items():
+        da = f(alpha[:, None])[:, 0]
+        dz = f(P)
+        tr_m = afn_logdet_grad(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, G, J, th)
+        dM = afn_dM(X, windows, kind, ell, sigma_f, sigma_eps, L, F, KLL, KFL, S, G, J, th)
+        s = np.sum(U * dz, axis=0) - np.sum(P * (dM @ P), axis=0)
+        grads[th] = 0.5 * (-(alpha @ da) + tr_m + float(np.mean(s)))
+    return nlml, grads

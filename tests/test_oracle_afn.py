@@ -2,7 +2,10 @@
 factor of the Schur complement against the textbook Cholesky inverse, the
 exactness of the factorisation with a full pattern, the block identities of
 M, the determinant and its derivative against dense linear algebra and
-finite differences, and the iteration saving of Sec. 5's first experiment."""
+finite differences, the iteration saving of Sec. 5's first experiment, and
+the pieces of the AFN-preconditioned likelihood estimate (dG and dM against
+finite differences, the probe covariance, exactness with a full pattern,
+agreement with a dense Hutchinson average over a full Krylov space)."""
 import math
 
 import numpy as np
@@ -147,3 +150,88 @@ def test_afn_pcg_needs_fewer_iterations_than_cg():
     assert rel[0] <= 1e-4
     assert np.linalg.norm(K @ xs - b) <= 1.01e-4 * np.linalg.norm(b)
     assert it_p[0] < 0.5 * it_cg[0], (it_p, it_cg)
+
+
+def _fd(f, th, which, h_rel=1e-5):
+    h = h_rel * th[which]
+    tp, tm = dict(th), dict(th)
+    tp[which] += h
+    tm[which] -= h
+    return (f(tp) - f(tm)) / (2 * h)
+
+
+@pytest.mark.parametrize("which", ["ell", "sigma_f", "sigma_eps"])
+def test_dG_and_dM_match_finite_differences(which):
+    X, W, th, L, _ = _problem(36)
+    fill = 5
+    Lf, F, KLL, KFL, S, G, J = _factors(X, W, th, L, fill)
+    args = (X, W, "gauss", th["ell"], th["sigma_f"], th["sigma_eps"], Lf, F, KLL, KFL, S, G, J,
+            which)
+    dG = O.afn_dG(*args)
+    fdG = _fd(lambda t: _factors(X, W, t, L, fill)[5], th, which)
+    np.testing.assert_allclose(dG, fdG, rtol=1e-5, atol=1e-6 * np.abs(fdG).max())
+
+    def M_of(t):
+        a = _factors(X, W, t, L, fill)
+        return O.afn_matrix(a[0], a[1], a[2], a[3], a[5])
+
+    dM = O.afn_dM(*args)
+    fdM = _fd(M_of, th, which)
+    np.testing.assert_allclose(dM, fdM, rtol=1e-5, atol=1e-6 * np.abs(fdM).max())
+    # and its trace against the log-determinant derivative
+    M = M_of(th)
+    tr = float(np.trace(np.linalg.solve(M, dM)))
+    g = O.afn_logdet_grad(X, W, "gauss", th["ell"], th["sigma_f"], th["sigma_eps"], Lf, F, KLL, KFL,
+                          G, J, which)
+    assert abs(tr - g) <= 1e-8 * max(1.0, abs(g))
+
+
+def test_probes_have_covariance_M():
+    X, W, th, L, _ = _problem(30)
+    Lf, F, KLL, KFL, _, G, _ = _factors(X, W, th, L, fill=4)
+    Z = O.afn_probes(Lf, F, KLL, KFL, G, np.eye(30))
+    np.testing.assert_allclose(Z @ Z.T, O.afn_matrix(Lf, F, KLL, KFL, G), rtol=1e-10, atol=1e-12)
+
+
+def test_afn_estimate_with_full_pattern_is_exact():
+    """fill >= n - k: M = K_hat, so M^{-1} K_hat = I, every SLQ term vanishes,
+    p_i = u_i and dM = dK_hat: the estimate is the exact NLML and gradient
+    whatever the probes."""
+    X, W, th, L, rng = _problem(40)
+    n = len(X)
+    y = rng.standard_normal(n)
+    K = O.dense_matrix(X, W, "gauss", th["ell"], th["sigma_f"], th["sigma_eps"])
+    dK = {w: O.dense_matrix(X, W, "gauss", th["ell"], th["sigma_f"], th["sigma_eps"], which=w)
+          for w in ("ell", "sigma_f", "sigma_eps")}
+    nl, g = O.nlml_estimate_afn(lambda P: K @ P, {w: (lambda P, A=A: A @ P) for w, A in dK.items()},
+                                y, rng.standard_normal((n, 5)), 6, X, W, "gauss", th["ell"],
+                                th["sigma_f"], th["sigma_eps"], L, 10 ** 6)
+    assert abs(nl - O.nlml_exact(K, y)) <= 1e-9 * abs(nl)
+    a = np.linalg.solve(K, y)
+    for w, A in dK.items():
+        exact = 0.5 * (-(a @ A @ a) + np.trace(np.linalg.solve(K, A)))
+        assert abs(g[w] - exact) <= 1e-8 * max(1.0, abs(exact)), (w, g[w], exact)
+
+
+def test_afn_estimate_with_full_krylov_space_is_hutchinson():
+    """With as many PCG steps as points each SLQ term is exact, so the
+    estimate equals log det M + the Hutchinson average of z~^T log(M^{-1/2}
+    K_hat M^{-1/2}) z~ (z~ = M^{-1/2} z), from a dense eigendecomposition."""
+    X, W, th, L, rng = _problem(24)
+    n = len(X)
+    fill = 3
+    y = rng.standard_normal(n)
+    Wn = rng.standard_normal((n, 4))
+    K = O.dense_matrix(X, W, "gauss", th["ell"], th["sigma_f"], th["sigma_eps"])
+    nl, _ = O.nlml_estimate_afn(lambda P: K @ P, {}, y, Wn, n, X, W, "gauss", th["ell"],
+                                th["sigma_f"], th["sigma_eps"], L, fill)
+    Lf, F, KLL, KFL, _, G, _ = _factors(X, W, th, L, fill)
+    M = O.afn_matrix(Lf, F, KLL, KFL, G)
+    ew, V = np.linalg.eigh(M)
+    Mh = V @ np.diag(ew ** -0.5) @ V.T
+    ew2, V2 = np.linalg.eigh(Mh @ K @ Mh)
+    logm = V2 @ np.diag(np.log(ew2)) @ V2.T
+    Zt = Mh @ O.afn_probes(Lf, F, KLL, KFL, G, Wn)
+    quad = np.mean(np.sum(Zt * (logm @ Zt), axis=0))
+    want = 0.5 * (y @ np.linalg.solve(K, y) + O.afn_logdet(KLL, G) + quad + n * math.log(2 * math.pi))
+    assert abs(nl - want) <= 1e-7 * abs(want)
