@@ -290,6 +290,26 @@ agp_status agp_pcg_solve_afn(agp_plan plan, agp_afn afn, const void* B, int64_t 
                              int64_t ldx, int R, double rtol, int maxit, int* iters,
                              double* relres, void* stream);
 
+/* NLML estimate and gradient with the AFN preconditioner M of `afn` (Sec. 1
+ * eqs. (1.3)-(1.5)), the estimator of agp_nlml_grad_pc with
+ *   probes     z_i = Phi [C wL_i; G^{-1} wF_i] (covariance M), where wL_i and
+ *              wF_i are the landmark rows and the other rows of column i of Wn;
+ *   log det M  = log det K_LL - 2 sum_t log G_tt;
+ *   tr(M^{-1} dM_j) = d log det M / dtheta_j (exact, with the landmarks and
+ *              the pattern of G held fixed);
+ *   p_i^T dM_j p_i from the exact derivative of M (dG row by row).
+ * G^{-1} is applied by forward substitution level by level (the rows of a
+ * level depend only on earlier levels). The first call builds the
+ * derivative data of `afn` (about 3 fill + k doubles per point).
+ * Y: device [n]; Wn: device [n][ldwn] in the plan precision, 1 <= nz <= 31
+ * columns with covariance I; 1 <= lanczos_steps <= 64; rtol / maxit as in
+ * agp_nlml_grad_pc. nlml: host double; grad: host double[3] (ell, sigma_f,
+ * sigma_eps). AGP_EINVAL if `afn` was built for other hyperparameters.
+ * Synchronises `stream`. */
+agp_status agp_nlml_grad_afn(agp_plan plan, agp_afn afn, const void* Y, const void* Wn,
+                             int64_t ldwn, int nz, int lanczos_steps, double rtol, int maxit,
+                             double* nlml, double* grad, void* stream);
+
 /* ---- Batches of independent problems ----------------------------------------
  * Many independent GP problems of different sizes (independent plans, each
  * with its own points, windows and hyperparameters) applied together: every

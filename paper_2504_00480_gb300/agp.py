@@ -81,6 +81,9 @@ _SIGS = {
     "agp_afn_pattern": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "agp_pcg_solve_afn": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int,
                                   c_double, c_int, POINTER(c_int), POINTER(c_double), c_void_p]),
+    "agp_nlml_grad_afn": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int,
+                                  c_double, c_int, POINTER(c_double), POINTER(c_double),
+                                  c_void_p]),
     "agp_dot_columns": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int,
                                 POINTER(c_double), c_void_p]),
     "agp_dot_columns_static": (c_int, [c_int, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int,
@@ -347,6 +350,21 @@ def agp_pcg_solve_afn(plan: c_void_p, afn: c_void_p, B: torch.Tensor, Xsol: torc
     return np.array(it[:], dtype=np.int64), np.array(rel[:], dtype=np.float64)
 
 
+def agp_nlml_grad_afn(plan: c_void_p, afn: c_void_p, y: torch.Tensor, Wn: torch.Tensor,
+                      lanczos_steps: int = 20, rtol: float = 0.0, maxit: int = 0):
+    """(nlml, grads) with the AFN preconditioner; Wn: device [n][nz] vectors
+    with covariance I in the plan precision."""
+    if y.dim() != 1 or not y.is_contiguous():
+        raise ValueError("y must be a contiguous 1-D tensor")
+    wp, ldw, nz = _block(Wn, y.dtype, "Wn")
+    nl = c_double()
+    g = (c_double * 3)()
+    _check(load_library().agp_nlml_grad_afn(plan, afn, y.data_ptr(), wp, ldw, nz,
+                                            int(lanczos_steps), float(rtol), int(maxit), byref(nl),
+                                            g, _stream()))
+    return nl.value, {"ell": g[0], "sigma_f": g[1], "sigma_eps": g[2]}
+
+
 class Afn:
     """The additive AFN preconditioner of a plan at its current hyperparameters."""
 
@@ -380,6 +398,10 @@ class Afn:
 
     def pattern(self):
         return agp_afn_pattern(self._h, self.plan.n, self.fill)
+
+    def nlml_grad(self, y: torch.Tensor, Wn: torch.Tensor, lanczos_steps: int = 20,
+                  rtol: float = 0.0, maxit: int = 0):
+        return agp_nlml_grad_afn(self.plan.handle, self._h, y, Wn, lanczos_steps, rtol, maxit)
 
     def solve(self, B: torch.Tensor, rtol: float = 1e-4, maxit: int = 200,
               raise_not_converged: bool = True):

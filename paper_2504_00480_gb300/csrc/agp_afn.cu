@@ -36,6 +36,19 @@ namespace {
 constexpr int kKnnWarps = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// out[a][j] = sf2 d kernel_sum(rows_a, L_j) / dell, FP64 [m][k]
+template <typename T>
+__global__ void k_kernel_cols_rows(const WinPts<T>* __restrict__ wp, int P, int64_t n,
+                                   const int32_t* __restrict__ rows, int64_t m,
+                                   const int32_t* __restrict__ lm, int k, int kernel, double ell,
+                                   double sf2, double* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * k) return;
+  const int64_t a = e / k;
+  const int j = (int)(e - a * k);
+  out[e] = sf2 * kernel_sum<T>(wp, P, n, rows[a], lm[j], kernel, ell, 1);
+}
+
 // out[a][j] = sf2 kernel_sum(rows_a, L_j), FP64 [m][k]
 template <typename T>
 __global__ void k_kernel_rows(const WinPts<T>* __restrict__ wp, int P, int64_t n,
@@ -47,6 +60,14 @@ __global__ void k_kernel_rows(const WinPts<T>* __restrict__ wp, int P, int64_t n
   const int64_t a = e / k;
   const int j = (int)(e - a * k);
   out[e] = sf2 * kernel_sum<T>(wp, P, n, rows[a], lm[j], kernel, ell, 0);
+}
+
+// out = the lower triangle of A (k x k), zeros above the diagonal
+__global__ void k_lower_copy(const double* __restrict__ A, int k, double* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)k * k) return;
+  const int i = (int)(e / k), j = (int)(e - (int64_t)i * k);
+  out[e] = j <= i ? A[e] : 0.0;
 }
 
 // W[a][j] = sum_{i <= j} Ci[j][i] Bf[a][i]   (W = Bf C^{-T}, Ci = C^{-1} lower)
@@ -163,13 +184,24 @@ k_knn_lower(const float* __restrict__ xf, int pf, int64_t m, int fill, int32_t* 
 
 // Row a of G (one CTA): S[J, J] in shared memory (lower triangle, stride
 // fill + 1), its Cholesky factor R in place, then R^T g = e_last by columns.
-template <typename T>
+// With DER, also the derivatives of the row for theta = (ell, sigma_f,
+// sigma_eps) with the pattern fixed: v = dS[J, J] g, y = S[J, J]^{-1} v by
+// two triangular solves with R, dG[a][J] = -y + g (g^T v) / 2 and
+// quad[theta][a] = g^T v. With omega = sum_b g_b W_b, delta = sum_b g_b Dl_b
+// (rows of W = K_FL C^{-T} and Dl = dK_FL/dell C^{-T} at the pattern),
+// E = C^{-1} dK_LL/dell C^{-T} and Pm = C^{-1} C^{-T}:
+//   v_ell[a]   = sum_b dK_ab g_b - Dl_a.omega - W_a.delta + W_a.(E omega)
+//   v_sf[a]    = (2 / sigma_f) ([a = last] / g_last - s2 g_a - s2 W_a.(Pm omega))
+//   v_seps[a]  = 2 sigma_eps (g_a + W_a.(Pm omega)),
+// using S[J, J] g = e_last / g_last.
+template <typename T, bool DER>
 __global__ void __launch_bounds__(256)
 k_fsai_rows(const WinPts<T>* __restrict__ wp, int P, int64_t n, const int32_t* __restrict__ F,
             const double* __restrict__ W, int k, const int32_t* __restrict__ J,
-            const int32_t* __restrict__ len, int fill, int kernel, double ell, double sf2,
-            double s2, double* __restrict__ Gval, double* __restrict__ logdiag,
-            int* __restrict__ flag) {
+            const int32_t* __restrict__ len, int64_t m, int fill, int kernel, double ell,
+            double sf, double se, double* __restrict__ Gval, double* __restrict__ logdiag,
+            int* __restrict__ flag, const double* __restrict__ Dl, const double* __restrict__ E,
+            const double* __restrict__ Pm, double* __restrict__ dGval, double* __restrict__ quad) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* S = reinterpret_cast<double*>(smem_raw);
   __shared__ int pos[kAfnMaxFill], idx[kAfnMaxFill];
@@ -178,6 +210,7 @@ k_fsai_rows(const WinPts<T>* __restrict__ wp, int P, int64_t n, const int32_t* _
   const int64_t a = blockIdx.x;
   const int L = len[a];
   const int ldS = fill + 1;
+  const double sf2 = sf * sf, s2 = se * se;
   for (int q = tid; q < L; q += bs) {
     pos[q] = J[a * fill + q];
     idx[q] = F[pos[q]];
@@ -221,6 +254,86 @@ k_fsai_rows(const WinPts<T>* __restrict__ wp, int P, int64_t n, const int32_t* _
   }
   for (int q = tid; q < fill; q += bs) Gval[a * fill + q] = q < L ? g[q] : 0.0;
   if (tid == 0) logdiag[a] = log(g[L - 1]);
+  if constexpr (DER) {
+    __shared__ double om[kMaxLandmarkSet], de[kMaxLandmarkSet], eom[kMaxLandmarkSet],
+        pom[kMaxLandmarkSet];
+    __shared__ double v[3][kAfnMaxFill], z[3][kAfnMaxFill], y[3][kAfnMaxFill],
+        acc3[3][kAfnMaxFill];
+    __shared__ double qd[3];
+    for (int j = tid; j < k; j += bs) {
+      double o = 0.0, d = 0.0;
+      for (int b = 0; b < L; ++b) {
+        o = fma(g[b], W[(int64_t)pos[b] * k + j], o);
+        d = fma(g[b], Dl[(int64_t)pos[b] * k + j], d);
+      }
+      om[j] = o;
+      de[j] = d;
+    }
+    __syncthreads();
+    for (int j = tid; j < k; j += bs) {
+      double e1 = 0.0, p1 = 0.0;
+      for (int i = 0; i < k; ++i) {
+        e1 = fma(E[(int64_t)j * k + i], om[i], e1);
+        p1 = fma(Pm[(int64_t)j * k + i], om[i], p1);
+      }
+      eom[j] = e1;
+      pom[j] = p1;
+    }
+    __syncthreads();
+    for (int q = tid; q < L; q += bs) {
+      const double* wa = W + (int64_t)pos[q] * k;
+      const double* da = Dl + (int64_t)pos[q] * k;
+      double s_dw = 0.0, s_wd = 0.0, s_we = 0.0, s_wp = 0.0;
+      for (int j = 0; j < k; ++j) {
+        s_dw = fma(da[j], om[j], s_dw);
+        s_wd = fma(wa[j], de[j], s_wd);
+        s_we = fma(wa[j], eom[j], s_we);
+        s_wp = fma(wa[j], pom[j], s_wp);
+      }
+      double dkg = 0.0;
+      for (int b = 0; b < L; ++b)
+        dkg = fma(sf2 * kernel_sum<T>(wp, P, n, idx[q], idx[b], kernel, ell, 1), g[b], dkg);
+      v[0][q] = dkg - s_dw - s_wd + s_we;
+      v[1][q] = (2.0 / sf) * ((q == L - 1 ? 1.0 / g[L - 1] : 0.0) - s2 * g[q] - s2 * s_wp);
+      v[2][q] = 2.0 * se * (g[q] + s_wp);
+      acc3[0][q] = acc3[1][q] = acc3[2][q] = 0.0;
+    }
+    __syncthreads();
+    // R z = v (forward, by columns)
+    for (int i = 0; i < L; ++i) {
+      if (tid < 3) z[tid][i] = (v[tid][i] - acc3[tid][i]) / S[i * ldS + i];
+      __syncthreads();
+      const int r = L - i - 1;
+      for (int e = tid; e < 3 * r; e += bs) {
+        const int th = e / r, j = i + 1 + e % r;
+        acc3[th][j] = fma(S[j * ldS + i], z[th][i], acc3[th][j]);
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < 3 * L; e += bs) acc3[e / L][e % L] = 0.0;
+    __syncthreads();
+    // R^T y = z (backward, by columns)
+    for (int i = L - 1; i >= 0; --i) {
+      if (tid < 3) y[tid][i] = (z[tid][i] - acc3[tid][i]) / S[i * ldS + i];
+      __syncthreads();
+      for (int e = tid; e < 3 * i; e += bs) {
+        const int th = e / i, j = e % i;
+        acc3[th][j] = fma(S[i * ldS + j], y[th][i], acc3[th][j]);
+      }
+      __syncthreads();
+    }
+    if (tid < 3) {
+      double q = 0.0;
+      for (int b = 0; b < L; ++b) q = fma(g[b], v[tid][b], q);
+      qd[tid] = q;
+      quad[(int64_t)tid * m + a] = q;
+    }
+    __syncthreads();
+    for (int e = tid; e < 3 * fill; e += bs) {
+      const int th = e / fill, q = e - th * fill;
+      dGval[((int64_t)th * m + a) * fill + q] = q < L ? fma(0.5 * qd[th], g[q], -y[th][q]) : 0.0;
+    }
+  }
 }
 
 __global__ void k_col_count(const int32_t* __restrict__ J, const int32_t* __restrict__ len,
@@ -385,6 +498,38 @@ __global__ void k_afn_lm_out(const double* __restrict__ h, const int32_t* __rest
   Y[(int64_t)L[j] * ldy + r] = s;
 }
 
+// One level of the forward substitution G y = x: for the rows t of the level
+// (their dependencies are in earlier levels), y[t][r] = (x[t][r] -
+// sum_{q < len - 1} G[t][q] y[J[t][q]][r]) / G[t][len - 1]. A warp per row.
+__global__ void __launch_bounds__(256)
+k_afn_trsv_level(const int32_t* __restrict__ rows, int64_t nrows, const double* __restrict__ Gval,
+                 const int32_t* __restrict__ J, const int32_t* __restrict__ len, int fill, int R,
+                 const double* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x % 32;
+  if (lane >= R) return;
+  for (int64_t q0 = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; q0 < nrows;
+       q0 += (int64_t)gridDim.x * 8) {
+    const int64_t t = rows[q0];
+    const int L = len[t];
+    double s = x[t * R + lane];
+    for (int q = 0; q < L - 1; ++q)
+      s = fma(-Gval[t * fill + q], y[(int64_t)J[t * fill + q] * R + lane], s);
+    y[t * R + lane] = s / Gval[t * fill + L - 1];
+  }
+}
+
+// out[j][r] = sum_z partial[z][j][r]
+__global__ void k_sum_slices(const double* __restrict__ partial, int nz, int k, int R,
+                             double* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * R) return;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += partial[(int64_t)z * k * R + e];
+  out[e] = s;
+}
+
+inline int fsai_threads(int fill) { return fill <= 32 ? 64 : (fill <= 64 ? 128 : 256); }
+
 }  // namespace
 
 void afn_free(Afn* af) {
@@ -392,7 +537,8 @@ void afn_free(Afn* af) {
   for (void* p : {(void*)af->L, (void*)af->F, (void*)af->Ci, (void*)af->W, (void*)af->J,
                   (void*)af->len, (void*)af->Gval, (void*)af->colptr, (void*)af->colrow,
                   (void*)af->colval, (void*)af->v, (void*)af->t, (void*)af->u, (void*)af->w,
-                  (void*)af->partial, (void*)af->h})
+                  (void*)af->partial, (void*)af->h, (void*)af->C, (void*)af->Dl,
+                  (void*)af->dGval, (void*)af->lvl_rows})
     cudaFree(p);
   *af = Afn();
 }
@@ -454,6 +600,8 @@ agp_status afn_build(agp_plan_s* pl, int k_req, int fill, int rmax, Afn* af, cud
                                                                pl->ell, sf2, 0, s2, KLL);
   k_cholesky<<<1, 1024, 0, st>>>(KLL, k, flag);
   k_tri_inverse<<<nblk(k, 128), 128, 0, st>>>(KLL, k, af->Ci);
+  AGP_CUDA(cudaMalloc(&af->C, sizeof(double) * k * k));
+  k_lower_copy<<<nblk((int64_t)k * k, 256), 256, 0, st>>>(KLL, k, af->C);
   k_diag<<<nblk(k, 128), 128, 0, st>>>(KLL, k, dg);
   std::vector<double> diag(k);
   int hflag = 0;
@@ -502,12 +650,11 @@ agp_status afn_build(agp_plan_s* pl, int k_req, int fill, int rmax, Afn* af, cud
     AGP_CUDA(cudaMallocAsync(&logdiag, sizeof(double) * m, st));
     AGP_CUDA(cudaMalloc(&af->Gval, sizeof(double) * m * fill));
     const size_t fsmem = sizeof(double) * (size_t)fill * (fill + 1);
-    AGP_CUDA(cudaFuncSetAttribute(k_fsai_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fsmem));
-    const int fthreads = fill <= 32 ? 64 : (fill <= 64 ? 128 : 256);
-    k_fsai_rows<T><<<(unsigned)m, fthreads, fsmem, st>>>(wpd, P, n, af->F, af->W, k, af->J,
-                                                         af->len, fill, pl->kernel, pl->ell, sf2,
-                                                         s2, af->Gval, logdiag, flag);
+    AGP_CUDA(cudaFuncSetAttribute(k_fsai_rows<T, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    k_fsai_rows<T, false><<<(unsigned)m, fsai_threads(fill), fsmem, st>>>(
+        wpd, P, n, af->F, af->W, k, af->J, af->len, m, fill, pl->kernel, pl->ell, pl->sigma_f,
+        pl->sigma_eps, af->Gval, logdiag, flag, nullptr, nullptr, nullptr, nullptr, nullptr);
     // G^T as compressed columns
     int32_t *cnt = nullptr, *cursor = nullptr;
     AGP_CUDA(cudaMallocAsync(&cnt, sizeof(int32_t) * m, st));
@@ -592,6 +739,176 @@ agp_status afn_pattern(const Afn& af, int32_t* landmarks, int32_t* J, cudaStream
   return AGP_OK;
 }
 
+// Derivative data for the likelihood gradient: host K_LL, C, C^{-1} and
+// dK_LL/dell; Dl = (dK_FL/dell) C^{-T}; one pass of k_fsai_rows<T, true>
+// (dG for ell, sigma_f, sigma_eps and the row sums G_t^T dS G_t); the levels
+// of G for the forward substitution (row t depends on the earlier rows of
+// its pattern: level(t) = 1 + the largest level among them).
+template <typename T>
+agp_status afn_build_derivs(agp_plan_s* pl, Afn* af, cudaStream_t st) {
+  if (af->has_der) return AGP_OK;
+  const int64_t n = pl->n, m = af->m;
+  const int P = pl->P, k = af->k, fill = af->fill;
+  const size_t kk = (size_t)k * k;
+  const double sf2 = pl->sigma_f * pl->sigma_f, s2 = pl->sigma_eps * pl->sigma_eps;
+  CallerPoints<T> cp;
+  AGP_TRY(caller_points<T>(pl, cp, st));
+  WinPts<T>* wpd = nullptr;
+  double *Kd = nullptr, *Ed = nullptr, *Pd = nullptr, *logdiag = nullptr, *quad = nullptr;
+  int* flag = nullptr;
+  AGP_CUDA(cudaMallocAsync(&wpd, sizeof(WinPts<T>) * P, st));
+  AGP_CUDA(cudaMemcpyAsync(wpd, cp.wp.data(), sizeof(WinPts<T>) * P, cudaMemcpyHostToDevice, st));
+  AGP_CUDA(cudaMallocAsync(&Kd, sizeof(double) * kk, st));
+  AGP_CUDA(cudaMallocAsync(&flag, sizeof(int), st));
+  AGP_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  struct Free {
+    void** a;
+    int na;
+    cudaStream_t st;
+    ~Free() {
+      for (int i = 0; i < na; ++i)
+        if (a[i]) cudaFreeAsync(a[i], st);
+    }
+  };
+  void* tmp[7] = {wpd, Kd, flag, nullptr, nullptr, nullptr, nullptr};
+  Free fr{tmp, 7, st};
+  af->KLL_h.resize(kk);
+  af->dKLL_h.resize(kk);
+  af->C_h.resize(kk);
+  af->Ci_h.resize(kk);
+  k_kernel_block<T><<<nblk((int64_t)kk, 256), 256, 0, st>>>(wpd, P, n, af->L, k, pl->kernel,
+                                                            pl->ell, sf2, 0, s2, Kd);
+  AGP_CUDA(cudaMemcpyAsync(af->KLL_h.data(), Kd, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  k_kernel_block<T><<<nblk((int64_t)kk, 256), 256, 0, st>>>(wpd, P, n, af->L, k, pl->kernel,
+                                                            pl->ell, sf2, 1, 0.0, Kd);
+  AGP_CUDA(cudaMemcpyAsync(af->dKLL_h.data(), Kd, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaMemcpyAsync(af->C_h.data(), af->C, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaMemcpyAsync(af->Ci_h.data(), af->Ci, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  af->quad_sum[0] = af->quad_sum[1] = af->quad_sum[2] = 0.0;
+  if (m > 0) {
+    // E = C^{-1} dK_LL C^{-T}, Pm = C^{-1} C^{-T} (host FP64)
+    const std::vector<double>& Ci = af->Ci_h;
+    std::vector<double> T1(kk), E(kk), Pm(kk);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        double t = 0.0, p = 0.0;
+        for (int q = 0; q <= i; ++q) t += Ci[(size_t)i * k + q] * af->dKLL_h[(size_t)q * k + j];
+        for (int q = 0; q <= std::min(i, j); ++q) p += Ci[(size_t)i * k + q] * Ci[(size_t)j * k + q];
+        T1[(size_t)i * k + j] = t;
+        Pm[(size_t)i * k + j] = p;
+      }
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        double t = 0.0;
+        for (int q = 0; q <= j; ++q) t += T1[(size_t)i * k + q] * Ci[(size_t)j * k + q];
+        E[(size_t)i * k + j] = t;
+      }
+    AGP_CUDA(cudaMallocAsync(&Ed, sizeof(double) * kk, st));
+    AGP_CUDA(cudaMallocAsync(&Pd, sizeof(double) * kk, st));
+    tmp[3] = Ed;
+    tmp[4] = Pd;
+    AGP_CUDA(cudaMemcpyAsync(Ed, E.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, st));
+    AGP_CUDA(cudaMemcpyAsync(Pd, Pm.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, st));
+    // Dl = (dK_FL/dell) C^{-T}
+    double* Bf = nullptr;
+    AGP_CUDA(cudaMallocAsync(&Bf, sizeof(double) * m * k, st));
+    AGP_CUDA(cudaMalloc(&af->Dl, sizeof(double) * m * k));
+    k_kernel_cols_rows<T><<<nblk(m * k, 256), 256, 0, st>>>(wpd, P, n, af->F, m, af->L, k,
+                                                            pl->kernel, pl->ell, sf2, Bf);
+    k_times_lower_t<<<nblk(m * k, 256), 256, 0, st>>>(Bf, m, k, af->Ci, af->Dl);
+    cudaFreeAsync(Bf, st);
+    // derivative rows of G
+    AGP_CUDA(cudaMallocAsync(&logdiag, sizeof(double) * m, st));
+    AGP_CUDA(cudaMallocAsync(&quad, sizeof(double) * 3 * m, st));
+    tmp[5] = logdiag;
+    tmp[6] = quad;
+    AGP_CUDA(cudaMalloc(&af->dGval, sizeof(double) * 3 * m * fill));
+    const size_t fsmem = sizeof(double) * (size_t)fill * (fill + 1);
+    AGP_CUDA(cudaFuncSetAttribute(k_fsai_rows<T, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    k_fsai_rows<T, true><<<(unsigned)m, fsai_threads(fill), fsmem, st>>>(
+        wpd, P, n, af->F, af->W, k, af->J, af->len, m, fill, pl->kernel, pl->ell, pl->sigma_f,
+        pl->sigma_eps, af->Gval, logdiag, flag, af->Dl, Ed, Pd, af->dGval, quad);
+    std::vector<double> qh(3 * m);
+    int hflag = 0;
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaMemcpyAsync(qh.data(), quad, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // levels of the forward substitution
+    std::vector<int32_t> Jh(m * fill), lenh(m);
+    AGP_CUDA(cudaMemcpyAsync(Jh.data(), af->J, sizeof(int32_t) * m * fill, cudaMemcpyDeviceToHost,
+                             st));
+    AGP_CUDA(cudaMemcpyAsync(lenh.data(), af->len, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    if (hflag) return set_error(AGP_ENAN, "AFN: a Schur complement block is not positive definite");
+    for (int th = 0; th < 3; ++th)
+      for (int64_t a = 0; a < m; ++a) af->quad_sum[th] += qh[(size_t)th * m + a];
+    std::vector<int32_t> lev(m);
+    int32_t depth = 0;
+    for (int64_t t = 0; t < m; ++t) {
+      int32_t l = 0;
+      for (int q = 0; q < lenh[t] - 1; ++q) l = std::max(l, lev[Jh[(size_t)t * fill + q]] + 1);
+      lev[t] = l;
+      depth = std::max(depth, l + 1);
+    }
+    af->lvl_off.assign(depth + 1, 0);
+    for (int64_t t = 0; t < m; ++t) ++af->lvl_off[lev[t] + 1];
+    for (int32_t l = 0; l < depth; ++l) af->lvl_off[l + 1] += af->lvl_off[l];
+    std::vector<int32_t> rows(m);
+    std::vector<int64_t> cur(af->lvl_off.begin(), af->lvl_off.end() - 1);
+    for (int64_t t = 0; t < m; ++t) rows[cur[lev[t]]++] = (int32_t)t;
+    AGP_CUDA(cudaMalloc(&af->lvl_rows, sizeof(int32_t) * m));
+    AGP_CUDA(cudaMemcpyAsync(af->lvl_rows, rows.data(), sizeof(int32_t) * m,
+                             cudaMemcpyHostToDevice, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+  }
+  af->has_der = true;
+  return cuda_status(cudaGetLastError(), "afn_build_derivs");
+}
+
+agp_status afn_trsv(const Afn& af, const double* X, double* Y, int R, cudaStream_t st) {
+  if (!af.has_der || R < 1 || R > 32) return set_error(AGP_EINVAL, "AFN: no levels / bad R");
+  for (size_t l = 0; l + 1 < af.lvl_off.size(); ++l) {
+    const int64_t nr = af.lvl_off[l + 1] - af.lvl_off[l];
+    const unsigned blocks = (unsigned)std::min<int64_t>(nblk(nr, 8), 152 * 16);
+    k_afn_trsv_level<<<blocks, 256, 0, st>>>(af.lvl_rows + af.lvl_off[l], nr, af.Gval, af.J, af.len,
+                                             af.fill, R, X, Y);
+  }
+  return cuda_status(cudaGetLastError(), "afn_trsv");
+}
+
+agp_status afn_dg_apply(const Afn& af, int theta, const double* X, double* Y, int R,
+                        cudaStream_t st) {
+  if (!af.has_der || theta < 0 || theta > 2 || R < 1 || R > 32)
+    return set_error(AGP_EINVAL, "AFN: no derivatives / bad arguments");
+  if (af.m == 0) return AGP_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>(nblk(af.m, 8), 152 * 16);
+  k_afn_g<<<blocks, 256, 0, st>>>(af.dGval + (int64_t)theta * af.m * af.fill, af.J, af.len,
+                                  af.fill, af.m, R, X, Y);
+  return cuda_status(cudaGetLastError(), "afn_dg_apply");
+}
+
+agp_status afn_wt(const Afn& af, const double* A, const double* X, int R, double* out,
+                  cudaStream_t st) {
+  if (R < 1 || R > af.rmax) return set_error(AGP_EINVAL, "AFN: bad R");
+  const int k = af.k;
+  if (af.m == 0) {
+    std::fill(out, out + (size_t)k * R, 0.0);
+    return AGP_OK;
+  }
+  k_afn_wt<<<dim3((k + 31) / 32, af.slices), 256, 0, st>>>(A, X, af.m, k, R, af.rows_per_slice,
+                                                          af.partial);
+  k_sum_slices<<<nblk((int64_t)k * R, 128), 128, 0, st>>>(af.partial, af.slices, k, R, af.h);
+  AGP_CUDA(cudaGetLastError());
+  AGP_CUDA(cudaMemcpyAsync(out, af.h, sizeof(double) * k * R, cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  return AGP_OK;
+}
+
+template agp_status afn_build_derivs<float>(agp_plan_s*, Afn*, cudaStream_t);
+template agp_status afn_build_derivs<double>(agp_plan_s*, Afn*, cudaStream_t);
 template agp_status afn_build<float>(agp_plan_s*, int, int, int, Afn*, cudaStream_t);
 template agp_status afn_build<double>(agp_plan_s*, int, int, int, Afn*, cudaStream_t);
 

@@ -261,6 +261,16 @@ struct Afn {
   double* colval = nullptr;   // [nnz]
   double *v = nullptr, *h = nullptr, *partial = nullptr;   // apply workspace
   double *t = nullptr, *u = nullptr, *w = nullptr;
+  double* C = nullptr;        // [k][k] C (lower; zeros above the diagonal)
+  // likelihood data (afn_build_derivs): derivatives with the landmarks and
+  // the pattern held fixed, in the order ell, sigma_f, sigma_eps
+  bool has_der = false;
+  std::vector<double> KLL_h, C_h, Ci_h, dKLL_h;   // host [k][k]: K_LL, C, C^{-1}, dK_LL/dell
+  double quad_sum[3] = {0, 0, 0};   // sum_t G_t^T dS[J_t, J_t] G_t
+  double* Dl = nullptr;       // [m][k] (dK_FL/dell) C^{-T}
+  double* dGval = nullptr;    // [3][m][fill] dG/dtheta on the pattern
+  int32_t* lvl_rows = nullptr;        // rows of G ordered by level (triangular solve)
+  std::vector<int64_t> lvl_off;       // host: level l holds lvl_rows[lvl_off[l] .. lvl_off[l+1])
 };
 void afn_free(Afn* af);
 template <typename T>
@@ -270,6 +280,18 @@ agp_status afn_apply(const Afn& af, const double* X, int64_t ldx, double* Y, int
                      cudaStream_t st);
 // Host copies of the landmarks [k] and the pattern [m][fill] (either may be null).
 agp_status afn_pattern(const Afn& af, int32_t* landmarks, int32_t* J, cudaStream_t st);
+// Derivative data for the likelihood gradient (once per object).
+template <typename T>
+agp_status afn_build_derivs(agp_plan_s* pl, Afn* af, cudaStream_t st);
+// Y[t][r] = (G^{-1} X)[t][r] for FP64 [m][R] blocks (level-scheduled forward
+// substitution; R <= 32).
+agp_status afn_trsv(const Afn& af, const double* X, double* Y, int R, cudaStream_t st);
+// Y = dG_theta X for FP64 [m][R] blocks (theta = 0, 1, 2).
+agp_status afn_dg_apply(const Afn& af, int theta, const double* X, double* Y, int R,
+                        cudaStream_t st);
+// out[j][r] = sum_a A[a][j] X[a][r] over the m rows (A = W or Dl), host [k][R].
+agp_status afn_wt(const Afn& af, const double* A, const double* X, int R, double* out,
+                  cudaStream_t st);
 
 // ---- DFT stages (agp_fft.cu), one launch per stage for a group of windows ----
 template <typename T>

@@ -28,13 +28,13 @@
 
 // Compile-time tuning knobs (defaults are the measured best on GB300).
 #ifndef AGP_SPREAD_SUB
-#define AGP_SPREAD_SUB 128          // points per shared-memory stage of k_spread
+#define AGP_SPREAD_SUB 64           // points per shared-memory stage of k_spread
 #endif
 #ifndef AGP_INTERP_T2_UNROLL
 #define AGP_INTERP_T2_UNROLL 5      // rows of the block contracted together in k_interp2
 #endif
 #ifndef AGP_SPREAD_STAGES
-#define AGP_SPREAD_STAGES 2         // shared-memory stages in flight in k_spread (2 or 3)
+#define AGP_SPREAD_STAGES 3         // shared-memory stages in flight in k_spread (2 or 3)
 #endif
 #ifndef AGP_SPREAD_POINT_UNROLL
 #define AGP_SPREAD_POINT_UNROLL 1   // points of a stage processed together in k_spread

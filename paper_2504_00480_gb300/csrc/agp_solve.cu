@@ -690,6 +690,251 @@ agp_status nlml_pc_t(agp_plan_s* pl, const T* Y, const T* Wn, int64_t ldwn, cons
   return AGP_OK;
 }
 
+// out[j][r] = X[rows_j][r] (FP64 [cnt][R] from the plan precision [n][ldx])
+template <typename T>
+__global__ void k_gather_rows(const T* __restrict__ X, int64_t ldx, const int32_t* __restrict__ rows,
+                              int64_t cnt, int R, double* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= cnt * R) return;
+  const int64_t j = e / R;
+  out[e] = (double)X[(int64_t)rows[j] * ldx + (e - j * R)];
+}
+
+// AFN probes: Z[F_a][r] = sum_j W[a][j] wL[j][r] + y[a][r] (a warp per row,
+// wL staged in shared memory), Z[L_j][r] = zL[j][r]; Z in the plan precision
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_afn_probe_f(const double* __restrict__ W, const int32_t* __restrict__ F, int64_t m, int k, int nz,
+              const double* __restrict__ wL, const double* __restrict__ y, T* __restrict__ Z,
+              int64_t ldz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sw = reinterpret_cast<double*>(smem_raw);
+  for (int e = threadIdx.x; e < k * nz; e += blockDim.x) sw[e] = wL[e];
+  __syncthreads();
+  const int lane = threadIdx.x % 32;
+  if (lane >= nz) return;
+  for (int64_t a = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; a < m; a += (int64_t)gridDim.x * 8) {
+    const double* wr = W + a * k;
+    double s = y[a * nz + lane];
+    for (int j = 0; j < k; ++j) s = fma(wr[j], sw[j * nz + lane], s);
+    Z[(int64_t)F[a] * ldz + lane] = (T)s;
+  }
+}
+
+template <typename T>
+__global__ void k_scatter_rows(const double* __restrict__ src, const int32_t* __restrict__ rows,
+                               int cnt, int R, T* __restrict__ Z, int64_t ldz) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= cnt * R) return;
+  const int j = e / R;
+  Z[(int64_t)rows[j] * ldz + (e - j * R)] = (T)src[e];
+}
+
+// x = K_LL^{-1} b for the columns of b (host [k][R]) with the lower factor C
+void chol_solve_host(const std::vector<double>& C, int k, int R, std::vector<double>& b) {
+  for (int r = 0; r < R; ++r) {
+    for (int i = 0; i < k; ++i) {
+      double v = b[(size_t)i * R + r];
+      for (int j = 0; j < i; ++j) v -= C[(size_t)i * k + j] * b[(size_t)j * R + r];
+      b[(size_t)i * R + r] = v / C[(size_t)i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double v = b[(size_t)i * R + r];
+      for (int j = i + 1; j < k; ++j) v -= C[(size_t)j * k + i] * b[(size_t)j * R + r];
+      b[(size_t)i * R + r] = v / C[(size_t)i * k + i];
+    }
+  }
+}
+
+// NLML estimate and gradient with the additive AFN preconditioner (Sec. 1
+// eqs. (1.3)-(1.5), M of Sec. 2.3 as built by afn_build): the estimator of
+// nlml_pc_t with
+//   probes     z_L = C w_L, z_F = W w_L + G^{-1} w_F  (covariance M),
+//   log det M  from the factors, tr(M^{-1} dM) = d log det M / dtheta =
+//              tr(K_LL^{-1} dK_LL) + sum_t G_t^T dS G_t,
+//   p^T dM p = 2 (dX^T w).z_L + q_L^T dK_LL q_L - 2 u^T (dG t)
+// for p = M^{-1} z, where X = K_FL K_LL^{-1}, q_L = K_LL^{-1} z_L, and t =
+// z_F - X z_L, u = G t, w = G^T u = p_F are the apply's intermediates;
+// dX^T w = K_LL^{-1} (dK_LF w - dK_LL X^T w) with X^T w = C^{-T} W^T w.
+template <typename T>
+agp_status nlml_afn_t(agp_plan_s* pl, Afn* af, const T* Y, const T* Wn, int64_t ldwn, int nz,
+                      int steps, double rtol, int maxit, double* nlml, double* grad,
+                      cudaStream_t st) {
+  const int64_t n = pl->n, m = af->m;
+  const int R = 1 + nz, k = af->k;
+  const double sig = pl->sigma_eps, s2 = sig * sig, sf = pl->sigma_f;
+  AGP_TRY(afn_build_derivs<T>(pl, af, st));
+  const std::vector<double>& C = af->C_h;
+  T *Bblk = nullptr, *Xs = nullptr, *Din = nullptr, *Dout = nullptr;
+  double *wF = nullptr, *yF = nullptr, *wL = nullptr, *Zd = nullptr, *Pd = nullptr, *dots = nullptr,
+         *part = nullptr, *tmp = nullptr;
+  AGP_CUDA(cudaMallocAsync(&Bblk, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&Xs, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&Din, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&Dout, sizeof(T) * n * R, st));
+  AGP_CUDA(cudaMallocAsync(&wF, sizeof(double) * std::max<int64_t>(1, m) * nz, st));
+  AGP_CUDA(cudaMallocAsync(&yF, sizeof(double) * std::max<int64_t>(1, m) * nz, st));
+  AGP_CUDA(cudaMallocAsync(&tmp, sizeof(double) * std::max<int64_t>(1, m) * nz, st));
+  AGP_CUDA(cudaMallocAsync(&wL, sizeof(double) * k * nz, st));
+  AGP_CUDA(cudaMallocAsync(&Zd, sizeof(double) * n * nz, st));
+  AGP_CUDA(cudaMallocAsync(&Pd, sizeof(double) * n * nz, st));
+  AGP_CUDA(cudaMallocAsync(&dots, sizeof(double) * 4 * R, st));
+  AGP_CUDA(cudaMallocAsync(&part, sizeof(double) * kMaxDotBlocks * R, st));
+  struct Free {
+    void* a[12];
+    cudaStream_t st;
+    ~Free() {
+      for (void* p : a) cudaFreeAsync(p, st);
+    }
+  } fr{{Bblk, Xs, Din, Dout, wF, yF, tmp, wL, Zd, Pd, dots, part}, st};
+  // probes
+  std::vector<double> wLh((size_t)k * nz);
+  k_gather_rows<T><<<nblk((int64_t)k * nz, 256), 256, 0, st>>>(Wn, ldwn, af->L, k, nz, wL);
+  AGP_CUDA(cudaMemcpyAsync(wLh.data(), wL, sizeof(double) * k * nz, cudaMemcpyDeviceToHost, st));
+  k_copy_block<T, T><<<nblk(n, 256), 256, 0, st>>>(Y, 1, Bblk, R, n, 1);
+  pl->launches[3] += 2;
+  if (m > 0) {
+    k_gather_rows<T><<<nblk(m * nz, 256), 256, 0, st>>>(Wn, ldwn, af->F, m, nz, wF);
+    AGP_TRY(afn_trsv(*af, wF, yF, nz, st));
+    const size_t smem = sizeof(double) * (size_t)k * nz;
+    AGP_CUDA(cudaFuncSetAttribute(k_afn_probe_f<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(double) * kMaxLandmarkSet * 32)));
+    const unsigned blocks = (unsigned)std::min<int64_t>(nblk(m, 8), 152 * 16);
+    k_afn_probe_f<T><<<blocks, 256, smem, st>>>(af->W, af->F, m, k, nz, wL, yF, Bblk + 1, R);
+    pl->launches[3] += (int64_t)af->lvl_off.size() + 1;
+  }
+  AGP_CUDA(cudaStreamSynchronize(st));
+  std::vector<double> zLh((size_t)k * nz, 0.0);
+  for (int i = 0; i < k; ++i)
+    for (int r = 0; r < nz; ++r) {
+      double v = 0.0;
+      for (int j = 0; j <= i; ++j) v += C[(size_t)i * k + j] * wLh[(size_t)j * nz + r];
+      zLh[(size_t)i * nz + r] = v;
+    }
+  AGP_CUDA(cudaMemcpyAsync(wL, zLh.data(), sizeof(double) * k * nz, cudaMemcpyHostToDevice, st));
+  k_scatter_rows<T><<<nblk((int64_t)k * nz, 128), 128, 0, st>>>(wL, af->L, k, nz, Bblk + 1, R);
+  pl->launches[3] += 1;
+  AGP_CUDA(cudaGetLastError());
+  // PCG-Lanczos on [y, z_1..z_nz]
+  std::vector<int> mi(R, steps);
+  std::vector<double> tl(R, 0.0);
+  if (rtol > 0) {
+    mi[0] = maxit;
+    tl[0] = rtol;
+  }
+  std::vector<double> h(2 * R);
+  {
+    Workspace<T> ws;
+    AGP_TRY(cg_run<T>(pl, Bblk, R, Xs, R, R, mi, tl, rtol > 0 ? 5 : 0, ws, st, nullptr, af));
+    AGP_TRY(col_dot(Bblk, R, Xs, R, n, 1, ws.partial, dots, st, pl));
+    k_slq_logdet<<<nblk(nz, kSlqThreads), kSlqThreads, 0, st>>>(ws.ahist, ws.bhist, ws.iscal + R,
+                                                                 ws.rz0, R, 1, dots + R);
+    pl->launches[3] += 1;
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaMemcpyAsync(h.data(), dots, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+  }
+  double quad = 0.0;
+  for (int c = 1; c < R; ++c) quad += h[R + c];
+  *nlml = 0.5 * (h[0] + af->logdet + quad / nz + (double)n * std::log(2.0 * M_PI));
+
+  // p = M^{-1} z (z as rounded to the plan precision); the apply leaves t, u
+  // and w = p_F in af->t, af->u, af->w
+  k_copy_block<T, double><<<nblk(n * nz, 256), 256, 0, st>>>(Bblk + 1, R, Zd, nz, n, nz);
+  pl->launches[3] += 1;
+  AGP_TRY(afn_apply(*af, Zd, nz, Pd, nz, nz, st));
+  std::vector<double> zL((size_t)k * nz), WTw((size_t)k * nz), DTw((size_t)k * nz);
+  k_gather_rows<double><<<nblk((int64_t)k * nz, 256), 256, 0, st>>>(Zd, nz, af->L, k, nz, wL);
+  AGP_CUDA(cudaMemcpyAsync(zL.data(), wL, sizeof(double) * k * nz, cudaMemcpyDeviceToHost, st));
+  AGP_TRY(afn_wt(*af, af->W, af->w, nz, WTw.data(), st));
+  AGP_TRY(afn_wt(*af, af->Dl, af->w, nz, DTw.data(), st));
+  // -2 u^T (dG_theta t), per column
+  std::vector<double> udgt[3];
+  for (int th = 0; th < 3; ++th) {
+    udgt[th].assign(nz, 0.0);
+    if (m == 0) continue;
+    AGP_TRY(afn_dg_apply(*af, th, af->t, tmp, nz, st));
+    AGP_TRY(col_dot(af->u, nz, tmp, nz, m, nz, part, dots, st, pl));
+    AGP_CUDA(cudaMemcpyAsync(udgt[th].data(), dots, sizeof(double) * nz, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+  }
+  // host k x k algebra
+  std::vector<double> qL = zL;
+  chol_solve_host(C, k, nz, qL);                       // K_LL^{-1} z_L
+  std::vector<double> XTw((size_t)k * nz);             // C^{-T} W^T w
+  for (int r = 0; r < nz; ++r)
+    for (int i = k - 1; i >= 0; --i) {
+      double v = WTw[(size_t)i * nz + r];
+      for (int j = i + 1; j < k; ++j) v -= C[(size_t)j * k + i] * XTw[(size_t)j * nz + r];
+      XTw[(size_t)i * nz + r] = v / C[(size_t)i * k + i];
+    }
+  std::vector<double> KinvXTw = XTw;
+  chol_solve_host(C, k, nz, KinvXTw);
+  // dX^T w for ell: K_LL^{-1} (C (Dl^T w) - dK_LL X^T w)
+  std::vector<double> dxw((size_t)k * nz);
+  for (int i = 0; i < k; ++i)
+    for (int r = 0; r < nz; ++r) {
+      double v = 0.0;
+      for (int j = 0; j <= i; ++j) v += C[(size_t)i * k + j] * DTw[(size_t)j * nz + r];
+      for (int j = 0; j < k; ++j) v -= af->dKLL_h[(size_t)i * k + j] * XTw[(size_t)j * nz + r];
+      dxw[(size_t)i * nz + r] = v;
+    }
+  chol_solve_host(C, k, nz, dxw);
+  // K_LL^{-1} (host, from C^{-1}) for the traces
+  const std::vector<double>& Ci = af->Ci_h;
+  double tr_kinv = 0.0, tr_kinv_dk = 0.0;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      double v = 0.0;   // (C^{-T} C^{-1})_ij
+      for (int q = std::max(i, j); q < k; ++q) v += Ci[(size_t)q * k + i] * Ci[(size_t)q * k + j];
+      if (i == j) tr_kinv += v;
+      tr_kinv_dk += v * af->dKLL_h[(size_t)j * k + i];
+    }
+  const double tr_dm[3] = {tr_kinv_dk + af->quad_sum[0],
+                           (2.0 / sf) * ((double)k - s2 * tr_kinv) + af->quad_sum[1],
+                           2.0 * sig * tr_kinv + af->quad_sum[2]};
+  std::vector<double> pdp[3] = {std::vector<double>(nz), std::vector<double>(nz),
+                                std::vector<double>(nz)};
+  for (int r = 0; r < nz; ++r) {
+    double t1[3] = {0, 0, 0}, qkq = 0.0, qdq = 0.0, qq = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const double zl = zL[(size_t)i * nz + r], ql = qL[(size_t)i * nz + r];
+      t1[0] += dxw[(size_t)i * nz + r] * zl;
+      t1[1] += (2.0 / sf) * s2 * KinvXTw[(size_t)i * nz + r] * zl;
+      t1[2] += -2.0 * sig * KinvXTw[(size_t)i * nz + r] * zl;
+      qq += ql * ql;
+      double a = 0.0, b = 0.0;
+      for (int j = 0; j < k; ++j) {
+        a += af->KLL_h[(size_t)i * k + j] * qL[(size_t)j * nz + r];
+        b += af->dKLL_h[(size_t)i * k + j] * qL[(size_t)j * nz + r];
+      }
+      qkq += ql * a;
+      qdq += ql * b;
+    }
+    pdp[0][r] = 2.0 * t1[0] + qdq - 2.0 * udgt[0][r];
+    pdp[1][r] = 2.0 * t1[1] + (2.0 / sf) * (qkq - s2 * qq) - 2.0 * udgt[1][r];
+    pdp[2][r] = 2.0 * t1[2] + 2.0 * sig * qq - 2.0 * udgt[2][r];
+  }
+  // dK applied to [alpha, p_1..p_nz], dotted with [alpha, u_1..u_nz]
+  k_copy_block<T, T><<<nblk(n, 256), 256, 0, st>>>(Xs, R, Din, R, n, 1);
+  k_copy_block<double, T><<<nblk(n * nz, 256), 256, 0, st>>>(Pd, nz, Din + 1, R, n, nz);
+  pl->launches[3] += 2;
+  const agp_param ths[3] = {AGP_D_ELL, AGP_D_SIGMA_F, AGP_D_SIGMA_EPS};
+  for (int t = 0; t < 3; ++t) {
+    AGP_TRY(agp_deriv_matvec(pl, ths[t], Din, R, Dout, R, R, st));
+    AGP_TRY(col_dot(Xs, R, Dout, R, n, R, part, dots, st, pl));
+    std::vector<double> g(R);
+    AGP_CUDA(cudaMemcpyAsync(g.data(), dots, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    double smean = 0.0;
+    for (int r = 0; r < nz; ++r) smean += g[1 + r] - pdp[t][r];
+    grad[t] = 0.5 * (-g[0] + tr_dm[t] + smean / nz);
+  }
+  if (!std::isfinite(*nlml))
+    return set_error(AGP_ENAN, "SLQ met a non-positive Ritz value: K_hat is indefinite here");
+  return AGP_OK;
+}
+
 }  // namespace
 }  // namespace agp
 
@@ -778,6 +1023,24 @@ agp_status agp_pcg_solve_afn(agp_plan pl, agp_afn afn, const void* B, int64_t ld
                         relres, st, af);
   return pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, 0, iters,
                        relres, st, af);
+}
+
+agp_status agp_nlml_grad_afn(agp_plan pl, agp_afn afn, const void* Y, const void* Wn,
+                             int64_t ldwn, int nz, int lanczos_steps, double rtol, int maxit,
+                             double* nlml, double* grad, void* stream) {
+  if (!pl || !afn || !Y || !Wn || !nlml || !grad || nz < 1 || nz > 31 || ldwn < nz ||
+      lanczos_steps < 1 || lanczos_steps > kMaxLanczos || !(rtol >= 0) || (rtol > 0 && maxit < 1))
+    return set_error(AGP_EINVAL, "bad arguments");
+  Afn* af = reinterpret_cast<Afn*>(afn);
+  if (af->n != pl->n || af->ell != pl->ell || af->sigma_f != pl->sigma_f ||
+      af->sigma_eps != pl->sigma_eps || af->kernel != (int)pl->kernel)
+    return set_error(AGP_EINVAL, "the AFN preconditioner was built for other hyperparameters");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl->prec == AGP_F32)
+    return nlml_afn_t<float>(pl, af, (const float*)Y, (const float*)Wn, ldwn, nz, lanczos_steps,
+                             rtol, maxit, nlml, grad, st);
+  return nlml_afn_t<double>(pl, af, (const double*)Y, (const double*)Wn, ldwn, nz, lanczos_steps,
+                            rtol, maxit, nlml, grad, st);
 }
 
 agp_status agp_plan_landmarks(agp_plan pl, int n_landmarks, int32_t* idx, int cap, int* count,
