@@ -80,7 +80,11 @@ def kernel(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
     Sec. 2.1, eq. (2.2): Gaussian exp(-r^2 / (2 ell^2)) and Matern(1/2)
     exp(-r / ell); the Matern(3/2) kernel of the remark in Sec. 4,
     (1 + sqrt(3) r / l) exp(-sqrt(3) r / l) with l = sqrt(3) ell, i.e.
-    (1 + r / ell) exp(-r / ell). None carries sigma_f (it multiplies the sum)."""
+    (1 + r / ell) exp(-r / ell); and two of the further kernels named in
+    Sec. 4 (generalisation), normalised to kappa(0) = 1 with c = ell: the
+    inverse multiquadric (r^2 + c^2)^{-1/2} c = (1 + r^2/ell^2)^{-1/2} and
+    the sinc kernel sin(r / ell) / (r / ell). None carries sigma_f (it
+    multiplies the sum)."""
     r = np.asarray(r, dtype=np.float64)
     if kind == "gauss":
         return np.exp(-(r * r) / (2.0 * ell * ell))
@@ -88,6 +92,10 @@ def kernel(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
         return np.exp(-r / ell)
     if kind == "matern32":
         return (1.0 + r / ell) * np.exp(-r / ell)
+    if kind == "imq":
+        return 1.0 / np.sqrt(1.0 + (r / ell) ** 2)
+    if kind == "sinc":
+        return np.sinc(r / (ell * math.pi))   # numpy's sinc(x) = sin(pi x) / (pi x)
     raise ValueError(kind)
 
 
@@ -102,6 +110,19 @@ def kernel_der_ell(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
         return r / ell ** 2 * kernel(kind, r, ell)
     if kind == "matern32":
         return (r * r) / ell ** 3 * np.exp(-r / ell)
+    if kind == "imq":
+        # d/dell (1 + r^2/ell^2)^{-1/2} = r^2/ell^3 (1 + r^2/ell^2)^{-3/2}
+        return (r * r) / ell ** 3 * (1.0 + (r / ell) ** 2) ** -1.5
+    if kind == "sinc":
+        # d/dell [ell sin(u) / r], u = r / ell: (sin(u)/u - cos(u)) / ell, and
+        # for small u its series u^2/3 - u^4/30 + u^6/840 - u^8/45360 (the
+        # closed form cancels there)
+        u = r / ell
+        with np.errstate(divide="ignore", invalid="ignore"):
+            closed = (np.sin(u) / u - np.cos(u)) / ell
+        u2 = u * u
+        series = u2 * (1.0 / 3 - u2 * (1.0 / 30 - u2 * (1.0 / 840 - u2 / 45360))) / ell
+        return np.where(u < 0.05, series, closed)
     raise ValueError(kind)
 
 

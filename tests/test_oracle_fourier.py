@@ -11,7 +11,7 @@ import pytest
 import oracle as O
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-KINDS = ["gauss", "matern12", "matern32"]
+KINDS = ["gauss", "matern12", "matern32", "imq", "sinc"]
 
 
 def _read_golden(name):

@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 
-KINDS = ["gauss", "matern12", "matern32"]
+KINDS = ["gauss", "matern12", "matern32", "imq", "sinc"]
 
 
 def test_kernel_textbook_values():
@@ -43,9 +43,13 @@ def _brute(X, windows, kind, ell, sf, se, v):
                     k = math.exp(-d2 / (2 * ell * ell))
                 elif kind == "matern12":
                     k = math.exp(-r / ell)
-                else:   # Matern(3/2) in the form of Sec. 4 with l = sqrt(3) ell
+                elif kind == "matern32":   # the form of Sec. 4 with l = sqrt(3) ell
                     l = math.sqrt(3.0) * ell
                     k = (1 + math.sqrt(3.0) * r / l) * math.exp(-math.sqrt(3.0) * r / l)
+                elif kind == "imq":        # c (r^2 + c^2)^{-1/2}, c = ell
+                    k = ell / math.sqrt(d2 + ell * ell)
+                else:                      # sinc: sin(r / ell) / (r / ell)
+                    k = 1.0 if r == 0 else math.sin(r / ell) * ell / r
                 acc += k * v[j]
         out[i] = sf * sf * acc + se * se * v[i]
     return np.array(out)
@@ -155,3 +159,24 @@ def test_matern32_textbook_values():
     r = 0.6
     assert O.kernel("matern32", r, 0.25) == pytest.approx(
         (1 + math.sqrt(3.0) * r / l) * math.exp(-math.sqrt(3.0) * r / l), rel=1e-14)
+
+
+def test_imq_and_sinc_textbook_values():
+    # inverse multiquadric at r = ell: 1/sqrt(2); at r = sqrt(3) ell: 1/2
+    assert O.kernel("imq", 0.3, 0.3) == pytest.approx(1.0 / math.sqrt(2.0), rel=1e-15)
+    assert O.kernel("imq", math.sqrt(3.0) * 0.2, 0.2) == pytest.approx(0.5, rel=1e-15)
+    # sinc: zero at r = pi ell, 2/pi at r = pi ell / 2, 1 at r = 0
+    assert abs(O.kernel("sinc", math.pi * 0.1, 0.1)) < 1e-15
+    assert O.kernel("sinc", math.pi * 0.05, 0.1) == pytest.approx(2.0 / math.pi, rel=1e-15)
+    assert O.kernel("sinc", 0.0, 0.1) == 1.0
+
+
+def test_sinc_derivative_series_meets_closed_form():
+    # the small-argument series and the closed form agree where both are
+    # accurate, and the derivative vanishes at r = 0
+    ell = 0.2
+    r = np.array([0.04, 0.049, 0.0501, 0.06]) * ell
+    u = r / ell
+    closed = (np.sin(u) / u - np.cos(u)) / ell
+    np.testing.assert_allclose(O.kernel_der_ell("sinc", r, ell), closed, rtol=1e-11)
+    assert O.kernel_der_ell("sinc", 0.0, ell) == 0.0
