@@ -55,8 +55,16 @@ typedef enum {
 } agp_status;
 
 /* Sec. 2.1 eq. (2.2): Gaussian exp(-r^2/(2 ell^2)), Matern(1/2) exp(-r/ell);
- * Matern(3/2) of the remark in Sec. 4, (1 + r/ell) exp(-r/ell) (its l = sqrt(3) ell). */
-typedef enum { AGP_GAUSS = 0, AGP_MATERN12 = 1, AGP_MATERN32 = 2 } agp_kernel;
+ * Matern(3/2) of the remark in Sec. 4, (1 + r/ell) exp(-r/ell) (its l = sqrt(3) ell);
+ * two further kernels named in Sec. 4, normalised to 1 at r = 0 with c = ell:
+ * the inverse multiquadric (1 + r^2/ell^2)^{-1/2} and sinc sin(r/ell) / (r/ell). */
+typedef enum {
+  AGP_GAUSS = 0,
+  AGP_MATERN12 = 1,
+  AGP_MATERN32 = 2,
+  AGP_IMQ = 3,
+  AGP_SINC = 4
+} agp_kernel;
 typedef enum { AGP_F32 = 0, AGP_F64 = 1 } agp_prec;
 typedef enum { AGP_D_ELL = 0, AGP_D_SIGMA_F = 1, AGP_D_SIGMA_EPS = 2 } agp_param;
 

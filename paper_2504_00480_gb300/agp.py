@@ -21,7 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libagp.so")
 
 AGP_OK, AGP_EINVAL, AGP_EDOMAIN, AGP_ECUDA, AGP_ENOMEM, AGP_NOT_CONVERGED, AGP_TIMEOUT, AGP_ENAN = range(8)
-KERNELS = {"gauss": 0, "matern12": 1, "matern32": 2}
+KERNELS = {"gauss": 0, "matern12": 1, "matern32": 2, "imq": 3, "sinc": 4}
 PARAMS = {"ell": 0, "sigma_f": 1, "sigma_eps": 2}
 
 

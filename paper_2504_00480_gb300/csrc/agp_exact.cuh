@@ -81,9 +81,8 @@ struct WinPts {
 };
 
 // sum_s kappa_s(|x_i^s - x_l^s|) (der = 0) or its ell-derivative (der = 1;
-// Sec. 2.1 eq. (2.3): Gaussian kappa r^2 / ell^3, Matern(1/2) kappa r / ell^2,
-// Matern(3/2) r^2 / ell^3 e^{-r/ell}),
-// exact kernel in FP64 from the plan-precision coordinates
+// Sec. 2.1 eq. (2.3) and kernel_value), exact kernel in FP64 from the
+// plan-precision coordinates
 template <typename T>
 __device__ double kernel_sum(const WinPts<T>* __restrict__ wp, int P, int64_t n, int64_t i,
                              int64_t l, int kernel, double ell, int der) {
@@ -95,18 +94,7 @@ __device__ double kernel_sum(const WinPts<T>* __restrict__ wp, int P, int64_t n,
       const double u = (double)p.x[(int64_t)t * n + i] - (double)p.x[(int64_t)t * n + l];
       r2 += u * u;
     }
-    if (kernel == AGP_GAUSS) {
-      const double kv = exp(-r2 / (2.0 * ell * ell));
-      s += der ? kv * r2 / (ell * ell * ell) : kv;
-    } else if (kernel == AGP_MATERN12) {
-      const double r = sqrt(r2);
-      const double kv = exp(-r / ell);
-      s += der ? kv * r / (ell * ell) : kv;
-    } else {   // Matern(3/2)
-      const double r = sqrt(r2);
-      const double ex = exp(-r / ell);
-      s += der ? r2 / (ell * ell * ell) * ex : (1.0 + r / ell) * ex;
-    }
+    s += kernel_value(kernel, r2, ell, der);
   }
   return s;
 }

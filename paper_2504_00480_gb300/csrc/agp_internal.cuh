@@ -94,6 +94,39 @@ __device__ __forceinline__ double kb_psi(double delta, double s, double b, doubl
   return sinh(b * r) / r * norm;
 }
 
+// kappa(r) (der = 0) or d kappa / d ell (der = 1) for the kernels of
+// agp_kernel, from r^2, in FP64 (Sec. 2.1 eqs. (2.2)-(2.3), Sec. 4).
+__device__ __forceinline__ double kernel_value(int kernel, double r2, double ell, int der) {
+  if (kernel == AGP_GAUSS) {
+    const double kv = exp(-r2 / (2.0 * ell * ell));
+    return der ? kv * r2 / (ell * ell * ell) : kv;
+  }
+  if (kernel == AGP_MATERN12) {
+    const double r = sqrt(r2);
+    const double kv = exp(-r / ell);
+    return der ? kv * r / (ell * ell) : kv;
+  }
+  if (kernel == AGP_MATERN32) {   // (1 + r/ell) e^{-r/ell}; derivative r^2/ell^3 e^{-r/ell}
+    const double r = sqrt(r2);
+    const double ex = exp(-r / ell);
+    return der ? r2 / (ell * ell * ell) * ex : (1.0 + r / ell) * ex;
+  }
+  if (kernel == AGP_IMQ) {        // (1 + r^2/ell^2)^{-1/2}; derivative r^2/ell^3 (.)^{-3/2}
+    const double q = 1.0 / (1.0 + r2 / (ell * ell));
+    const double kv = sqrt(q);
+    return der ? r2 / (ell * ell * ell) * kv * q : kv;
+  }
+  // sinc: sin(u)/u with u = r/ell; derivative (sin(u)/u - cos(u)) / ell, by its
+  // series u^2/3 - u^4/30 + u^6/840 - u^8/45360 for u < 0.05 (cancellation)
+  const double u = sqrt(r2) / ell;
+  if (!der) return u < 1e-4 ? 1.0 - u * u / 6.0 : sin(u) / u;
+  if (u < 0.05) {
+    const double u2 = u * u;
+    return u2 * (1.0 / 3 - u2 * (1.0 / 30 - u2 * (1.0 / 840 - u2 / 45360))) / ell;
+  }
+  return (sin(u) / u - cos(u)) / ell;
+}
+
 __device__ __forceinline__ float dev_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double dev_floor(double x) { return floor(x); }
 

@@ -171,20 +171,7 @@ __global__ void k_kernel_samples(double* __restrict__ out, int N, int d, int ker
     const double x = (double)l / N;
     r2 += x * x;
   }
-  double v;
-  if (kernel == AGP_GAUSS) {
-    v = exp(-r2 / (2.0 * ell * ell));
-    if (der) v *= r2 / (ell * ell * ell);
-  } else if (kernel == AGP_MATERN12) {
-    const double r = sqrt(r2);
-    v = exp(-r / ell);
-    if (der) v *= r / (ell * ell);
-  } else {   // Matern(3/2): (1 + r/ell) e^{-r/ell}, derivative r^2/ell^3 e^{-r/ell}
-    const double r = sqrt(r2);
-    const double ex = exp(-r / ell);
-    v = der ? r2 / (ell * ell * ell) * ex : (1.0 + r / ell) * ex;
-  }
-  out[e] = v;
+  out[e] = kernel_value(kernel, r2, ell, der);
 }
 
 // One axis of the d-dimensional DFT of eq. (3.2). The samples are real and
@@ -397,7 +384,7 @@ agp_status validate(const agp_plan_desc* d) {
   if (!(d->ell > 0) || !std::isfinite(d->ell) || !std::isfinite(d->sigma_f) ||
       !std::isfinite(d->sigma_eps))
     return set_error(AGP_EINVAL, "bad hyperparameters");
-  if (d->kernel != AGP_GAUSS && d->kernel != AGP_MATERN12 && d->kernel != AGP_MATERN32)
+  if (d->kernel < AGP_GAUSS || d->kernel > AGP_SINC)
     return set_error(AGP_EINVAL, "bad kernel");
   if (d->prec != AGP_F32 && d->prec != AGP_F64) return set_error(AGP_EINVAL, "bad prec");
   std::vector<int> used(d->p, 0);

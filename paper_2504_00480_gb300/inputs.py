@@ -72,7 +72,7 @@ class Workload:
     name: str
     X: np.ndarray                 # (n, p) scaled points, float64 holding `dtype` values
     windows: list                 # list of lists of 0-based feature ids
-    kernel: str                   # "gauss" | "matern12" | "matern32"
+    kernel: str                   # "gauss" | "matern12" | "matern32" | "imq" | "sinc"
     ell: float
     sigma_f: float
     sigma_eps: float

@@ -86,7 +86,7 @@ def test_domain_error(agp):
 # ---------------------------------------------------------------------------
 # a1: coefficients b_k (FP64 on the device)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["gauss", "matern12", "matern32"])
+@pytest.mark.parametrize("kind", ["gauss", "matern12", "matern32", "imq", "sinc"])
 @pytest.mark.parametrize("d,N", [(1, 32), (2, 64), (3, 32), (3, 16)])
 def test_coeffs_match_oracle(agp, kind, d, N):
     rng = np.random.default_rng(7)
@@ -237,13 +237,14 @@ def test_cutoffs_and_bandwidths(agp, s, N):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_matern32_matvec_and_derivatives(agp, dtype):
-    # the Matern(3/2) kernel of the remark in Sec. 4 on mixed windows (d = 3, 2, 1)
+@pytest.mark.parametrize("kind", ["matern32", "imq", "sinc"])
+def test_further_kernels_matvec_and_derivatives(agp, dtype, kind):
+    # the kernels of Sec. 4 beyond eq. (2.2) on mixed windows (d = 3, 2, 1)
     rng = np.random.default_rng(32)
     npdt = np.float32 if dtype == torch.float32 else np.float64
     X = points(rng, 2500, 6, npdt)
     W = [[0, 1, 2], [3, 4], [5]]
-    w = inputs.Workload("matern32", X, W, "matern32", 0.2, 0.8, 0.3, [32, 32, 32], 5, npdt,
+    w = inputs.Workload(kind, X, W, kind, 0.2, 0.8, 0.3, [32, 32, 32], 5, npdt,
                         V=rng.standard_normal((2500, 9)))
     check_matvec(agp, w, dtype)
 
