@@ -69,6 +69,8 @@ _SIGS = {
                               c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
     "agp_plan_landmarks": (c_int, [c_void_p, c_int, c_void_p, c_int, POINTER(c_int), c_void_p]),
     "agp_plan_set_item_points": (c_int, [c_void_p, c_int, c_void_p]),
+    "agp_plan_set_tensor_cores": (c_int, [c_void_p, c_int]),
+    "agp_plan_check": (c_int, [c_void_p, c_void_p]),
     "agp_plan_autotune": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_double),
                                   c_void_p]),
     "agp_nlml_grad_pc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, POINTER(c_double), c_int,
@@ -616,6 +618,13 @@ class Plan:
 
     def afn(self, n_landmarks: int, fill: int) -> Afn:
         return Afn(self, n_landmarks, fill)
+
+    def set_tensor_cores(self, enable: bool = True):
+        _check(load_library().agp_plan_set_tensor_cores(self._h, int(bool(enable))))
+
+    def check(self):
+        """Raise AgpError (AGP_TIMEOUT) if a bounded device wait expired."""
+        _check(load_library().agp_plan_check(self._h, _stream()))
 
     def autotune(self, R: int = 32, reps: int = 3):
         return agp_plan_autotune(self._h, R, reps)

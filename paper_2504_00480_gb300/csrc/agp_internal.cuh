@@ -184,6 +184,7 @@ struct agp_plan_s {
   double kb_b = 0, kb_norm = 0;
   int rc_max = 32;
   int item_points = agp::kItemPoints;   // points per work item (bin size), see agp_plan_autotune
+  int use_tc = 0;                // spreading on the tensor cores where supported
   std::vector<agp::Window> win;
   void* wins_dev = nullptr;      // WinDev<T>[P]
   int4* items_all = nullptr;     // work items of every window, grouped by d
@@ -216,6 +217,23 @@ template <typename T>
 cudaError_t spread_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
                          int64_t n_items, int d, int s, int RC, const T* V, int64_t ldv, int R,
                          cudaStream_t st);
+// Tensor-core spreading (agp_spread_tc.cu): FP32, d = 3, RC = 32, s = 4 or 5.
+// err receives bit 2 if a bounded wait expired.
+bool spread_tc_supported(int d, int s, int RC);
+cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
+                            int64_t n_items, int s, const float* V, int64_t ldv, int R, int* err,
+                            cudaStream_t st);
+// spread_items, or spread_items_tc when `tc` is set and the case is supported
+template <typename T>
+cudaError_t spread_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
+                             int64_t n_items, int d, int s, int RC, const T* V, int64_t ldv, int R,
+                             int tc, int* err, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (tc && spread_tc_supported(d, s, RC))
+      return spread_items_tc(wins, io, items, n_items, s, V, ldv, R, err, st);
+  }
+  return spread_items<T>(wins, io, items, n_items, d, s, RC, V, ldv, R, st);
+}
 // Interpolate the grids of those windows and add scale * result into
 // Out[:, 0..R) (with io: Out, ldo and scale of io[window]).
 template <typename T>

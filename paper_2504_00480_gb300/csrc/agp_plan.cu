@@ -51,7 +51,7 @@ agp_status cuda_status(cudaError_t e, const char* what) {
 
 namespace {
 
-enum : int { kErrDomain = 1 };
+enum : int { kErrDomain = 1, kErrTimeout = 2 };
 
 // ---------------------------------------------------------------------------
 // a0: binning and counting sort
@@ -699,8 +699,8 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 0, st, dd);
-      AGP_CUDA(spread_items<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc, V + r0, ldv,
-                               Rc, st));
+      AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
+                                   V + r0, ldv, Rc, pl->use_tc, pl->err_dev, st));
       pl->launches[0] += 1;
     }
     {
@@ -770,7 +770,8 @@ agp_status adjoint_nfft_t(agp_plan_s* pl, int window, const T* V, int64_t ldv, i
   for (int r0 = 0; r0 < R; r0 += rc) {
     const int Rc = R - r0 < rc ? R - r0 : rc;
     AGP_CUDA(zero_grids<T>(g, rc, st));
-    AGP_CUDA(spread_items<T>(wins, nullptr, w.items, w.n_items, w.d, pl->s, rc, V + r0, ldv, Rc, st));
+    AGP_CUDA(spread_items_sel<T>(wins, nullptr, w.items, w.n_items, w.d, pl->s, rc, V + r0, ldv,
+                                 Rc, pl->use_tc, pl->err_dev, st));
     AGP_CUDA(fft_forward<T>(g, rc, st));
     const T2* spec = (const T2*)((w.d % 2) ? w.specA : w.specB);
     k_extract_spectrum<T, T2><<<nblk(w.cells * Rc, 256), 256, 0, st>>>(
@@ -1007,6 +1008,27 @@ agp_status agp_profile_read(agp_plan pl, agp_profile_t* out, int reset, void* st
     }
     pl->prof_ev.clear();
     for (int k = 0; k < 4; ++k) pl->launches[k] = 0;
+  }
+  return AGP_OK;
+}
+
+agp_status agp_plan_set_tensor_cores(agp_plan pl, int enable) {
+  if (!pl) return set_error(AGP_EINVAL, "bad arguments");
+  pl->use_tc = enable ? 1 : 0;
+  return AGP_OK;
+}
+
+agp_status agp_plan_check(agp_plan pl, void* stream) {
+  if (!pl) return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int err = 0;
+  AGP_CUDA(cudaMemcpyAsync(&err, pl->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  if (err & kErrTimeout) {
+    const int keep = err & ~kErrTimeout;
+    AGP_CUDA(cudaMemcpyAsync(pl->err_dev, &keep, sizeof(int), cudaMemcpyHostToDevice, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    return set_error(AGP_TIMEOUT, "a bounded wait in a tensor-core kernel expired");
   }
   return AGP_OK;
 }

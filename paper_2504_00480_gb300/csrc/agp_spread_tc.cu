@@ -1,0 +1,395 @@
+// Spreading (adjoint NFFT, Appendix A) of d = 3 windows on the 5th-generation
+// tensor cores. For one work item (the points of one grid cell) the update
+// of the cell's (2s)^3 x R block of grid values is a dense contraction over
+// the points j:
+//     G[(t1, t2), (t3, r)] += sum_j A[(t1, t2), j] B[(t3, r), j],
+//     A[(t1, t2), j] = psi1_j(t1) psi2_j(t2),  B[(t3, r), j] = psi3_j(t3) v_j(r),
+// i.e. a [(2s)^2 x m] x [m x 2s R] matrix product per item (m <= item size).
+// Each CTA takes one item and 16 of the 32 right-hand sides: M = 128 rows
+// ((2s)^2 = 100 or 64, zero padded), N = 2s x 16 = 160 or 128 columns,
+// accumulated in tensor memory (TMEM) by tcgen05.mma kind::tf32 over chunks
+// of 16 points (two K = 8 steps). FP32 accuracy from TF32 inputs by the split
+// x = x_hi + x_lo (x_hi = x rounded to TF32, x_lo = the rounded remainder):
+//     A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// whose dropped term A_lo B_lo is ~2^-22 relative; products of TF32 values
+// are exact and the tensor cores accumulate in FP32.
+//
+// Pipeline (384 threads): the window values and V rows of later chunks are
+// staged with cp.async (kTcStages - 1 chunks ahead, perm indices one chunk
+// before that) while all threads form chunk c's four operand matrices in shared memory (K-major, no
+// swizzle: 8 x 16-byte core matrices, leading byte offset 128, stride byte
+// offset 512; each thread owns one element slot of every core matrix it
+// writes, so its window values are loaded once per chunk); one barrier per
+// chunk, after which thread 0 issues the chunk's six MMAs and commits them
+// to the buffer's mbarrier while the next chunk is formed in the other
+// buffer. The epilogue reads TMEM (warp w owns lanes 32 (w % 4) .. + 31 =
+// rows), transposes each 32 x 16 tile through shared memory and adds the
+// block into the window's grid with vector atomics, four lanes per row. Every mbarrier wait is bounded: on expiry the CTA records
+// a timeout in the plan's error word, waits (bounded) for its MMAs and
+// releases its TMEM.
+#include <type_traits>
+
+#include "agp_nufft_kernels.cuh"
+
+namespace agp {
+namespace {
+
+#ifndef AGP_TC_THREADS
+#define AGP_TC_THREADS 384          // threads per CTA of k_spread_tc (128 .. 512)
+#endif
+constexpr int kTcThreads = AGP_TC_THREADS;
+#ifndef AGP_TC_STAGES
+#define AGP_TC_STAGES 4             // staging buffers of k_spread_tc (prefetch distance - 1)
+#endif
+constexpr int kTcStages = AGP_TC_STAGES;
+constexpr int kTcKC = 16;       // points per chunk
+constexpr int kTcRH = 16;       // right-hand sides per CTA
+constexpr int kTcLBO = 128;     // bytes between core matrices along K
+constexpr int kTcSBO = (kTcKC / 4) * 128;   // bytes between 8-row groups
+constexpr long long kTcSpinLimit = 1ll << 26;
+
+template <int S>
+struct TcSpreadShape {
+  static constexpr int TT = 2 * S, TTP = ttp_of(S);
+  static constexpr int ROWS = TT * TT;
+  static constexpr int RG8 = (ROWS + 7) / 8;          // 8-row groups written per chunk
+  static constexpr int MR = 128;
+  static constexpr int NN = TT * kTcRH;
+  static constexpr int WPP = wpp_of(3, S);
+  static constexpr int A_BYTES = MR * kTcKC * 4;
+  static constexpr int B_BYTES = NN * kTcKC * 4;
+  static constexpr int OPND = 2 * A_BYTES + 2 * B_BYTES;     // hi and lo of A and B
+  static constexpr int STG_W = kTcKC * WPP;                   // floats
+  static constexpr int STG = (STG_W + kTcKC * kTcRH) * 4;     // bytes
+  static constexpr int SMEM = 2 * OPND + kTcStages * STG;
+  static constexpr int TMEM_COLS = NN <= 128 ? 128 : 256;
+  static_assert(ROWS <= MR, "(2s)^2 rows must fit one M = 128 tile");
+  static_assert(NN % 16 == 0 && NN <= 256, "N must be a multiple of 16, at most 256");
+  static_assert((WPP * 4) % 16 == 0, "window values must be 16-byte rows");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((kTcLBO >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((kTcSBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+// x rounded to the nearest TF32 value (10 fraction bits; ties away from zero)
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(smem_u32(bar)));
+}
+
+// bounded wait for the given phase parity; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kTcSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(a), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+
+// Operand formation of one chunk for thread group G (of NG) of a CTA, in the
+// thread's fixed element slot (row r8, point k4 of every core matrix of point
+// quad kq; element offset (row group (KC/4) + kq) 32 + lane). Fully unrolled:
+// every store offset is a constant relative to the thread's base pointer.
+template <int S, int G, int NG>
+__device__ __forceinline__ void form_a(const float* __restrict__ pw, bool live, int r8,
+                                       float* __restrict__ ph, float* __restrict__ pl) {
+  using Sh = TcSpreadShape<S>;
+  constexpr int TT = Sh::TT, TTP = Sh::TTP;
+  constexpr int RGA = G * Sh::RG8 / NG, RGB = (G + 1) * Sh::RG8 / NG;
+  int row = RGA * 8 + r8;
+  int t1 = row / TT, t2 = row - t1 * TT;
+#pragma unroll
+  for (int rg = RGA; rg < RGB; ++rg) {
+    const float x = (live && row < Sh::ROWS) ? pw[t1] * pw[TTP + t2] : 0.0f;
+    const float h = tf32_round(x);
+    ph[rg * (kTcKC / 4) * 32] = h;
+    pl[rg * (kTcKC / 4) * 32] = tf32_round(x - h);
+    row += 8;
+    t2 += 8;
+    if (t2 >= TT) {
+      t2 -= TT;
+      ++t1;
+    }
+  }
+}
+
+// B rows n = 8 rg + r8 = (t3, r): t3 = rg / 2, r = 8 (rg % 2) + r8; thread
+// group G of NG takes its share of the t3 range
+template <int S, int G, int NG>
+__device__ __forceinline__ void form_b(const float* __restrict__ p3, bool live, float v0, float v1,
+                                       float* __restrict__ ph, float* __restrict__ pl) {
+  constexpr int TT = 2 * S, T3A = G * TT / NG, T3B = (G + 1) * TT / NG;
+#pragma unroll
+  for (int t3 = T3A; t3 < T3B; ++t3) {
+    const float p = live ? p3[2 * t3] : 0.0f;
+    const float x0 = p * v0, x1 = p * v1;
+    const float h0 = tf32_round(x0), h1 = tf32_round(x1);
+    ph[(2 * t3) * (kTcKC / 4) * 32] = h0;
+    pl[(2 * t3) * (kTcKC / 4) * 32] = tf32_round(x0 - h0);
+    ph[(2 * t3 + 1) * (kTcKC / 4) * 32] = h1;
+    pl[(2 * t3 + 1) * (kTcKC / 4) * 32] = tf32_round(x1 - h1);
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kTcThreads)
+k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict__ io,
+            const int4* __restrict__ items, const float* __restrict__ V, int64_t ldv, int R,
+            int* __restrict__ err) {
+  using Sh = TcSpreadShape<S>;
+  constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, KC = kTcKC, RH = kTcRH;
+  static_assert(kTcThreads % 128 == 0 && kTcThreads <= 512, "groups of 128 threads");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int4 it = items[blockIdx.x >> 1];
+  const int r0 = (blockIdx.x & 1) * RH;           // right-hand sides r0 .. r0 + 15
+  if (r0 >= R) return;                            // whole CTA: nothing to add
+  const WinDev<float> w = wins[it.x];
+  if (io) {
+    V = io[it.x].V;
+    ldv = io[it.x].ldv;
+  }
+  const bool vec_ok = (ldv % 4 == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0);
+  const int j0 = it.z, m = it.w;
+  // operand buffer b (0, 1) at smem_raw + b OPND; staging buffer q (0 .. kTcStages - 1)
+  // at smem_raw + 2 OPND + q STG
+  auto opnd = [&](int b) { return smem_raw + b * Sh::OPND; };
+  auto stg = [&](int b) { return reinterpret_cast<float*>(smem_raw + 2 * Sh::OPND + b * Sh::STG); };
+
+  // zero the padding rows of A (hi and lo) of both buffers once
+  for (int b = 0; b < 2; ++b)
+    for (int e = Sh::RG8 * 8 * KC + tid; e < Sh::MR * KC; e += kTcThreads) {
+      reinterpret_cast<float*>(opnd(b))[e] = 0.0f;
+      reinterpret_cast<float*>(opnd(b) + Sh::A_BYTES)[e] = 0.0f;
+    }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(&tmem_slot)), "n"(Sh::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+
+  // staging runs PD = kTcStages - 1 chunks ahead of the formation: thread
+  // tid < 4 KC copies 16 bytes of one point's V row (point tid / 4, columns
+  // r0 + 4 (tid % 4) ..), its perm index loaded one chunk before that; one
+  // cp.async group is committed per chunk step (empty past the last chunk)
+  constexpr int PD = kTcStages - 1;
+  const int nchunk = (m + KC - 1) / KC;
+  const int vq = tid >> 2, vk = (tid & 3) * 4;
+  auto perm_of = [&](int c) -> int64_t {
+    const int q = c * KC + vq;
+    return (tid < 4 * KC && c < nchunk && q < m) ? (int64_t)__ldg(w.perm + j0 + q) : 0;
+  };
+  auto stage = [&](int c, int64_t pi) {
+    if (c >= nchunk) {
+      cp_async_commit();
+      return;
+    }
+    float* sw = stg(c % kTcStages);
+    float* sv = sw + Sh::STG_W;
+    const int q0 = c * KC;
+    const int ns = min(KC, m - q0);
+    const float* wsrc = w.wts + (int64_t)(j0 + q0) * WPP;
+    for (int e = tid; e < ns * (WPP / 4); e += kTcThreads) cp_async16(sw + e * 4, wsrc + e * 4, 16);
+    if (vec_ok) {
+      if (tid < 4 * KC && vq < ns) {
+        const int valid = max(0, min(4, R - (r0 + vk)));
+        cp_async16(sv + vq * RH + vk, V + pi * ldv + (valid > 0 ? r0 + vk : 0), valid * 4);
+      }
+    } else {
+      for (int e = tid; e < ns * RH; e += kTcThreads) {
+        const int q = e / RH, r = e % RH;
+        const int64_t i = __ldg(w.perm + j0 + q0 + q);
+        sv[e] = (r0 + r < R) ? V[i * ldv + r0 + r] : 0.0f;
+      }
+    }
+    cp_async_commit();
+  };
+
+  const uint32_t idesc = umma_idesc_tf32(Sh::MR, Sh::NN);
+  // this thread's slot in every core matrix it writes: row r8 and point k4
+  // within the core, point quad kq, and its share g of the row groups
+  const int slot = tid & 127, g = tid >> 7;
+  const int kq = slot >> 5, r8 = (lane >> 2), k4 = lane & 3;
+  const int kk = kq * 4 + k4;                      // point within the chunk
+  bool ok = true;
+  for (int c = 0; c < PD; ++c) stage(c, perm_of(c));
+  int64_t pf = perm_of(PD);
+  cp_async_wait<PD - 1>();                 // chunk 0 staged
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  for (int c = 0; c < nchunk; ++c) {
+    const int b = c & 1;
+    stage(c + PD, pf);                     // its buffer was last read by chunk c - 1
+    pf = perm_of(c + PD + 1);
+    if (c >= 2 && !mbar_wait(&bar[b], ((c - 2) >> 1) & 1)) ok = false;   // MMAs of chunk c-2
+    const float* sw = stg(c % kTcStages);
+    const float* sv = sw + Sh::STG_W;
+    const bool live = kk < min(KC, m - c * KC);
+    float* ahi = reinterpret_cast<float*>(opnd(b));
+    float* alo = reinterpret_cast<float*>(opnd(b) + Sh::A_BYTES);
+    float* bhi = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES);
+    float* blo = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES + Sh::B_BYTES);
+    {
+      const float* pw = sw + kk * WPP;
+      const float v0 = live ? sv[kk * RH + r8] : 0.0f;
+      const float v1 = live ? sv[kk * RH + 8 + r8] : 0.0f;
+      const int o = kq * 32 + lane;
+      constexpr int NG = kTcThreads / 128;
+      auto form = [&](auto gc) {
+        constexpr int G = decltype(gc)::value;
+        form_a<S, G, NG>(pw, live, r8, ahi + o, alo + o);
+        form_b<S, G, NG>(pw + 2 * TTP, live, v0, v1, bhi + o, blo + o);
+      };
+      switch (g) {
+        case 0: form(std::integral_constant<int, 0>()); break;
+        case 1: if constexpr (NG > 1) form(std::integral_constant<int, 1>()); break;
+        case 2: if constexpr (NG > 2) form(std::integral_constant<int, 2>()); break;
+        case 3: if constexpr (NG > 3) form(std::integral_constant<int, 3>()); break;
+      }
+    }
+    cp_async_wait<PD - 1>();              // chunk c + 1 staged (this thread's copies)
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();                      // operands of chunk c and staging of c + 1 complete
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      // descriptors differ only in the start address field (address >> 4)
+      const uint64_t a0 = umma_desc(smem_u32(ahi)), a1 = umma_desc(smem_u32(alo));
+      const uint64_t b0 = umma_desc(smem_u32(bhi)), b1 = umma_desc(smem_u32(blo));
+#pragma unroll
+      for (int s2 = 0; s2 < KC / 8; ++s2) {
+        const uint64_t off = (uint64_t)(s2 * 2 * kTcLBO) >> 4;
+        mma_tf32(tmem, a0 + off, b0 + off, idesc, (c > 0 || s2 > 0) ? 1u : 0u);
+        mma_tf32(tmem, a0 + off, b1 + off, idesc, 1u);
+        mma_tf32(tmem, a1 + off, b0 + off, idesc, 1u);
+      }
+      mma_commit(&bar[b]);
+    }
+  }
+  // the last commit covers every MMA of this CTA
+  if (!mbar_wait(&bar[(nchunk - 1) & 1], ((nchunk - 1) >> 1) & 1)) ok = false;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows (t1, t2)); with more
+    // than four warps the t3 range is split between the warps of a quarter.
+    // Each 32 x 16 tile (rows x right-hand sides) goes through shared memory
+    // (the operand buffers are free now) so that four lanes cover one row's
+    // 16 contiguous values: every vector atomic instruction of a warp then
+    // touches 8 rows x 64 bytes instead of 32 rows x 16 bytes.
+    constexpr int NQ = kTcThreads / 128;              // warps per lane quarter
+    const int quarter = warp % 4, part = warp / 4;
+    float* tile = reinterpret_cast<float*>(smem_raw) + warp * (32 * 17);
+    int cc[3];
+    decode_cell<3>(it.y, w.N, cc);
+    const int ta = part * TT / NQ, tb = (part + 1) * TT / NQ;
+    const int c4 = (lane & 3) * 4;
+#pragma unroll 1
+    for (int t3 = ta; t3 < tb; ++t3) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t3 * RH);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int q = 0; q < 16; ++q) tile[lane * 17 + q] = __uint_as_float(v[q]);
+      __syncwarp();
+#pragma unroll
+      for (int q8 = 0; q8 < 4; ++q8) {
+        const int rl = q8 * 8 + (lane >> 2);            // row within the quarter
+        const int row = quarter * 32 + rl;
+        if (row < Sh::ROWS && r0 + c4 < R) {
+          const int t1 = row / TT, t2 = row - (row / TT) * TT;
+          const int64_t base = ((int64_t)(cc[0] + t1) * w.W + (cc[1] + t2)) * w.W + cc[2] + t3;
+          const float* src = tile + rl * 17 + c4;
+          atomicAdd(reinterpret_cast<float4*>(w.grid + base * 32 + r0 + c4),
+                    make_float4(src[0], src[1], src[2], src[3]));
+        }
+      }
+      __syncwarp();
+    }
+  } else if (tid == 0) {
+    atomicOr(err, 2);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "n"(Sh::TMEM_COLS));
+}
+
+template <int S>
+cudaError_t spread_tc_s(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
+                        int64_t n_items, const float* V, int64_t ldv, int R, int* err,
+                        cudaStream_t st) {
+  using Sh = TcSpreadShape<S>;
+  cudaError_t e = cudaFuncSetAttribute(k_spread_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Sh::SMEM);
+  if (e != cudaSuccess) return e;
+  if (n_items <= 0) return cudaSuccess;
+  k_spread_tc<S><<<(unsigned)(2 * n_items), kTcThreads, Sh::SMEM, st>>>(wins, io, items, V, ldv,
+                                                                        R, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool spread_tc_supported(int d, int s, int RC) { return d == 3 && RC == 32 && (s == 4 || s == 5); }
+
+cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
+                            int64_t n_items, int s, const float* V, int64_t ldv, int R, int* err,
+                            cudaStream_t st) {
+  switch (s) {
+    case 4: return spread_tc_s<4>(wins, io, items, n_items, V, ldv, R, err, st);
+    case 5: return spread_tc_s<5>(wins, io, items, n_items, V, ldv, R, err, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace agp
