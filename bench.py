@@ -120,6 +120,14 @@ def measured_hbm_peak():
         return None
 
 
+def measured_bf16_peak():
+    """Dense BF16 tensor throughput (burst) measured on this machine, TFLOP/s."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def measured_traffic(kernel, n, R):
     """DRAM bytes (read + write) of one launch of `kernel` from the committed
     ncu summary in profiles/traffic.json, or None when the summary does not
@@ -220,6 +228,10 @@ def run_gpu(args):
     V = torch.tensor(w.V, dtype=torch.float32, device=dev)
     Out = torch.empty_like(V)
     plan = agp.Plan(X, w.windows, w.N, w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
+    # spreading and interpolation of the d=3 windows on the tensor cores (the
+    # library default for FP32 plans), or on the FP32 FMA pipes with --no-tc
+    tc = not args.no_tc and R == 32
+    plan.set_tensor_cores(tc)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ells = [w.ell * (1.0 + 1e-3 * k) for k in range(args.warmup + args.steps + 1)]
@@ -265,11 +277,30 @@ def run_gpu(args):
     launch_ms = prof[dom]["ms_by_dim"][3] / max(1, prof[dom]["timed_by_dim"][3])
     taps3 = sum((2 * w.cutoff) ** len(win) for win in w.windows if len(win) == 3)
     flops_launch = 2.0 * w.n * R * taps3
-    achieved = flops_launch / (launch_ms / 1e3) / 1e12
+    useful_tflops = flops_launch / (launch_ms / 1e3) / 1e12
     clocks = clk.summary()
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12   # FP32 FMA at max SM clock
-    kname = (f"k_spread<float, 3, {w.cutoff}, 32>" if dom == "spread"
-             else f"k_interp2<3, {w.cutoff}, 32>")
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12   # FP32 FMA at max SM clock
+    if tc:
+        # tensor-core kernels: the split-TF32 scheme performs three TF32
+        # products per FP32-accurate product, so the algorithmic tensor work
+        # of a launch is 3 x the useful flops (the M-padding of the (2s)^2 =
+        # 100 grid rows to 128 is waste and not counted); the TF32 dense peak
+        # is the measured BF16 burst peak x the nominal TF32 / BF16 ratio
+        # (1.1 / 2.25 PFLOP/s)
+        bound, flops_alg = "tensor", 3.0 * flops_launch
+        achieved = flops_alg / (launch_ms / 1e3) / 1e12
+        bf16 = measured_bf16_peak()
+        peak = None if bf16 is None else bf16 * (1.1 / 2.25)
+        peak_source = ("MEASURED_PEAKS.json bf16_tflops (burst) x 1.1/2.25 (nominal TF32/BF16 "
+                       "dense ratio)")
+        kname = f"k_spread_tc<{w.cutoff}>" if dom == "spread" else f"k_interp_tc<{w.cutoff}>"
+    else:
+        bound, flops_alg = "alu", flops_launch
+        achieved = useful_tflops
+        peak = fp32_peak
+        peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal maximum clock)"
+        kname = (f"k_spread<float, 3, {w.cutoff}, 32>" if dom == "spread"
+                 else f"k_interp2<3, {w.cutoff}, 32>")
     traffic = measured_traffic(kname, w.n, R)
     # HBM view of the same launch: algorithmic bytes = per point and d=3
     # window its 3 x 2s window values, its permutation index and its R-value
@@ -325,12 +356,14 @@ def run_gpu(args):
                         "pipelined": "upload of step k+1 and download of step k-1 overlap "
                                      "step k (double-buffered device blocks, three streams)"},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
-                "roofline": {"bound": "alu", "kernel": kname,
+                "roofline": {"bound": bound, "kernel": kname,
                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": traffic,
-                             "launch_ms": launch_ms, "flop_per_launch": flops_launch,
-                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz "
-                                            "(nominal maximum clock)"},
+                             "frac": None if peak is None else achieved / peak,
+                             "traffic": traffic, "launch_ms": launch_ms,
+                             "flop_per_launch": flops_alg, "peak_source": peak_source,
+                             "useful": {"flop_per_launch": flops_launch,
+                                        "tflops": useful_tflops,
+                                        "frac_of_fp32_fma_peak": useful_tflops / fp32_peak}},
                 "hbm": hbm,
                 "stages_ms_per_step": {s: prof[s]["ms"] / args.steps for s in prof},
                 "stage_launches_per_step": {s: prof[s]["launches"] / args.steps for s in prof},
@@ -485,6 +518,8 @@ def main():
     ap.add_argument("--plain-reps", type=int, default=5)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-nlml-pc", action="store_true")
+    ap.add_argument("--no-tc", action="store_true",
+                    help="spread and interpolate on the FP32 FMA pipes instead of the tensor cores")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -211,13 +211,16 @@ agp_status agp_pcg_solve(agp_plan plan, const void* B, int64_t ldb, void* Xsol, 
 agp_status agp_plan_landmarks(agp_plan plan, int n_landmarks, int32_t* idx, int cap, int* count,
                               void* stream);
 
-/* Spreading on the tensor cores (FP32 plans, d = 3 windows, s = 4 or 5, 32
- * right-hand sides per pass; other cases keep the FP32 FMA path): per work
- * item the cell's (2s)^2 x (2s R) block update is the matrix product of the
- * window-value matrices [(t1, t2) x points] and [points x (t3, r)], computed
- * by tcgen05.mma on TF32 operands split into a rounded part and its rounded
- * remainder (three products, about FP32 accuracy), accumulated in FP32.
- * enable: 1 on, 0 off (the default). */
+/* Spreading and interpolation on the tensor cores (FP32 plans, d = 3
+ * windows, s = 4 or 5, 32 right-hand sides per pass; other cases keep the
+ * FP32 FMA path). Per work item, spreading's update of the cell's
+ * (2s)^2 x (2s R) grid block is the matrix product [(t1, t2) x points] x
+ * [points x (t3, r)] of window-value matrices, and interpolation's sum over
+ * the first two dimensions is the product [points x (t1, t2)] x
+ * [(t1, t2) x (t3, r)] with the grid block; both run as tcgen05.mma on TF32
+ * operands split into a rounded part and its rounded remainder (three
+ * products, about FP32 accuracy), accumulated in FP32.
+ * enable: 1 on (the default for FP32 plans), 0 off (FMA path only). */
 agp_status agp_plan_set_tensor_cores(agp_plan plan, int enable);
 
 /* AGP_TIMEOUT if a bounded wait inside a tensor-core kernel expired since

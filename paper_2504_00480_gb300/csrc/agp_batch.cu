@@ -204,7 +204,8 @@ agp_status batch_matvec(agp_batch_s* b, int which, cudaStream_t st) {
   for (int dd = 1; dd <= kMaxDim; ++dd) {
     const int64_t a = b->items_by_d[dd - 1], e = b->items_by_d[dd];
     if (e > a)
-      AGP_CUDA(spread_items<T>(wins, io, b->items + a, e - a, dd, b->s, b->rc, nullptr, 0, b->R, st));
+      AGP_CUDA(spread_items_sel<T>(wins, io, b->items + a, e - a, dd, b->s, b->rc, nullptr, 0,
+                                   b->R, b->plans[0]->use_tc, b->plans[0]->err_dev, st));
   }
   for (const auto& g : b->groups) {
     AGP_CUDA(fft_forward<T>(g, b->rc, st));
@@ -214,8 +215,8 @@ agp_status batch_matvec(agp_batch_s* b, int which, cudaStream_t st) {
   for (int dd = 1; dd <= kMaxDim; ++dd) {
     const int64_t a = b->items_by_d[dd - 1], e = b->items_by_d[dd];
     if (e > a)
-      AGP_CUDA(interp_items<T>(wins, io, b->items + a, e - a, dd, b->s, b->rc, nullptr, 0, b->R,
-                               T(0), st));
+      AGP_CUDA(interp_items_sel<T>(wins, io, b->items + a, e - a, dd, b->s, b->rc, nullptr, 0,
+                                   b->R, T(0), b->plans[0]->use_tc, b->plans[0]->err_dev, st));
   }
   return AGP_OK;
 }

@@ -184,7 +184,7 @@ struct agp_plan_s {
   double kb_b = 0, kb_norm = 0;
   int rc_max = 32;
   int item_points = agp::kItemPoints;   // points per work item (bin size), see agp_plan_autotune
-  int use_tc = 0;                // spreading on the tensor cores where supported
+  int use_tc = 1;                // spreading and interpolation on the tensor cores where supported
   std::vector<agp::Window> win;
   void* wins_dev = nullptr;      // WinDev<T>[P]
   int4* items_all = nullptr;     // work items of every window, grouped by d
@@ -234,12 +234,29 @@ cudaError_t spread_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const in
   }
   return spread_items<T>(wins, io, items, n_items, d, s, RC, V, ldv, R, st);
 }
+// Tensor-core interpolation (agp_interp_tc.cu): FP32, d = 3, RC = 32, s = 4 or 5.
+bool interp_tc_supported(int d, int s, int RC);
+cudaError_t interp_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
+                            int64_t n_items, int s, float* Out, int64_t ldo, int R, float scale,
+                            int* err, cudaStream_t st);
 // Interpolate the grids of those windows and add scale * result into
 // Out[:, 0..R) (with io: Out, ldo and scale of io[window]).
 template <typename T>
 cudaError_t interp_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
                          int64_t n_items, int d, int s, int RC, T* Out, int64_t ldo, int R,
                          T scale, cudaStream_t st);
+
+// interp_items, or interp_items_tc when `tc` is set and the case is supported
+template <typename T>
+cudaError_t interp_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
+                             int64_t n_items, int d, int s, int RC, T* Out, int64_t ldo, int R,
+                             T scale, int tc, int* err, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (tc && interp_tc_supported(d, s, RC))
+      return interp_items_tc(wins, io, items, n_items, s, Out, ldo, R, scale, err, st);
+  }
+  return interp_items<T>(wins, io, items, n_items, d, s, RC, Out, ldo, R, scale, st);
+}
 
 // ---- landmark (Nystrom) preconditioner (agp_precond.cu) ----
 // M^{-1} = sigma_eps^{-2} (I - B Ginv B^T), B = K_{:,L} [n][k] stored in the

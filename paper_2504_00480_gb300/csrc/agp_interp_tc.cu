@@ -1,0 +1,279 @@
+// Interpolation (NFFT, Appendix A) of d = 3 windows on the 5th-generation
+// tensor cores. For the points of one work item (one grid cell) the first
+// two dimensions of the separable window sum are a dense product over the
+// (2s)^2 grid rows (t1, t2) of the cell's block:
+//     H[p, (t3, r)] = sum_{(t1, t2)} A[p, (t1, t2)] B[(t3, r), (t1, t2)],
+//     A[p, (t1, t2)] = psi1_p(t1) psi2_p(t2),  B[(t3, r), (t1, t2)] = G[t1, t2, t3][r],
+// and the last dimension is contracted in the epilogue:
+//     h_p(r) = sum_t3 psi3_p(t3) H[p, (t3, r)].
+// Each CTA takes one item (up to 128 points per tile, M = 128) and 16 of the
+// 32 right-hand sides (N = 2s x 16 = 160 or 128), accumulates H in TMEM with
+// tcgen05.mma kind::tf32 over chunks of 8 grid rows (K = 8), with operands
+// split into TF32 hi and lo parts (A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi),
+// then contracts with psi3, and adds scale * h into the caller's output rows
+// with vector atomics (other windows add into the same rows).
+//
+// Pipeline (256 threads): the tile's window values and perm indices are
+// staged once; per chunk all threads form A (from the window values) and B
+// (grid values read from L2, prefetched a chunk ahead into registers) in one
+// of two operand buffers, and after one barrier thread 0 issues the chunk's
+// three MMAs and commits them to the buffer's mbarrier. Every mbarrier wait
+// is bounded: on expiry the CTA records a timeout in the plan's error word.
+#include <type_traits>
+
+#include "agp_nufft_kernels.cuh"
+#include "agp_tc.cuh"
+
+namespace agp {
+namespace {
+
+constexpr int kItThreads = 256;
+constexpr int kItKC = 8;                      // grid rows (t1, t2) per chunk
+constexpr int kItRH = 16;                     // right-hand sides per CTA
+constexpr int kItMP = 128;                    // points per tile
+constexpr int kItLBO = 128;
+constexpr int kItSBO = (kItKC / 4) * 128;
+constexpr int kItNG = kItThreads / 64;        // formation groups (64 element slots each)
+
+template <int S>
+struct TcInterpShape {
+  static constexpr int TT = 2 * S, TTP = ttp_of(S);
+  static constexpr int ROWS = TT * TT;                       // K (grid rows)
+  static constexpr int NCH = (ROWS + kItKC - 1) / kItKC;     // chunks per tile
+  static constexpr int NN = TT * kItRH;
+  static constexpr int WPP = wpp_of(3, S);
+  static constexpr int A_BYTES = kItMP * kItKC * 4;
+  static constexpr int B_BYTES = NN * kItKC * 4;
+  static constexpr int OPND = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int WS_BYTES = kItMP * WPP * 4;
+  static constexpr int PB_BYTES = 2 * kItMP * 17 * 4;        // epilogue partial sums
+  static constexpr int SMEM_USED = (2 * OPND > PB_BYTES ? 2 * OPND : PB_BYTES) + WS_BYTES + kItMP * 4;
+  // at least 76 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM
+  static constexpr int SMEM = SMEM_USED > 76 * 1024 ? SMEM_USED : 76 * 1024;
+  static constexpr int TMEM_COLS = NN <= 128 ? 128 : 256;
+  static constexpr int BPER = (NN / 8 + kItNG - 1) / kItNG;  // B row groups per thread
+  static_assert(NN % 16 == 0 && NN <= 256, "N must be a multiple of 16, at most 256");
+  static_assert((WPP * 4) % 16 == 0, "window values must be 16-byte rows");
+};
+
+template <int S>
+__global__ void __launch_bounds__(kItThreads)
+k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict__ io,
+            const int4* __restrict__ items, float* __restrict__ Out, int64_t ldo, int R,
+            float scale, int* __restrict__ err) {
+  using Sh = TcInterpShape<S>;
+  constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, KC = kItKC, RH = kItRH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int4 it = items[blockIdx.x >> 1];
+  const int r0 = (blockIdx.x & 1) * RH;
+  if (r0 >= R) return;
+  const WinDev<float> w = wins[it.x];
+  if (io) {
+    Out = io[it.x].Out;
+    ldo = io[it.x].ldo;
+    scale = io[it.x].scale;
+  }
+  const int j0 = it.z, m = it.w;
+  int cc[3];
+  decode_cell<3>(it.y, w.N, cc);
+  auto opnd = [&](int b) { return smem_raw + b * Sh::OPND; };
+  float* pb = reinterpret_cast<float*>(smem_raw);   // epilogue partials (operands are free then)
+  float* ws = reinterpret_cast<float*>(smem_raw + (2 * Sh::OPND > Sh::PB_BYTES ? 2 * Sh::OPND
+                                                                              : Sh::PB_BYTES));
+  int* sperm = reinterpret_cast<int*>(ws + kItMP * WPP);
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(&tmem_slot)), "n"(Sh::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+
+  // element slot of this thread in every core matrix it writes: row r8 and
+  // column k4 of the core, column quad kq (KC / 4 = 2 quads), group g of the
+  // row groups
+  const int kq = (tid >> 5) & 1, r8 = lane >> 2, k4 = lane & 3, g = tid >> 6;
+  const int kk4 = kq * 4 + k4;                   // grid row within the chunk
+  const int o = kq * 32 + lane;                  // element offset in the row group 0 core
+  constexpr int CORE = (KC / 4) * 32;            // floats between 8-row groups
+  const uint32_t idesc = umma_idesc_tf32(kItMP, Sh::NN);
+  const float* gbase = w.grid + r0;
+  // the grid value of B row group rg (rows n = 8 rg + r8: t3 = rg / 2, r = 8 (rg % 2) + r8)
+  // at grid row kk = (t1, t2)
+  auto grid_val = [&](int rg, int kk) -> float {
+    if (kk >= Sh::ROWS) return 0.0f;
+    const int t1 = kk / TT, t2 = kk - (kk / TT) * TT, t3 = rg >> 1;
+    const int64_t cell = ((int64_t)(cc[0] + t1) * w.W + (cc[1] + t2)) * w.W + cc[2] + t3;
+    return __ldg(gbase + cell * 32 + ((rg & 1) << 3) + r8);
+  };
+  const int rga = g * Sh::BPER, rgb = min(Sh::NN / 8, rga + Sh::BPER);
+  bool ok = true;
+  int gc = 0;                                    // chunks issued so far (both tiles)
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  for (int p0 = 0; p0 < m; p0 += kItMP) {
+    const int np = min(kItMP, m - p0);
+    // stage the tile's window values and perm indices
+    const float* wsrc = w.wts + (int64_t)(j0 + p0) * WPP;
+    for (int e = tid; e < np * (WPP / 4); e += kItThreads) cp_async16(ws + e * 4, wsrc + e * 4, 16);
+    cp_async_commit();
+    for (int e = tid; e < np; e += kItThreads) sperm[e] = __ldg(w.perm + j0 + p0 + e);
+    float gb[Sh::BPER];                          // B values of the next chunk
+#pragma unroll
+    for (int q = 0; q < Sh::BPER; ++q) gb[q] = (rga + q < rgb) ? grid_val(rga + q, kk4) : 0.0f;
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int c = 0; c < Sh::NCH; ++c, ++gc) {
+      const int b = gc & 1;
+      if (gc >= 2 && !mbar_wait(&bar[b], ((gc - 2) >> 1) & 1)) ok = false;
+      float* ahi = reinterpret_cast<float*>(opnd(b));
+      float* alo = reinterpret_cast<float*>(opnd(b) + Sh::A_BYTES);
+      float* bhi = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES);
+      float* blo = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES + Sh::B_BYTES);
+      const int kk = c * KC + kk4;               // this thread's grid row (t1, t2)
+      // B: the prefetched grid values
+#pragma unroll
+      for (int q = 0; q < Sh::BPER; ++q) {
+        if (rga + q < rgb) {
+          const float x = gb[q];
+          const float h = tf32_round(x);
+          bhi[(rga + q) * CORE + o] = h;
+          blo[(rga + q) * CORE + o] = tf32_round(x - h);
+        }
+      }
+      if (c + 1 < Sh::NCH) {
+#pragma unroll
+        for (int q = 0; q < Sh::BPER; ++q)
+          gb[q] = (rga + q < rgb) ? grid_val(rga + q, kk + KC) : 0.0f;
+      }
+      // A: points p = 8 rg + r8 (16 row groups, 4 per group), weights of (t1, t2)
+      {
+        const bool krow = kk < Sh::ROWS;
+        const int t1 = kk / TT, t2 = kk - (kk / TT) * TT;
+#pragma unroll
+        for (int q = 0; q < 16 / kItNG; ++q) {
+          const int rg = g * (16 / kItNG) + q;
+          const int p = rg * 8 + r8;
+          const float x = (krow && p < np) ? ws[p * WPP + t1] * ws[p * WPP + TTP + t2] : 0.0f;
+          const float h = tf32_round(x);
+          ahi[rg * CORE + o] = h;
+          alo[rg * CORE + o] = tf32_round(x - h);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint64_t a0 = umma_desc(smem_u32(ahi), kItLBO, kItSBO);
+        const uint64_t a1 = umma_desc(smem_u32(alo), kItLBO, kItSBO);
+        const uint64_t b0 = umma_desc(smem_u32(bhi), kItLBO, kItSBO);
+        const uint64_t b1 = umma_desc(smem_u32(blo), kItLBO, kItSBO);
+        mma_tf32(tmem, a0, b0, idesc, c > 0 ? 1u : 0u);
+        mma_tf32(tmem, a0, b1, idesc, 1u);
+        mma_tf32(tmem, a1, b0, idesc, 1u);
+        mma_commit(&bar[b]);
+      }
+    }
+    // the last commit covers every MMA of the tile
+    if (!mbar_wait(&bar[(gc - 1) & 1], ((gc - 1) >> 1) & 1)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+      // warp w: points 32 (w % 4) .. + 31 (TMEM lanes), t3 half w / 4; partial
+      // sums over its t3 range go to shared memory, then four threads per
+      // point add the halves and issue one 16-byte atomic each
+      const int quarter = warp % 4, part = warp / 4;
+      const int p = quarter * 32 + lane;
+      float acc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+      const int ta = part * TT / 2, tb = (part + 1) * TT / 2;
+#pragma unroll 1
+      for (int t3 = ta; t3 < tb; ++t3) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t3 * RH);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const float ps = p < np ? ws[p * WPP + 2 * TTP + 2 * t3] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = fmaf(ps, __uint_as_float(v[q]), acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) pb[(part * kItMP + p) * 17 + q] = acc[q];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (ok) {
+      const bool vec = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(Out) & 15) == 0);
+      for (int e = tid; e < np * 4; e += kItThreads) {
+        const int p = e >> 2, c4 = (e & 3) * 4;
+        if (r0 + c4 >= R) continue;
+        const float* s0 = pb + p * 17 + c4;
+        const float* s1 = pb + (kItMP + p) * 17 + c4;
+        float4 val = make_float4(scale * (s0[0] + s1[0]), scale * (s0[1] + s1[1]),
+                                 scale * (s0[2] + s1[2]), scale * (s0[3] + s1[3]));
+        float* dst = Out + (int64_t)sperm[p] * ldo + r0 + c4;
+        if (vec && r0 + c4 + 4 <= R) {
+          atomicAdd(reinterpret_cast<float4*>(dst), val);
+        } else {
+          const float vv[4] = {val.x, val.y, val.z, val.w};
+          for (int q = 0; q < 4 && r0 + c4 + q < R; ++q) atomicAdd(dst + q, vv[q]);
+        }
+      }
+    } else if (tid == 0) {
+      atomicOr(err, 2);
+    }
+    __syncthreads();                             // partials, ws and sperm free for the next tile
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "n"(Sh::TMEM_COLS));
+}
+
+template <int S>
+cudaError_t interp_tc_s(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
+                        int64_t n_items, float* Out, int64_t ldo, int R, float scale, int* err,
+                        cudaStream_t st) {
+  using Sh = TcInterpShape<S>;
+  cudaError_t e = cudaFuncSetAttribute(k_interp_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Sh::SMEM);
+  if (e != cudaSuccess) return e;
+  if (n_items <= 0) return cudaSuccess;
+  k_interp_tc<S><<<(unsigned)(2 * n_items), kItThreads, Sh::SMEM, st>>>(wins, io, items, Out, ldo,
+                                                                        R, scale, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool interp_tc_supported(int d, int s, int RC) { return d == 3 && RC == 32 && (s == 4 || s == 5); }
+
+cudaError_t interp_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
+                            int64_t n_items, int s, float* Out, int64_t ldo, int R, float scale,
+                            int* err, cudaStream_t st) {
+  switch (s) {
+    case 4: return interp_tc_s<4>(wins, io, items, n_items, Out, ldo, R, scale, err, st);
+    case 5: return interp_tc_s<5>(wins, io, items, n_items, Out, ldo, R, scale, err, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace agp

@@ -716,8 +716,8 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 2, st, dd);
-      AGP_CUDA(interp_items<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc, Out + r0, ldo,
-                               Rc, scale, st));
+      AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
+                                   Out + r0, ldo, Rc, scale, pl->use_tc, pl->err_dev, st));
       pl->launches[2] += 1;
     }
   }

@@ -30,6 +30,7 @@
 #include <type_traits>
 
 #include "agp_nufft_kernels.cuh"
+#include "agp_tc.cuh"
 
 namespace agp {
 namespace {
@@ -46,7 +47,6 @@ constexpr int kTcKC = 16;       // points per chunk
 constexpr int kTcRH = 16;       // right-hand sides per CTA
 constexpr int kTcLBO = 128;     // bytes between core matrices along K
 constexpr int kTcSBO = (kTcKC / 4) * 128;   // bytes between 8-row groups
-constexpr long long kTcSpinLimit = 1ll << 26;
 
 template <int S>
 struct TcSpreadShape {
@@ -67,57 +67,6 @@ struct TcSpreadShape {
   static_assert(NN % 16 == 0 && NN <= 256, "N must be a multiple of 16, at most 256");
   static_assert((WPP * 4) % 16 == 0, "window values must be 16-byte rows");
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// shared-memory matrix descriptor: K-major, no swizzle
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
-  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((kTcLBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((kTcSBO >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// instruction descriptor: D = F32, A = B = TF32, both K-major, M x N
-__host__ __device__ constexpr uint32_t umma_idesc_tf32(int m, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
-}
-
-// x rounded to the nearest TF32 value (10 fraction bits; ties away from zero)
-__device__ __forceinline__ float tf32_round(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-               ::"r"(smem_u32(bar)));
-}
-
-// bounded wait for the given phase parity; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kTcSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done) : "r"(a), "r"(parity));
-    if (done) return true;
-  }
-  return false;
-}
 
 // Operand formation of one chunk for thread group G (of NG) of a CTA, in the
 // thread's fixed element slot (row r8, point k4 of every core matrix of point
@@ -296,8 +245,8 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       // descriptors differ only in the start address field (address >> 4)
-      const uint64_t a0 = umma_desc(smem_u32(ahi)), a1 = umma_desc(smem_u32(alo));
-      const uint64_t b0 = umma_desc(smem_u32(bhi)), b1 = umma_desc(smem_u32(blo));
+      const uint64_t a0 = umma_desc(smem_u32(ahi), kTcLBO, kTcSBO), a1 = umma_desc(smem_u32(alo), kTcLBO, kTcSBO);
+      const uint64_t b0 = umma_desc(smem_u32(bhi), kTcLBO, kTcSBO), b1 = umma_desc(smem_u32(blo), kTcLBO, kTcSBO);
 #pragma unroll
       for (int s2 = 0; s2 < KC / 8; ++s2) {
         const uint64_t off = (uint64_t)(s2 * 2 * kTcLBO) >> 4;

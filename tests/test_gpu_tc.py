@@ -1,8 +1,8 @@
-"""Spreading on the tensor cores (tcgen05, split TF32): the matvec and the
-derivative operators with the tensor-core spread against the oracle at the
-FP32 tolerance, against the FMA-pipe spread of the same plan, for both
-supported cutoffs, a ragged right-hand-side count, strided blocks and the
-full-size workload on sampled rows."""
+"""Spreading and interpolation on the tensor cores (tcgen05, split TF32):
+the matvec and the derivative operators with the tensor-core kernels
+against the oracle at the FP32 tolerance, against the FMA-pipe kernels of
+the same plan, for both supported cutoffs, a ragged right-hand-side count,
+strided blocks and the full-size workload on sampled rows."""
 import numpy as np
 import pytest
 
@@ -44,6 +44,7 @@ def test_tc_spread_matches_oracle_and_fma_path(agp, s, N, R):
     plan = agp.Plan(torch.tensor(X, dtype=torch.float32, device=DEV), W, N, s, "gauss",
                     0.15, 0.9, 0.2)
     Vt = torch.tensor(V, dtype=torch.float32, device=DEV)
+    plan.set_tensor_cores(False)
     ref = plan.matvec(Vt).cpu().numpy()
     plan.set_tensor_cores(True)
     got = plan.matvec(Vt).cpu().numpy()
@@ -65,7 +66,7 @@ def test_tc_spread_strided_and_adjoint_nfft(agp):
     V = rng.standard_normal((n, 40))
     plan = agp.Plan(torch.tensor(X, dtype=torch.float32, device=DEV), [[0, 1, 2]], 32, 5,
                     "matern12", 0.2, 1.0, 0.1)
-    plan.set_tensor_cores(True)
+    plan.set_tensor_cores(True)              # the default for FP32 plans
     Vt = torch.tensor(V, dtype=torch.float32, device=DEV)[:, 3:35]   # ldv = 40, unaligned start
     got = plan.matvec(Vt).cpu().numpy()
     want = O.truncated_matvec(X, [[0, 1, 2]], "matern12", 0.2, 1.0, 0.1, V[:, 3:35], 32)
@@ -83,6 +84,7 @@ def test_tc_spread_full_size_sampled_rows(agp):
     X = torch.tensor(w.X, dtype=torch.float32, device=DEV)
     V = torch.tensor(w.V, dtype=torch.float32, device=DEV)
     plan = agp.Plan(X, w.windows, w.N, w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
+    plan.set_tensor_cores(False)
     ref = plan.matvec(V)
     plan.set_tensor_cores(True)
     got = plan.matvec(V)
