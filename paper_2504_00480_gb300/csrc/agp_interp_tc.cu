@@ -8,16 +8,17 @@
 //     h_p(r) = sum_t3 psi3_p(t3) H[p, (t3, r)].
 // Each CTA takes one item (up to 128 points per tile, M = 128) and 16 of the
 // 32 right-hand sides (N = 2s x 16 = 160 or 128), accumulates H in TMEM with
-// tcgen05.mma kind::tf32 over chunks of 8 grid rows (K = 8), with operands
+// tcgen05.mma kind::tf32 over chunks of 16 grid rows (two K = 8 steps), with operands
 // split into TF32 hi and lo parts (A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi),
 // then contracts with psi3, and adds scale * h into the caller's output rows
 // with vector atomics (other windows add into the same rows).
 //
 // Pipeline (256 threads): the tile's window values and perm indices are
-// staged once; per chunk all threads form A (from the window values) and B
-// (grid values read from L2, prefetched a chunk ahead into registers) in one
-// of two operand buffers, and after one barrier thread 0 issues the chunk's
-// three MMAs and commits them to the buffer's mbarrier. Every mbarrier wait
+// staged once; per chunk of 16 grid rows all threads form A (from the window
+// values) and B (grid values read from L2, prefetched a chunk ahead into
+// registers) in one of two operand buffers, and after one barrier thread 0
+// issues the chunk's six MMAs (two K = 8 steps) and commits them to the
+// buffer's mbarrier. Every mbarrier wait
 // is bounded: on expiry the CTA records a timeout in the plan's error word.
 #include <type_traits>
 
@@ -28,12 +29,12 @@ namespace agp {
 namespace {
 
 constexpr int kItThreads = 256;
-constexpr int kItKC = 8;                      // grid rows (t1, t2) per chunk
+constexpr int kItKC = 16;                     // grid rows (t1, t2) per chunk
 constexpr int kItRH = 16;                     // right-hand sides per CTA
 constexpr int kItMP = 128;                    // points per tile
 constexpr int kItLBO = 128;
 constexpr int kItSBO = (kItKC / 4) * 128;
-constexpr int kItNG = kItThreads / 64;        // formation groups (64 element slots each)
+constexpr int kItNG = kItThreads / 128;       // formation groups (128 element slots each)
 
 template <int S>
 struct TcInterpShape {
@@ -51,13 +52,60 @@ struct TcInterpShape {
   // at least 76 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM
   static constexpr int SMEM = SMEM_USED > 76 * 1024 ? SMEM_USED : 76 * 1024;
   static constexpr int TMEM_COLS = NN <= 128 ? 128 : 256;
-  static constexpr int BPER = (NN / 8 + kItNG - 1) / kItNG;  // B row groups per thread
+  static constexpr int BPER = NN / 8 / kItNG;                 // B row groups per thread
+  static_assert((NN / 8) % kItNG == 0 && 16 % kItNG == 0, "row groups split evenly");
   static_assert(NN % 16 == 0 && NN <= 256, "N must be a multiple of 16, at most 256");
   static_assert((WPP * 4) % 16 == 0, "window values must be 16-byte rows");
 };
 
+// Operand formation for thread group G: the thread's element slot is row r8
+// and column k4 of every core matrix of column quad kq; rows of group G are
+// row groups [G * 16/NG, (G+1) * 16/NG) of A (points) and
+// [G * NN/8/NG, (G+1) * NN/8/NG) of B ((t3, r)). Offsets relative to the
+// thread's base pointers are compile-time constants.
+template <int S, int G>
+__device__ __forceinline__ void it_load_b(const float* __restrict__ gp, bool krow, float* gb) {
+  constexpr int NRG = 2 * S * kItRH / 8, PER = NRG / kItNG, RGA = G * PER;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int rg = RGA + q;
+    gb[q] = krow ? __ldg(gp + (rg >> 1) * 32 + (rg & 1) * 8) : 0.0f;
+  }
+}
+
+template <int S, int G>
+__device__ __forceinline__ void it_store_b(const float* gb, float* __restrict__ bh,
+                                           float* __restrict__ bl) {
+  constexpr int NRG = 2 * S * kItRH / 8, PER = NRG / kItNG, RGA = G * PER;
+  constexpr int CORE = (kItKC / 4) * 32;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const float x = gb[q];
+    const float h = tf32_round(x);
+    bh[(RGA + q) * CORE] = h;
+    bl[(RGA + q) * CORE] = tf32_round(x - h);
+  }
+}
+
+template <int S, int G>
+__device__ __forceinline__ void it_form_a(const float* __restrict__ w1, const float* __restrict__ w2,
+                                          int np, int r8, bool krow, float* __restrict__ ah,
+                                          float* __restrict__ al) {
+  constexpr int WPP = wpp_of(3, S), PER = 16 / kItNG, RGA = G * PER;
+  constexpr int CORE = (kItKC / 4) * 32;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int rg = RGA + q;
+    const int p = rg * 8 + r8;
+    const float x = (krow && p < np) ? w1[rg * 8 * WPP] * w2[rg * 8 * WPP] : 0.0f;
+    const float h = tf32_round(x);
+    ah[rg * CORE] = h;
+    al[rg * CORE] = tf32_round(x - h);
+  }
+}
+
 template <int S>
-__global__ void __launch_bounds__(kItThreads)
+__global__ void __launch_bounds__(kItThreads, 2)
 k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict__ io,
             const int4* __restrict__ items, float* __restrict__ Out, int64_t ldo, int R,
             float scale, int* __restrict__ err) {
@@ -97,25 +145,26 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   }
 
   // element slot of this thread in every core matrix it writes: row r8 and
-  // column k4 of the core, column quad kq (KC / 4 = 2 quads), group g of the
-  // row groups
-  const int kq = (tid >> 5) & 1, r8 = lane >> 2, k4 = lane & 3, g = tid >> 6;
+  // column k4 of the core, column quad kq (KC / 4 quads), group g of the rows
+  const int kq = (tid >> 5) & (KC / 4 - 1), r8 = lane >> 2, k4 = lane & 3, g = tid >> 7;
   const int kk4 = kq * 4 + k4;                   // grid row within the chunk
   const int o = kq * 32 + lane;                  // element offset in the row group 0 core
-  constexpr int CORE = (KC / 4) * 32;            // floats between 8-row groups
   const uint32_t idesc = umma_idesc_tf32(kItMP, Sh::NN);
-  const float* gbase = w.grid + r0;
-  // the grid value of B row group rg (rows n = 8 rg + r8: t3 = rg / 2, r = 8 (rg % 2) + r8)
-  // at grid row kk = (t1, t2)
-  auto grid_val = [&](int rg, int kk) -> float {
-    if (kk >= Sh::ROWS) return 0.0f;
-    const int t1 = kk / TT, t2 = kk - (kk / TT) * TT, t3 = rg >> 1;
-    const int64_t cell = ((int64_t)(cc[0] + t1) * w.W + (cc[1] + t2)) * w.W + cc[2] + t3;
-    return __ldg(gbase + cell * 32 + ((rg & 1) << 3) + r8);
+  // base pointer of this thread's B elements at grid row kk = (t1, t2):
+  // grid + 32 cell(t1, t2, 0) + r0 + r8; row group rg adds 32 (rg / 2) + 8 (rg % 2)
+  auto bptr = [&](int kk) -> const float* {
+    const int t1 = kk / TT, t2 = kk - (kk / TT) * TT;
+    const int64_t cell = ((int64_t)(cc[0] + t1) * w.W + (cc[1] + t2)) * w.W + cc[2];
+    return w.grid + cell * 32 + r0 + r8;
   };
-  const int rga = g * Sh::BPER, rgb = min(Sh::NN / 8, rga + Sh::BPER);
+  auto load_b = [&](int kk, float* gb) {
+    const bool krow = kk < Sh::ROWS;
+    const float* gp = krow ? bptr(kk) : w.grid;
+    if (g == 0) it_load_b<S, 0>(gp, krow, gb);
+    else it_load_b<S, 1>(gp, krow, gb);
+  };
   bool ok = true;
-  int gc = 0;                                    // chunks issued so far (both tiles)
+  int gc = 0;                                    // chunks issued so far (all tiles)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
@@ -128,8 +177,7 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     cp_async_commit();
     for (int e = tid; e < np; e += kItThreads) sperm[e] = __ldg(w.perm + j0 + p0 + e);
     float gb[Sh::BPER];                          // B values of the next chunk
-#pragma unroll
-    for (int q = 0; q < Sh::BPER; ++q) gb[q] = (rga + q < rgb) ? grid_val(rga + q, kk4) : 0.0f;
+    load_b(kk4, gb);
     cp_async_wait<0>();
     __syncthreads();
     for (int c = 0; c < Sh::NCH; ++c, ++gc) {
@@ -140,34 +188,16 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
       float* bhi = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES);
       float* blo = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES + Sh::B_BYTES);
       const int kk = c * KC + kk4;               // this thread's grid row (t1, t2)
-      // B: the prefetched grid values
-#pragma unroll
-      for (int q = 0; q < Sh::BPER; ++q) {
-        if (rga + q < rgb) {
-          const float x = gb[q];
-          const float h = tf32_round(x);
-          bhi[(rga + q) * CORE + o] = h;
-          blo[(rga + q) * CORE + o] = tf32_round(x - h);
-        }
-      }
-      if (c + 1 < Sh::NCH) {
-#pragma unroll
-        for (int q = 0; q < Sh::BPER; ++q)
-          gb[q] = (rga + q < rgb) ? grid_val(rga + q, kk + KC) : 0.0f;
-      }
-      // A: points p = 8 rg + r8 (16 row groups, 4 per group), weights of (t1, t2)
+      if (g == 0) it_store_b<S, 0>(gb, bhi + o, blo + o);
+      else it_store_b<S, 1>(gb, bhi + o, blo + o);
+      if (c + 1 < Sh::NCH) load_b(kk + KC, gb);  // next chunk's grid values, in flight
       {
         const bool krow = kk < Sh::ROWS;
-        const int t1 = kk / TT, t2 = kk - (kk / TT) * TT;
-#pragma unroll
-        for (int q = 0; q < 16 / kItNG; ++q) {
-          const int rg = g * (16 / kItNG) + q;
-          const int p = rg * 8 + r8;
-          const float x = (krow && p < np) ? ws[p * WPP + t1] * ws[p * WPP + TTP + t2] : 0.0f;
-          const float h = tf32_round(x);
-          ahi[rg * CORE + o] = h;
-          alo[rg * CORE + o] = tf32_round(x - h);
-        }
+        const int t1 = krow ? kk / TT : 0, t2 = krow ? kk - (kk / TT) * TT : 0;
+        const float* w1 = ws + r8 * WPP + t1;
+        const float* w2 = ws + r8 * WPP + TTP + t2;
+        if (g == 0) it_form_a<S, 0>(w1, w2, np, r8, krow, ahi + o, alo + o);
+        else it_form_a<S, 1>(w1, w2, np, r8, krow, ahi + o, alo + o);
       }
       asm volatile("fence.proxy.async.shared::cta;");
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -178,9 +208,13 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
         const uint64_t a1 = umma_desc(smem_u32(alo), kItLBO, kItSBO);
         const uint64_t b0 = umma_desc(smem_u32(bhi), kItLBO, kItSBO);
         const uint64_t b1 = umma_desc(smem_u32(blo), kItLBO, kItSBO);
-        mma_tf32(tmem, a0, b0, idesc, c > 0 ? 1u : 0u);
-        mma_tf32(tmem, a0, b1, idesc, 1u);
-        mma_tf32(tmem, a1, b0, idesc, 1u);
+#pragma unroll
+        for (int s2 = 0; s2 < KC / 8; ++s2) {
+          const uint64_t off = (uint64_t)(s2 * 2 * kItLBO) >> 4;
+          mma_tf32(tmem, a0 + off, b0 + off, idesc, (c > 0 || s2 > 0) ? 1u : 0u);
+          mma_tf32(tmem, a0 + off, b1 + off, idesc, 1u);
+          mma_tf32(tmem, a1 + off, b0 + off, idesc, 1u);
+        }
         mma_commit(&bar[b]);
       }
     }

@@ -661,7 +661,18 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
   return AGP_OK;
 }
 
-int pick_rc(const agp_plan_s* pl, int R) { return rhs_block_width(pl->prec, R); }
+// Right-hand sides per pass. With the tensor-core kernels on, FP32 plans
+// with a d = 3 window that they support take 9 or more columns in passes of
+// 32: a tensor-core pass over 17 columns costs about what one over 32 does,
+// and still less than the FMA kernels' 24-column pass (columns 16 .. 31 of a
+// pass are skipped when R <= 16).
+int pick_rc(const agp_plan_s* pl, int R) {
+  if (pl->use_tc && pl->prec == AGP_F32 && R >= 9) {
+    for (const Window& w : pl->win)
+      if (spread_tc_supported(w.d, pl->s, 32) && interp_tc_supported(w.d, pl->s, 32)) return 32;
+  }
+  return rhs_block_width(pl->prec, R);
+}
 
 // Stage timing: a pair of events around a group of launches on `st`.
 struct StageTimer {
