@@ -106,6 +106,7 @@ agp_status batch_build(agp_batch_s* b, cudaStream_t st) {
       d.perm = w.perm;
       d.wts = reinterpret_cast<const T*>(w.wts);
       d.grid = reinterpret_cast<T*>(w.grid);
+      d.cell_start = w.cell_start;
       d.n = pl->n;
       d.N = w.N;
       d.n_os = w.n_os;

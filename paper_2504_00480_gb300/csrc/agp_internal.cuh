@@ -36,9 +36,22 @@ struct WinDev {
   const int32_t* perm;    // sorted position -> caller's point index
   const T* wts;           // window values, sorted order, [n][window_wpp(d, s)]
   T* grid;                // active-box grid, [W^d][RC]
+  const int32_t* cell_start;   // [cells + 1] first sorted point of every cell
   int64_t n;
   int N, n_os, W;
 };
+
+// Work units of the tensor-core kernels for d = 3 windows: runs of up to
+// kRunCells consecutive cells along the last dimension (aligned to multiples
+// of kRunCells, so one (t1, t2, t3) grid block of 2s + kRunCells - 1 planes
+// covers all their points). int4 (window | L << 16, first cell, first sorted
+// point, point count); L = 0 means a single cell (plain work items).
+constexpr int kRunCells = 4;
+// Points per run unit: longer runs are split into units of at most this many
+// points (each a separate accumulation in tensor memory; the tensor cores'
+// FP32 accumulation error grows with the number of MMAs summed into one
+// accumulator).
+constexpr int kRunPoints = 256;
 
 // Window values stored per point and dimension: the 2s taps padded with zeros
 // to a multiple of 4 (16-byte vector loads).
@@ -188,6 +201,8 @@ struct agp_plan_s {
   std::vector<agp::Window> win;
   void* wins_dev = nullptr;      // WinDev<T>[P]
   int4* items_all = nullptr;     // work items of every window, grouped by d
+  int4* runs3 = nullptr;         // tensor-core work units (cell runs) of the d = 3 windows
+  int64_t n_runs3 = 0;
   int64_t items_by_d[agp::kMaxDim + 1] = {0, 0, 0, 0};   // offsets of each d group
   std::vector<agp::FftGroup> groups;   // windows grouped by (d, N) for the DFT stages
   int* err_dev = nullptr;        // device error flags

@@ -5,9 +5,11 @@
 //     H[p, (t3, r)] = sum_{(t1, t2)} A[p, (t1, t2)] B[(t3, r), (t1, t2)],
 //     A[p, (t1, t2)] = psi1_p(t1) psi2_p(t2),  B[(t3, r), (t1, t2)] = G[t1, t2, t3][r],
 // and the last dimension is contracted in the epilogue:
-//     h_p(r) = sum_t3 psi3_p(t3) H[p, (t3, r)].
-// Each CTA takes one item (up to 128 points per tile, M = 128) and 16 of the
-// 32 right-hand sides (N = 2s x 16 = 160 or 128), accumulates H in TMEM with
+//     h_p(r) = sum_t3 psi3_p(t3) H[p, (t3 + delta_p, r)],
+// delta_p the cell of point p within the run.
+// Each CTA takes one run of up to four cells along the last dimension (tiles
+// of up to 128 points, M = 128; the run's block has 2s + L - 1 planes t3) and
+// 16 of the 32 right-hand sides (N = (2s + L - 1) x 16), accumulates H in TMEM with
 // tcgen05.mma kind::tf32 over chunks of 16 grid rows (two K = 8 steps), with operands
 // split into TF32 hi and lo parts (A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi),
 // then contracts with psi3, and adds scale * h into the caller's output rows
@@ -41,14 +43,16 @@ struct TcInterpShape {
   static constexpr int TT = 2 * S, TTP = ttp_of(S);
   static constexpr int ROWS = TT * TT;                       // K (grid rows)
   static constexpr int NCH = (ROWS + kItKC - 1) / kItKC;     // chunks per tile
-  static constexpr int NN = TT * kItRH;
+  static constexpr int T3M = TT + kRunCells - 1;             // planes of a run's block
+  static constexpr int NN = T3M * kItRH;                     // largest MMA N
   static constexpr int WPP = wpp_of(3, S);
   static constexpr int A_BYTES = kItMP * kItKC * 4;
   static constexpr int B_BYTES = NN * kItKC * 4;
   static constexpr int OPND = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int WS_BYTES = kItMP * WPP * 4;
   static constexpr int PB_BYTES = 2 * kItMP * 17 * 4;        // epilogue partial sums
-  static constexpr int SMEM_USED = (2 * OPND > PB_BYTES ? 2 * OPND : PB_BYTES) + WS_BYTES + kItMP * 4;
+  static constexpr int SMEM_USED =
+      (2 * OPND > PB_BYTES ? 2 * OPND : PB_BYTES) + WS_BYTES + 2 * kItMP * 4;
   // at least 76 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM
   static constexpr int SMEM = SMEM_USED > 76 * 1024 ? SMEM_USED : 76 * 1024;
   static constexpr int TMEM_COLS = NN <= 128 ? 128 : 256;
@@ -64,19 +68,20 @@ struct TcInterpShape {
 // [G * NN/8/NG, (G+1) * NN/8/NG) of B ((t3, r)). Offsets relative to the
 // thread's base pointers are compile-time constants.
 template <int S, int G>
-__device__ __forceinline__ void it_load_b(const float* __restrict__ gp, bool krow, float* gb) {
-  constexpr int NRG = 2 * S * kItRH / 8, PER = NRG / kItNG, RGA = G * PER;
+__device__ __forceinline__ void it_load_b(const float* __restrict__ gp, bool krow, int nrg,
+                                          float* gb) {
+  constexpr int NRG = (2 * S + kRunCells - 1) * kItRH / 8, PER = NRG / kItNG, RGA = G * PER;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int rg = RGA + q;
-    gb[q] = krow ? __ldg(gp + (rg >> 1) * 32 + (rg & 1) * 8) : 0.0f;
+    gb[q] = (krow && rg < nrg) ? __ldg(gp + (rg >> 1) * 32 + (rg & 1) * 8) : 0.0f;
   }
 }
 
 template <int S, int G>
 __device__ __forceinline__ void it_store_b(const float* gb, float* __restrict__ bh,
                                            float* __restrict__ bl) {
-  constexpr int NRG = 2 * S * kItRH / 8, PER = NRG / kItNG, RGA = G * PER;
+  constexpr int NRG = (2 * S + kRunCells - 1) * kItRH / 8, PER = NRG / kItNG, RGA = G * PER;
   constexpr int CORE = (kItKC / 4) * 32;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -118,12 +123,18 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   const int4 it = items[blockIdx.x >> 1];
   const int r0 = (blockIdx.x & 1) * RH;
   if (r0 >= R) return;
-  const WinDev<float> w = wins[it.x];
+  const int win = it.x & 0xFFFF, L = max(1, it.x >> 16);   // window, cells in the run
+  const int nu = TT + L - 1;                      // planes of the run's block
+  const WinDev<float> w = wins[win];
   if (io) {
-    Out = io[it.x].Out;
-    ldo = io[it.x].ldo;
-    scale = io[it.x].scale;
+    Out = io[win].Out;
+    ldo = io[win].ldo;
+    scale = io[win].scale;
   }
+  int bnd[kRunCells - 1];                         // first sorted point of cells 1 .. L-1
+#pragma unroll
+  for (int q = 0; q < kRunCells - 1; ++q)
+    bnd[q] = (q + 1 < L) ? __ldg(w.cell_start + it.y + q + 1) : 0x7FFFFFFF;
   const int j0 = it.z, m = it.w;
   int cc[3];
   decode_cell<3>(it.y, w.N, cc);
@@ -132,6 +143,7 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   float* ws = reinterpret_cast<float*>(smem_raw + (2 * Sh::OPND > Sh::PB_BYTES ? 2 * Sh::OPND
                                                                               : Sh::PB_BYTES));
   int* sperm = reinterpret_cast<int*>(ws + kItMP * WPP);
+  int* sdelta = sperm + kItMP;                      // cell of each point within the run
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
@@ -149,7 +161,7 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   const int kq = (tid >> 5) & (KC / 4 - 1), r8 = lane >> 2, k4 = lane & 3, g = tid >> 7;
   const int kk4 = kq * 4 + k4;                   // grid row within the chunk
   const int o = kq * 32 + lane;                  // element offset in the row group 0 core
-  const uint32_t idesc = umma_idesc_tf32(kItMP, Sh::NN);
+  const uint32_t idesc = umma_idesc_tf32(kItMP, nu * RH);
   // base pointer of this thread's B elements at grid row kk = (t1, t2):
   // grid + 32 cell(t1, t2, 0) + r0 + r8; row group rg adds 32 (rg / 2) + 8 (rg % 2)
   auto bptr = [&](int kk) -> const float* {
@@ -160,8 +172,8 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   auto load_b = [&](int kk, float* gb) {
     const bool krow = kk < Sh::ROWS;
     const float* gp = krow ? bptr(kk) : w.grid;
-    if (g == 0) it_load_b<S, 0>(gp, krow, gb);
-    else it_load_b<S, 1>(gp, krow, gb);
+    if (g == 0) it_load_b<S, 0>(gp, krow, 2 * nu, gb);
+    else it_load_b<S, 1>(gp, krow, 2 * nu, gb);
   };
   bool ok = true;
   int gc = 0;                                    // chunks issued so far (all tiles)
@@ -175,7 +187,14 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     const float* wsrc = w.wts + (int64_t)(j0 + p0) * WPP;
     for (int e = tid; e < np * (WPP / 4); e += kItThreads) cp_async16(ws + e * 4, wsrc + e * 4, 16);
     cp_async_commit();
-    for (int e = tid; e < np; e += kItThreads) sperm[e] = __ldg(w.perm + j0 + p0 + e);
+    for (int e = tid; e < np; e += kItThreads) {
+      const int jj = j0 + p0 + e;
+      sperm[e] = __ldg(w.perm + jj);
+      int delta = 0;
+#pragma unroll
+      for (int q = 0; q < kRunCells - 1; ++q) delta += jj >= bnd[q];
+      sdelta[e] = delta;
+    }
     float gb[Sh::BPER];                          // B values of the next chunk
     load_b(kk4, gb);
     cp_async_wait<0>();
@@ -230,9 +249,10 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
       float acc[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
-      const int ta = part * TT / 2, tb = (part + 1) * TT / 2;
+      const int ta = part * nu / 2, tb = (part + 1) * nu / 2;
+      const int dp = p < np ? sdelta[p] : 0;
 #pragma unroll 1
-      for (int t3 = ta; t3 < tb; ++t3) {
+      for (int t3 = ta; t3 < tb; ++t3) {            // plane of the run's block
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t3 * RH);
         asm volatile(
@@ -243,7 +263,8 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        const float ps = p < np ? ws[p * WPP + 2 * TTP + 2 * t3] : 0.0f;
+        const int tp = t3 - dp;                     // this point's tap
+        const float ps = (p < np && tp >= 0 && tp < TT) ? ws[p * WPP + 2 * TTP + 2 * tp] : 0.0f;
 #pragma unroll
         for (int q = 0; q < 16; ++q) acc[q] = fmaf(ps, __uint_as_float(v[q]), acc[q]);
       }

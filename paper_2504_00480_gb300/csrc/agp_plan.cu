@@ -455,6 +455,7 @@ void free_plan(agp_plan_s* pl) {
     cudaEventDestroy(e.b);
   }
   cudaFree(pl->items_all);
+  cudaFree(pl->runs3);
   cudaFree(pl->wins_dev);
   cudaFree(pl->err_dev);
   delete pl;
@@ -511,6 +512,31 @@ agp_status build_items(agp_plan_s* pl, int cap, cudaStream_t st) {
   if (pl->items_all) cudaFree(pl->items_all);
   pl->items_all = items;
   pl->item_points = cap;
+  // runs of kRunCells cells along the last dimension for the tensor-core
+  // kernels (host: cell_start of every d = 3 window, the non-empty runs)
+  if (!pl->runs3) {
+    std::vector<int4> runs;
+    for (int s = 0; s < pl->P; ++s) {
+      const Window& w = pl->win[s];
+      if (w.d != 3 || w.N % kRunCells != 0) continue;
+      std::vector<int32_t> cs(w.cells + 1);
+      AGP_CUDA(cudaMemcpyAsync(cs.data(), w.cell_start, sizeof(int32_t) * (w.cells + 1),
+                               cudaMemcpyDeviceToHost, st));
+      AGP_CUDA(cudaStreamSynchronize(st));
+      for (int64_t c = 0; c < w.cells; c += kRunCells) {
+        const int a = cs[c], b = cs[c + kRunCells];
+        for (int q = a; q < b; q += kRunPoints)
+          runs.push_back(make_int4(s | (kRunCells << 16), (int)c, q, std::min(kRunPoints, b - q)));
+      }
+    }
+    pl->n_runs3 = (int64_t)runs.size();
+    if (!runs.empty()) {
+      AGP_CUDA(cudaMalloc(&pl->runs3, sizeof(int4) * runs.size()));
+      AGP_CUDA(cudaMemcpyAsync(pl->runs3, runs.data(), sizeof(int4) * runs.size(),
+                               cudaMemcpyHostToDevice, st));
+      AGP_CUDA(cudaStreamSynchronize(st));
+    }
+  }
   return AGP_OK;
 }
 
@@ -620,6 +646,7 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
     wd[s].perm = w.perm;
     wd[s].wts = reinterpret_cast<const T*>(w.wts);
     wd[s].grid = reinterpret_cast<T*>(w.grid);
+    wd[s].cell_start = w.cell_start;
     wd[s].n = n;
     wd[s].N = w.N;
     wd[s].n_os = w.n_os;
@@ -710,8 +737,12 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 0, st, dd);
-      AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
-                                   V + r0, ldv, Rc, pl->use_tc, pl->err_dev, st));
+      if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 && spread_tc_supported(3, pl->s, rc))
+        AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc, V + r0,
+                                     ldv, Rc, 1, pl->err_dev, st));
+      else
+        AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
+                                     V + r0, ldv, Rc, pl->use_tc, pl->err_dev, st));
       pl->launches[0] += 1;
     }
     {
@@ -727,8 +758,12 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 2, st, dd);
-      AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
-                                   Out + r0, ldo, Rc, scale, pl->use_tc, pl->err_dev, st));
+      if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 && interp_tc_supported(3, pl->s, rc))
+        AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc,
+                                     Out + r0, ldo, Rc, scale, 1, pl->err_dev, st));
+      else
+        AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
+                                     Out + r0, ldo, Rc, scale, pl->use_tc, pl->err_dev, st));
       pl->launches[2] += 1;
     }
   }

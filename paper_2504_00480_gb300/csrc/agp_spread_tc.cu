@@ -4,9 +4,12 @@
 // the points j:
 //     G[(t1, t2), (t3, r)] += sum_j A[(t1, t2), j] B[(t3, r), j],
 //     A[(t1, t2), j] = psi1_j(t1) psi2_j(t2),  B[(t3, r), j] = psi3_j(t3) v_j(r),
+// (for a run of cells, t3 counts the block's planes and B[(u, r), j] is
+// psi3_j(u - delta_j) v_j(r), delta_j the cell of point j within the run),
 // i.e. a [(2s)^2 x m] x [m x 2s R] matrix product per item (m <= item size).
-// Each CTA takes one item and 16 of the 32 right-hand sides: M = 128 rows
-// ((2s)^2 = 100 or 64, zero padded), N = 2s x 16 = 160 or 128 columns,
+// Each CTA takes one run of up to four cells along the last dimension (its
+// (2s)^2 x (2s + L - 1) block) and 16 of the 32 right-hand sides: M = 128 rows
+// ((2s)^2 = 100 or 64, zero padded), N = (2s + L - 1) x 16 columns,
 // accumulated in tensor memory (TMEM) by tcgen05.mma kind::tf32 over chunks
 // of 16 points (two K = 8 steps). FP32 accuracy from TF32 inputs by the split
 // x = x_hi + x_lo (x_hi = x rounded to TF32, x_lo = the rounded remainder):
@@ -54,7 +57,8 @@ struct TcSpreadShape {
   static constexpr int ROWS = TT * TT;
   static constexpr int RG8 = (ROWS + 7) / 8;          // 8-row groups written per chunk
   static constexpr int MR = 128;
-  static constexpr int NN = TT * kTcRH;
+  static constexpr int T3M = TT + kRunCells - 1;              // t3 planes of a run's block
+  static constexpr int NN = T3M * kTcRH;                       // largest MMA N
   static constexpr int WPP = wpp_of(3, S);
   static constexpr int A_BYTES = MR * kTcKC * 4;
   static constexpr int B_BYTES = NN * kTcKC * 4;
@@ -95,21 +99,27 @@ __device__ __forceinline__ void form_a(const float* __restrict__ pw, bool live, 
   }
 }
 
-// B rows n = 8 rg + r8 = (t3, r): t3 = rg / 2, r = 8 (rg % 2) + r8; thread
-// group G of NG takes its share of the t3 range
+// B rows n = 8 rg + r8 = (u, r): plane u of the run's block (u = rg / 2,
+// the point's tap t3 = u - delta for its cell offset delta in the run),
+// r = 8 (rg % 2) + r8; thread group G of NG takes its share of the planes
+// u < nu
 template <int S, int G, int NG>
-__device__ __forceinline__ void form_b(const float* __restrict__ p3, bool live, float v0, float v1,
-                                       float* __restrict__ ph, float* __restrict__ pl) {
-  constexpr int TT = 2 * S, T3A = G * TT / NG, T3B = (G + 1) * TT / NG;
+__device__ __forceinline__ void form_b(const float* __restrict__ p3, bool live, int delta, int nu,
+                                       float v0, float v1, float* __restrict__ ph,
+                                       float* __restrict__ pl) {
+  constexpr int TT = 2 * S, T3M = TT + kRunCells - 1;
+  constexpr int T3A = G * T3M / NG, T3B = (G + 1) * T3M / NG;
 #pragma unroll
-  for (int t3 = T3A; t3 < T3B; ++t3) {
-    const float p = live ? p3[2 * t3] : 0.0f;
+  for (int u = T3A; u < T3B; ++u) {
+    if (u >= nu) break;
+    const int t3 = u - delta;
+    const float p = (live && t3 >= 0 && t3 < TT) ? p3[2 * t3] : 0.0f;
     const float x0 = p * v0, x1 = p * v1;
     const float h0 = tf32_round(x0), h1 = tf32_round(x1);
-    ph[(2 * t3) * (kTcKC / 4) * 32] = h0;
-    pl[(2 * t3) * (kTcKC / 4) * 32] = tf32_round(x0 - h0);
-    ph[(2 * t3 + 1) * (kTcKC / 4) * 32] = h1;
-    pl[(2 * t3 + 1) * (kTcKC / 4) * 32] = tf32_round(x1 - h1);
+    ph[(2 * u) * (kTcKC / 4) * 32] = h0;
+    pl[(2 * u) * (kTcKC / 4) * 32] = tf32_round(x0 - h0);
+    ph[(2 * u + 1) * (kTcKC / 4) * 32] = h1;
+    pl[(2 * u + 1) * (kTcKC / 4) * 32] = tf32_round(x1 - h1);
   }
 }
 
@@ -128,11 +138,19 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   const int4 it = items[blockIdx.x >> 1];
   const int r0 = (blockIdx.x & 1) * RH;           // right-hand sides r0 .. r0 + 15
   if (r0 >= R) return;                            // whole CTA: nothing to add
-  const WinDev<float> w = wins[it.x];
+  const int win = it.x & 0xFFFF, L = max(1, it.x >> 16);   // window, cells in the run
+  const int nu = TT + L - 1;                      // planes of the run's block
+  const WinDev<float> w = wins[win];
   if (io) {
-    V = io[it.x].V;
-    ldv = io[it.x].ldv;
+    V = io[win].V;
+    ldv = io[win].ldv;
   }
+  // first sorted point of cells 1 .. L-1 of the run: a point's cell offset
+  // delta is the number of these it has reached
+  int bnd[kRunCells - 1];
+#pragma unroll
+  for (int q = 0; q < kRunCells - 1; ++q)
+    bnd[q] = (q + 1 < L) ? __ldg(w.cell_start + it.y + q + 1) : 0x7FFFFFFF;
   const bool vec_ok = (ldv % 4 == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0);
   const int j0 = it.z, m = it.w;
   // operand buffer b (0, 1) at smem_raw + b OPND; staging buffer q (0 .. kTcStages - 1)
@@ -194,7 +212,7 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     cp_async_commit();
   };
 
-  const uint32_t idesc = umma_idesc_tf32(Sh::MR, Sh::NN);
+  const uint32_t idesc = umma_idesc_tf32(Sh::MR, nu * RH);
   // this thread's slot in every core matrix it writes: row r8 and point k4
   // within the core, point quad kq, and its share g of the row groups
   const int slot = tid & 127, g = tid >> 7;
@@ -224,12 +242,16 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
       const float* pw = sw + kk * WPP;
       const float v0 = live ? sv[kk * RH + r8] : 0.0f;
       const float v1 = live ? sv[kk * RH + 8 + r8] : 0.0f;
+      const int jj = j0 + c * KC + kk;             // this point's sorted index
+      int delta = 0;
+#pragma unroll
+      for (int q = 0; q < kRunCells - 1; ++q) delta += jj >= bnd[q];
       const int o = kq * 32 + lane;
       constexpr int NG = kTcThreads / 128;
       auto form = [&](auto gc) {
         constexpr int G = decltype(gc)::value;
         form_a<S, G, NG>(pw, live, r8, ahi + o, alo + o);
-        form_b<S, G, NG>(pw + 2 * TTP, live, v0, v1, bhi + o, blo + o);
+        form_b<S, G, NG>(pw + 2 * TTP, live, delta, nu, v0, v1, bhi + o, blo + o);
       };
       switch (g) {
         case 0: form(std::integral_constant<int, 0>()); break;
@@ -272,10 +294,10 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     float* tile = reinterpret_cast<float*>(smem_raw) + warp * (32 * 17);
     int cc[3];
     decode_cell<3>(it.y, w.N, cc);
-    const int ta = part * TT / NQ, tb = (part + 1) * TT / NQ;
+    const int ta = part * nu / NQ, tb = (part + 1) * nu / NQ;
     const int c4 = (lane & 3) * 4;
 #pragma unroll 1
-    for (int t3 = ta; t3 < tb; ++t3) {
+    for (int t3 = ta; t3 < tb; ++t3) {              // plane of the run's block
       uint32_t v[16];
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t3 * RH);
       asm volatile(
