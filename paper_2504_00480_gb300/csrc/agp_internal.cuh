@@ -232,12 +232,12 @@ template <typename T>
 cudaError_t spread_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
                          int64_t n_items, int d, int s, int RC, const T* V, int64_t ldv, int R,
                          cudaStream_t st);
-// Tensor-core spreading (agp_spread_tc.cu): FP32, d = 3, RC = 32, s = 4 or 5.
+// Tensor-core spreading (agp_spread_tc.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5.
 // err receives bit 2 if a bounded wait expired.
 bool spread_tc_supported(int d, int s, int RC);
 cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
-                            int64_t n_items, int s, const float* V, int64_t ldv, int R, int* err,
-                            cudaStream_t st);
+                            int64_t n_items, int s, const float* V, int64_t ldv, int R, int rc,
+                            int* err, cudaStream_t st);
 // spread_items, or spread_items_tc when `tc` is set and the case is supported
 template <typename T>
 cudaError_t spread_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
@@ -245,15 +245,15 @@ cudaError_t spread_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const in
                              int tc, int* err, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (tc && spread_tc_supported(d, s, RC))
-      return spread_items_tc(wins, io, items, n_items, s, V, ldv, R, err, st);
+      return spread_items_tc(wins, io, items, n_items, s, V, ldv, R, RC, err, st);
   }
   return spread_items<T>(wins, io, items, n_items, d, s, RC, V, ldv, R, st);
 }
-// Tensor-core interpolation (agp_interp_tc.cu): FP32, d = 3, RC = 32, s = 4 or 5.
+// Tensor-core interpolation (agp_interp_tc.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5.
 bool interp_tc_supported(int d, int s, int RC);
 cudaError_t interp_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
                             int64_t n_items, int s, float* Out, int64_t ldo, int R, float scale,
-                            int* err, cudaStream_t st);
+                            int rc, int* err, cudaStream_t st);
 // Interpolate the grids of those windows and add scale * result into
 // Out[:, 0..R) (with io: Out, ldo and scale of io[window]).
 template <typename T>
@@ -268,7 +268,7 @@ cudaError_t interp_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const in
                              T scale, int tc, int* err, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (tc && interp_tc_supported(d, s, RC))
-      return interp_items_tc(wins, io, items, n_items, s, Out, ldo, R, scale, err, st);
+      return interp_items_tc(wins, io, items, n_items, s, Out, ldo, R, scale, RC, err, st);
   }
   return interp_items<T>(wins, io, items, n_items, d, s, RC, Out, ldo, R, scale, st);
 }

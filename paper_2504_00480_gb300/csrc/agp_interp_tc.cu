@@ -68,13 +68,13 @@ struct TcInterpShape {
 // [G * NN/8/NG, (G+1) * NN/8/NG) of B ((t3, r)). Offsets relative to the
 // thread's base pointers are compile-time constants.
 template <int S, int G>
-__device__ __forceinline__ void it_load_b(const float* __restrict__ gp, bool krow, int nrg,
+__device__ __forceinline__ void it_load_b(const float* __restrict__ gp, bool krow, int nrg, int rc,
                                           float* gb) {
   constexpr int NRG = (2 * S + kRunCells - 1) * kItRH / 8, PER = NRG / kItNG, RGA = G * PER;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int rg = RGA + q;
-    gb[q] = (krow && rg < nrg) ? __ldg(gp + (rg >> 1) * 32 + (rg & 1) * 8) : 0.0f;
+    const int rg = RGA + q;             // plane rg / 2 (cell stride rc), columns 8 (rg % 2) ..
+    gb[q] = (krow && rg < nrg) ? __ldg(gp + (rg >> 1) * rc + (rg & 1) * 8) : 0.0f;
   }
 }
 
@@ -113,15 +113,16 @@ template <int S>
 __global__ void __launch_bounds__(kItThreads, 2)
 k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict__ io,
             const int4* __restrict__ items, float* __restrict__ Out, int64_t ldo, int R,
-            float scale, int* __restrict__ err) {
+            float scale, int rc, int* __restrict__ err) {
   using Sh = TcInterpShape<S>;
   constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, KC = kItKC, RH = kItRH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int4 it = items[blockIdx.x >> 1];
-  const int r0 = (blockIdx.x & 1) * RH;
+  const int nh = rc / 16;                         // 16-column halves of the grid rows
+  const int4 it = items[blockIdx.x / nh];
+  const int r0 = (blockIdx.x % nh) * RH;
   if (r0 >= R) return;
   const int win = it.x & 0xFFFF, L = max(1, it.x >> 16);   // window, cells in the run
   const int nu = TT + L - 1;                      // planes of the run's block
@@ -167,13 +168,13 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   auto bptr = [&](int kk) -> const float* {
     const int t1 = kk / TT, t2 = kk - (kk / TT) * TT;
     const int64_t cell = ((int64_t)(cc[0] + t1) * w.W + (cc[1] + t2)) * w.W + cc[2];
-    return w.grid + cell * 32 + r0 + r8;
+    return w.grid + cell * rc + r0 + r8;
   };
   auto load_b = [&](int kk, float* gb) {
     const bool krow = kk < Sh::ROWS;
     const float* gp = krow ? bptr(kk) : w.grid;
-    if (g == 0) it_load_b<S, 0>(gp, krow, 2 * nu, gb);
-    else it_load_b<S, 1>(gp, krow, 2 * nu, gb);
+    if (g == 0) it_load_b<S, 0>(gp, krow, 2 * nu, rc, gb);
+    else it_load_b<S, 1>(gp, krow, 2 * nu, rc, gb);
   };
   bool ok = true;
   int gc = 0;                                    // chunks issued so far (all tiles)
@@ -305,28 +306,30 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
 
 template <int S>
 cudaError_t interp_tc_s(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
-                        int64_t n_items, float* Out, int64_t ldo, int R, float scale, int* err,
-                        cudaStream_t st) {
+                        int64_t n_items, float* Out, int64_t ldo, int R, float scale, int rc,
+                        int* err, cudaStream_t st) {
   using Sh = TcInterpShape<S>;
   cudaError_t e = cudaFuncSetAttribute(k_interp_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Sh::SMEM);
   if (e != cudaSuccess) return e;
   if (n_items <= 0) return cudaSuccess;
-  k_interp_tc<S><<<(unsigned)(2 * n_items), kItThreads, Sh::SMEM, st>>>(wins, io, items, Out, ldo,
-                                                                        R, scale, err);
+  k_interp_tc<S><<<(unsigned)(rc / 16 * n_items), kItThreads, Sh::SMEM, st>>>(wins, io, items, Out, ldo,
+                                                                        R, scale, rc, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool interp_tc_supported(int d, int s, int RC) { return d == 3 && RC == 32 && (s == 4 || s == 5); }
+bool interp_tc_supported(int d, int s, int RC) {
+  return d == 3 && (RC == 32 || RC == 16) && (s == 4 || s == 5);
+}
 
 cudaError_t interp_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
                             int64_t n_items, int s, float* Out, int64_t ldo, int R, float scale,
-                            int* err, cudaStream_t st) {
+                            int rc, int* err, cudaStream_t st) {
   switch (s) {
-    case 4: return interp_tc_s<4>(wins, io, items, n_items, Out, ldo, R, scale, err, st);
-    case 5: return interp_tc_s<5>(wins, io, items, n_items, Out, ldo, R, scale, err, st);
+    case 4: return interp_tc_s<4>(wins, io, items, n_items, Out, ldo, R, scale, rc, err, st);
+    case 5: return interp_tc_s<5>(wins, io, items, n_items, Out, ldo, R, scale, rc, err, st);
   }
   return cudaErrorInvalidValue;
 }

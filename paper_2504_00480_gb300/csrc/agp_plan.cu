@@ -688,15 +688,18 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
   return AGP_OK;
 }
 
-// Right-hand sides per pass. With the tensor-core kernels on, FP32 plans
-// with a d = 3 window that they support take 9 or more columns in passes of
-// 32: a tensor-core pass over 17 columns costs about what one over 32 does,
-// and still less than the FMA kernels' 24-column pass (columns 16 .. 31 of a
-// pass are skipped when R <= 16).
+// Right-hand sides of the next pass for R remaining columns. With the
+// tensor-core kernels on, FP32 plans with a d = 3 window that they support
+// take 17 or more columns in a pass of 32 and 9 .. 16 columns in a pass of
+// 16: a tensor-core pass costs about the same for any column count up to its
+// width (a 17-column pass of 32 is still cheaper than the FMA kernels'
+// 24-column pass, and than 16 columns plus a narrow FMA pass for the rest),
+// and a 16-column pass saves half of the DFT work of a 32-column one.
 int pick_rc(const agp_plan_s* pl, int R) {
   if (pl->use_tc && pl->prec == AGP_F32 && R >= 9) {
     for (const Window& w : pl->win)
-      if (spread_tc_supported(w.d, pl->s, 32) && interp_tc_supported(w.d, pl->s, 32)) return 32;
+      if (spread_tc_supported(w.d, pl->s, 32) && interp_tc_supported(w.d, pl->s, 32))
+        return R >= 17 ? 32 : 16;
   }
   return rhs_block_width(pl->prec, R);
 }
@@ -724,9 +727,9 @@ struct StageTimer {
 template <typename T>
 agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_t ldo, int R,
                          int der, T scale, cudaStream_t st) {
-  const int rc = pick_rc(pl, R);
   const WinDev<T>* wins = reinterpret_cast<const WinDev<T>*>(pl->wins_dev);
-  for (int r0 = 0; r0 < R; r0 += rc) {
+  for (int r0 = 0, rc = 0; r0 < R; r0 += rc) {
+    rc = pick_rc(pl, R - r0);
     const int Rc = R - r0 < rc ? R - r0 : rc;
     {
       StageTimer tm(pl, 3, st);

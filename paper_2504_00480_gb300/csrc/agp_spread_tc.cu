@@ -127,7 +127,7 @@ template <int S>
 __global__ void __launch_bounds__(kTcThreads)
 k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict__ io,
             const int4* __restrict__ items, const float* __restrict__ V, int64_t ldv, int R,
-            int* __restrict__ err) {
+            int rc, int* __restrict__ err) {
   using Sh = TcSpreadShape<S>;
   constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, KC = kTcKC, RH = kTcRH;
   static_assert(kTcThreads % 128 == 0 && kTcThreads <= 512, "groups of 128 threads");
@@ -135,8 +135,9 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int4 it = items[blockIdx.x >> 1];
-  const int r0 = (blockIdx.x & 1) * RH;           // right-hand sides r0 .. r0 + 15
+  const int nh = rc / 16;                         // 16-column halves of the grid rows
+  const int4 it = items[blockIdx.x / nh];
+  const int r0 = (blockIdx.x % nh) * RH;          // right-hand sides r0 .. r0 + 15
   if (r0 >= R) return;                            // whole CTA: nothing to add
   const int win = it.x & 0xFFFF, L = max(1, it.x >> 16);   // window, cells in the run
   const int nu = TT + L - 1;                      // planes of the run's block
@@ -319,7 +320,7 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
           const int t1 = row / TT, t2 = row - (row / TT) * TT;
           const int64_t base = ((int64_t)(cc[0] + t1) * w.W + (cc[1] + t2)) * w.W + cc[2] + t3;
           const float* src = tile + rl * 17 + c4;
-          atomicAdd(reinterpret_cast<float4*>(w.grid + base * 32 + r0 + c4),
+          atomicAdd(reinterpret_cast<float4*>(w.grid + base * rc + r0 + c4),
                     make_float4(src[0], src[1], src[2], src[3]));
         }
       }
@@ -337,28 +338,30 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
 
 template <int S>
 cudaError_t spread_tc_s(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
-                        int64_t n_items, const float* V, int64_t ldv, int R, int* err,
+                        int64_t n_items, const float* V, int64_t ldv, int R, int rc, int* err,
                         cudaStream_t st) {
   using Sh = TcSpreadShape<S>;
   cudaError_t e = cudaFuncSetAttribute(k_spread_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Sh::SMEM);
   if (e != cudaSuccess) return e;
   if (n_items <= 0) return cudaSuccess;
-  k_spread_tc<S><<<(unsigned)(2 * n_items), kTcThreads, Sh::SMEM, st>>>(wins, io, items, V, ldv,
-                                                                        R, err);
+  k_spread_tc<S><<<(unsigned)(rc / 16 * n_items), kTcThreads, Sh::SMEM, st>>>(
+      wins, io, items, V, ldv, R, rc, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool spread_tc_supported(int d, int s, int RC) { return d == 3 && RC == 32 && (s == 4 || s == 5); }
+bool spread_tc_supported(int d, int s, int RC) {
+  return d == 3 && (RC == 32 || RC == 16) && (s == 4 || s == 5);
+}
 
 cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
-                            int64_t n_items, int s, const float* V, int64_t ldv, int R, int* err,
-                            cudaStream_t st) {
+                            int64_t n_items, int s, const float* V, int64_t ldv, int R, int rc,
+                            int* err, cudaStream_t st) {
   switch (s) {
-    case 4: return spread_tc_s<4>(wins, io, items, n_items, V, ldv, R, err, st);
-    case 5: return spread_tc_s<5>(wins, io, items, n_items, V, ldv, R, err, st);
+    case 4: return spread_tc_s<4>(wins, io, items, n_items, V, ldv, R, rc, err, st);
+    case 5: return spread_tc_s<5>(wins, io, items, n_items, V, ldv, R, rc, err, st);
   }
   return cudaErrorInvalidValue;
 }
