@@ -12,7 +12,10 @@ paper is silent or ambiguous this module takes the following readings:
   set the complex sum has a small imaginary part, and the paper's own 1-D
   figure (Sec. 3.1) shows the real cosine series.
 * ``kappa_R(l/N)`` at ``l_t = -N/2`` is the plain kernel value (no boundary
-  smoothing, Sec. 3.1).
+  smoothing, Sec. 3.1), unless outer boundary smoothing is asked for
+  (``boundary = (eps_b, p)``): then kappa_R follows the two-point Taylor
+  regularisation of ``boundary_polynomial``, whose value at r = 1/2 is
+  kappa(1/2).
 * One lengthscale and one ``sigma_f`` are shared by all windows (Sec. 2.1).
 * NFFT (Appendix A): Kaiser-Bessel window with oversampling ``sigma_os``
   (default 2, so the oversampled grid has ``n_os = 2N`` points per dimension).
@@ -30,6 +33,12 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
 * ``truncated_matvec``: exact agreement with the dense sum on lattice points
   (trigonometric interpolation property), convergence to the dense sum at
   small ell, exact symmetry, eq. (3.4) derivative consistency.
+* ``kernel_taylor``: symbolic derivatives (sympy); ``boundary_polynomial``:
+  the 2p interpolation conditions checked by finite differences of the
+  regularised kernel, continuity of kappa_R's derivatives; the smoothed
+  truncated sum converges to the dense sum faster than the unsmoothed one
+  (Gaussian, Matern(3/2)), and eq. (3.4) derivative consistency holds with
+  smoothing.
 * ``kb_window_hat``: numerical quadrature of the truncated window.
 * ``nfft``/``nfft_adjoint``: error against the exact NDFT below the window
   error bound of Appendix A.
@@ -54,6 +63,7 @@ import scipy.special
 __all__ = [
     "kernel", "kernel_der_ell", "window_points",
     "dense_matvec", "dense_deriv_matvec", "dense_matrix",
+    "kernel_taylor", "boundary_polynomial", "kernel_regularised",
     "index_set", "fourier_coeffs", "ndft_adjoint", "ndft",
     "truncated_matvec", "truncated_deriv_matvec",
     "bins", "kb_shape", "kb_window", "kb_window_hat",
@@ -84,8 +94,9 @@ def kernel(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
     Sec. 4 (generalisation), normalised to kappa(0) = 1 with c = ell: the
     inverse multiquadric (r^2 + c^2)^{-1/2} c = (1 + r^2/ell^2)^{-1/2} and
     the sinc kernel sin(r / ell) / (r / ell). None carries sigma_f (it
-    multiplies the sum)."""
-    r = np.asarray(r, dtype=np.float64)
+    multiplies the sum). A complex ``r`` evaluates the same formulas (used
+    by ``kernel_taylor``)."""
+    r = _as_arg(r)
     if kind == "gauss":
         return np.exp(-(r * r) / (2.0 * ell * ell))
     if kind == "matern12":
@@ -95,6 +106,8 @@ def kernel(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
     if kind == "imq":
         return 1.0 / np.sqrt(1.0 + (r / ell) ** 2)
     if kind == "sinc":
+        if np.iscomplexobj(r):
+            return np.sin(r / ell) / (r / ell)
         return np.sinc(r / (ell * math.pi))   # numpy's sinc(x) = sin(pi x) / (pi x)
     raise ValueError(kind)
 
@@ -103,7 +116,7 @@ def kernel_der_ell(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
     """Derivative of kappa_s with respect to ell, Sec. 2.1 eq. (2.3):
     Gaussian r^2/ell^3 kappa^G, Matern(1/2) r/ell^2 kappa^M; Matern(3/2):
     d/dell (1 + r/ell) e^{-r/ell} = r^2/ell^3 e^{-r/ell}."""
-    r = np.asarray(r, dtype=np.float64)
+    r = _as_arg(r)
     if kind == "gauss":
         return (r * r) / ell ** 3 * kernel(kind, r, ell)
     if kind == "matern12":
@@ -122,8 +135,13 @@ def kernel_der_ell(kind: str, r: np.ndarray, ell: float) -> np.ndarray:
             closed = (np.sin(u) / u - np.cos(u)) / ell
         u2 = u * u
         series = u2 * (1.0 / 3 - u2 * (1.0 / 30 - u2 * (1.0 / 840 - u2 / 45360))) / ell
-        return np.where(u < 0.05, series, closed)
+        return np.where(np.abs(u) < 0.05, series, closed)
     raise ValueError(kind)
+
+
+def _as_arg(r):
+    r = np.asarray(r)
+    return r.astype(np.complex128) if np.iscomplexobj(r) else r.astype(np.float64)
 
 
 def window_points(X: np.ndarray, window) -> np.ndarray:
@@ -205,6 +223,70 @@ def dense_matrix(X, windows, kind, ell, sigma_f, sigma_eps, which=None):
 # O2: Fourier-truncated sum (Sec. 3.1 eqs. (3.1)-(3.3), Sec. 3.2)
 # ---------------------------------------------------------------------------
 
+def kernel_taylor(kind: str, a: float, ell: float, p: int, der: bool = False,
+                  M: int = 256) -> np.ndarray:
+    """Taylor coefficients f^(j)(a) / j!, j < p, of f = kappa (or its
+    ell-derivative) as a function of r, by Cauchy's integral formula
+    c_j = (1 / 2 pi i) closed-integral f(z) (z - a)^{-j-1} dz on the circle
+    |z - a| = a/2, discretised by the trapezoid rule with M nodes (exact up
+    to aliasing c_{j+M} rho^M for a function analytic on the disc; every
+    kernel here is analytic on it: the inverse multiquadric's branch points
+    r = +-i ell lie outside it)."""
+    rho = 0.5 * a
+    theta = TWO_PI * np.arange(M) / M
+    z = a + rho * np.exp(1j * theta)
+    f = (kernel_der_ell if der else kernel)(kind, z, ell)
+    return np.array([np.real(np.mean(f * np.exp(-1j * j * theta))) / rho ** j
+                     for j in range(p)])
+
+
+def boundary_polynomial(kind: str, ell: float, eps_b: float, p: int, der: bool = False):
+    """Outer boundary regularisation of kappa_R (Sec. 3.1 mentions smoothing
+    the outer boundary and sets it to zero; the construction is the standard
+    one of the NFFT fast summation literature it cites): on the layer
+    a = 1/2 - eps_b < r < 1/2 the radial kernel is replaced by the two-point
+    Taylor polynomial T of degree 2p - 1 with T^(j)(a) = f^(j)(a) and, at
+    r = 1/2, T = f(1/2) and T^(j) = 0 for 1 <= j < p; for r >= 1/2 kappa_R is
+    the constant f(1/2), so its periodic continuation is p - 1 times
+    continuously differentiable. The value f(1/2) at the outer end is a
+    reading (the paper does not fix it).
+
+    Returns e with T(r) = sum_q e_q ((r - a) / eps_b)^q, from the 2p x 2p
+    linear system of the 2p conditions in the scaled variable."""
+    a = 0.5 - eps_b
+    c = kernel_taylor(kind, a, ell, p, der)
+    f_half = float((kernel_der_ell if der else kernel)(kind, np.array(0.5), ell))
+    A = np.zeros((2 * p, 2 * p))
+    rhs = np.zeros(2 * p)
+    for j in range(p):
+        # d^j/ds^j of s^q at s = 0 and s = 1, s = (r - a) / eps_b
+        A[j, j] = math.factorial(j)
+        for q in range(j, 2 * p):
+            A[p + j, q] = math.factorial(q) / math.factorial(q - j)
+        rhs[j] = math.factorial(j) * c[j] * eps_b ** j   # f^(j)(a) eps_b^j
+        rhs[p + j] = f_half if j == 0 else 0.0
+    return np.linalg.solve(A, rhs)
+
+
+def kernel_regularised(kind: str, r, ell: float, eps_b: float, p: int, der: bool = False):
+    """kappa_R of Sec. 3.1 with outer boundary smoothing (see
+    ``boundary_polynomial``): kappa for r <= 1/2 - eps_b, the boundary
+    polynomial on the layer, kappa(1/2) beyond r = 1/2. With eps_b = 0 or
+    p = 0 it is kappa itself."""
+    r = np.asarray(r, dtype=np.float64)
+    f = (kernel_der_ell if der else kernel)
+    out = f(kind, r, ell)
+    if eps_b <= 0 or p <= 0:
+        return out
+    a = 0.5 - eps_b
+    e = boundary_polynomial(kind, ell, eps_b, p, der)
+    layer = (r > a) & (r < 0.5)
+    sl = (r[layer] - a) / eps_b
+    out[layer] = sum(e[q] * sl ** q for q in range(2 * p))
+    out[r >= 0.5] = float(f(kind, np.array(0.5), ell))
+    return out
+
+
 def index_set(N: int) -> np.ndarray:
     """I_N = {-N/2, ..., N/2 - 1} (Sec. 3.1, one dimension)."""
     if N % 2:
@@ -212,19 +294,23 @@ def index_set(N: int) -> np.ndarray:
     return np.arange(-N // 2, N // 2)
 
 
-def fourier_coeffs(kind: str, ell: float, N: int, d: int, der: bool = False):
+def fourier_coeffs(kind: str, ell: float, N: int, d: int, der: bool = False,
+                   boundary=None):
     """Discrete Fourier coefficients b_k(kappa_R), k in I_N^d.
 
     Sec. 3.1 eq. (3.2): b_k = N^{-d} sum_{l in I_N^d} kappa_R(l/N) e^{-2 pi i l.k/N}.
     The samples l/N lie in [-1/2, 1/2)^d, where kappa_R is kappa itself (no
-    boundary smoothing). With der=True the samples are those of the
-    ell-derivative kernel (Sec. 3.2). The d-dimensional sum is evaluated one
-    axis at a time (the exponential factorises over the axes).
+    boundary smoothing, the paper's setting) or, with ``boundary = (eps_b,
+    p)``, the regularised kernel of ``kernel_regularised``. With der=True the
+    samples are those of the ell-derivative kernel (Sec. 3.2). The
+    d-dimensional sum is evaluated one axis at a time (the exponential
+    factorises over the axes).
     Returns a complex array indexed [k_1 + N/2, ..., k_d + N/2]."""
     idx = index_set(N)
     grids = np.meshgrid(*([idx / N] * d), indexing="ij")
     r = np.sqrt(sum(g * g for g in grids))
-    samples = (kernel_der_ell if der else kernel)(kind, r, ell).astype(np.complex128)
+    eps_b, p = boundary if boundary is not None else (0.0, 0)
+    samples = kernel_regularised(kind, r, ell, eps_b, p, der).astype(np.complex128)
     F = np.exp(-1j * TWO_PI * np.outer(idx, idx) / N) / N   # F[k, l]
     b = samples
     for axis in range(d):
@@ -283,9 +369,9 @@ def ndft(x, C, N, chunk=256):
     return out
 
 
-def _truncated_window_apply(kind, xw, V, ell, N, der, rows):
+def _truncated_window_apply(kind, xw, V, ell, N, der, rows, boundary=None):
     d = xw.shape[1]
-    b = fourier_coeffs(kind, ell, N, d, der)
+    b = fourier_coeffs(kind, ell, N, d, der, boundary)
     c = ndft_adjoint(xw, V, N)
     f = b[..., None] * c
     xo = xw if rows is None else xw[np.asarray(rows)]
@@ -293,13 +379,14 @@ def _truncated_window_apply(kind, xw, V, ell, N, der, rows):
 
 
 def truncated_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, rows=None,
-                     add_noise=True):
+                     add_noise=True, boundary=None):
     """K_hat V with every sub-kernel replaced by its truncated Fourier series.
 
     Sec. 3.1: per window, h(x_i) = Re sum_{k in I_N} b_k (sum_j v_j
-    e^{-2 pi i k.x_j}) e^{2 pi i k.x_i} (eq. (3.3)); "the approximate products
-    K_s v are then summed up and weighted" (end of Sec. 3.1):
-    sigma_f^2 sum_s h_s + sigma_eps^2 v. ``N`` is an int or one per window."""
+    e^{-2 pi i k.x_j}) e^{2 pi i k.x_i} (eq. (3.3)); the approximate
+    products of the windows are summed and weighted (end of Sec. 3.1):
+    sigma_f^2 sum_s h_s + sigma_eps^2 v. ``N`` is an int or one per window;
+    ``boundary = (eps_b, p)`` smooths kappa_R's outer boundary."""
     V = np.asarray(V, dtype=np.float64)
     if V.ndim == 1:
         V = V[:, None]
@@ -307,7 +394,7 @@ def truncated_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, rows=None,
     out = 0.0
     for w, Nw in zip(windows, Ns):
         out = out + _truncated_window_apply(kind, window_points(X, w), V, ell, Nw,
-                                            False, rows)
+                                            False, rows, boundary)
     out = sigma_f ** 2 * out
     if add_noise:
         vr = V if rows is None else V[np.asarray(rows)]
@@ -316,11 +403,14 @@ def truncated_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, rows=None,
 
 
 def truncated_deriv_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, which,
-                           rows=None):
+                           rows=None, boundary=None):
     """Derivative operators of the truncated sum. For ell the coefficients are
     those of the derivative kernel, which Sec. 3.2 eq. (3.4) shows equal the
     ell-derivative of the truncated series; sigma_f and sigma_eps as in
-    Sec. 2.1."""
+    Sec. 2.1. With boundary smoothing the derivative kernel is regularised
+    by the same construction, which is linear in the kernel's values and
+    derivatives at the layer's ends, so it is the ell-derivative of the
+    regularised kernel."""
     V = np.asarray(V, dtype=np.float64)
     if V.ndim == 1:
         V = V[:, None]
@@ -331,7 +421,7 @@ def truncated_deriv_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, whic
     out = 0.0
     for w, Nw in zip(windows, Ns):
         out = out + _truncated_window_apply(kind, window_points(X, w), V, ell, Nw,
-                                            which == "ell", rows)
+                                            which == "ell", rows, boundary)
     if which == "ell":
         return sigma_f ** 2 * out
     if which == "sigma_f":
@@ -469,7 +559,7 @@ def nfft(x, C, N, s, sigma_os=2.0):
 
 
 def nfft_fastsum_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, s,
-                        sigma_os=2.0, add_noise=True):
+                        sigma_os=2.0, add_noise=True, boundary=None):
     """The method itself on the CPU: eq. (3.3) with the inner sum by the
     adjoint NFFT and the outer sum by the NFFT (Sec. 3.1 and Appendix A),
     real part, then the weighted window sum."""
@@ -480,7 +570,7 @@ def nfft_fastsum_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, s,
     out = 0.0
     for w, Nw in zip(windows, Ns):
         xw = window_points(X, w)
-        b = fourier_coeffs(kind, ell, Nw, xw.shape[1])
+        b = fourier_coeffs(kind, ell, Nw, xw.shape[1], boundary=boundary)
         chat = nfft_adjoint(xw, V, Nw, s, sigma_os)
         out = out + np.real(nfft(xw, b[..., None] * chat, Nw, s, sigma_os))
     out = sigma_f ** 2 * out
