@@ -212,8 +212,9 @@ agp_status agp_plan_landmarks(agp_plan plan, int n_landmarks, int32_t* idx, int 
                               void* stream);
 
 /* Spreading and interpolation on the tensor cores (FP32 plans, d = 3
- * windows, s = 4 or 5, 32 right-hand sides per pass; other cases keep the
- * FP32 FMA path). Per work item, spreading's update of the cell's
+ * windows, s = 4 or 5, passes of 9 to 16 right-hand sides on 16-column grids
+ * and of 17 or more on 32-column grids; other cases keep the FP32 FMA
+ * path). Per work item, spreading's update of the cell's
  * (2s)^2 x (2s R) grid block is the matrix product [(t1, t2) x points] x
  * [points x (t3, r)] of window-value matrices, and interpolation's sum over
  * the first two dimensions is the product [points x (t1, t2)] x
@@ -222,6 +223,26 @@ agp_status agp_plan_landmarks(agp_plan plan, int n_landmarks, int32_t* idx, int 
  * products, about FP32 accuracy), accumulated in FP32.
  * enable: 1 on (the default for FP32 plans), 0 off (FMA path only). */
 agp_status agp_plan_set_tensor_cores(agp_plan plan, int enable);
+
+/* Outer boundary smoothing of the periodic kernel kappa_R (Sec. 3.1: the
+ * periodic extension may be smoothed at its outer boundary; the paper's own
+ * runs leave it unsmoothed, which is this library's default). With
+ * eps_b > 0 and p > 0, kappa_R(r) is kappa(r) for r <= a = 1/2 - eps_b, on
+ * the layer a < r < 1/2 the two-point Taylor polynomial T of degree 2p - 1
+ * with T^(j)(a) = kappa^(j)(a) and T(1/2) = kappa(1/2), T^(j)(1/2) = 0
+ * (1 <= j < p), and kappa(1/2) for r >= 1/2; its periodic continuation is
+ * p - 1 times continuously differentiable, so the truncated Fourier series
+ * of eq. (3.1) converges faster for smooth kernels. The ell-derivative
+ * kernel of eq. (3.4) is regularised the same way. kappa_R equals kappa at
+ * every point difference only if |x_i - x_j| <= 1/2 - eps_b, so every
+ * window's scaled points must lie in the ball |x| <= 1/4 - eps_b/2.
+ * eps_b: layer width in [0, 1/4]; p: order in [0, 8] (eps_b = 0 or p = 0
+ * switches the smoothing off). Recomputes the Fourier coefficients on
+ * `stream` (and again at every agp_set_hyper with a new ell).
+ * Returns AGP_EINVAL for arguments out of range and AGP_EDOMAIN if a point
+ * lies outside the ball (the plan then keeps its previous setting).
+ * Synchronises `stream`. */
+agp_status agp_plan_set_boundary(agp_plan plan, double eps_b, int p, void* stream);
 
 /* AGP_TIMEOUT if a bounded wait inside a tensor-core kernel expired since
  * the last check (the flag is then cleared), else AGP_OK. Synchronises

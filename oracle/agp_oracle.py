@@ -252,20 +252,38 @@ def boundary_polynomial(kind: str, ell: float, eps_b: float, p: int, der: bool =
     reading (the paper does not fix it).
 
     Returns e with T(r) = sum_q e_q ((r - a) / eps_b)^q, from the 2p x 2p
-    linear system of the 2p conditions in the scaled variable."""
+    linear system of the 2p conditions in the scaled variable, solved
+    exactly in rational arithmetic (the system is a confluent Vandermonde
+    matrix, too ill-conditioned at p = 8 for a floating-point solve)."""
+    from fractions import Fraction
     a = 0.5 - eps_b
     c = kernel_taylor(kind, a, ell, p, der)
     f_half = float((kernel_der_ell if der else kernel)(kind, np.array(0.5), ell))
-    A = np.zeros((2 * p, 2 * p))
-    rhs = np.zeros(2 * p)
+    n2 = 2 * p
+    A = [[Fraction(0)] * n2 for _ in range(n2)]
+    rhs = [Fraction(0)] * n2
     for j in range(p):
         # d^j/ds^j of s^q at s = 0 and s = 1, s = (r - a) / eps_b
-        A[j, j] = math.factorial(j)
-        for q in range(j, 2 * p):
-            A[p + j, q] = math.factorial(q) / math.factorial(q - j)
-        rhs[j] = math.factorial(j) * c[j] * eps_b ** j   # f^(j)(a) eps_b^j
-        rhs[p + j] = f_half if j == 0 else 0.0
-    return np.linalg.solve(A, rhs)
+        A[j][j] = Fraction(math.factorial(j))
+        for q in range(j, n2):
+            A[p + j][q] = Fraction(math.factorial(q) // math.factorial(q - j))
+        rhs[j] = Fraction(math.factorial(j)) * Fraction(float(c[j] * eps_b ** j))
+        rhs[p + j] = Fraction(f_half) if j == 0 else Fraction(0)
+    # Gaussian elimination (exact, so any nonzero pivot will do)
+    for col in range(n2):
+        piv = next(r for r in range(col, n2) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        rhs[col], rhs[piv] = rhs[piv], rhs[col]
+        for r in range(col + 1, n2):
+            if A[r][col] != 0:
+                m = A[r][col] / A[col][col]
+                A[r] = [x - m * y for x, y in zip(A[r], A[col])]
+                rhs[r] -= m * rhs[col]
+    e = [Fraction(0)] * n2
+    for col in range(n2 - 1, -1, -1):
+        acc = rhs[col] - sum(A[col][k] * e[k] for k in range(col + 1, n2))
+        e[col] = acc / A[col][col]
+    return np.array([float(v) for v in e])
 
 
 def kernel_regularised(kind: str, r, ell: float, eps_b: float, p: int, der: bool = False):

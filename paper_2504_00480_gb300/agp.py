@@ -70,6 +70,7 @@ _SIGS = {
     "agp_plan_landmarks": (c_int, [c_void_p, c_int, c_void_p, c_int, POINTER(c_int), c_void_p]),
     "agp_plan_set_item_points": (c_int, [c_void_p, c_int, c_void_p]),
     "agp_plan_set_tensor_cores": (c_int, [c_void_p, c_int]),
+    "agp_plan_set_boundary": (c_int, [c_void_p, c_double, c_int, c_void_p]),
     "agp_plan_check": (c_int, [c_void_p, c_void_p]),
     "agp_plan_autotune": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_double),
                                   c_void_p]),
@@ -275,6 +276,12 @@ def agp_nlml_grad_pc(plan: c_void_p, y: torch.Tensor, Wn: torch.Tensor, Wk: np.n
 
 def agp_plan_set_item_points(plan: c_void_p, points: int):
     _check(load_library().agp_plan_set_item_points(plan, int(points), _stream()))
+
+
+def agp_plan_set_boundary(plan: c_void_p, eps_b: float, p: int):
+    """Outer boundary smoothing of kappa_R (layer width eps_b, order p; 0
+    switches it off); the points must lie in the ball |x| <= 1/4 - eps_b/2."""
+    _check(load_library().agp_plan_set_boundary(plan, float(eps_b), int(p), _stream()))
 
 
 def agp_plan_autotune(plan: c_void_p, R: int = 32, reps: int = 3):
@@ -621,6 +628,9 @@ class Plan:
 
     def set_tensor_cores(self, enable: bool = True):
         _check(load_library().agp_plan_set_tensor_cores(self._h, int(bool(enable))))
+
+    def set_boundary(self, eps_b: float, p: int):
+        agp_plan_set_boundary(self._h, eps_b, p)
 
     def check(self):
         """Raise AgpError (AGP_TIMEOUT) if a bounded device wait expired."""

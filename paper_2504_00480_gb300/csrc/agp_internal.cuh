@@ -52,6 +52,10 @@ constexpr int kRunCells = 4;
 // FP32 accumulation error grows with the number of MMAs summed into one
 // accumulator).
 constexpr int kRunPoints = 256;
+// Outer boundary smoothing: largest order p, and the stride of one boundary
+// polynomial record (2p coefficients, padded, then the constant kappa(1/2)).
+constexpr int kBndMaxP = 8;
+constexpr int kBndStride = 2 * kBndMaxP + 1;
 
 // Window values stored per point and dimension: the 2s taps padded with zeros
 // to a multiple of 4 (16-byte vector loads).
@@ -198,6 +202,9 @@ struct agp_plan_s {
   int rc_max = 32;
   int item_points = agp::kItemPoints;   // points per work item (bin size), see agp_plan_autotune
   int use_tc = 1;                // spreading and interpolation on the tensor cores where supported
+  double bnd_eps = 0.0;          // outer boundary smoothing of kappa_R: layer width (0: off)
+  int bnd_p = 0;                 // ... and its order (derivatives matched at each end)
+  double* bnd_poly = nullptr;    // [2][kBndStride] boundary polynomials (kernel, ell-derivative)
   std::vector<agp::Window> win;
   void* wins_dev = nullptr;      // WinDev<T>[P]
   int4* items_all = nullptr;     // work items of every window, grouped by d

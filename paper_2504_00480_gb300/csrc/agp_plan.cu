@@ -156,9 +156,164 @@ __global__ void k_bins_out(const T* __restrict__ xs, const int32_t* __restrict__
 // ---------------------------------------------------------------------------
 // a1: Fourier coefficients (FP64)
 // ---------------------------------------------------------------------------
-// samples[l] = kappa(|l / N|) (or its ell-derivative), l in I_N^d row-major.
+// ---- outer boundary smoothing of kappa_R (Sec. 3.1) ----
+// kappa_R(r) = kappa(r) for r <= a = 1/2 - eps, T(r) on the layer a < r < 1/2
+// and kappa(1/2) beyond, with T the two-point Taylor polynomial of degree
+// 2p - 1: T^(j)(a) = kappa^(j)(a), T(1/2) = kappa(1/2), T^(j)(1/2) = 0 for
+// 1 <= j < p. The derivative kernel is regularised the same way (the
+// construction is linear in the end data, so this is d kappa_R / d ell).
+//
+// The Taylor coefficients of kappa at a come from truncated power series
+// arithmetic ("jets") in t = r - a: every kernel is a composition of +, *,
+// 1/x, sqrt, exp and sin/cos, each with a standard recurrence for its
+// series coefficients.
+namespace jet {
+__device__ void mul(const double* x, const double* y, double* z, int p) {
+  double o[kBndMaxP];
+  for (int k = 0; k < p; ++k) {
+    double acc = 0.0;
+    for (int j = 0; j <= k; ++j) acc += x[j] * y[k - j];
+    o[k] = acc;
+  }
+  for (int k = 0; k < p; ++k) z[k] = o[k];
+}
+__device__ void scale(const double* x, double c, double* z, int p) {
+  for (int k = 0; k < p; ++k) z[k] = c * x[k];
+}
+__device__ void exp_(const double* x, double* g, int p) {   // g' = x' g
+  double o[kBndMaxP];
+  o[0] = exp(x[0]);
+  for (int k = 1; k < p; ++k) {
+    double acc = 0.0;
+    for (int j = 1; j <= k; ++j) acc += j * x[j] * o[k - j];
+    o[k] = acc / k;
+  }
+  for (int k = 0; k < p; ++k) g[k] = o[k];
+}
+__device__ void recip(const double* x, double* g, int p) {  // x g = 1
+  double o[kBndMaxP];
+  o[0] = 1.0 / x[0];
+  for (int k = 1; k < p; ++k) {
+    double acc = 0.0;
+    for (int j = 1; j <= k; ++j) acc += x[j] * o[k - j];
+    o[k] = -acc * o[0];
+  }
+  for (int k = 0; k < p; ++k) g[k] = o[k];
+}
+__device__ void sqrt_(const double* x, double* g, int p) {  // g g = x
+  double o[kBndMaxP];
+  o[0] = sqrt(x[0]);
+  for (int k = 1; k < p; ++k) {
+    double acc = x[k];
+    for (int j = 1; j < k; ++j) acc -= o[j] * o[k - j];
+    o[k] = acc / (2.0 * o[0]);
+  }
+  for (int k = 0; k < p; ++k) g[k] = o[k];
+}
+__device__ void sincos_(const double* x, double* sn, double* cs, int p) {  // sn' = x' cs, cs' = -x' sn
+  sn[0] = sin(x[0]);
+  cs[0] = cos(x[0]);
+  for (int k = 1; k < p; ++k) {
+    double a = 0.0, b = 0.0;
+    for (int j = 1; j <= k; ++j) {
+      a += j * x[j] * cs[k - j];
+      b += j * x[j] * sn[k - j];
+    }
+    sn[k] = a / k;
+    cs[k] = -b / k;
+  }
+}
+}  // namespace jet
+
+// Taylor coefficients kappa^(j)(a) / j! (or of the ell-derivative), j < p.
+__device__ void kernel_jet(int kernel, double a, double ell, int der, int p, double* f) {
+  double r[kBndMaxP] = {0}, r2[kBndMaxP], t[kBndMaxP], u[kBndMaxP];
+  r[0] = a;
+  if (p > 1) r[1] = 1.0;
+  jet::mul(r, r, r2, p);
+  const double il = 1.0 / ell, il3 = il * il * il;
+  if (kernel == AGP_GAUSS) {                 // exp(-r^2 / (2 ell^2)); der r^2/ell^3 kappa
+    jet::scale(r2, -0.5 * il * il, t, p);
+    jet::exp_(t, f, p);
+    if (der) { jet::mul(f, r2, f, p); jet::scale(f, il3, f, p); }
+  } else if (kernel == AGP_MATERN12) {       // exp(-r/ell); der r/ell^2 kappa
+    jet::scale(r, -il, t, p);
+    jet::exp_(t, f, p);
+    if (der) { jet::mul(f, r, f, p); jet::scale(f, il * il, f, p); }
+  } else if (kernel == AGP_MATERN32) {       // (1 + r/ell) exp(-r/ell); der r^2/ell^3 exp(-r/ell)
+    jet::scale(r, -il, t, p);
+    jet::exp_(t, u, p);
+    if (der) {
+      jet::mul(u, r2, f, p);
+      jet::scale(f, il3, f, p);
+    } else {
+      jet::scale(r, il, t, p);
+      t[0] += 1.0;
+      jet::mul(t, u, f, p);
+    }
+  } else if (kernel == AGP_IMQ) {            // q = 1/(1 + r^2/ell^2), sqrt(q); der r^2/ell^3 sqrt(q) q
+    jet::scale(r2, il * il, t, p);
+    t[0] += 1.0;
+    jet::recip(t, u, p);                     // q
+    jet::sqrt_(u, f, p);
+    if (der) { jet::mul(f, u, f, p); jet::mul(f, r2, f, p); jet::scale(f, il3, f, p); }
+  } else {                                   // sinc: sin(w)/w, w = r/ell; der (sin(w)/w - cos(w))/ell
+    double sn[kBndMaxP], cs[kBndMaxP];
+    jet::scale(r, il, t, p);
+    jet::sincos_(t, sn, cs, p);
+    jet::recip(t, u, p);
+    jet::mul(sn, u, f, p);
+    if (der) for (int k = 0; k < p; ++k) f[k] = (f[k] - cs[k]) * il;
+  }
+}
+
+// poly[der][j] = kappa^(j)(a)/j! eps^j (j < p, the Taylor data at the inner
+// end in s = (r - a) / eps) and poly[der][2 kBndMaxP] = kappa(1/2). One
+// thread per der.
+__global__ void k_boundary_poly(double* __restrict__ poly, int kernel, double ell, double eps,
+                                int p) {
+  const int der = threadIdx.x;
+  if (der > 1) return;
+  double* e = poly + der * kBndStride;
+  double f[kBndMaxP];
+  kernel_jet(kernel, 0.5 - eps, ell, der, p, f);
+  double pw = 1.0;
+  for (int j = 0; j < p; ++j, pw *= eps) e[j] = f[j] * pw;
+  e[2 * kBndMaxP] = kernel_value(kernel, 0.25, ell, der);
+}
+
+// The two-point Taylor polynomial on s in [0, 1] with Taylor data f_j at
+// s = 0, value g at s = 1 and vanishing derivatives 1..p-1 there, in the
+// two-point Taylor (Hermite) basis, which needs no linear solve:
+//   T(s) = (1-s)^p sum_{j<p} f_j s^j sum_{k<p-j} C(p+k-1, k) s^k
+//        + g s^p sum_{k<p} C(p+k-1, k) (1-s)^k.
+__device__ double boundary_eval(const double* __restrict__ c, int p, double sl) {
+  const double u = 1.0 - sl;
+  double acc = 0.0, sj = 1.0;
+  for (int j = 0; j < p; ++j, sj *= sl) {
+    double sum = 0.0, bin = 1.0, sk = 1.0;          // bin = C(p+k-1, k)
+    for (int k = 0; k < p - j; ++k) {
+      sum += bin * sk;
+      sk *= sl;
+      bin = bin * (p + k) / (k + 1);
+    }
+    acc += c[j] * sj * sum;
+  }
+  double up = 1.0, sp = 1.0;
+  for (int k = 0; k < p; ++k) { up *= u; sp *= sl; }
+  double tail = 0.0, bin = 1.0, uk = 1.0;
+  for (int k = 0; k < p; ++k) {
+    tail += bin * uk;
+    uk *= u;
+    bin = bin * (p + k) / (k + 1);
+  }
+  return up * acc + c[2 * kBndMaxP] * sp * tail;
+}
+
+// samples[l] = kappa_R(|l / N|) (or its ell-derivative), l in I_N^d row-major;
+// with p > 0 the outer boundary of kappa_R is smoothed by `poly`.
 __global__ void k_kernel_samples(double* __restrict__ out, int N, int d, int kernel, double ell,
-                                 int der) {
+                                 int der, double eps, int p, const double* __restrict__ poly) {
   int64_t total = 1;
   for (int t = 0; t < d; ++t) total *= N;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -171,7 +326,35 @@ __global__ void k_kernel_samples(double* __restrict__ out, int N, int d, int ker
     const double x = (double)l / N;
     r2 += x * x;
   }
+  if (p > 0) {
+    const double* c = poly + der * kBndStride;
+    const double r = sqrt(r2), a = 0.5 - eps;
+    if (r >= 0.5) { out[e] = c[2 * kBndMaxP]; return; }
+    if (r > a) {
+      out[e] = boundary_eval(c, p, (r - a) / eps);
+      return;
+    }
+  }
   out[e] = kernel_value(kernel, r2, ell, der);
+}
+
+// Largest squared norm of a window's (sorted) points, as the bit pattern of a
+// non-negative double (monotone in the value), for the smoothing's domain.
+template <typename T>
+__global__ void k_max_norm2(const T* __restrict__ xs, int64_t n, int d,
+                            unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double r2 = 0.0;
+    for (int t = 0; t < d; ++t) {
+      const double x = (double)xs[t * n + j];
+      r2 += x * x;
+    }
+    m = fmax(m, r2);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
 // One axis of the d-dimensional DFT of eq. (3.2). The samples are real and
@@ -406,6 +589,8 @@ agp_status validate(const agp_plan_desc* d) {
 
 template <typename T>
 agp_status compute_coeffs(agp_plan_s* pl, cudaStream_t st) {
+  if (pl->bnd_p > 0)
+    k_boundary_poly<<<1, 32, 0, st>>>(pl->bnd_poly, pl->kernel, pl->ell, pl->bnd_eps, pl->bnd_p);
   for (auto& w : pl->win) {
     double* tmp = nullptr;
     AGP_CUDA(cudaMallocAsync(&tmp, sizeof(double) * w.cells * 2, st));
@@ -413,7 +598,8 @@ agp_status compute_coeffs(agp_plan_s* pl, cudaStream_t st) {
     double* t1 = tmp + w.cells;
     for (int der = 0; der < 2; ++der) {
       double* dst = der ? w.bder : w.b;
-      k_kernel_samples<<<nblk(w.cells, 256), 256, 0, st>>>(t0, w.N, w.d, pl->kernel, pl->ell, der);
+      k_kernel_samples<<<nblk(w.cells, 256), 256, 0, st>>>(t0, w.N, w.d, pl->kernel, pl->ell, der,
+                                                           pl->bnd_eps, pl->bnd_p, pl->bnd_poly);
       double* src = t0;
       for (int axis = 0; axis < w.d; ++axis) {
         double* o = (axis == w.d - 1) ? dst : (src == t0 ? t1 : t0);
@@ -458,6 +644,7 @@ void free_plan(agp_plan_s* pl) {
   cudaFree(pl->runs3);
   cudaFree(pl->wins_dev);
   cudaFree(pl->err_dev);
+  cudaFree(pl->bnd_poly);
   delete pl;
 }
 
@@ -1065,6 +1252,49 @@ agp_status agp_plan_set_tensor_cores(agp_plan pl, int enable) {
   if (!pl) return set_error(AGP_EINVAL, "bad arguments");
   pl->use_tc = enable ? 1 : 0;
   return AGP_OK;
+}
+
+agp_status agp_plan_set_boundary(agp_plan pl, double eps_b, int p, void* stream) {
+  if (!pl) return set_error(AGP_EINVAL, "plan is NULL");
+  if (!(eps_b >= 0.0) || !(eps_b <= 0.25) || p < 0 || p > kBndMaxP)
+    return set_error(AGP_EINVAL, "boundary smoothing needs 0 <= eps_b <= 1/4 and 0 <= p <= 8");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool on = eps_b > 0.0 && p > 0;
+  if (on) {
+    // every window's points inside the ball |x| <= 1/4 - eps_b/2, so that all
+    // differences have |x_i - x_j| <= 1/2 - eps_b, where kappa_R = kappa
+    unsigned long long* mx = nullptr;
+    AGP_CUDA(cudaMallocAsync(&mx, sizeof(unsigned long long) * pl->P, st));
+    AGP_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * pl->P, st));
+    for (int w = 0; w < pl->P; ++w) {
+      const Window& win = pl->win[w];
+      const int blocks = (int)std::min<int64_t>(nblk(pl->n, 256), 1216);
+      if (pl->prec == AGP_F32)
+        k_max_norm2<float><<<blocks, 256, 0, st>>>(reinterpret_cast<const float*>(win.xs), pl->n,
+                                                   win.d, mx + w);
+      else
+        k_max_norm2<double><<<blocks, 256, 0, st>>>(reinterpret_cast<const double*>(win.xs),
+                                                    pl->n, win.d, mx + w);
+    }
+    AGP_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> h(pl->P);
+    AGP_CUDA(cudaMemcpyAsync(h.data(), mx, sizeof(unsigned long long) * pl->P,
+                             cudaMemcpyDeviceToHost, st));
+    AGP_CUDA(cudaFreeAsync(mx, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    const double rad = 0.25 - 0.5 * eps_b;
+    for (int w = 0; w < pl->P; ++w) {
+      double r2;
+      std::memcpy(&r2, &h[w], sizeof r2);
+      if (!(r2 <= rad * rad))
+        return set_error(AGP_EDOMAIN, "boundary smoothing needs every window's points in the "
+                                      "ball |x| <= 1/4 - eps_b/2");
+    }
+    if (!pl->bnd_poly) AGP_CUDA(cudaMalloc(&pl->bnd_poly, sizeof(double) * 2 * kBndStride));
+  }
+  pl->bnd_eps = on ? eps_b : 0.0;
+  pl->bnd_p = on ? p : 0;
+  return pl->prec == AGP_F32 ? compute_coeffs<float>(pl, st) : compute_coeffs<double>(pl, st);
 }
 
 agp_status agp_plan_check(agp_plan pl, void* stream) {

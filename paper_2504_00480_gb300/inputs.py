@@ -39,6 +39,19 @@ def minmax_scale(X: np.ndarray, lo: float = LO, hi: float = HI) -> np.ndarray:
     return np.clip(Y, lo, hi)
 
 
+def ball_scale(X: np.ndarray, windows, radius: float) -> np.ndarray:
+    """Scale each window's columns (already centred, e.g. by minmax_scale) by
+    one factor so that the largest Euclidean norm of a window point is
+    ``radius`` (float64)."""
+    Y = np.array(X, dtype=np.float64)
+    for w in windows:
+        cols = list(w)
+        m = np.sqrt((Y[:, cols] ** 2).sum(axis=1)).max()
+        if m > 0:
+            Y[:, cols] *= radius / m
+    return Y
+
+
 def standardize(X: np.ndarray) -> np.ndarray:
     X = np.asarray(X, dtype=np.float64)
     sd = X.std(axis=0, keepdims=True)
