@@ -219,8 +219,9 @@ agp_status agp_plan_landmarks(agp_plan plan, int n_landmarks, int32_t* idx, int 
  * [points x (t3, r)] of window-value matrices, and interpolation's sum over
  * the first two dimensions is the product [points x (t1, t2)] x
  * [(t1, t2) x (t3, r)] with the grid block; both run as tcgen05.mma on TF32
- * operands split into a rounded part and its rounded remainder (three
- * products, about FP32 accuracy), accumulated in FP32.
+ * operands split into a rounded part and its remainder, of which the tensor
+ * cores use the TF32 bits (three products, about FP32 accuracy), accumulated
+ * in FP32.
  * enable: 1 on (the default for FP32 plans), 0 off (FMA path only). */
 agp_status agp_plan_set_tensor_cores(agp_plan plan, int enable);
 

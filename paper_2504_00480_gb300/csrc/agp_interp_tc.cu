@@ -88,7 +88,7 @@ __device__ __forceinline__ void it_store_b(const float* gb, float* __restrict__ 
     const float x = gb[q];
     const float h = tf32_round(x);
     bh[(RGA + q) * CORE] = h;
-    bl[(RGA + q) * CORE] = tf32_round(x - h);
+    bl[(RGA + q) * CORE] = x - h;          // the tensor cores use its TF32 bits
   }
 }
 
@@ -105,7 +105,7 @@ __device__ __forceinline__ void it_form_a(const float* __restrict__ w1, const fl
     const float x = (krow && p < np) ? w1[rg * 8 * WPP] * w2[rg * 8 * WPP] : 0.0f;
     const float h = tf32_round(x);
     ah[rg * CORE] = h;
-    al[rg * CORE] = tf32_round(x - h);
+    al[rg * CORE] = x - h;
   }
 }
 

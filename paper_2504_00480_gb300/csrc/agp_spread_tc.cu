@@ -12,7 +12,8 @@
 // ((2s)^2 = 100 or 64, zero padded), N = (2s + L - 1) x 16 columns,
 // accumulated in tensor memory (TMEM) by tcgen05.mma kind::tf32 over chunks
 // of 16 points (two K = 8 steps). FP32 accuracy from TF32 inputs by the split
-// x = x_hi + x_lo (x_hi = x rounded to TF32, x_lo = the rounded remainder):
+// x = x_hi + x_lo (x_hi = x rounded to TF32, x_lo = the exact remainder, of
+// which the tensor cores use the TF32 bits, ~2^-21 relative to x):
 //     A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
 // whose dropped term A_lo B_lo is ~2^-22 relative; products of TF32 values
 // are exact and the tensor cores accumulate in FP32.
@@ -89,7 +90,7 @@ __device__ __forceinline__ void form_a(const float* __restrict__ pw, bool live, 
     const float x = (live && row < Sh::ROWS) ? pw[t1] * pw[TTP + t2] : 0.0f;
     const float h = tf32_round(x);
     ph[rg * (kTcKC / 4) * 32] = h;
-    pl[rg * (kTcKC / 4) * 32] = tf32_round(x - h);
+    pl[rg * (kTcKC / 4) * 32] = x - h;
     row += 8;
     t2 += 8;
     if (t2 >= TT) {
@@ -102,7 +103,8 @@ __device__ __forceinline__ void form_a(const float* __restrict__ pw, bool live, 
 // B rows n = 8 rg + r8 = (u, r): plane u of the run's block (u = rg / 2,
 // the point's tap t3 = u - delta for its cell offset delta in the run),
 // r = 8 (rg % 2) + r8; thread group G of NG takes its share of the planes
-// u < nu
+// u < nu. (An A row group costs more than a B plane, but moving B planes
+// between the groups to even out their instruction counts was slower.)
 template <int S, int G, int NG>
 __device__ __forceinline__ void form_b(const float* __restrict__ p3, bool live, int delta, int nu,
                                        float v0, float v1, float* __restrict__ ph,
@@ -117,9 +119,9 @@ __device__ __forceinline__ void form_b(const float* __restrict__ p3, bool live, 
     const float x0 = p * v0, x1 = p * v1;
     const float h0 = tf32_round(x0), h1 = tf32_round(x1);
     ph[(2 * u) * (kTcKC / 4) * 32] = h0;
-    pl[(2 * u) * (kTcKC / 4) * 32] = tf32_round(x0 - h0);
+    pl[(2 * u) * (kTcKC / 4) * 32] = x0 - h0;
     ph[(2 * u + 1) * (kTcKC / 4) * 32] = h1;
-    pl[(2 * u + 1) * (kTcKC / 4) * 32] = tf32_round(x1 - h1);
+    pl[(2 * u + 1) * (kTcKC / 4) * 32] = x1 - h1;
   }
 }
 
