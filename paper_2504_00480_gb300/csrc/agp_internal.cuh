@@ -147,6 +147,20 @@ __device__ __forceinline__ double kernel_value(int kernel, double r2, double ell
 __device__ __forceinline__ float dev_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double dev_floor(double x) { return floor(x); }
 
+// One coefficient job of a plan (a1): the kernel (der = 0) or ell-derivative
+// (der = 1) coefficients of one window, computed in the scratch arrays s0/s1
+// and left in b; dmul receives the spectral multipliers (plan precision).
+struct CoefJob {
+  double* s0 = nullptr;
+  double* s1 = nullptr;
+  double* b = nullptr;
+  const double* costab = nullptr;
+  const double* winhat = nullptr;
+  void* dmul = nullptr;
+  int N = 0, d = 0, der = 0;
+  int64_t cells = 0, dmul_elems = 0;
+};
+
 // One window of a plan (host side).
 struct Window {
   int d = 0, N = 0, n_os = 0, W = 0, K = 0, Kh = 0, s = 0;
@@ -205,6 +219,10 @@ struct agp_plan_s {
   double bnd_eps = 0.0;          // outer boundary smoothing of kappa_R: layer width (0: off)
   int bnd_p = 0;                 // ... and its order (derivatives matched at each end)
   double* bnd_poly = nullptr;    // [2][kBndStride] boundary polynomials (kernel, ell-derivative)
+  agp::CoefJob* coef_jobs = nullptr;   // [2 P] coefficient jobs (device), see compute_coeffs
+  double* coef_scratch = nullptr;      // their scratch arrays
+  int n_coef_jobs = 0, coef_dmax = 0;
+  int64_t coef_cells_max = 0, coef_dmul_max = 0;
   std::vector<agp::Window> win;
   void* wins_dev = nullptr;      // WinDev<T>[P]
   int4* items_all = nullptr;     // work items of every window, grouped by d

@@ -310,14 +310,15 @@ __device__ double boundary_eval(const double* __restrict__ c, int p, double sl) 
   return up * acc + c[2 * kBndMaxP] * sp * tail;
 }
 
-// samples[l] = kappa_R(|l / N|) (or its ell-derivative), l in I_N^d row-major;
-// with p > 0 the outer boundary of kappa_R is smoothed by `poly`.
-__global__ void k_kernel_samples(double* __restrict__ out, int N, int d, int kernel, double ell,
-                                 int der, double eps, int p, const double* __restrict__ poly) {
-  int64_t total = 1;
-  for (int t = 0; t < d; ++t) total *= N;
+// samples[l] = kappa_R(|l / N|) (or its ell-derivative), l in I_N^d row-major,
+// for coefficient job blockIdx.y; with p > 0 the outer boundary of kappa_R is
+// smoothed by `poly`.
+__global__ void k_kernel_samples(const CoefJob* __restrict__ jobs, int kernel, double ell,
+                                 double eps, int p, const double* __restrict__ poly) {
+  const CoefJob& jb = jobs[blockIdx.y];
+  const int N = jb.N, d = jb.d, der = jb.der;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= total) return;
+  if (e >= jb.cells) return;
   int64_t rem = e;
   double r2 = 0.0;
   for (int t = d - 1; t >= 0; --t) {
@@ -326,6 +327,7 @@ __global__ void k_kernel_samples(double* __restrict__ out, int N, int d, int ker
     const double x = (double)l / N;
     r2 += x * x;
   }
+  double* out = jb.s0;
   if (p > 0) {
     const double* c = poly + der * kBndStride;
     const double r = sqrt(r2), a = 0.5 - eps;
@@ -362,13 +364,19 @@ __global__ void k_max_norm2(const T* __restrict__ xs, int64_t n, int d,
 // l_t = -N/2 multiplies exp(i pi k_t) = (-1)^k_t), so the transform along each
 // axis is the cosine sum sum_l in[l] costab[k][l], costab = cos(2 pi l k / N) / N
 // (indices shifted by N/2), precomputed once per plan.
-__global__ void k_cos_axis(const double* __restrict__ in, double* __restrict__ out,
-                           const double* __restrict__ costab, int N, int d, int axis) {
-  int64_t total = 1, stride = 1;
-  for (int t = 0; t < d; ++t) total *= N;
+// Job blockIdx.y's axes alternate between its two scratch arrays and end in
+// its b: axis 0 reads s0, odd axes read s1 and even axes s0.
+__global__ void k_cos_axis(const CoefJob* __restrict__ jobs, int axis) {
+  const CoefJob& jb = jobs[blockIdx.y];
+  const int N = jb.N, d = jb.d;
+  if (axis >= d) return;
+  const double* __restrict__ in = (axis & 1) ? jb.s1 : jb.s0;
+  double* __restrict__ out = (axis == d - 1) ? jb.b : ((axis & 1) ? jb.s0 : jb.s1);
+  const double* __restrict__ costab = jb.costab;
+  int64_t stride = 1;
   for (int t = d - 1; t > axis; --t) stride *= N;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= total) return;
+  if (e >= jb.cells) return;
   const int kk = (int)((e / stride) % N);
   const int64_t base = e - (int64_t)kk * stride;
   const double* row = costab + (int64_t)kk * N;
@@ -412,13 +420,15 @@ __global__ void k_window_values(const T* __restrict__ xs, int64_t n, int d, int 
 //   w(k) = (1[k in I_N] + 1[-k in I_N]) / 2,
 // the real-part symmetrisation of eq. (3.3) over the asymmetric I_N.
 template <typename T>
-__global__ void k_build_dmul(const double* __restrict__ b, const double* __restrict__ winhat,
-                             int N, int d, T* __restrict__ dmul) {
+__global__ void k_build_dmul(const CoefJob* __restrict__ jobs) {
+  const CoefJob& jb = jobs[blockIdx.y];
+  const int N = jb.N, d = jb.d;
+  const double* __restrict__ b = jb.b;
+  const double* __restrict__ winhat = jb.winhat;
+  T* __restrict__ dmul = reinterpret_cast<T*>(jb.dmul);
   const int K = N + 1, Kh = N / 2 + 1;
-  int64_t total = Kh;
-  for (int t = 0; t < d - 1; ++t) total *= K;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= total) return;
+  if (e >= jb.dmul_elems) return;
   int k[3];
   int64_t rem = e;
   k[d - 1] = (int)(rem % Kh);
@@ -587,32 +597,56 @@ agp_status validate(const agp_plan_desc* d) {
   return AGP_OK;
 }
 
+// The coefficient jobs of a plan (window s, der) -> 2 s + der, with their
+// scratch arrays; built once, the buffers they point to never move.
+agp_status build_coef_jobs(agp_plan_s* pl) {
+  std::vector<CoefJob> jobs;
+  int64_t scratch = 0;
+  for (const Window& w : pl->win) scratch += 4 * w.cells;
+  AGP_CUDA(cudaMalloc(&pl->coef_scratch, sizeof(double) * scratch));
+  double* sp = pl->coef_scratch;
+  for (Window& w : pl->win)
+    for (int der = 0; der < 2; ++der) {
+      CoefJob jb;
+      jb.s0 = sp;
+      jb.s1 = sp + w.cells;
+      sp += 2 * w.cells;
+      jb.b = der ? w.bder : w.b;
+      jb.costab = w.costab;
+      jb.winhat = reinterpret_cast<const double*>(w.winhat);
+      jb.dmul = der ? w.dmul_der : w.dmul;
+      jb.N = w.N;
+      jb.d = w.d;
+      jb.der = der;
+      jb.cells = w.cells;
+      jb.dmul_elems = w.dmul_elems;
+      jobs.push_back(jb);
+      pl->coef_cells_max = std::max(pl->coef_cells_max, w.cells);
+      pl->coef_dmul_max = std::max(pl->coef_dmul_max, w.dmul_elems);
+      pl->coef_dmax = std::max(pl->coef_dmax, w.d);
+    }
+  AGP_CUDA(cudaMalloc(&pl->coef_jobs, sizeof(CoefJob) * jobs.size()));
+  AGP_CUDA(cudaMemcpy(pl->coef_jobs, jobs.data(), sizeof(CoefJob) * jobs.size(),
+                      cudaMemcpyHostToDevice));
+  pl->n_coef_jobs = (int)jobs.size();
+  return AGP_OK;
+}
+
+// a1 for every window and both coefficient sets: one launch per stage
+// (samples, each DFT axis, multipliers), the jobs along gridDim.y.
 template <typename T>
 agp_status compute_coeffs(agp_plan_s* pl, cudaStream_t st) {
+  if (!pl->coef_jobs) AGP_TRY(build_coef_jobs(pl));
   if (pl->bnd_p > 0)
     k_boundary_poly<<<1, 32, 0, st>>>(pl->bnd_poly, pl->kernel, pl->ell, pl->bnd_eps, pl->bnd_p);
-  for (auto& w : pl->win) {
-    double* tmp = nullptr;
-    AGP_CUDA(cudaMallocAsync(&tmp, sizeof(double) * w.cells * 2, st));
-    double* t0 = tmp;
-    double* t1 = tmp + w.cells;
-    for (int der = 0; der < 2; ++der) {
-      double* dst = der ? w.bder : w.b;
-      k_kernel_samples<<<nblk(w.cells, 256), 256, 0, st>>>(t0, w.N, w.d, pl->kernel, pl->ell, der,
-                                                           pl->bnd_eps, pl->bnd_p, pl->bnd_poly);
-      double* src = t0;
-      for (int axis = 0; axis < w.d; ++axis) {
-        double* o = (axis == w.d - 1) ? dst : (src == t0 ? t1 : t0);
-        k_cos_axis<<<nblk(w.cells, 256), 256, 0, st>>>(src, o, w.costab, w.N, w.d, axis);
-        src = o;
-      }
-      k_build_dmul<T><<<nblk(w.dmul_elems, 256), 256, 0, st>>>(
-          dst, reinterpret_cast<const double*>(w.winhat), w.N, w.d,
-          reinterpret_cast<T*>(der ? w.dmul_der : w.dmul));
-    }
-    AGP_CUDA(cudaGetLastError());
-    AGP_CUDA(cudaFreeAsync(tmp, st));
-  }
+  const dim3 gs(nblk(pl->coef_cells_max, 256), pl->n_coef_jobs);
+  k_kernel_samples<<<gs, 256, 0, st>>>(pl->coef_jobs, pl->kernel, pl->ell, pl->bnd_eps,
+                                       pl->bnd_p, pl->bnd_poly);
+  for (int axis = 0; axis < pl->coef_dmax; ++axis)
+    k_cos_axis<<<gs, 256, 0, st>>>(pl->coef_jobs, axis);
+  const dim3 gm(nblk(pl->coef_dmul_max, 256), pl->n_coef_jobs);
+  k_build_dmul<T><<<gm, 256, 0, st>>>(pl->coef_jobs);
+  AGP_CUDA(cudaGetLastError());
   return AGP_OK;
 }
 
@@ -645,6 +679,8 @@ void free_plan(agp_plan_s* pl) {
   cudaFree(pl->wins_dev);
   cudaFree(pl->err_dev);
   cudaFree(pl->bnd_poly);
+  cudaFree(pl->coef_jobs);
+  cudaFree(pl->coef_scratch);
   delete pl;
 }
 
