@@ -8,8 +8,10 @@
 // matrix applied along one axis:
 //   forward  X[k] = sum_a g[a] exp(-2 pi i k (a + lo) / n_os)
 //   inverse  g[a] = sum_k X[k] exp(+2 pi i k (a + lo) / n_os)
-// The last axis is real <-> Hermitian half (k_d in [0, N/2]). Each thread owns
-// one column of the batched transform and keeps its K outputs in registers;
+// The last axis is real <-> Hermitian half (k_d in [0, N/2]). A thread owns
+// one column of the batched transform and a chunk of its outputs (blockIdx.z:
+// KC frequencies of a forward pass, a range of grid positions of an inverse
+// pass), so that even the small transforms of a d = 2 window fill the GPU;
 // the twiddles are read through the read-only cache (every lane of a warp
 // reads the same twiddle). Cost is O(W K) per column, a few percent of the
 // spreading / interpolation work at the sizes used here.
@@ -17,6 +19,8 @@
 // Every kernel serves a group of windows with the same (d, N, s) -- the
 // windows of one plan, or of every problem of a batch -- in one launch:
 // blockIdx.y selects the window's entry in a device table of buffer pointers.
+#include <algorithm>
+
 #include "agp_internal.cuh"
 
 namespace agp {
@@ -35,36 +39,42 @@ __device__ __forceinline__ P* buf(const FftWin& f, int sel) {
 // Forward along the last axis, real -> half spectrum:
 // grid [M][W][RC] real -> specA [M][KH][RC] complex, KH = N/2 + 1.
 // tw rows are k + N/2 for k in [-N/2, N/2]; rows N/2 .. N are k = 0 .. N/2.
+// Outputs per thread of a forward pass with K outputs per column.
+__host__ __device__ constexpr int fwd_chunk(int K) { return K <= 33 ? (K + 2) / 3 : (K + 4) / 5; }
+
 template <typename T, int KH>
 __global__ void __launch_bounds__(128)
 k_fwd_last(const FftWin* __restrict__ tab, int W, int RC, int64_t M) {
   using T2 = typename C2<T>::t;
+  constexpr int KC = fwd_chunk(KH);
   const FftWin f = tab[blockIdx.y];
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M * RC) return;
   const int64_t m = e / RC;
   const int r = (int)(e - m * RC);
+  const int k0 = blockIdx.z * KC;                  // this thread's frequencies k0 .. k0 + KC - 1
   const T2* twh = reinterpret_cast<const T2*>(f.tw) + (int64_t)(KH - 1) * W;   // row of k = 0
-  T re[KH], im[KH];
+  T re[KC], im[KC];
 #pragma unroll
-  for (int k = 0; k < KH; ++k) re[k] = im[k] = T(0);
+  for (int k = 0; k < KC; ++k) re[k] = im[k] = T(0);
   const T* src = buf<const T>(f, 0) + m * W * RC + r;
   for (int a = 0; a < W; ++a) {
     const T x = src[(int64_t)a * RC];
 #pragma unroll
-    for (int k = 0; k < KH; ++k) {
-      const T2 t = __ldg(twh + (int64_t)k * W + a);
+    for (int k = 0; k < KC; ++k) {
+      const T2 t = __ldg(twh + (int64_t)min(k0 + k, KH - 1) * W + a);
       re[k] = fma(x, t.x, re[k]);
       im[k] = fma(x, t.y, im[k]);
     }
   }
   T2* dst = buf<T2>(f, 1) + m * KH * RC + r;
 #pragma unroll
-  for (int k = 0; k < KH; ++k) {
+  for (int k = 0; k < KC; ++k) {
+    if (k0 + k >= KH) break;
     T2 v;
     v.x = re[k];
     v.y = im[k];
-    dst[(int64_t)k * RC] = v;
+    dst[(int64_t)(k0 + k) * RC] = v;
   }
 }
 
@@ -76,18 +86,20 @@ k_fwd_mid(const FftWin* __restrict__ tab, int src_sel, int dst_sel, int W, int64
   const FftWin f = tab[blockIdx.y];
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M * I) return;
+  constexpr int KC = fwd_chunk(K);
   const int64_t m = e / I;
   const int64_t i = e - m * I;
+  const int k0 = blockIdx.z * KC;
   const T2* tw = reinterpret_cast<const T2*>(f.tw);
-  T re[K], im[K];
+  T re[KC], im[KC];
 #pragma unroll
-  for (int k = 0; k < K; ++k) re[k] = im[k] = T(0);
+  for (int k = 0; k < KC; ++k) re[k] = im[k] = T(0);
   const T2* src = buf<const T2>(f, src_sel) + m * W * I + i;
   for (int a = 0; a < W; ++a) {
     const T2 x = src[(int64_t)a * I];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const T2 t = __ldg(tw + (int64_t)k * W + a);
+    for (int k = 0; k < KC; ++k) {
+      const T2 t = __ldg(tw + (int64_t)min(k0 + k, K - 1) * W + a);
       re[k] = fma(x.x, t.x, re[k]);
       re[k] = fma(-x.y, t.y, re[k]);
       im[k] = fma(x.x, t.y, im[k]);
@@ -96,11 +108,12 @@ k_fwd_mid(const FftWin* __restrict__ tab, int src_sel, int dst_sel, int W, int64
   }
   T2* dst = buf<T2>(f, dst_sel) + m * K * I + i;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < KC; ++k) {
+    if (k0 + k >= K) break;
     T2 v;
     v.x = re[k];
     v.y = im[k];
-    dst[(int64_t)k * I] = v;
+    dst[(int64_t)(k0 + k) * I] = v;
   }
 }
 
@@ -124,7 +137,8 @@ k_inv_mid(const FftWin* __restrict__ tab, int src_sel, int dst_sel, int W, int64
     xi[k] = x.y;
   }
   T2* dst = buf<T2>(f, dst_sel) + m * W * I + i;
-  for (int a = 0; a < W; ++a) {
+  const int aw = (W + gridDim.z - 1) / gridDim.z, a1 = min(W, (int)(blockIdx.z + 1) * aw);
+  for (int a = blockIdx.z * aw; a < a1; ++a) {
     T re = T(0), im = T(0);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -163,7 +177,8 @@ k_inv_last(const FftWin* __restrict__ tab, int src_sel, int W, int RC, int64_t M
     xi[k] = s * x.y;
   }
   T* dst = buf<T>(f, 0) + m * W * RC + r;
-  for (int a = 0; a < W; ++a) {
+  const int aw = (W + gridDim.z - 1) / gridDim.z, a1 = min(W, (int)(blockIdx.z + 1) * aw);
+  for (int a = blockIdx.z * aw; a < a1; ++a) {
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < KH; ++k) {
@@ -207,18 +222,28 @@ inline int64_t powi(int64_t b, int e) {
   return r;
 }
 
+// Grid-position chunks of an inverse pass with `columns` columns in all: about
+// 128k threads in flight, chunks of at least 8 positions.
+unsigned inv_chunks(int64_t columns, int W) {
+  int64_t z = (131072 + columns - 1) / columns;
+  z = std::min<int64_t>(z, std::max(1, W / 8));
+  return (unsigned)std::max<int64_t>(z, 1);
+}
+
 template <typename T, int N>
 cudaError_t forward_n(const FftGroup& g, int RC, cudaStream_t st) {
   constexpr int K = N + 1, KH = N / 2 + 1;
   const int W = g.W;
   const int64_t M = powi(W, g.d - 1);
-  k_fwd_last<T, KH><<<dim3(blocks_for(M * RC, 128), g.count), 128, 0, st>>>(g.tab, W, RC, M);
+  k_fwd_last<T, KH><<<dim3(blocks_for(M * RC, 128), g.count, (KH + fwd_chunk(KH) - 1) / fwd_chunk(KH)),
+                      128, 0, st>>>(g.tab, W, RC, M);
   // remaining axes from the second-to-last down to the first (ping-pong A/B)
   int src = 1, dst = 2;
   int64_t I = (int64_t)KH * RC;
   for (int axis = g.d - 2; axis >= 0; --axis) {
     const int64_t Mo = powi(W, axis);
-    k_fwd_mid<T, K><<<dim3(blocks_for(Mo * I, 128), g.count), 128, 0, st>>>(g.tab, src, dst, W, Mo, I);
+    k_fwd_mid<T, K><<<dim3(blocks_for(Mo * I, 128), g.count, (K + fwd_chunk(K) - 1) / fwd_chunk(K)),
+                      128, 0, st>>>(g.tab, src, dst, W, Mo, I);
     I *= K;
     const int t = src;
     src = dst;
@@ -237,13 +262,15 @@ cudaError_t inverse_n(const FftGroup& g, int RC, cudaStream_t st) {
   for (int axis = 0; axis <= g.d - 2; ++axis) {
     I /= K;
     const int64_t Mo = powi(W, axis);
-    k_inv_mid<T, K><<<dim3(blocks_for(Mo * I, 128), g.count), 128, 0, st>>>(g.tab, src, dst, W, Mo, I);
+    k_inv_mid<T, K><<<dim3(blocks_for(Mo * I, 128), g.count, inv_chunks(Mo * I * g.count, W)), 128,
+                      0, st>>>(g.tab, src, dst, W, Mo, I);
     const int t = src;
     src = dst;
     dst = t;
   }
   const int64_t M = powi(W, g.d - 1);
-  k_inv_last<T, KH><<<dim3(blocks_for(M * RC, 128), g.count), 128, 0, st>>>(g.tab, src, W, RC, M);
+  k_inv_last<T, KH><<<dim3(blocks_for(M * RC, 128), g.count, inv_chunks(M * RC * g.count, W)), 128,
+                       0, st>>>(g.tab, src, W, RC, M);
   return cudaGetLastError();
 }
 
