@@ -61,16 +61,24 @@ struct TcSpreadShape {
   static constexpr int T3M = TT + kRunCells - 1;              // t3 planes of a run's block
   static constexpr int NN = T3M * kTcRH;                       // largest MMA N
   static constexpr int WPP = wpp_of(3, S);
+  // staging row strides (floats) of a point's window values and V row, chosen
+  // so that the loads of the operand formation (4 points x 8 rows per warp
+  // instruction) spread over the shared-memory banks: 40 (s = 4) is free of
+  // conflicts, 56 (s = 5) takes 33 wavefronts where 26 loads need 26 (44: 38);
+  // V rows at stride 24 are conflict-free
+  static constexpr int WPS = S == 4 ? 40 : (S == 5 ? 56 : WPP);
+  static constexpr int VS = 24;
   static constexpr int A_BYTES = MR * kTcKC * 4;
   static constexpr int B_BYTES = NN * kTcKC * 4;
   static constexpr int OPND = 2 * A_BYTES + 2 * B_BYTES;     // hi and lo of A and B
-  static constexpr int STG_W = kTcKC * WPP;                   // floats
-  static constexpr int STG = (STG_W + kTcKC * kTcRH) * 4;     // bytes
+  static constexpr int STG_W = kTcKC * WPS;                   // floats
+  static constexpr int STG = (STG_W + kTcKC * VS) * 4;        // bytes
   static constexpr int SMEM = 2 * OPND + kTcStages * STG;
   static constexpr int TMEM_COLS = NN <= 128 ? 128 : 256;
   static_assert(ROWS <= MR, "(2s)^2 rows must fit one M = 128 tile");
   static_assert(NN % 16 == 0 && NN <= 256, "N must be a multiple of 16, at most 256");
-  static_assert((WPP * 4) % 16 == 0, "window values must be 16-byte rows");
+  static_assert((WPP * 4) % 16 == 0 && WPS % 4 == 0 && WPS >= WPP && VS % 4 == 0 && VS >= kTcRH,
+                "window values and V rows must be 16-byte rows");
 };
 
 // Operand formation of one chunk for thread group G (of NG) of a CTA, in the
@@ -131,7 +139,8 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
             const int4* __restrict__ items, const float* __restrict__ V, int64_t ldv, int R,
             int rc, int* __restrict__ err) {
   using Sh = TcSpreadShape<S>;
-  constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, KC = kTcKC, RH = kTcRH;
+  constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, WPS = Sh::WPS, VS = Sh::VS;
+  constexpr int KC = kTcKC, RH = kTcRH;
   static_assert(kTcThreads % 128 == 0 && kTcThreads <= 512, "groups of 128 threads");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -199,17 +208,20 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     const int q0 = c * KC;
     const int ns = min(KC, m - q0);
     const float* wsrc = w.wts + (int64_t)(j0 + q0) * WPP;
-    for (int e = tid; e < ns * (WPP / 4); e += kTcThreads) cp_async16(sw + e * 4, wsrc + e * 4, 16);
+    for (int e = tid; e < ns * (WPP / 4); e += kTcThreads) {
+      const int q = e / (WPP / 4), c = e - q * (WPP / 4);     // point q, 16-byte chunk c
+      cp_async16(sw + q * WPS + c * 4, wsrc + e * 4, 16);
+    }
     if (vec_ok) {
       if (tid < 4 * KC && vq < ns) {
         const int valid = max(0, min(4, R - (r0 + vk)));
-        cp_async16(sv + vq * RH + vk, V + pi * ldv + (valid > 0 ? r0 + vk : 0), valid * 4);
+        cp_async16(sv + vq * VS + vk, V + pi * ldv + (valid > 0 ? r0 + vk : 0), valid * 4);
       }
     } else {
       for (int e = tid; e < ns * RH; e += kTcThreads) {
         const int q = e / RH, r = e % RH;
         const int64_t i = __ldg(w.perm + j0 + q0 + q);
-        sv[e] = (r0 + r < R) ? V[i * ldv + r0 + r] : 0.0f;
+        sv[q * VS + r] = (r0 + r < R) ? V[i * ldv + r0 + r] : 0.0f;
       }
     }
     cp_async_commit();
@@ -242,9 +254,9 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     float* bhi = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES);
     float* blo = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES + Sh::B_BYTES);
     {
-      const float* pw = sw + kk * WPP;
-      const float v0 = live ? sv[kk * RH + r8] : 0.0f;
-      const float v1 = live ? sv[kk * RH + 8 + r8] : 0.0f;
+      const float* pw = sw + kk * WPS;
+      const float v0 = live ? sv[kk * VS + r8] : 0.0f;
+      const float v1 = live ? sv[kk * VS + 8 + r8] : 0.0f;
       const int jj = j0 + c * KC + kk;             // this point's sorted index
       int delta = 0;
 #pragma unroll
@@ -291,10 +303,13 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     // Each 32 x 16 tile (rows x right-hand sides) goes through shared memory
     // (the operand buffers are free now) so that four lanes cover one row's
     // 16 contiguous values: every vector atomic instruction of a warp then
-    // touches 8 rows x 64 bytes instead of 32 rows x 16 bytes.
+    // touches 8 rows x 64 bytes instead of 32 rows x 16 bytes. The tile's
+    // rows are 16 floats; 16-byte chunk c of row l sits at chunk position
+    // c ^ ((l >> 1) & 3), so that both the row-wise writes and the
+    // four-lanes-per-row reads of 16-byte vectors are free of bank conflicts.
     constexpr int NQ = kTcThreads / 128;              // warps per lane quarter
     const int quarter = warp % 4, part = warp / 4;
-    float* tile = reinterpret_cast<float*>(smem_raw) + warp * (32 * 17);
+    float* tile = reinterpret_cast<float*>(smem_raw) + warp * (32 * 16);
     int cc[3];
     decode_cell<3>(it.y, w.N, cc);
     const int ta = part * nu / NQ, tb = (part + 1) * nu / NQ;
@@ -312,7 +327,10 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-      for (int q = 0; q < 16; ++q) tile[lane * 17 + q] = __uint_as_float(v[q]);
+      for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<float4*>(tile + lane * 16 + ((c ^ ((lane >> 1) & 3)) << 2)) =
+            make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
+                        __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
       __syncwarp();
 #pragma unroll
       for (int q8 = 0; q8 < 4; ++q8) {
@@ -321,9 +339,9 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
         if (row < Sh::ROWS && r0 + c4 < R) {
           const int t1 = row / TT, t2 = row - (row / TT) * TT;
           const int64_t base = ((int64_t)(cc[0] + t1) * w.W + (cc[1] + t2)) * w.W + cc[2] + t3;
-          const float* src = tile + rl * 17 + c4;
-          atomicAdd(reinterpret_cast<float4*>(w.grid + base * rc + r0 + c4),
-                    make_float4(src[0], src[1], src[2], src[3]));
+          const float4 val = *reinterpret_cast<const float4*>(
+              tile + rl * 16 + (((lane & 3) ^ ((rl >> 1) & 3)) << 2));
+          atomicAdd(reinterpret_cast<float4*>(w.grid + base * rc + r0 + c4), val);
         }
       }
       __syncwarp();
