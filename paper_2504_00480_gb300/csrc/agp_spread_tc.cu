@@ -44,7 +44,7 @@ namespace {
 #endif
 constexpr int kTcThreads = AGP_TC_THREADS;
 #ifndef AGP_TC_STAGES
-#define AGP_TC_STAGES 3             // staging buffers of k_spread_tc (prefetch distance + 1)
+#define AGP_TC_STAGES 2             // staging buffers of k_spread_tc (prefetch distance + 1)
 #endif
 constexpr int kTcStages = AGP_TC_STAGES;
 constexpr int kTcKC = 16;       // points per chunk
