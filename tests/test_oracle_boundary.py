@@ -162,3 +162,18 @@ def test_derivative_consistency_with_smoothing(kind):
     fd = (fp - fm) / (2 * h)
     an = O.truncated_deriv_matvec(X, [[0, 1]], kind, ell, 1.0, 0.0, V, N, "ell", boundary=b)
     np.testing.assert_allclose(an, fd, rtol=0, atol=1e-6 * np.abs(an).max())
+
+
+def test_nfft_fastsum_with_smoothing_matches_truncated_sum():
+    """The method on the CPU (adjoint NFFT, multiply, NFFT; Appendix A) with
+    the smoothed coefficients reproduces the smoothed truncated sum to the
+    Kaiser-Bessel window error (s = 5, sigma = 2)."""
+    d, N, eps_b, p = 2, 16, 0.125, 4
+    X = _ball_points(400, d, 0.25 - eps_b / 2, seed=6)
+    V = np.random.default_rng(7).standard_normal((len(X), 2))
+    b = (eps_b, p)
+    fast = O.nfft_fastsum_matvec(X, [[0, 1]], "gauss", 0.2, 1.0, 0.1, V, N, 5, boundary=b)
+    trunc = O.truncated_matvec(X, [[0, 1]], "gauss", 0.2, 1.0, 0.1, V, N, boundary=b)
+    assert np.linalg.norm(fast - trunc) / np.linalg.norm(trunc) < 1e-8
+    plain = O.truncated_matvec(X, [[0, 1]], "gauss", 0.2, 1.0, 0.1, V, N)
+    assert np.linalg.norm(plain - trunc) / np.linalg.norm(trunc) > 1e-6   # smoothing changed it
