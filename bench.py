@@ -46,7 +46,6 @@ METRIC = ("additive-kernel MVMs/s (n=1M, 32 RHS) vs plain FP64 path; HBM GB/s")
 UNIT = "MVM/s"
 N_POINTS = 1_000_000
 R = 32
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
@@ -276,31 +275,35 @@ def run_gpu(args):
     dom = max(("spread", "interp"), key=lambda s: prof[s]["ms_by_dim"][3])
     launch_ms = prof[dom]["ms_by_dim"][3] / max(1, prof[dom]["timed_by_dim"][3])
     taps3 = sum((2 * w.cutoff) ** len(win) for win in w.windows if len(win) == 3)
+    # the method's work of one launch: one FMA (2 flop) per tap, point and RHS
     flops_launch = 2.0 * w.n * R * taps3
     useful_tflops = flops_launch / (launch_ms / 1e3) / 1e12
     clocks = clk.summary()
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12   # FP32 FMA at max SM clock
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12   # FP32 FMA at max SM clock
     if tc:
-        # tensor-core kernels: the split-TF32 scheme performs three TF32
-        # products per FP32-accurate product, so the algorithmic tensor work
-        # of a launch is 3 x the useful flops (the M-padding of the (2s)^2 =
-        # 100 grid rows to 128 is waste and not counted); the TF32 dense peak
-        # is the measured BF16 burst peak x the nominal TF32 / BF16 ratio
-        # (1.1 / 2.25 PFLOP/s)
-        bound, flops_alg = "tensor", 3.0 * flops_launch
-        achieved = flops_alg / (launch_ms / 1e3) / 1e12
+        # tensor-core kernels: `achieved` counts only the method's flops; the
+        # split-TF32 scheme issues three TF32 products per FP32-accurate
+        # product (and pads M and N), which is reported apart as `issued`.
+        # Peak: TF32 dense = the measured BF16 burst x the nominal TF32/BF16
+        # ratio (1.1 / 2.25 PFLOP/s)
+        bound = "tensor"
         bf16 = measured_bf16_peak()
         peak = None if bf16 is None else bf16 * (1.1 / 2.25)
         peak_source = ("MEASURED_PEAKS.json bf16_tflops (burst) x 1.1/2.25 (nominal TF32/BF16 "
                        "dense ratio)")
         kname = f"k_spread_tc<{w.cutoff}>" if dom == "spread" else f"k_interp_tc<{w.cutoff}>"
+        issued = {"products_per_flop": 3, "tflops": 3.0 * useful_tflops,
+                  "frac_of_peak": None if peak is None else 3.0 * useful_tflops / peak}
     else:
-        bound, flops_alg = "alu", flops_launch
-        achieved = useful_tflops
+        bound = "alu"
         peak = fp32_peak
-        peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal maximum clock)"
+        peak_source = (f"{sm_count} SMs (device query) x 128 FP32 lanes x 2 flop x 2070 MHz "
+                       "(nominal maximum clock)")
         kname = (f"k_spread<float, 3, {w.cutoff}, 32>" if dom == "spread"
                  else f"k_interp2<3, {w.cutoff}, 32>")
+        issued = None
+    achieved = useful_tflops
     traffic = measured_traffic(kname, w.n, R)
     # HBM view of the same launch: algorithmic bytes = per point and d=3
     # window its 3 x 2s window values, its permutation index and its R-value
@@ -315,6 +318,7 @@ def run_gpu(args):
            "algorithmic_gbs": alg_bytes / (launch_ms / 1e3) / 1e9,
            "measured_gbs": None if traffic is None else traffic / (launch_ms / 1e3) / 1e9}
     hbm["algorithmic_frac"] = None if hbm_peak is None else hbm["algorithmic_gbs"] / hbm_peak
+    hbm["traffic_over_algorithmic"] = None if traffic is None else traffic / alg_bytes
 
     # end-to-end through the C ABI with host buffers: every step copies its
     # right-hand sides from pinned host memory and its result back. Steps are
@@ -360,10 +364,9 @@ def run_gpu(args):
                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": None if peak is None else achieved / peak,
                              "traffic": traffic, "launch_ms": launch_ms,
-                             "flop_per_launch": flops_alg, "peak_source": peak_source,
-                             "useful": {"flop_per_launch": flops_launch,
-                                        "tflops": useful_tflops,
-                                        "frac_of_fp32_fma_peak": useful_tflops / fp32_peak}},
+                             "flop_per_launch": flops_launch, "peak_source": peak_source,
+                             "sm_count": sm_count, "issued": issued,
+                             "frac_of_fp32_fma_peak": useful_tflops / fp32_peak},
                 "hbm": hbm,
                 "stages_ms_per_step": {s: prof[s]["ms"] / args.steps for s in prof},
                 "stage_launches_per_step": {s: prof[s]["launches"] / args.steps for s in prof},

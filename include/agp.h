@@ -130,6 +130,39 @@ agp_status agp_matvec(agp_plan plan, const void* V, int64_t ldv, void* Out, int6
 agp_status agp_deriv_matvec(agp_plan plan, agp_param which, const void* V, int64_t ldv,
                             void* Out, int64_t ldo, int R, void* stream);
 
+/* ---- Spectra and the spectral quadratic form (Sec. 3.2) -----------------------
+ * For the gradient of a scalar L = sum_r G_r^T K_hat V_r with respect to the
+ * hyperparameters, eq. (3.4) moves the ell-derivative onto the Fourier
+ * coefficients, so G^T (dK/dell) V needs only the adjoint sums of G and V:
+ *   G^T K_s V      = sum_k D_k Re(conj(g_k) v_k),
+ *   G^T K_s^der V  = sum_k D^der_k Re(conj(g_k) v_k),
+ * where g_k, v_k are the forward DFTs of the spread grids of G and V and D,
+ * D^der the spectral multipliers (b_k over the squared window transform,
+ * Appendix A) of the kernel and of its ell-derivative -- exactly the
+ * operator agp_matvec applies, since interpolation is the transpose of
+ * spreading. No interpolation and no second spread are needed.
+ *
+ * agp_spectra_size: number of complex elements (plan precision) of the
+ * spectra of R columns (all windows). */
+agp_status agp_spectra_size(agp_plan plan, int R, int64_t* elems);
+
+/* Out = K_hat V as agp_matvec, and the forward spectra of V (all windows,
+ * R columns) written to spec: device, agp_spectra_size(R) complex elements
+ * of the plan precision, an internal layout that only agp_spectral_form
+ * reads. With Out = NULL only the spectra are computed (spreading and the
+ * forward DFT). Asynchronous on `stream`. */
+agp_status agp_matvec_spectra(agp_plan plan, const void* V, int64_t ldv, void* Out, int64_t ldo,
+                              int R, int add_noise, void* spec, void* stream);
+
+/* out[r] = G_r^T Op V_r from the spectra A (of G) and B (of V) of
+ * agp_matvec_spectra, for Op = sigma_f^2 sum_s K_s (which = -1), the
+ * ell-derivative sigma_f^2 sum_s K_s^der (which = AGP_D_ELL, Sec. 3.2 eq.
+ * (3.4)) or 2 sigma_f sum_s K_s (which = AGP_D_SIGMA_F), with the plan's
+ * current coefficients. out: device double[R], overwritten (FP64
+ * accumulation). Asynchronous on `stream`. */
+agp_status agp_spectral_form(agp_plan plan, int which, const void* A, const void* B, int R,
+                             double* out, void* stream);
+
 /* Adjoint NFFT of one window (Appendix A, the inner sum of eq. (3.3)):
  * chat[r][k] ~= sum_j V[j][r] exp(-2 pi i k . x_j^{W_s}), k in I_N^d, stored
  * row-major over (k_1 + N/2, ..., k_d + N/2), as interleaved (re, im) pairs.
@@ -177,10 +210,16 @@ agp_status agp_plan_query(agp_plan plan, int64_t* n, int* P, int window, int* d,
                           int* N, int64_t* n_items);
 
 /* Batched conjugate gradients for K_hat X = B (Sec. 1: CG with zero initial
- * guess, one independent recursion per column; vectors in the plan precision,
- * every scalar -- column dot products, alpha, beta, residual norms -- in FP64
- * on the device). Column r stops when its recursive relative residual
- * |r_k|_2 / |b|_2 <= rtol or after maxit iterations.
+ * guess, one independent recursion per column; the iterates x, r, p in FP64,
+ * the matvec in the plan precision, every scalar -- column dot products,
+ * alpha, beta, residual norms -- in FP64 on the device). Residual
+ * replacement: every 5 iterations, a column whose recursive residual has
+ * fallen 10x since its last recomputation, or has reached rtol, gets
+ * r = b - K_hat x recomputed (x split into its plan-precision rounding and
+ * the remainder, two matvecs), so that the recursion cannot drift from the
+ * operator's true residual. Column r stops when its relative residual
+ * |b - K_hat x|_2 / |b|_2, so recomputed, is <= rtol, or after maxit
+ * iterations (relres then holds the last recursive value).
  * B: device [n][ldb]; Xsol: device [n][ldx], overwritten with the iterates;
  * iters, relres: optional host arrays [R] (NULL to skip).
  * n_landmarks: 0 for plain CG, or 1..480 for CG preconditioned with the
@@ -203,8 +242,9 @@ agp_status agp_pcg_solve(agp_plan plan, const void* B, int64_t ldb, void* Xsol, 
  * (1..480; Sec. 2.3): ceil(n_landmarks / P) indices per feature window by
  * farthest point sampling on that window's coordinates (in the plan
  * precision; first landmark point 0; each next one maximises the squared
- * distance to those already chosen, compared after rounding to float32,
- * ties to the lowest index), merged into increasing order without repeats.
+ * Euclidean distance to those already chosen, evaluated and compared in
+ * FP64, ties to the lowest index), merged into increasing order without
+ * repeats.
  * idx: host int32 array with room for cap entries; count: host int, set to
  * the size of the set (at most P * ceil(n_landmarks / P)). Returns AGP_EINVAL
  * if cap is smaller (count is still set). Synchronises `stream`. */
@@ -247,8 +287,22 @@ agp_status agp_plan_set_boundary(agp_plan plan, double eps_b, int p, void* strea
 
 /* AGP_TIMEOUT if a bounded wait inside a tensor-core kernel expired since
  * the last check (the flag is then cleared), else AGP_OK. Synchronises
- * `stream`. */
+ * `stream`. The entry points that synchronise anyway (agp_pcg_solve,
+ * agp_pcg_solve_afn, agp_nlml_grad, agp_nlml_grad_pc, agp_nlml_grad_afn,
+ * agp_dot_columns) make this check themselves and return AGP_TIMEOUT in
+ * place of their result status; after asynchronous calls (agp_matvec,
+ * agp_deriv_matvec, agp_batch_matvec) call it before trusting the output.
+ * A batch reports through the error word of its first plan. */
 agp_status agp_plan_check(agp_plan plan, void* stream);
+
+/* Number of polls after which a bounded mbarrier wait inside the plan's
+ * tensor-core kernels gives up (0: the default, 2^26). On expiry the CTA
+ * agrees on the failure, stops issuing tensor-core work, drains what it
+ * issued (with the default bound), records AGP_TIMEOUT for agp_plan_check
+ * and leaves its part of the output unwritten, so the result is invalid but
+ * the device stays usable. A small limit is only useful to exercise that
+ * path. (Not from the paper: a property of the GPU kernels.) */
+agp_status agp_plan_set_wait_limit(agp_plan plan, int64_t polls);
 
 /* Negative log marginal likelihood and its gradient with respect to
  * (ell, sigma_f, sigma_eps), estimated as in Sec. 1 eqs. (1.4) and (1.5) with
@@ -302,8 +356,8 @@ agp_status agp_nlml_grad_pc(agp_plan plan, const void* Y, const void* Wn, int64_
  * with the exact kernel in FP64. G is lower triangular: row t (the t-th point
  * of F) holds t and its min(fill - 1, t) nearest earlier points of F, by the
  * squared Euclidean distance over all window features (in window order)
- * computed in float32 with one rounding per subtraction, product and sum,
- * ties to the lower index; on that pattern J_t, G[t, J_t] = g / sqrt(g_t)
+ * computed in FP64, ties to the lower index; on that pattern J_t,
+ * G[t, J_t] = g / sqrt(g_t)
  * with S[J_t, J_t] g = e_t. M's landmark rows equal those of K_hat; with a
  * full pattern M = K_hat; with fill = 1 G is the inverse square root of S's
  * diagonal. log det M = log det K_LL - 2 sum_t log G_tt.
@@ -367,6 +421,9 @@ agp_status agp_nlml_grad_afn(agp_plan plan, agp_afn afn, const void* Y, const vo
  * cutoff; the batch refers to them, so they must outlive it. */
 typedef struct agp_batch_s* agp_batch;
 
+/* All plans must share precision, cutoff and the tensor-core setting
+ * (agp_plan_set_tensor_cores); AGP_EINVAL otherwise. The batch's tensor-core
+ * kernels use the wait limit and the error word of plans[0]. */
 agp_status agp_batch_create(agp_batch* out, const agp_plan* plans, int nprob, void* stream);
 agp_status agp_batch_destroy(agp_batch batch);
 
@@ -389,7 +446,8 @@ agp_status agp_batch_matvec(agp_batch batch, int which, void* stream);
 /* Column dot products out[r] = sum_i A[i][r] * B[i][r], r < R, accumulated in
  * FP64 (two-pass, deterministic order) for blocks of the plan precision.
  * A: device [n][lda], B: device [n][ldb], n = the plan's point count;
- * out: host double[R]. Synchronises `stream`. */
+ * out: host double[R]. Synchronises `stream`; returns AGP_TIMEOUT if a
+ * tensor-core wait of the plan expired before (see agp_plan_check). */
 agp_status agp_dot_columns(agp_plan plan, const void* A, int64_t lda, const void* B, int64_t ldb,
                            int R, double* out, void* stream);
 
@@ -405,7 +463,10 @@ agp_status agp_dot_columns(agp_plan plan, const void* A, int64_t lda, const void
  *    that loads the library until the process exits. Nothing in it needs to
  *    start at zero: each call writes every partial sum it reads.
  *  - The first call on a device looks the array up for that device (with it
- *    current); make that first call before any stream capture.
+ *    current) and caches the address per device index; make that first call
+ *    before any stream capture. The cached address is not valid after the
+ *    device is reset (cudaDeviceReset) within the same process: do not call
+ *    this entry point after such a reset.
  *  - Every call shares the array: calls whose work overlaps on the GPU (two
  *    streams, or two threads) race. Serialise them.
  *  - prec: element type of A and B. A: device [n][lda], B: device [n][ldb];

@@ -65,15 +65,16 @@ __all__ = [
     "dense_matvec", "dense_deriv_matvec", "dense_matrix",
     "kernel_taylor", "boundary_polynomial", "kernel_regularised",
     "index_set", "fourier_coeffs", "ndft_adjoint", "ndft",
-    "truncated_matvec", "truncated_deriv_matvec",
+    "truncated_matvec", "truncated_deriv_matvec", "truncated_operators", "truncated_forms",
     "bins", "kb_shape", "kb_window", "kb_window_hat",
     "nfft_adjoint", "nfft", "nfft_fastsum_matvec",
-    "cg", "pcg", "farthest_point_sampling", "additive_landmarks", "nystrom_preconditioner",
+    "cg", "pcg", "farthest_point_sampling", "farthest_point_gaps", "additive_landmarks",
+    "nystrom_preconditioner",
     "lanczos_tridiag_from_cg", "slq_quadratic",
     "nlml_exact", "nlml_estimate",
     "landmark_jitter", "nystrom_blocks", "nystrom_matrix", "nystrom_logdet", "nystrom_probes", "pcg_lanczos",
     "nystrom_dM_quadratic", "nystrom_trace_Minv_dM", "nlml_estimate_preconditioned",
-    "afn_split", "fsai_pattern", "afn_factors", "afn_matrix", "afn_apply_inverse",
+    "afn_split", "fsai_pattern", "fsai_pattern_gaps", "afn_factors", "afn_matrix", "afn_apply_inverse",
     "afn_logdet", "afn_logdet_grad", "afn_dG", "afn_dM", "afn_probes", "nlml_estimate_afn",
 ]
 
@@ -447,6 +448,65 @@ def truncated_deriv_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, whic
     raise ValueError(which)
 
 
+def truncated_operators(X, windows, kind, ell, sigma_f, sigma_eps, V, N, rows=None):
+    """K_hat V and the three derivative operators applied to V, all from the
+    truncated sum of Sec. 3.1 eq. (3.3): per window the inner sums
+    c_k = sum_j v_j e^{-2 pi i k.x_j} are formed once and weighted by b_k of
+    the kernel and of its ell-derivative (Sec. 3.2 eq. (3.4)); then
+    K_hat V = sigma_f^2 sum_s h_s + sigma_eps^2 V, dK/dell V = sigma_f^2
+    sum_s h_s^der, dK/dsigma_f V = 2 sigma_f sum_s h_s, dK/dsigma_eps V =
+    2 sigma_eps V (Sec. 2.1). Returns a dict with keys "K", "ell", "sigma_f",
+    "sigma_eps", each (len(rows) or n, R)."""
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    Ns = [N] * len(windows) if np.isscalar(N) else list(N)
+    h = 0.0
+    hd = 0.0
+    for w, Nw in zip(windows, Ns):
+        xw = window_points(X, w)
+        d = xw.shape[1]
+        c = ndft_adjoint(xw, V, Nw)
+        xo = xw if rows is None else xw[np.asarray(rows)]
+        b = fourier_coeffs(kind, ell, Nw, d, False)
+        bd = fourier_coeffs(kind, ell, Nw, d, True)
+        h = h + np.real(ndft(xo, b[..., None] * c, Nw))
+        hd = hd + np.real(ndft(xo, bd[..., None] * c, Nw))
+    vr = V if rows is None else V[np.asarray(rows)]
+    return {"K": sigma_f ** 2 * h + sigma_eps ** 2 * vr, "ell": sigma_f ** 2 * hd,
+            "sigma_f": 2.0 * sigma_f * h, "sigma_eps": 2.0 * sigma_eps * vr}
+
+
+def truncated_forms(X, windows, kind, ell, sigma_f, sigma_eps, G, V, N):
+    """sum_r G_r^T Op V_r for Op = K_hat and its three derivative operators,
+    with the truncated sum of Sec. 3.1 eq. (3.3) summed against G:
+    G^T K_s V = sum_i G_i Re sum_k b_k c_k(V) e^{2 pi i k.x_i}
+              = Re sum_k b_k c_k(V) conj(c_k(G))   (G real),
+    c_k(.) the inner sums; b_k of the ell-derivative kernel for "ell"
+    (Sec. 3.2 eq. (3.4)). Returns a dict with keys "K", "ell", "sigma_f",
+    "sigma_eps" (floats)."""
+    G = np.asarray(G, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    if G.ndim == 1:
+        G = G[:, None]
+    if V.ndim == 1:
+        V = V[:, None]
+    Ns = [N] * len(windows) if np.isscalar(N) else list(N)
+    q = 0.0
+    qd = 0.0
+    for w, Nw in zip(windows, Ns):
+        xw = window_points(X, w)
+        d = xw.shape[1]
+        cv = ndft_adjoint(xw, V, Nw)
+        cg = ndft_adjoint(xw, G, Nw)
+        prod = (np.conj(cg) * cv).sum(axis=-1)
+        q += float(np.real(np.sum(fourier_coeffs(kind, ell, Nw, d, False) * prod)))
+        qd += float(np.real(np.sum(fourier_coeffs(kind, ell, Nw, d, True) * prod)))
+    gv = float(np.sum(G * V))
+    return {"K": sigma_f ** 2 * q + sigma_eps ** 2 * gv, "ell": sigma_f ** 2 * qd,
+            "sigma_f": 2.0 * sigma_f * q, "sigma_eps": 2.0 * sigma_eps * gv}
+
+
 # ---------------------------------------------------------------------------
 # NFFT (Appendix A): Kaiser-Bessel window, adjoint NFFT and NFFT
 # ---------------------------------------------------------------------------
@@ -690,20 +750,29 @@ def farthest_point_sampling(x, k):
     """Greedy farthest point sampling of k indices of the rows of x (Sec. 2.3,
     the landmark choice of the additive AFN preconditioner): start at index 0,
     then repeatedly take the point whose distance to the chosen set is
-    largest, the lowest index among equal distances. The squared distances
-    are compared after rounding to float32 (the precision in which the GPU
-    path takes this decision)."""
+    largest, the lowest index among equal distances. Distances are squared
+    Euclidean distances in FP64."""
+    return [i for i, _, _ in farthest_point_gaps(x, k)]
+
+
+def farthest_point_gaps(x, k):
+    """``farthest_point_sampling(x, k)`` with, for each step, the chosen
+    index, its distance to the set chosen before it and the gap between that
+    distance and the largest distance of any other point (inf for the first
+    point). A gap near zero marks a near-tie, where a distance evaluated with
+    other rounding may decide differently."""
     x = np.asarray(x, dtype=np.float64)
     n = x.shape[0]
     k = min(k, n)
-    chosen = [0]
+    out = [(0, np.inf, np.inf)]
     dist = np.full(n, np.inf)
     for _ in range(1, k):
-        last = x[chosen[-1]]
+        last = x[out[-1][0]]
         dist = np.minimum(dist, np.sum((x - last) ** 2, axis=1))
-        d32 = dist.astype(np.float32)
-        chosen.append(int(np.argmax(d32)))     # argmax returns the first maximum
-    return chosen
+        i = int(np.argmax(dist))                # argmax returns the first maximum
+        rest = np.delete(dist, i)
+        out.append((i, float(dist[i]), float(dist[i] - rest.max()) if rest.size else np.inf))
+    return out
 
 
 def additive_landmarks(X, windows, k_total):
@@ -996,26 +1065,33 @@ def fsai_pattern(X, windows, landmarks, fill, rows=None):
     t = 0 .. |F|-1 of the non-landmark points F in ascending index order.
     Row t holds t and its min(fill - 1, t) nearest earlier positions u < t,
     by the squared Euclidean distance over the window features (every
-    window's features in window order), evaluated in float32 with one
-    rounding per subtraction, product and sum, in feature order; ties go to
-    the lower position. Returns one ascending position list per row (t last),
-    for every row or for the positions listed in ``rows``."""
+    window's features in window order) in FP64; ties go to the lower
+    position. Returns one ascending position list per row (t last), for
+    every row or for the positions listed in ``rows``."""
+    return [J for J, _ in fsai_pattern_gaps(X, windows, landmarks, fill, rows)]
+
+
+def fsai_pattern_gaps(X, windows, landmarks, fill, rows=None):
+    """``fsai_pattern`` with, per row, the gap between the fill-th and the
+    (fill-1)-th smallest distance (inf when every earlier position is
+    kept): a gap near zero marks a near-tie, where a distance evaluated with
+    other rounding may decide differently. Returns (J_t, gap_t) pairs."""
     n = X.shape[0]
     _, F = afn_split(n, landmarks)
     cols = [c for w in windows for c in w]
-    x = np.asarray(X, dtype=np.float64)[F][:, cols].astype(np.float32)
-    J = []
+    x = np.asarray(X, dtype=np.float64)[F][:, cols]
+    out = []
     for t in (range(len(F)) if rows is None else rows):
         if t == 0 or fill <= 1:
-            J.append([t])
+            out.append(([t], np.inf))
             continue
-        acc = np.zeros(t, dtype=np.float32)
+        acc = np.zeros(t)
         for c in range(len(cols)):
-            dd = (x[:t, c] - x[t, c]).astype(np.float32)
-            acc = (acc + (dd * dd).astype(np.float32)).astype(np.float32)
+            acc = acc + (x[:t, c] - x[t, c]) ** 2
         order = np.lexsort((np.arange(t), acc))     # by distance, then position
-        J.append(sorted(int(u) for u in order[:fill - 1]) + [t])
-    return J
+        gap = float(acc[order[fill - 1]] - acc[order[fill - 2]]) if t > fill - 1 else np.inf
+        out.append((sorted(int(u) for u in order[:fill - 1]) + [t], gap))
+    return out
 
 
 def afn_factors(X, windows, kind, ell, sigma_f, sigma_eps, landmarks, fill):

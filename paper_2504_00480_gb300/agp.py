@@ -96,8 +96,14 @@ _SIGS = {
     "agp_batch_bind": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_int64), POINTER(c_void_p),
                                POINTER(c_int64), c_int, c_void_p]),
     "agp_batch_matvec": (c_int, [c_void_p, c_int, c_void_p]),
+    "agp_spectra_size": (c_int, [c_void_p, c_int, POINTER(c_int64)]),
+    "agp_matvec_spectra": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_int,
+                                   c_void_p, c_void_p]),
+    "agp_spectral_form": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p,
+                                  c_void_p]),
     "agp_profile_enable": (c_int, [c_void_p, c_int]),
     "agp_profile_read": (c_int, [c_void_p, POINTER(Profile), c_int, c_void_p]),
+    "agp_plan_set_wait_limit": (c_int, [c_void_p, ctypes.c_int64]),
     "agp_status_string": (ctypes.c_char_p, [c_int]),
     "agp_last_error": (ctypes.c_char_p, []),
 }
@@ -203,6 +209,42 @@ def agp_deriv_matvec(plan: c_void_p, which: str, V: torch.Tensor, Out: torch.Ten
     if Ro != R or Out.shape[0] != V.shape[0]:
         raise ValueError("Out must have V's shape")
     _check(load_library().agp_deriv_matvec(plan, PARAMS[which], vp, ldv, op, ldo, R, _stream()))
+
+
+def agp_spectra_size(plan: c_void_p, R: int) -> int:
+    e = c_int64()
+    _check(load_library().agp_spectra_size(plan, int(R), byref(e)))
+    return e.value
+
+
+def agp_matvec_spectra(plan: c_void_p, V: torch.Tensor, Out: torch.Tensor | None,
+                       spec: torch.Tensor, add_noise: bool = True):
+    """Out = K_hat V (skipped when Out is None) and the forward spectra of V
+    into spec (complex tensor of agp_spectra_size(R) elements)."""
+    vp, ldv, R = _block(V, V.dtype, "V")
+    if Out is None:
+        op, ldo = None, R
+    else:
+        op, ldo, Ro = _block(Out, V.dtype, "Out")
+        if Ro != R or Out.shape[0] != V.shape[0]:
+            raise ValueError("Out must have V's shape")
+    cdt = torch.complex64 if V.dtype == torch.float32 else torch.complex128
+    if spec.dtype != cdt or not spec.is_contiguous() or spec.numel() < agp_spectra_size(plan, R):
+        raise ValueError("spec must be a contiguous complex tensor of agp_spectra_size(R) elements")
+    _check(load_library().agp_matvec_spectra(plan, vp, ldv, op, ldo, R, int(bool(add_noise)),
+                                             spec.data_ptr(), _stream()))
+
+
+def agp_spectral_form(plan: c_void_p, which: str | None, A: torch.Tensor, B: torch.Tensor,
+                      R: int) -> torch.Tensor:
+    """Device float64 [R]: G_r^T Op V_r from the spectra A (of G) and B (of V);
+    Op = sigma_f^2 sum_s K_s (which None), its ell-derivative ("ell") or
+    2 sigma_f sum_s K_s ("sigma_f")."""
+    out = torch.empty(R, dtype=torch.float64, device=A.device)
+    w = -1 if which is None else PARAMS[which]
+    _check(load_library().agp_spectral_form(plan, w, A.data_ptr(), B.data_ptr(), int(R),
+                                            out.data_ptr(), _stream()))
+    return out
 
 
 def agp_adjoint_nfft(plan: c_void_p, window: int, V: torch.Tensor, chat: torch.Tensor):
@@ -575,10 +617,31 @@ class Plan:
         agp_set_hyper(self._h, ell, sigma_f, sigma_eps)
         self.ell, self.sigma_f, self.sigma_eps = float(ell), float(sigma_f), float(sigma_eps)
 
+    def ensure_hyper(self, ell: float, sigma_f: float, sigma_eps: float):
+        """set_hyper, skipped when the plan already holds these values."""
+        if (float(ell), float(sigma_f), float(sigma_eps)) != (self.ell, self.sigma_f,
+                                                                self.sigma_eps):
+            self.set_hyper(ell, sigma_f, sigma_eps)
+
     def matvec(self, V: torch.Tensor, out: torch.Tensor | None = None, add_noise: bool = True):
         out = torch.empty_like(V) if out is None else out
         agp_matvec(self._h, V, out, add_noise)
         return out
+
+    def spectra(self, V: torch.Tensor, out: torch.Tensor | None = None,
+                add_noise: bool = True) -> tuple:
+        """(K_hat V or None, spectra of V): with `out` (a tensor, or True for a
+        new one) the matvec is applied too."""
+        R = V.shape[1]
+        cdt = torch.complex64 if self.dtype == torch.float32 else torch.complex128
+        spec = torch.empty(agp_spectra_size(self._h, R), dtype=cdt, device=V.device)
+        if out is True:
+            out = torch.empty_like(V)
+        agp_matvec_spectra(self._h, V, out if out is not None else None, spec, add_noise)
+        return out, spec
+
+    def spectral_form(self, which: str | None, A: torch.Tensor, B: torch.Tensor, R: int):
+        return agp_spectral_form(self._h, which, A, B, R)
 
     def deriv_matvec(self, which: str, V: torch.Tensor, out: torch.Tensor | None = None):
         out = torch.empty_like(V) if out is None else out
@@ -635,6 +698,10 @@ class Plan:
     def check(self):
         """Raise AgpError (AGP_TIMEOUT) if a bounded device wait expired."""
         _check(load_library().agp_plan_check(self._h, _stream()))
+
+    def set_wait_limit(self, polls: int = 0):
+        """Polls per bounded tensor-core wait (0: the library default)."""
+        _check(load_library().agp_plan_set_wait_limit(self._h, int(polls)))
 
     def autotune(self, R: int = 32, reps: int = 3):
         return agp_plan_autotune(self._h, R, reps)

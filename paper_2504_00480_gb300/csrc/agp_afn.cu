@@ -9,9 +9,9 @@
 //     M = Phi diag(K_LL, (G^T G)^{-1}) Phi^T,  Phi = [I 0; K_FL K_LL^{-1} I],
 // where G is lower triangular with at most `fill` entries per row: row t
 // holds t and its fill-1 nearest earlier positions u < t of F (squared
-// Euclidean distance over the window features in float32, rounded after
-// every subtraction, product and sum, in feature order; ties to the lower
-// position), and G[t, J_t] = g / sqrt(g_t) with S[J_t, J_t] g = e_t, so that
+// Euclidean distance over the window features in FP64, the squared
+// differences summed in feature order; ties to the lower position), and
+// G[t, J_t] = g / sqrt(g_t) with S[J_t, J_t] g = e_t, so that
 // G S G^T has unit diagonal. With C the lower Cholesky factor of K_LL and
 // W = K_FL C^{-T} ([m][k]),
 //     M^{-1} r:  v = C^{-1} r_L;  t = r_F - W v;  w = G^T G t;
@@ -35,6 +35,12 @@ namespace {
 
 constexpr int kKnnWarps = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// shared memory of one warp of k_knn_lower: kAfnMaxFill distances (FP64) and
+// positions, then the row's pf features (FP64); a multiple of 8 bytes
+__host__ __device__ constexpr size_t knn_warp_bytes(int pf) {
+  return (size_t)kAfnMaxFill * (sizeof(double) + sizeof(int)) + (size_t)pf * sizeof(double);
+}
 
 // out[a][j] = sf2 d kernel_sum(rows_a, L_j) / dell, FP64 [m][k]
 template <typename T>
@@ -82,16 +88,16 @@ __global__ void k_times_lower_t(const double* __restrict__ Bf, int64_t m, int k,
   W[e] = s;
 }
 
-// xf[c0 + t][a] = float32 of coordinate t of point F_a (one window, caller order [d][n])
+// xf[c0 + t][a] = coordinate t of point F_a in FP64 (one window, caller order [d][n])
 template <typename T>
 __global__ void k_gather_feat(const T* __restrict__ x, int d, int64_t n,
                               const int32_t* __restrict__ F, int64_t m, int c0,
-                              float* __restrict__ xf) {
+                              double* __restrict__ xf) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m * d) return;
   const int t = (int)(e / m);
   const int64_t a = e - (int64_t)t * m;
-  xf[(int64_t)(c0 + t) * m + a] = (float)x[(int64_t)t * n + F[a]];
+  xf[(int64_t)(c0 + t) * m + a] = (double)x[(int64_t)t * n + F[a]];
 }
 
 // Pattern of row a (one warp per row): the fill-1 nearest earlier positions
@@ -99,29 +105,30 @@ __global__ void k_gather_feat(const T* __restrict__ x, int d, int64_t n,
 // u = 0 .. a-1 are scanned 32 at a time and inserted one by one. Writes
 // J[a][0 .. len) ascending with a last, -1 after, and len[a].
 __global__ void __launch_bounds__(kKnnWarps * 32)
-k_knn_lower(const float* __restrict__ xf, int pf, int64_t m, int fill, int32_t* __restrict__ J,
+k_knn_lower(const double* __restrict__ xf, int pf, int64_t m, int fill, int32_t* __restrict__ J,
             int32_t* __restrict__ len) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t a = (int64_t)blockIdx.x * kKnnWarps + warp;
   if (a >= m) return;   // the whole warp leaves together
-  float* ld = reinterpret_cast<float*>(smem_raw) + (size_t)warp * (2 * kAfnMaxFill + pf);
+  // per warp: the sorted list's distances and positions, then the row's features
+  double* ld = reinterpret_cast<double*>(smem_raw + (size_t)warp * knn_warp_bytes(pf));
   int* lp = reinterpret_cast<int*>(ld + kAfnMaxFill);
-  float* q = ld + 2 * kAfnMaxFill;
+  double* q = reinterpret_cast<double*>(lp + kAfnMaxFill);
   for (int c = lane; c < pf; c += 32) q[c] = xf[(int64_t)c * m + a];
   __syncwarp();
   const int cap = fill - 1;
   int cnt = 0;
-  float thr_d = 0.0f;
+  double thr_d = 0.0;
   int thr_p = 0;
   for (int64_t u0 = 0; u0 < a && cap > 0; u0 += 32) {
     const int64_t u = u0 + lane;
     const bool valid = u < a;
-    float dist = 0.0f;
+    double dist = 0.0;
     if (valid)
       for (int c = 0; c < pf; ++c) {
-        const float dd = __fsub_rn(xf[(int64_t)c * m + u], q[c]);
-        dist = __fadd_rn(dist, __fmul_rn(dd, dd));
+        const double dd = xf[(int64_t)c * m + u] - q[c];
+        dist = __dadd_rn(dist, __dmul_rn(dd, dd));
       }
     const bool pass =
         valid && (cnt < cap || dist < thr_d || (dist == thr_d && (int)u < thr_p));
@@ -129,7 +136,7 @@ k_knn_lower(const float* __restrict__ xf, int pf, int64_t m, int fill, int32_t* 
     while (mask) {
       const int src = __ffs(mask) - 1;
       mask &= mask - 1;
-      const float dc = __shfl_sync(kFull, dist, src);
+      const double dc = __shfl_sync(kFull, dist, src);
       const int uc = (int)(u0 + src);
       if (cnt == cap && !(dc < thr_d || (dc == thr_d && uc < thr_p))) continue;
       int below = 0;
@@ -139,7 +146,7 @@ k_knn_lower(const float* __restrict__ xf, int pf, int64_t m, int fill, int32_t* 
         below += __popc(__ballot_sync(kFull, lt));
       }
       const int newcnt = min(cnt + 1, cap);
-      float rd[kAfnMaxFill / 32];
+      double rd[kAfnMaxFill / 32];
       int rp[kAfnMaxFill / 32];
 #pragma unroll
       for (int qq = 0; qq < kAfnMaxFill / 32; ++qq) {
@@ -629,17 +636,17 @@ agp_status afn_build(agp_plan_s* pl, int k_req, int fill, int rmax, Afn* af, cud
                                                        pl->ell, sf2, Bf);
     k_times_lower_t<<<nblk(m * k, 256), 256, 0, st>>>(Bf, m, k, af->Ci, af->W);
     cudaFreeAsync(Bf, st);
-    // pattern: float32 window features of F, nearest earlier positions
+    // pattern: FP64 window features of F, nearest earlier positions
     int pf = 0;
     for (int s = 0; s < P; ++s) pf += pl->win[s].d;
-    float* xf = nullptr;
-    AGP_CUDA(cudaMallocAsync(&xf, sizeof(float) * pf * m, st));
+    double* xf = nullptr;
+    AGP_CUDA(cudaMallocAsync(&xf, sizeof(double) * pf * m, st));
     for (int s = 0, c0 = 0; s < P; c0 += pl->win[s].d, ++s)
       k_gather_feat<T><<<nblk(m * pl->win[s].d, 256), 256, 0, st>>>(
           cp.xo[s], pl->win[s].d, n, af->F, m, c0, xf);
     AGP_CUDA(cudaMalloc(&af->J, sizeof(int32_t) * m * fill));
     AGP_CUDA(cudaMalloc(&af->len, sizeof(int32_t) * m));
-    const size_t ksmem = sizeof(float) * kKnnWarps * (2 * kAfnMaxFill + pf);
+    const size_t ksmem = kKnnWarps * knn_warp_bytes(pf);
     AGP_CUDA(cudaFuncSetAttribute(k_knn_lower, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)ksmem));
     k_knn_lower<<<nblk(m, kKnnWarps), kKnnWarps * 32, ksmem, st>>>(xf, pf, m, fill, af->J,

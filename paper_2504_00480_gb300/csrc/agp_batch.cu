@@ -206,7 +206,8 @@ agp_status batch_matvec(agp_batch_s* b, int which, cudaStream_t st) {
     const int64_t a = b->items_by_d[dd - 1], e = b->items_by_d[dd];
     if (e > a)
       AGP_CUDA(spread_items_sel<T>(wins, io, b->items + a, e - a, dd, b->s, b->rc, nullptr, 0,
-                                   b->R, b->plans[0]->use_tc, b->plans[0]->err_dev, st));
+                                   b->R, b->plans[0]->use_tc, b->plans[0]->err_dev,
+                                   b->plans[0]->wait_limit, st));
   }
   for (const auto& g : b->groups) {
     AGP_CUDA(fft_forward<T>(g, b->rc, st));
@@ -217,7 +218,8 @@ agp_status batch_matvec(agp_batch_s* b, int which, cudaStream_t st) {
     const int64_t a = b->items_by_d[dd - 1], e = b->items_by_d[dd];
     if (e > a)
       AGP_CUDA(interp_items_sel<T>(wins, io, b->items + a, e - a, dd, b->s, b->rc, nullptr, 0,
-                                   b->R, T(0), b->plans[0]->use_tc, b->plans[0]->err_dev, st));
+                                   b->R, T(0), b->plans[0]->use_tc, b->plans[0]->err_dev,
+                                   b->plans[0]->wait_limit, st));
   }
   return AGP_OK;
 }
@@ -237,6 +239,8 @@ agp_status agp_batch_create(agp_batch* out, const agp_plan* plans, int nprob, vo
     if (!plans[q]) return set_error(AGP_EINVAL, "NULL plan in batch");
     if (plans[q]->prec != plans[0]->prec || plans[q]->s != plans[0]->s)
       return set_error(AGP_EINVAL, "batched plans must share precision and cutoff");
+    if (plans[q]->use_tc != plans[0]->use_tc)
+      return set_error(AGP_EINVAL, "batched plans must share the tensor-core setting");
   }
   auto* b = new (std::nothrow) agp_batch_s();
   if (!b) return set_error(AGP_ENOMEM, "host allocation");

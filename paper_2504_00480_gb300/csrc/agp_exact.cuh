@@ -41,20 +41,50 @@ __global__ void k_fill_double(double* __restrict__ p, int64_t n, double v) {
   if (e < n) p[e] = v;
 }
 
-// One FPS step: fold the previous landmark into the running minimum distances
-// and record the argmax as key (distance bits << 32 | ~index).
+// Farthest point sampling (Sec. 2.3), one step in two launches. k_fps_dist
+// folds landmark chosen[step - 1] into the running minimum squared distances
+// and writes each block's farthest point; k_fps_pick reduces the blocks'
+// candidates into chosen[step]. Distances and the comparison are FP64: the
+// squared distance is the plainly rounded sum ((u_0^2 + u_1^2) + u_2^2) of
+// the coordinate differences (no fused multiply-add, so the choice does not
+// depend on how the compiler contracts it); the farthest point is the one
+// with the largest distance, the lowest index among equal distances.
+__device__ __forceinline__ void fps_better(double& bd, int64_t& bi, double od, int64_t oi) {
+  if (od > bd || (od == bd && oi < bi)) {
+    bd = od;
+    bi = oi;
+  }
+}
+
+constexpr int kFpsThreads = 256;
+
+// block-wide (distance, index) maximum of the calling block, valid in thread 0
+__device__ void fps_block_best(double& bd, int64_t& bi) {
+  __shared__ double sd[kFpsThreads / 32];
+  __shared__ int64_t si[kFpsThreads / 32];
+  for (int o = 16; o > 0; o >>= 1)
+    fps_better(bd, bi, __shfl_xor_sync(0xFFFFFFFFu, bd, o), __shfl_xor_sync(0xFFFFFFFFu, bi, o));
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) {
+    sd[warp] = bd;
+    si[warp] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < kFpsThreads / 32; ++w) fps_better(bd, bi, sd[w], si[w]);
+}
+
 template <typename T>
-__global__ void k_fps_step(const T* __restrict__ x, int64_t n, int d, int step,
-                           unsigned long long* __restrict__ keys, double* __restrict__ dist) {
-  const unsigned last = (step == 1) ? 0u : 0xFFFFFFFFu - (unsigned)(keys[step - 1] & 0xFFFFFFFFull);
+__global__ void __launch_bounds__(kFpsThreads)
+k_fps_dist(const T* __restrict__ x, int64_t n, int d, const int32_t* __restrict__ chosen, int step,
+           double* __restrict__ dist, double* __restrict__ cand_d, int64_t* __restrict__ cand_i) {
+  const int64_t last = chosen[step - 1];
   double xl[3] = {0, 0, 0};
   for (int t = 0; t < d; ++t) xl[t] = (double)x[(int64_t)t * n + last];
-  unsigned long long best = 0;
+  double bd = -1.0;
+  int64_t bi = n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    // explicit rounding (no fused multiply-add): the squared distance is the
-    // plainly rounded sum ((u_0^2 + u_1^2) + u_2^2), so the choice does not
-    // depend on how the compiler contracts it
     double d2 = 0.0;
     for (int t = 0; t < d; ++t) {
       const double u = (double)x[(int64_t)t * n + i] - xl[t];
@@ -62,15 +92,23 @@ __global__ void k_fps_step(const T* __restrict__ x, int64_t n, int d, int step,
     }
     const double m = fmin(dist[i], d2);
     dist[i] = m;
-    const unsigned long long key =
-        ((unsigned long long)__float_as_uint((float)m) << 32) | (0xFFFFFFFFull - (unsigned long long)i);
-    best = key > best ? key : best;
+    fps_better(bd, bi, m, i);
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-    best = other > best ? other : best;
+  fps_block_best(bd, bi);
+  if (threadIdx.x == 0) {
+    cand_d[blockIdx.x] = bd;
+    cand_i[blockIdx.x] = bi;
   }
-  if ((threadIdx.x & 31) == 0) atomicMax(keys + step, best);
+}
+
+__global__ void __launch_bounds__(kFpsThreads)
+k_fps_pick(const double* __restrict__ cand_d, const int64_t* __restrict__ cand_i, int nb,
+           int32_t* __restrict__ chosen, int step) {
+  double bd = -1.0;
+  int64_t bi = INT64_MAX;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) fps_better(bd, bi, cand_d[b], cand_i[b]);
+  fps_block_best(bd, bi);
+  if (threadIdx.x == 0) chosen[step] = (int32_t)bi;
 }
 
 // B[i][j] = sigma_f^2 sum_s kappa_s(|x_i^s - x_{L_j}^s|) (exact kernel, Sec. 2.1)

@@ -28,6 +28,7 @@ namespace agp {
 constexpr int kMaxDim = 3;
 constexpr int kMaxWindows = 64;
 constexpr int kItemPoints = 256;     // points per work item (one grid cell or part of one)
+constexpr long long kDefaultWaitLimit = 1ll << 26;   // polls per bounded tensor-core wait
 
 // Per-window view handed to the spreading / interpolation kernels.
 template <typename T>
@@ -231,6 +232,7 @@ struct agp_plan_s {
   int64_t items_by_d[agp::kMaxDim + 1] = {0, 0, 0, 0};   // offsets of each d group
   std::vector<agp::FftGroup> groups;   // windows grouped by (d, N) for the DFT stages
   int* err_dev = nullptr;        // device error flags
+  long long wait_limit = agp::kDefaultWaitLimit;   // polls per bounded mbarrier wait
   // stage profiler
   bool prof = false;
   struct Ev { int stage, dim; cudaEvent_t a, b; };
@@ -243,6 +245,12 @@ namespace agp {
 // ---- error plumbing (agp_plan.cu) ----
 agp_status set_error(agp_status s, const std::string& msg);
 agp_status cuda_status(cudaError_t e, const char* what);
+// AGP_TIMEOUT (and the timeout bit cleared) if a bounded tensor-core wait of
+// the plan expired since the last check, else AGP_OK. Synchronises `st`.
+agp_status timeout_check(agp_plan_s* pl, cudaStream_t st);
+// s, or AGP_TIMEOUT when s is a result (OK, NOT_CONVERGED, ENAN) and a wait
+// expired meanwhile: for entry points that synchronise anyway.
+agp_status with_timeout_check(agp_plan_s* pl, agp_status s, cudaStream_t st);
 
 // ---- kernel launchers (agp_nufft.cu) ----
 // Spread the columns V[:, 0..R) of the windows referenced by `items` (all of
@@ -262,15 +270,16 @@ cudaError_t spread_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* 
 bool spread_tc_supported(int d, int s, int RC);
 cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
                             int64_t n_items, int s, const float* V, int64_t ldv, int R, int rc,
-                            int* err, cudaStream_t st);
+                            int* err, long long spin, cudaStream_t st);
 // spread_items, or spread_items_tc when `tc` is set and the case is supported
+// (spin: polls per bounded wait of the tensor-core kernel)
 template <typename T>
 cudaError_t spread_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
                              int64_t n_items, int d, int s, int RC, const T* V, int64_t ldv, int R,
-                             int tc, int* err, cudaStream_t st) {
+                             int tc, int* err, long long spin, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (tc && spread_tc_supported(d, s, RC))
-      return spread_items_tc(wins, io, items, n_items, s, V, ldv, R, RC, err, st);
+      return spread_items_tc(wins, io, items, n_items, s, V, ldv, R, RC, err, spin, st);
   }
   return spread_items<T>(wins, io, items, n_items, d, s, RC, V, ldv, R, st);
 }
@@ -278,7 +287,7 @@ cudaError_t spread_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const in
 bool interp_tc_supported(int d, int s, int RC);
 cudaError_t interp_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
                             int64_t n_items, int s, float* Out, int64_t ldo, int R, float scale,
-                            int rc, int* err, cudaStream_t st);
+                            int rc, int* err, long long spin, cudaStream_t st);
 // Interpolate the grids of those windows and add scale * result into
 // Out[:, 0..R) (with io: Out, ldo and scale of io[window]).
 template <typename T>
@@ -290,10 +299,10 @@ cudaError_t interp_items(const WinDev<T>* wins, const WinIO<T>* io, const int4* 
 template <typename T>
 cudaError_t interp_items_sel(const WinDev<T>* wins, const WinIO<T>* io, const int4* items,
                              int64_t n_items, int d, int s, int RC, T* Out, int64_t ldo, int R,
-                             T scale, int tc, int* err, cudaStream_t st) {
+                             T scale, int tc, int* err, long long spin, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (tc && interp_tc_supported(d, s, RC))
-      return interp_items_tc(wins, io, items, n_items, s, Out, ldo, R, scale, RC, err, st);
+      return interp_items_tc(wins, io, items, n_items, s, Out, ldo, R, scale, RC, err, spin, st);
   }
   return interp_items<T>(wins, io, items, n_items, d, s, RC, Out, ldo, R, scale, st);
 }

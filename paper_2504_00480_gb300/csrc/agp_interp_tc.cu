@@ -20,8 +20,10 @@
 // values) and B (grid values read from L2, prefetched a chunk ahead into
 // registers) in one of two operand buffers, and after one barrier thread 0
 // issues the chunk's six MMAs (two K = 8 steps) and commits them to the
-// buffer's mbarrier. Every mbarrier wait
-// is bounded: on expiry the CTA records a timeout in the plan's error word.
+// buffer's mbarrier. Every mbarrier wait is bounded (the plan's wait limit)
+// and its outcome agreed by the CTA at the next barrier: on expiry the CTA
+// stops issuing MMAs, drains the committed ones, records a timeout in the
+// plan's error word, skips its remaining epilogues and releases its TMEM.
 #include <type_traits>
 
 #include "agp_nufft_kernels.cuh"
@@ -113,7 +115,7 @@ template <int S>
 __global__ void __launch_bounds__(kItThreads, 2)
 k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict__ io,
             const int4* __restrict__ items, float* __restrict__ Out, int64_t ldo, int R,
-            float scale, int rc, int* __restrict__ err) {
+            float scale, int rc, int* __restrict__ err, long long spin) {
   using Sh = TcInterpShape<S>;
   constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, KC = kItKC, RH = kItRH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -200,9 +202,9 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     load_b(kk4, gb);
     cp_async_wait<0>();
     __syncthreads();
-    for (int c = 0; c < Sh::NCH; ++c, ++gc) {
+    for (int c = 0; c < Sh::NCH; ++c) {
       const int b = gc & 1;
-      if (gc >= 2 && !mbar_wait(&bar[b], ((gc - 2) >> 1) & 1)) ok = false;
+      if (gc >= 2 && !mbar_wait(&bar[b], ((gc - 2) >> 1) & 1, spin)) ok = false;
       float* ahi = reinterpret_cast<float*>(opnd(b));
       float* alo = reinterpret_cast<float*>(opnd(b) + Sh::A_BYTES);
       float* bhi = reinterpret_cast<float*>(opnd(b) + 2 * Sh::A_BYTES);
@@ -221,7 +223,8 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
       }
       asm volatile("fence.proxy.async.shared::cta;");
       asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
+      ok = __syncthreads_and(ok);                // CTA-wide outcome of the waits so far
+      if (!ok) break;
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint64_t a0 = umma_desc(smem_u32(ahi), kItLBO, kItSBO);
@@ -237,11 +240,15 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
         }
         mma_commit(&bar[b]);
       }
+      ++gc;
     }
-    // the last commit covers every MMA of the tile
-    if (!mbar_wait(&bar[(gc - 1) & 1], ((gc - 1) >> 1) & 1)) ok = false;
+    if (!ok) break;
+    // the last commit covers every MMA of the tile (no other phase of its
+    // barrier is pending: the wait for the chunk two before it succeeded)
+    ok = __syncthreads_and(mbar_wait(&bar[(gc - 1) & 1], ((gc - 1) >> 1) & 1, spin));
+    if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok) {
+    {
       // warp w: points 32 (w % 4) .. + 31 (TMEM lanes), t3 half w / 4; partial
       // sums over its t3 range go to shared memory, then four threads per
       // point add the halves and issue one 16-byte atomic each
@@ -274,7 +281,7 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (ok) {
+    {
       const bool vec = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(Out) & 15) == 0);
       for (int e = tid; e < np * 4; e += kItThreads) {
         const int p = e >> 2, c4 = (e & 3) * 4;
@@ -291,12 +298,17 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
           for (int q = 0; q < 4 && r0 + c4 + q < R; ++q) atomicAdd(dst + q, vv[q]);
         }
       }
-    } else if (tid == 0) {
-      atomicOr(err, 2);
     }
     __syncthreads();                             // partials, ws and sperm free for the next tile
     asm volatile("tcgen05.fence::after_thread_sync;");
   }
+  if (!ok) {
+    // a wait expired (the CTA agreed on it): drain the committed MMAs with
+    // the fixed bound before TMEM is released, record the timeout
+    if (gc > 0) mbar_wait(&bar[(gc - 1) & 1], ((gc - 1) >> 1) & 1);
+    if (tid == 0) atomicOr(err, 2);
+  }
+  cp_async_wait<0>();
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
@@ -307,14 +319,14 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
 template <int S>
 cudaError_t interp_tc_s(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
                         int64_t n_items, float* Out, int64_t ldo, int R, float scale, int rc,
-                        int* err, cudaStream_t st) {
+                        int* err, long long spin, cudaStream_t st) {
   using Sh = TcInterpShape<S>;
   cudaError_t e = cudaFuncSetAttribute(k_interp_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Sh::SMEM);
   if (e != cudaSuccess) return e;
   if (n_items <= 0) return cudaSuccess;
   k_interp_tc<S><<<(unsigned)(rc / 16 * n_items), kItThreads, Sh::SMEM, st>>>(wins, io, items, Out, ldo,
-                                                                        R, scale, rc, err);
+                                                                        R, scale, rc, err, spin);
   return cudaGetLastError();
 }
 
@@ -326,10 +338,10 @@ bool interp_tc_supported(int d, int s, int RC) {
 
 cudaError_t interp_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
                             int64_t n_items, int s, float* Out, int64_t ldo, int R, float scale,
-                            int rc, int* err, cudaStream_t st) {
+                            int rc, int* err, long long spin, cudaStream_t st) {
   switch (s) {
-    case 4: return interp_tc_s<4>(wins, io, items, n_items, Out, ldo, R, scale, rc, err, st);
-    case 5: return interp_tc_s<5>(wins, io, items, n_items, Out, ldo, R, scale, rc, err, st);
+    case 4: return interp_tc_s<4>(wins, io, items, n_items, Out, ldo, R, scale, rc, err, spin, st);
+    case 5: return interp_tc_s<5>(wins, io, items, n_items, Out, ldo, R, scale, rc, err, spin, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "agp_internal.cuh"
 
@@ -49,9 +50,31 @@ agp_status cuda_status(cudaError_t e, const char* what) {
     if (s_ != AGP_OK) return s_;                                   \
   } while (0)
 
+constexpr int kErrTimeout = 2;      // error word bit: a bounded tensor-core wait expired
+
+agp_status timeout_check(agp_plan_s* pl, cudaStream_t st) {
+  int err = 0;
+  AGP_CUDA(cudaMemcpyAsync(&err, pl->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  AGP_CUDA(cudaStreamSynchronize(st));
+  if (err & kErrTimeout) {
+    const int keep = err & ~kErrTimeout;
+    AGP_CUDA(cudaMemcpyAsync(pl->err_dev, &keep, sizeof(int), cudaMemcpyHostToDevice, st));
+    AGP_CUDA(cudaStreamSynchronize(st));
+    return set_error(AGP_TIMEOUT, "a bounded wait in a tensor-core kernel expired");
+  }
+  return AGP_OK;
+}
+
+agp_status with_timeout_check(agp_plan_s* pl, agp_status s, cudaStream_t st) {
+  if (s != AGP_OK && s != AGP_NOT_CONVERGED && s != AGP_ENAN) return s;
+  const agp_status t = timeout_check(pl, st);
+  return t == AGP_OK ? s : t;
+}
+
+
 namespace {
 
-enum : int { kErrDomain = 1, kErrTimeout = 2 };
+enum : int { kErrDomain = 1 };
 
 // ---------------------------------------------------------------------------
 // a0: binning and counting sort
@@ -946,10 +969,71 @@ struct StageTimer {
   }
 };
 
+// Spectra of a block of right-hand sides, as agp_matvec_spectra stores them:
+// the windows in the order of the plan's DFT groups (a group = the windows of
+// one (d, N)), each window's Hermitian-half spectrum [K^(d-1) Kh] x R complex
+// (plan precision), the forward DFT of the spread grid before deconvolution.
+// k_save_spectra copies columns r0 .. r0 + Rc - 1 of one pass for every
+// window of a group (blockIdx.y: the window within the group).
+template <typename T2>
+__global__ void k_save_spectra(const FftWin* __restrict__ tab, int sel, int64_t E, int rc, int Rc,
+                               int R, int r0, T2* __restrict__ out) {
+  const FftWin f = tab[blockIdx.y];
+  const T2* spec = reinterpret_cast<const T2*>(sel == 1 ? f.specA : f.specB);
+  T2* o = out + (int64_t)blockIdx.y * E * R;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E * Rc;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / Rc;
+    const int c = (int)(e - k * Rc);
+    o[k * R + r0 + c] = spec[k * rc + c];
+  }
+}
+
+// out[c] += scale sum_s sum_k w_k D_k Re(conj(A_k) B_k) over the windows of
+// one group, D = the spectral multiplier of the kernel (der = 0) or of its
+// ell-derivative (der = 1), w_k = 1 for k_d = 0 and 2 for k_d > 0 (the
+// Hermitian half stands for the full symmetric index set). With A and B the
+// spectra of G and V this is G^T (sum_s K_s) V (der = 0) or
+// G^T (sum_s K_s^der) V (der = 1) for the operator agp_matvec applies:
+// interpolation is the transpose of spreading. FP64 accumulation.
+constexpr int kFormThreads = 256;
+template <typename T, typename T2>
+__global__ void __launch_bounds__(kFormThreads)
+k_spec_form(const FftWin* __restrict__ tab, int der, const T2* __restrict__ A,
+            const T2* __restrict__ B, int64_t E, int Kh, int R, double scale,
+            double* __restrict__ out) {
+  __shared__ double red[kFormThreads / 32][32];
+  const FftWin f = tab[blockIdx.y];
+  const T* dm = reinterpret_cast<const T*>(der ? f.dmul_der : f.dmul);
+  const T2* a = A + (int64_t)blockIdx.y * E * R;
+  const T2* b = B + (int64_t)blockIdx.y * E * R;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int c = blockIdx.z * 32 + lane;
+  double acc = 0.0;
+  if (c < R)
+    for (int64_t k = blockIdx.x * (int64_t)(kFormThreads / 32) + warp; k < E;
+         k += (int64_t)gridDim.x * (kFormThreads / 32)) {
+      const T2 x = a[k * R + c], y = b[k * R + c];
+      const double w = (k % Kh == 0) ? 1.0 : 2.0;
+      acc += w * (double)dm[k] * ((double)x.x * (double)y.x + (double)x.y * (double)y.y);
+    }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && c < R) {
+    double sum = 0.0;
+    for (int q = 0; q < kFormThreads / 32; ++q) sum += red[q][lane];
+    atomicAdd(out + c, scale * sum);
+  }
+}
+
 // Sum over windows of scale * K_s V (coefficient set `der`), added into Out.
+// With spec: the forward spectra of V are also stored there (layout of
+// k_save_spectra); with spec_only, nothing else is done (Out unused).
 template <typename T>
 agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_t ldo, int R,
-                         int der, T scale, cudaStream_t st) {
+                         int der, T scale, cudaStream_t st, void* spec = nullptr,
+                         bool spec_only = false) {
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   const WinDev<T>* wins = reinterpret_cast<const WinDev<T>*>(pl->wins_dev);
   for (int r0 = 0, rc = 0; r0 < R; r0 += rc) {
     rc = pick_rc(pl, R - r0);
@@ -965,31 +1049,46 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       StageTimer tm(pl, 0, st, dd);
       if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 && spread_tc_supported(3, pl->s, rc))
         AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc, V + r0,
-                                     ldv, Rc, 1, pl->err_dev, st));
+                                     ldv, Rc, 1, pl->err_dev, pl->wait_limit, st));
       else
         AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
-                                     V + r0, ldv, Rc, pl->use_tc, pl->err_dev, st));
+                                     V + r0, ldv, Rc, pl->use_tc, pl->err_dev, pl->wait_limit,
+                                     st));
       pl->launches[0] += 1;
     }
     {
       StageTimer tm(pl, 1, st);
+      int64_t goff = 0;
       for (const auto& g : pl->groups) {
         AGP_CUDA(fft_forward<T>(g, rc, st));
+        pl->launches[1] += g.d;
+        if (spec) {
+          const unsigned bx = (unsigned)std::min<int64_t>(nblk(g.dmul_elems * Rc, 256), 1024);
+          k_save_spectra<T2><<<dim3(bx, g.count), 256, 0, st>>>(
+              g.tab, (g.d % 2) ? 1 : 2, g.dmul_elems, rc, Rc, R, r0,
+              reinterpret_cast<T2*>(spec) + goff);
+          pl->launches[1] += 1;
+          goff += (int64_t)g.count * g.dmul_elems * R;
+        }
+        if (spec_only) continue;
         AGP_CUDA(spectral_multiply<T>(g, der, rc, st));
         AGP_CUDA(fft_inverse<T>(g, rc, st));
-        pl->launches[1] += 2 * g.d + 1;
+        pl->launches[1] += g.d + 1;
       }
     }
+    if (spec_only) continue;
     for (int dd = 1; dd <= kMaxDim; ++dd) {
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 2, st, dd);
       if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 && interp_tc_supported(3, pl->s, rc))
         AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc,
-                                     Out + r0, ldo, Rc, scale, 1, pl->err_dev, st));
+                                     Out + r0, ldo, Rc, scale, 1, pl->err_dev, pl->wait_limit,
+                                     st));
       else
         AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
-                                     Out + r0, ldo, Rc, scale, pl->use_tc, pl->err_dev, st));
+                                     Out + r0, ldo, Rc, scale, pl->use_tc, pl->err_dev,
+                                     pl->wait_limit, st));
       pl->launches[2] += 1;
     }
   }
@@ -998,15 +1097,39 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
 
 template <typename T>
 agp_status matvec_t(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_t ldo, int R,
-                    T noise, T scale, int der, bool windows, cudaStream_t st) {
-  {
+                    T noise, T scale, int der, bool windows, cudaStream_t st,
+                    void* spec = nullptr) {
+  if (Out) {
     StageTimer tm(pl, 3, st);
     k_init_out<T><<<nblk(pl->n * R, 256), 256, 0, st>>>(Out, ldo, V, ldv, pl->n, R, noise);
     pl->launches[3] += 1;
   }
   AGP_CUDA(cudaGetLastError());
-  if (windows) AGP_TRY(apply_windows<T>(pl, V, ldv, Out, ldo, R, der, scale, st));
+  if (windows) AGP_TRY(apply_windows<T>(pl, V, ldv, Out, ldo, R, der, scale, st, spec, !Out));
   return AGP_OK;
+}
+
+int64_t spectra_elems(const agp_plan_s* pl, int R) {
+  int64_t e = 0;
+  for (const auto& g : pl->groups) e += (int64_t)g.count * g.dmul_elems * R;
+  return e;
+}
+
+template <typename T>
+agp_status spectral_form_t(agp_plan_s* pl, int der, double scale, const void* A, const void* B,
+                           int R, double* out, cudaStream_t st) {
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  AGP_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * R, st));
+  int64_t goff = 0;
+  for (const auto& g : pl->groups) {
+    const unsigned bx = (unsigned)std::min<int64_t>((g.dmul_elems + 63) / 64, 256);
+    k_spec_form<T, T2><<<dim3(bx, g.count, (R + 31) / 32), kFormThreads, 0, st>>>(
+        g.tab, der, reinterpret_cast<const T2*>(A) + goff, reinterpret_cast<const T2*>(B) + goff,
+        g.dmul_elems, g.N / 2 + 1, R, scale, out);
+    pl->launches[1] += 1;
+    goff += (int64_t)g.count * g.dmul_elems * R;
+  }
+  return cuda_status(cudaGetLastError(), "spectral_form");
 }
 
 agp_status check_block(agp_plan pl, const void* V, int64_t ldv, const void* Out, int64_t ldo,
@@ -1043,7 +1166,7 @@ agp_status adjoint_nfft_t(agp_plan_s* pl, int window, const T* V, int64_t ldv, i
     const int Rc = R - r0 < rc ? R - r0 : rc;
     AGP_CUDA(zero_grids<T>(g, rc, st));
     AGP_CUDA(spread_items_sel<T>(wins, nullptr, w.items, w.n_items, w.d, pl->s, rc, V + r0, ldv,
-                                 Rc, pl->use_tc, pl->err_dev, st));
+                                 Rc, pl->use_tc, pl->err_dev, pl->wait_limit, st));
     AGP_CUDA(fft_forward<T>(g, rc, st));
     const T2* spec = (const T2*)((w.d % 2) ? w.specA : w.specB);
     k_extract_spectrum<T, T2><<<nblk(w.cells * Rc, 256), 256, 0, st>>>(
@@ -1184,6 +1307,46 @@ agp_status agp_matvec(agp_plan pl, const void* V, int64_t ldv, void* Out, int64_
                            (float)scale, 0, true, st);
   return matvec_t<double>(pl, (const double*)V, ldv, (double*)Out, ldo, R, noise, scale, 0, true,
                           st);
+}
+
+agp_status agp_spectra_size(agp_plan pl, int R, int64_t* elems) {
+  if (!pl || R < 1 || !elems) return set_error(AGP_EINVAL, "bad arguments");
+  *elems = spectra_elems(pl, R);
+  return AGP_OK;
+}
+
+agp_status agp_matvec_spectra(agp_plan pl, const void* V, int64_t ldv, void* Out, int64_t ldo,
+                              int R, int add_noise, void* spec, void* stream) {
+  if (!pl || !spec) return set_error(AGP_EINVAL, "bad arguments");
+  if (Out) {
+    AGP_TRY(check_block(pl, V, ldv, Out, ldo, R));
+  } else if (!V || R < 1 || ldv < R) {
+    return set_error(AGP_EINVAL, "need V, R >= 1, ldv >= R");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double noise = add_noise ? pl->sigma_eps * pl->sigma_eps : 0.0;
+  const double scale = pl->sigma_f * pl->sigma_f;
+  if (pl->prec == AGP_F32)
+    return matvec_t<float>(pl, (const float*)V, ldv, (float*)Out, ldo, R, (float)noise,
+                           (float)scale, 0, true, st, spec);
+  return matvec_t<double>(pl, (const double*)V, ldv, (double*)Out, ldo, R, noise, scale, 0, true,
+                          st, spec);
+}
+
+agp_status agp_spectral_form(agp_plan pl, int which, const void* A, const void* B, int R,
+                             double* out, void* stream) {
+  if (!pl || !A || !B || !out || R < 1) return set_error(AGP_EINVAL, "bad arguments");
+  double scale = 0.0;
+  int der = 0;
+  switch (which) {
+    case -1: scale = pl->sigma_f * pl->sigma_f; break;
+    case AGP_D_ELL: scale = pl->sigma_f * pl->sigma_f; der = 1; break;
+    case AGP_D_SIGMA_F: scale = 2.0 * pl->sigma_f; break;
+    default: return set_error(AGP_EINVAL, "which must be -1, AGP_D_ELL or AGP_D_SIGMA_F");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl->prec == AGP_F32) return spectral_form_t<float>(pl, der, scale, A, B, R, out, st);
+  return spectral_form_t<double>(pl, der, scale, A, B, R, out, st);
 }
 
 agp_status agp_deriv_matvec(agp_plan pl, agp_param which, const void* V, int64_t ldv, void* Out,
@@ -1333,19 +1496,15 @@ agp_status agp_plan_set_boundary(agp_plan pl, double eps_b, int p, void* stream)
   return pl->prec == AGP_F32 ? compute_coeffs<float>(pl, st) : compute_coeffs<double>(pl, st);
 }
 
+agp_status agp_plan_set_wait_limit(agp_plan pl, int64_t polls) {
+  if (!pl || polls < 0) return set_error(AGP_EINVAL, "bad arguments");
+  pl->wait_limit = polls == 0 ? kDefaultWaitLimit : (long long)polls;
+  return AGP_OK;
+}
+
 agp_status agp_plan_check(agp_plan pl, void* stream) {
   if (!pl) return set_error(AGP_EINVAL, "bad arguments");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int err = 0;
-  AGP_CUDA(cudaMemcpyAsync(&err, pl->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-  AGP_CUDA(cudaStreamSynchronize(st));
-  if (err & kErrTimeout) {
-    const int keep = err & ~kErrTimeout;
-    AGP_CUDA(cudaMemcpyAsync(pl->err_dev, &keep, sizeof(int), cudaMemcpyHostToDevice, st));
-    AGP_CUDA(cudaStreamSynchronize(st));
-    return set_error(AGP_TIMEOUT, "a bounded wait in a tensor-core kernel expired");
-  }
-  return AGP_OK;
+  return timeout_check(pl, static_cast<cudaStream_t>(stream));
 }
 
 agp_status agp_plan_set_item_points(agp_plan pl, int points, void* stream) {

@@ -266,25 +266,34 @@ agp_status select_landmarks(agp_plan_s* pl, const CallerPoints<T>& cp, int k_req
   const int64_t n = pl->n;
   const int P = pl->P;
   const int kw = std::max(1, (int)std::min<int64_t>(n, (k_req + P - 1) / P));
-  unsigned long long* keys = nullptr;
+  const unsigned blocks = (unsigned)std::min<int64_t>(nblk(n, kFpsThreads), 1024);
+  int32_t* chosen = nullptr;
   double* dist = nullptr;
-  AGP_CUDA(cudaMallocAsync(&keys, sizeof(unsigned long long) * kw, st));
+  double* cand_d = nullptr;
+  int64_t* cand_i = nullptr;
+  AGP_CUDA(cudaMallocAsync(&chosen, sizeof(int32_t) * kw, st));
   AGP_CUDA(cudaMallocAsync(&dist, sizeof(double) * n, st));
+  AGP_CUDA(cudaMallocAsync(&cand_d, sizeof(double) * blocks, st));
+  AGP_CUDA(cudaMallocAsync(&cand_i, sizeof(int64_t) * blocks, st));
   all.clear();
+  std::vector<int32_t> hk(kw);
   for (int s = 0; s < P; ++s) {
-    AGP_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * kw, st));
+    AGP_CUDA(cudaMemsetAsync(chosen, 0, sizeof(int32_t) * kw, st));   // first landmark: point 0
     k_fill_double<<<nblk(n, 256), 256, 0, st>>>(dist, n, INFINITY);
-    const unsigned blocks = (unsigned)std::min<int64_t>(nblk(n, 256), 1024);
-    for (int step = 1; step < kw; ++step)
-      k_fps_step<T><<<blocks, 256, 0, st>>>(cp.xo[s], n, pl->win[s].d, step, keys, dist);
-    std::vector<unsigned long long> hk(kw);
-    AGP_CUDA(cudaMemcpyAsync(hk.data(), keys, sizeof(unsigned long long) * kw, cudaMemcpyDeviceToHost, st));
+    for (int step = 1; step < kw; ++step) {
+      k_fps_dist<T><<<blocks, kFpsThreads, 0, st>>>(cp.xo[s], n, pl->win[s].d, chosen, step, dist,
+                                                    cand_d, cand_i);
+      k_fps_pick<<<1, kFpsThreads, 0, st>>>(cand_d, cand_i, (int)blocks, chosen, step);
+    }
+    AGP_CUDA(cudaGetLastError());
+    AGP_CUDA(cudaMemcpyAsync(hk.data(), chosen, sizeof(int32_t) * kw, cudaMemcpyDeviceToHost, st));
     AGP_CUDA(cudaStreamSynchronize(st));
-    all.push_back(0);
-    for (int step = 1; step < kw; ++step) all.push_back((int32_t)(0xFFFFFFFFull - (hk[step] & 0xFFFFFFFFull)));
+    all.insert(all.end(), hk.begin(), hk.end());
   }
-  cudaFreeAsync(keys, st);
+  cudaFreeAsync(chosen, st);
   cudaFreeAsync(dist, st);
+  cudaFreeAsync(cand_d, st);
+  cudaFreeAsync(cand_i, st);
   std::sort(all.begin(), all.end());
   all.erase(std::unique(all.begin(), all.end()), all.end());
   return AGP_OK;

@@ -91,6 +91,10 @@ struct CgState {
   double* rz;       // r^T M^{-1} r (preconditioned runs)
   double* rznew;
   int pc;           // 1: preconditioned recursion
+  // residual replacement (reliable updates; null when off)
+  double* rr_ref;   // |r|^2 when r was last recomputed as b - K x
+  int* want;        // 1: recompute r of this column at the next check
+  int* fresh;       // 1: r of this column was recomputed in this iteration
 };
 
 __global__ void k_cg_start(CgState s, int R) {
@@ -100,6 +104,64 @@ __global__ void k_cg_start(CgState s, int R) {
   s.iters[c] = 0;
   s.relres[c] = s.rr[c] > 0.0 ? 1.0 : 0.0;
   s.active[c] = (s.rr[c] > 0.0 && s.maxit[c] > 0) ? 1 : 0;
+  if (s.rr_ref) {
+    s.rr_ref[c] = s.rr[c];
+    s.want[c] = 0;
+    s.fresh[c] = 0;
+  }
+}
+
+// Residual replacement (reliable updates, after Sleijpen and van der Vorst):
+// the recursion r_k = r_{k-1} - alpha K p drifts from b - K x_k when the
+// operator carries rounding errors (FP32 plans; atomic accumulation makes
+// them differ between applications). A column asks for its residual to be
+// recomputed as b - K x once |r| has fallen 10x since the last
+// recomputation, and before it may stop at the tolerance.
+constexpr double kReplaceDrop2 = 1e-2;     // |r|^2 ratio that asks for a recomputation
+constexpr double kReplaceJoin2 = 1e-1;     // ... and that joins one already asked for
+__global__ void k_cg_want(CgState s, const double* __restrict__ rr_new, int R) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  const double rn = rr_new[c];
+  const bool conv = sqrt(rn / s.bn2[c]) <= s.tol[c];
+  s.want[c] = s.active[c] && (rn < kReplaceDrop2 * s.rr_ref[c] || conv) ? 1
+              : (s.active[c] && rn < kReplaceJoin2 * s.rr_ref[c] ? 2 : 0);
+}
+
+// x in the plan precision as x_hi + x_lo: part 0 writes x_hi = x rounded,
+// part 1 x_lo = x - x_hi rounded (for FP64 plans x_lo = 0)
+template <typename T>
+__global__ void k_cg_xsplit(const double* __restrict__ x, T* __restrict__ xt, int part,
+                            int64_t m) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const T hi = (T)x[e];
+  xt[e] = part == 0 ? hi : (T)(x[e] - (double)hi);
+}
+
+// the columns being recomputed: r = b - q (part 0, q = K x_hi), then
+// r -= q (part 1, q = K x_lo), so that r = b - K x without x's rounding to
+// the plan precision
+template <typename T>
+__global__ void k_cg_replace(double* __restrict__ r, const T* __restrict__ B, int64_t ldb,
+                             const T* __restrict__ q, const int* __restrict__ sel, int part,
+                             int64_t n, int R) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * R) return;
+  const int64_t i = e / R;
+  const int c = (int)(e - i * R);
+  if (!sel[c]) return;
+  r[e] = (part == 0 ? (double)B[i * ldb + c] : r[e]) - (double)q[e];
+}
+
+__global__ void k_cg_replaced(CgState s, const double* __restrict__ rr_new, int R) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  if (s.want[c]) {
+    s.rr_ref[c] = rr_new[c];
+    s.fresh[c] = 1;
+  }
+  s.want[c] = 0;
 }
 
 __global__ void k_cg_alpha(CgState s, int R) {
@@ -152,9 +214,13 @@ __global__ void k_cg_beta(CgState s, const double* __restrict__ rr_new, int it, 
     s.iters[c] = it + 1;
     s.relres[c] = sqrt(rn / s.bn2[c]);
     s.rr[c] = rn;
-    if (!(rn > 0.0) || s.relres[c] <= s.tol[c] || it + 1 >= s.maxit[c]) s.active[c] = 0;
+    // with residual replacement a column stops at the tolerance only on a
+    // recomputed residual
+    const bool conv = s.relres[c] <= s.tol[c] && (!s.fresh || s.fresh[c]);
+    if (!(rn > 0.0) || conv || it + 1 >= s.maxit[c]) s.active[c] = 0;
   }
   s.beta[c] = s.active[c] ? b : 0.0;
+  if (s.fresh) s.fresh[c] = 0;
 }
 
 // p = r + beta p (FP64), and its copy in the plan precision for the next matvec
@@ -336,11 +402,16 @@ agp_status col_dot(const TA* A, int64_t lda, const TB* B, int64_t ldb, int64_t n
 // recursion is preconditioned CG: z = M^{-1} r,
 // alpha = r^T z / p^T K p, beta = r_new^T z_new / r^T z, p = z + beta p; the
 // stopping test stays on the unpreconditioned relative residual.
+// Batched (P)CG. With `reliable`, residual replacement (k_cg_want): at every
+// check (each check_every iterations, check_every > 0) the columns that ask
+// for it get r = b - K x, with x rounded to the plan precision for the
+// matvec; a column stops at the tolerance only right after such a
+// recomputation.
 template <typename T>
 agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int R,
                   const std::vector<int>& maxit_h, const std::vector<double>& tol_h, int check_every,
                   Workspace<T>& ws, cudaStream_t st, const Precond* pc = nullptr,
-                  const Afn* afn = nullptr) {
+                  const Afn* afn = nullptr, bool reliable = false) {
   const int64_t n = pl->n;
   const bool pcon = pc || afn;
   auto apply_pc = [&]() -> agp_status {
@@ -358,8 +429,8 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   if (pcon) AGP_CUDA(cudaMallocAsync(&ws.z, sizeof(double) * n * R, st));
   if (pcon) AGP_CUDA(cudaMallocAsync(&ws.rz0, sizeof(double) * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.partial, sizeof(double) * kMaxDotBlocks * R, st));
-  AGP_CUDA(cudaMallocAsync(&ws.scal, sizeof(double) * 11 * R, st));
-  AGP_CUDA(cudaMallocAsync(&ws.iscal, sizeof(int) * 3 * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.scal, sizeof(double) * 12 * R, st));
+  AGP_CUDA(cudaMallocAsync(&ws.iscal, sizeof(int) * 5 * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.ahist, sizeof(double) * std::max(1, maxall) * R, st));
   AGP_CUDA(cudaMallocAsync(&ws.bhist, sizeof(double) * std::max(1, maxall) * R, st));
   CgState s;
@@ -379,6 +450,10 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   s.rz = ws.scal + 9 * R;
   s.rznew = ws.scal + 10 * R;
   s.pc = pcon ? 1 : 0;
+  reliable = reliable && check_every > 0;
+  s.rr_ref = reliable ? ws.scal + 11 * R : nullptr;
+  s.want = reliable ? ws.iscal + 3 * R : nullptr;
+  s.fresh = reliable ? ws.iscal + 4 * R : nullptr;
   AGP_CUDA(cudaMemcpyAsync(s.maxit, maxit_h.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
   AGP_CUDA(cudaMemcpyAsync(s.tol, tol_h.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
 
@@ -400,7 +475,7 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
   AGP_TRY(col_dot(ws.r, R, ws.r, R, n, R, ws.partial, s.rr, st, pl));
   k_cg_start<<<gc, 128, 0, st>>>(s, R);
   pl->launches[3] += 1;
-  std::vector<int> act(R);
+  std::vector<int> act(R), want(R);
   for (int it = 0; it < maxall; ++it) {
     AGP_TRY(agp_matvec(pl, ws.pt, R, ws.q, R, R, 1, st));
     AGP_TRY(col_dot(ws.p, R, ws.q, R, n, R, ws.partial, s.pq, st, pl));
@@ -408,6 +483,26 @@ agp_status cg_run(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, in
     k_cg_xr<T><<<gb, 256, 0, st>>>(ws.x, ws.r, ws.p, ws.q, s.alpha, n, R);
     pl->launches[3] += 2;
     AGP_TRY(col_dot(ws.r, R, ws.r, R, n, R, ws.partial, rrnew, st, pl));
+    if (reliable && (it + 1) % check_every == 0) {
+      k_cg_want<<<gc, 128, 0, st>>>(s, rrnew, R);
+      AGP_CUDA(cudaMemcpyAsync(want.data(), s.want, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+      AGP_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int v : want) any = any || v == 1;
+      if (any) {   // r = b - K x for every column that asked (or would soon)
+        for (int part = 0; part < (sizeof(T) == 4 ? 2 : 1); ++part) {
+          k_cg_xsplit<T><<<gb, 256, 0, st>>>(ws.x, ws.pt, part, n * R);
+          AGP_TRY(agp_matvec(pl, ws.pt, R, ws.q, R, R, 1, st));
+          k_cg_replace<T><<<gb, 256, 0, st>>>(ws.r, B, ldb, ws.q, s.want, part, n, R);
+          pl->launches[3] += 2;
+        }
+        AGP_TRY(col_dot(ws.r, R, ws.r, R, n, R, ws.partial, rrnew, st, pl));
+        k_cg_replaced<<<gc, 128, 0, st>>>(s, rrnew, R);
+        pl->launches[3] += 1;
+      } else {
+        AGP_CUDA(cudaMemsetAsync(s.want, 0, sizeof(int) * R, st));
+      }
+    }
     if (pcon) {
       AGP_TRY(apply_pc());
       AGP_TRY(col_dot(ws.r, R, ws.z, R, n, R, ws.partial, s.rznew, st, pl));
@@ -443,7 +538,7 @@ agp_status pcg_t(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int
   std::vector<int> mi(R, maxit);
   std::vector<double> tl(R, rtol);
   AGP_TRY(cg_run<T>(pl, B, ldb, X, ldx, R, mi, tl, 5, ws, st, n_landmarks > 0 ? &pc : nullptr,
-                    afn));
+                    afn, true));
   std::vector<int> it(R);
   std::vector<double> rel(R);
   AGP_CUDA(cudaMemcpyAsync(it.data(), ws.iscal + R, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
@@ -950,11 +1045,13 @@ agp_status agp_pcg_solve(agp_plan pl, const void* B, int64_t ldb, void* Xsol, in
   if (n_landmarks < 0 || n_landmarks > kMaxLandmarks || (n_landmarks > 0 && R > 32))
     return set_error(AGP_EINVAL, "n_landmarks must be in [0, 480] (and R <= 32 when > 0)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (pl->prec == AGP_F32)
-    return pcg_t<float>(pl, (const float*)B, ldb, (float*)Xsol, ldx, R, rtol, maxit, n_landmarks,
-                        iters, relres, st);
-  return pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, n_landmarks,
-                       iters, relres, st);
+  const agp_status s =
+      pl->prec == AGP_F32
+          ? pcg_t<float>(pl, (const float*)B, ldb, (float*)Xsol, ldx, R, rtol, maxit, n_landmarks,
+                         iters, relres, st)
+          : pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit,
+                          n_landmarks, iters, relres, st);
+  return with_timeout_check(pl, s, st);
 }
 
 agp_status agp_afn_create(agp_afn* out, agp_plan pl, int n_landmarks, int fill, void* stream) {
@@ -1018,11 +1115,13 @@ agp_status agp_pcg_solve_afn(agp_plan pl, agp_afn afn, const void* B, int64_t ld
       af->sigma_eps != pl->sigma_eps || af->kernel != (int)pl->kernel)
     return set_error(AGP_EINVAL, "the AFN preconditioner was built for other hyperparameters");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (pl->prec == AGP_F32)
-    return pcg_t<float>(pl, (const float*)B, ldb, (float*)Xsol, ldx, R, rtol, maxit, 0, iters,
-                        relres, st, af);
-  return pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, 0, iters,
-                       relres, st, af);
+  const agp_status s =
+      pl->prec == AGP_F32
+          ? pcg_t<float>(pl, (const float*)B, ldb, (float*)Xsol, ldx, R, rtol, maxit, 0, iters,
+                         relres, st, af)
+          : pcg_t<double>(pl, (const double*)B, ldb, (double*)Xsol, ldx, R, rtol, maxit, 0, iters,
+                          relres, st, af);
+  return with_timeout_check(pl, s, st);
 }
 
 agp_status agp_nlml_grad_afn(agp_plan pl, agp_afn afn, const void* Y, const void* Wn,
@@ -1036,11 +1135,13 @@ agp_status agp_nlml_grad_afn(agp_plan pl, agp_afn afn, const void* Y, const void
       af->sigma_eps != pl->sigma_eps || af->kernel != (int)pl->kernel)
     return set_error(AGP_EINVAL, "the AFN preconditioner was built for other hyperparameters");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (pl->prec == AGP_F32)
-    return nlml_afn_t<float>(pl, af, (const float*)Y, (const float*)Wn, ldwn, nz, lanczos_steps,
-                             rtol, maxit, nlml, grad, st);
-  return nlml_afn_t<double>(pl, af, (const double*)Y, (const double*)Wn, ldwn, nz, lanczos_steps,
-                            rtol, maxit, nlml, grad, st);
+  const agp_status s =
+      pl->prec == AGP_F32
+          ? nlml_afn_t<float>(pl, af, (const float*)Y, (const float*)Wn, ldwn, nz, lanczos_steps,
+                              rtol, maxit, nlml, grad, st)
+          : nlml_afn_t<double>(pl, af, (const double*)Y, (const double*)Wn, ldwn, nz,
+                               lanczos_steps, rtol, maxit, nlml, grad, st);
+  return with_timeout_check(pl, s, st);
 }
 
 agp_status agp_plan_landmarks(agp_plan pl, int n_landmarks, int32_t* idx, int cap, int* count,
@@ -1068,11 +1169,13 @@ agp_status agp_nlml_grad_pc(agp_plan pl, const void* Y, const void* Wn, int64_t 
   if (n_landmarks < 1 || n_landmarks > kMaxLandmarks)
     return set_error(AGP_EINVAL, "n_landmarks must be in [1, 480]");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (pl->prec == AGP_F32)
-    return nlml_pc_t<float>(pl, (const float*)Y, (const float*)Wn, ldwn, Wk, nz, n_landmarks,
-                            lanczos_steps, rtol, maxit, nlml, grad, st);
-  return nlml_pc_t<double>(pl, (const double*)Y, (const double*)Wn, ldwn, Wk, nz, n_landmarks,
-                           lanczos_steps, rtol, maxit, nlml, grad, st);
+  const agp_status s =
+      pl->prec == AGP_F32
+          ? nlml_pc_t<float>(pl, (const float*)Y, (const float*)Wn, ldwn, Wk, nz, n_landmarks,
+                             lanczos_steps, rtol, maxit, nlml, grad, st)
+          : nlml_pc_t<double>(pl, (const double*)Y, (const double*)Wn, ldwn, Wk, nz, n_landmarks,
+                              lanczos_steps, rtol, maxit, nlml, grad, st);
+  return with_timeout_check(pl, s, st);
 }
 
 agp_status agp_dot_columns(agp_plan pl, const void* A, int64_t lda, const void* B, int64_t ldb,
@@ -1095,7 +1198,7 @@ agp_status agp_dot_columns(agp_plan pl, const void* A, int64_t lda, const void* 
     s = cuda_status(e, "agp_dot_columns");
   }
   cudaFreeAsync(buf, st);
-  return s;
+  return with_timeout_check(pl, s, st);
 }
 
 agp_status agp_dot_columns_static(agp_prec prec, const void* A, int64_t lda, const void* B,
@@ -1127,11 +1230,13 @@ agp_status agp_nlml_grad(agp_plan pl, const void* Y, const void* Z, int64_t ldz,
       lanczos_steps > kMaxLanczos || !nlml || !grad || (rtol > 0 && maxit < 1))
     return set_error(AGP_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (pl->prec == AGP_F32)
-    return nlml_t<float>(pl, (const float*)Y, (const float*)Z, ldz, nz, lanczos_steps, rtol, maxit,
-                         nlml, grad, st);
-  return nlml_t<double>(pl, (const double*)Y, (const double*)Z, ldz, nz, lanczos_steps, rtol, maxit,
-                        nlml, grad, st);
+  const agp_status s =
+      pl->prec == AGP_F32
+          ? nlml_t<float>(pl, (const float*)Y, (const float*)Z, ldz, nz, lanczos_steps, rtol,
+                          maxit, nlml, grad, st)
+          : nlml_t<double>(pl, (const double*)Y, (const double*)Z, ldz, nz, lanczos_steps, rtol,
+                           maxit, nlml, grad, st);
+  return with_timeout_check(pl, s, st);
 }
 
 }  // extern "C"

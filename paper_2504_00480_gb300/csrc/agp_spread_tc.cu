@@ -28,9 +28,11 @@
 // to the buffer's mbarrier while the next chunk is formed in the other
 // buffer. The epilogue reads TMEM (warp w owns lanes 32 (w % 4) .. + 31 =
 // rows), transposes each 32 x 16 tile through shared memory and adds the
-// block into the window's grid with vector atomics, four lanes per row. Every mbarrier wait is bounded: on expiry the CTA records
-// a timeout in the plan's error word, waits (bounded) for its MMAs and
-// releases its TMEM.
+// block into the window's grid with vector atomics, four lanes per row.
+// Every mbarrier wait is bounded (the plan's wait limit) and its outcome is
+// agreed by the CTA at the chunk's barrier: on expiry the CTA stops issuing
+// MMAs, drains the committed ones, records a timeout in the plan's error
+// word, skips the epilogue and releases its TMEM.
 #include <type_traits>
 
 #include "agp_nufft_kernels.cuh"
@@ -137,7 +139,7 @@ template <int S>
 __global__ void __launch_bounds__(kTcThreads)
 k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict__ io,
             const int4* __restrict__ items, const float* __restrict__ V, int64_t ldv, int R,
-            int rc, int* __restrict__ err) {
+            int rc, int* __restrict__ err, long long spin) {
   using Sh = TcSpreadShape<S>;
   constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, WPS = Sh::WPS, VS = Sh::VS;
   constexpr int KC = kTcKC, RH = kTcRH;
@@ -241,11 +243,12 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
+  int issued = 0;                          // chunks whose MMAs are committed
   for (int c = 0; c < nchunk; ++c) {
     const int b = c & 1;
     stage(c + PD, pf);                     // its buffer was last read by chunk c - 1
     pf = perm_of(c + PD + 1);
-    if (c >= 2 && !mbar_wait(&bar[b], ((c - 2) >> 1) & 1)) ok = false;   // MMAs of chunk c-2
+    if (c >= 2 && !mbar_wait(&bar[b], ((c - 2) >> 1) & 1, spin)) ok = false;   // MMAs of chunk c-2
     const float* sw = stg(c % kTcStages);
     const float* sv = sw + Sh::STG_W;
     const bool live = kk < min(KC, m - c * KC);
@@ -278,7 +281,10 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
     cp_async_wait<PD - 1>();              // chunk c + 1 staged (this thread's copies)
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();                      // operands of chunk c and staging of c + 1 complete
+    // operands of chunk c and staging of c + 1 complete; the CTA agrees on
+    // whether every wait so far succeeded (on failure: issue nothing more)
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       // descriptors differ only in the start address field (address >> 4)
@@ -293,9 +299,16 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
       }
       mma_commit(&bar[b]);
     }
+    issued = c + 1;
   }
-  // the last commit covers every MMA of this CTA
-  if (!mbar_wait(&bar[(nchunk - 1) & 1], ((nchunk - 1) >> 1) & 1)) ok = false;
+  // The last commit covers every MMA of this CTA. Its barrier has no other
+  // phase pending: the wait for the chunk two before it succeeded (else the
+  // chunk would not have been issued).
+  const int lc = issued - 1;
+  const bool fin = issued == 0 || mbar_wait(&bar[lc & 1], (lc >> 1) & 1, spin);
+  ok = __syncthreads_and(ok && fin);
+  if (!ok && issued > 0) mbar_wait(&bar[lc & 1], (lc >> 1) & 1);   // drain before TMEM is freed
+  cp_async_wait<0>();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows (t1, t2)); with more
@@ -359,14 +372,14 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
 template <int S>
 cudaError_t spread_tc_s(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
                         int64_t n_items, const float* V, int64_t ldv, int R, int rc, int* err,
-                        cudaStream_t st) {
+                        long long spin, cudaStream_t st) {
   using Sh = TcSpreadShape<S>;
   cudaError_t e = cudaFuncSetAttribute(k_spread_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Sh::SMEM);
   if (e != cudaSuccess) return e;
   if (n_items <= 0) return cudaSuccess;
   k_spread_tc<S><<<(unsigned)(rc / 16 * n_items), kTcThreads, Sh::SMEM, st>>>(
-      wins, io, items, V, ldv, R, rc, err);
+      wins, io, items, V, ldv, R, rc, err, spin);
   return cudaGetLastError();
 }
 
@@ -378,10 +391,10 @@ bool spread_tc_supported(int d, int s, int RC) {
 
 cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, const int4* items,
                             int64_t n_items, int s, const float* V, int64_t ldv, int R, int rc,
-                            int* err, cudaStream_t st) {
+                            int* err, long long spin, cudaStream_t st) {
   switch (s) {
-    case 4: return spread_tc_s<4>(wins, io, items, n_items, V, ldv, R, rc, err, st);
-    case 5: return spread_tc_s<5>(wins, io, items, n_items, V, ldv, R, rc, err, st);
+    case 4: return spread_tc_s<4>(wins, io, items, n_items, V, ldv, R, rc, err, spin, st);
+    case 5: return spread_tc_s<5>(wins, io, items, n_items, V, ldv, R, rc, err, spin, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -2,6 +2,15 @@
 // shared-memory matrix and instruction descriptors (K-major operands without
 // swizzle: 8-row x 16-byte core matrices), the TF32 hi/lo split, MMA issue
 // and commit, and a bounded mbarrier wait.
+//
+// Wait discipline of the kernels that use them: every mbarrier wait polls at
+// most `limit` times (the plan's wait limit, kTcSpinLimit by default); the
+// outcome is agreed by the whole CTA at the next CTA barrier
+// (__syncthreads_and), so every branch that follows -- MMA issue, TMEM loads,
+// the epilogue -- is CTA-uniform. After a failed wait a CTA issues no further
+// MMAs, drains the ones it committed with the fixed bound kTcSpinLimit,
+// waits for its cp.async copies, sets the timeout bit in the error word,
+// skips its epilogue and releases its TMEM.
 #pragma once
 
 #include <stdint.h>
@@ -49,11 +58,21 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                ::"r"(smem_u32(bar)));
 }
 
-// bounded wait for the given phase parity; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait for the given phase parity (at most `limit` polls); false on
+// expiry. The first poll is a non-blocking test, the later ones may suspend
+// the thread for a while (try_wait), so a limit of 1 gives up at once unless
+// the phase is already complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kTcSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kTcSpinLimit; ++it) {
-    uint32_t done;
+  if (limit < 1) return false;
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done) : "r"(a), "r"(parity));
+  if (done) return true;
+  for (long long it = 1; it < limit; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"

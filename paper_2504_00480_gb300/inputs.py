@@ -126,14 +126,17 @@ def autograd(n: int = 100_000, seed: int = 1, R: int = 1) -> Workload:
                     extra={"W": W})
 
 
-def batched_pcg(n: int = 500_000, seed: int = 2, R: int = 32) -> Workload:
+def batched_pcg(n: int = 500_000, seed: int = 2, R: int = 32, ell: float = 0.5,
+                N: int = 64) -> Workload:
     """p=12 uniform[-1,1] features, four consecutive d=3 windows, Matern(1/2).
 
     Labels y = sum_w sin(2 pi x_w1) cos(pi x_w2) x_w3 + N(0, 0.05^2) on the raw
     features; right-hand sides [y, R-1 Rademacher probes]. Grid N = 64 per
-    dimension: at N = 32 the Fourier-truncated Matern operator has negative
-    coefficients that make K_hat indefinite on this point set already at
-    n = 20,000 (CG diverges in FP64)."""
+    dimension by default: at N = 32 the Fourier-truncated Matern operator
+    with ell = 0.5 has negative coefficients that make K_hat indefinite on
+    this point set already at n = 20,000 (CG diverges in FP64). ``ell`` and
+    ``N`` select a variant (the truncated series has no negative coefficient
+    for ell <= 0.09 at N = 32)."""
     rng = np.random.default_rng(seed)
     raw = rng.uniform(-1.0, 1.0, size=(n, 12))
     windows = [[0, 1, 2], [3, 4, 5], [6, 7, 8], [9, 10, 11]]
@@ -143,7 +146,7 @@ def batched_pcg(n: int = 500_000, seed: int = 2, R: int = 32) -> Workload:
     y += 0.05 * rng.standard_normal(n)
     V = np.concatenate([y[:, None], rademacher(n, R - 1, seed + 100)], axis=1)
     return Workload("batched_pcg", _points(raw, np.float32), windows, "matern12",
-                    0.5, 1.0, 0.05, [64] * 4, 5, np.float32, V=V, y=y)
+                    float(ell), 1.0, 0.05, [int(N)] * 4, 5, np.float32, V=V, y=y)
 
 
 def nlml_grad(n: int = 1_000_000, seed: int = 3, R: int = 32) -> Workload:

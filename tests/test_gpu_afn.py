@@ -38,6 +38,21 @@ def points(n, p, seed, dtype):
     return inputs.to_precision(X, dtype).astype(np.float64), rng
 
 
+def compare_pattern(J, want, rows, rel_bound=1e-12):
+    """Rows of the device pattern against the oracle's (J_t, gap_t): equal,
+    with -1 after the row's entries, except rows whose deciding gap is a
+    near-tie (positive, below rel_bound x the distance scale), which are
+    skipped and counted. Returns the number of skipped rows."""
+    skipped = 0
+    for t, (Jt, gap) in zip(rows, want):
+        if 0.0 < gap <= rel_bound:
+            skipped += 1
+            continue
+        row = J[t]
+        assert list(row[:len(Jt)]) == Jt and np.all(row[len(Jt):] == -1), t
+    return skipped
+
+
 def make(agp, X, W, dtype, kind, th, N=32, s=5):
     tdt = torch.float32 if dtype == np.float32 else torch.float64
     return agp.Plan(torch.tensor(X, dtype=tdt, device=DEV), W, N, s, kind, *th)
@@ -57,10 +72,10 @@ def test_pattern_inverse_and_logdet_match_oracle(agp, dtype, kind, th, fill):
     lm, J = afn.pattern()
     want_lm = O.additive_landmarks(X, W, 24)
     np.testing.assert_array_equal(lm, want_lm)
-    want_J = O.fsai_pattern(X, W, want_lm, fill)
-    for t, Jt in enumerate(want_J):
-        row = J[t]
-        assert list(row[:len(Jt)]) == Jt and np.all(row[len(Jt):] == -1), t
+    want = O.fsai_pattern_gaps(X, W, want_lm, fill)
+    want_J = [Jt for Jt, _ in want]
+    skipped = compare_pattern(J, want, range(len(want)))
+    assert skipped <= len(want) // 100, skipped
     L, F, KLL, KFL, _, G, _ = O.afn_factors(X, W, kind, *th, want_lm, fill)
     V = rng.standard_normal((len(X), 6))
     got = afn.apply(torch.tensor(V, device=DEV)).cpu().numpy()
@@ -116,9 +131,8 @@ def test_large_fp32_block_identity_and_sampled_pattern(agp):
     lm, J = afn.pattern()
     np.testing.assert_array_equal(lm, O.additive_landmarks(X, W, 30))
     sample = [0, 1, 2, 49, 50, 51, 1234, 30_000, n - len(lm) - 1]
-    want = O.fsai_pattern(X, W, lm, 50, rows=sample)
-    for t, Jt in zip(sample, want):
-        assert list(J[t][:len(Jt)]) == Jt, t
+    want = O.fsai_pattern_gaps(X, W, lm, 50, rows=sample)
+    assert compare_pattern(J, want, sample) == 0
     V = rng.standard_normal((n, 4))
     Y = afn.apply(torch.tensor(V, device=DEV)).cpu().numpy()
     KY = O.dense_matvec(X, W, "gauss", *th, Y, rows=lm)

@@ -1,0 +1,138 @@
+"""The autograd Function at the autograd workload's own size: n = 100,000
+points, p = 9, three d = 3 windows, Gaussian ell = 0.2, sigma_f = 1,
+sigma_eps = 0.1, N = 32, s = 5, FP32 plan (12 right-hand sides, so the
+spreading and interpolation run on the tensor cores in a 16-column pass).
+
+L = sum(W * K_hat(theta) V). Checked:
+  * dL/dV = K_hat W against the oracle's truncated sum on sampled rows;
+  * dL/d(ell, sigma_f, sigma_eps) against the oracle's truncated sum
+    (Sec. 3.1 eq. (3.3), Sec. 3.2 eq. (3.4)) over all n points;
+  * the spectral quadratic form (agp_spectral_form) against the derivative
+    matvec followed by a dot product, on the same plan;
+  * the same gradients on an FP64 plan against central finite differences
+    of L (h = 1e-4);
+  * the FP32 gradients on the first 5,000 points against the dense
+    kernel-sum oracle, within the truncated series' own distance from it.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_00480_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
+DEV = "cuda:0"
+R = 12
+
+
+@pytest.fixture(scope="module")
+def agp():
+    from paper_2504_00480_gb300 import agp as A
+    from paper_2504_00480_gb300 import build
+    build.build()
+    A.load_library()
+    return A
+
+
+@pytest.fixture(scope="module")
+def work():
+    w = inputs.autograd(n=100_000, R=R)
+    w.V = inputs.to_precision(w.V, np.float32).astype(np.float64)
+    w.extra["W"] = inputs.to_precision(w.extra["W"], np.float32).astype(np.float64)
+    return w
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def grads(agp, plan, w, dtype, V=None, Wt=None, need_v=True):
+    from paper_2504_00480_gb300.autograd import additive_kernel_matvec
+    V = w.V if V is None else V
+    Wt = w.extra["W"] if Wt is None else Wt
+    Vt = torch.tensor(V, dtype=dtype, device=DEV, requires_grad=need_v)
+    th = [torch.tensor(v, dtype=torch.float64, requires_grad=True)
+          for v in (w.ell, w.sigma_f, w.sigma_eps)]
+    Wd = torch.tensor(Wt, dtype=dtype, device=DEV)
+    L = (Wd.double() * additive_kernel_matvec(plan, Vt, *th).double()).sum()
+    out = torch.autograd.grad(L, ([Vt] if need_v else []) + th)
+    gV = out[0].double().cpu().numpy() if need_v else None
+    g = {k: float(v) for k, v in zip(["ell", "sigma_f", "sigma_eps"], out[-3:])}
+    return float(L), gV, g
+
+
+def test_fp32_tensor_core_gradients_against_the_oracle(agp, work):
+    w = work
+    plan = agp.Plan(torch.tensor(w.X, dtype=torch.float32, device=DEV), w.windows, w.N,
+                    w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
+    plan.set_tensor_cores(True)
+    _, gV, g = grads(agp, plan, w, torch.float32)
+    Wt = w.extra["W"]
+    rows = np.sort(np.random.default_rng(9).choice(w.n, 1000, replace=False))
+    refV = O.truncated_operators(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps, Wt,
+                                 w.N, rows=rows)["K"]
+    assert rel(gV[rows], refV) <= 1e-4
+    ref = O.truncated_forms(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps, Wt, w.V,
+                            w.N)
+    for k in g:
+        assert g[k] == pytest.approx(ref[k], rel=1e-4), (k, g[k], ref[k])
+    # the backward's spectral form equals the derivative matvec + dot product
+    Vt = torch.tensor(w.V, dtype=torch.float32, device=DEV)
+    Wd = torch.tensor(Wt, dtype=torch.float32, device=DEV)
+    _, sV = plan.spectra(Vt)
+    _, sW = plan.spectra(Wd)
+    for which in ["ell", "sigma_f"]:
+        form = plan.spectral_form(which, sW, sV, R).cpu().numpy()
+        dot = agp.agp_dot_columns(plan.handle, Wd, plan.deriv_matvec(which, Vt))
+        np.testing.assert_allclose(form, dot, rtol=2e-5, atol=2e-5 * np.abs(dot).max())
+    plan.check()
+    plan.close()
+
+
+def test_fp64_gradients_against_finite_differences(agp, work):
+    from paper_2504_00480_gb300.autograd import additive_kernel_matvec
+    w = work
+    V, Wt = w.V[:, :2], w.extra["W"][:, :2]
+    plan = agp.Plan(torch.tensor(w.X, dtype=torch.float64, device=DEV), w.windows, w.N,
+                    w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
+    _, gV, g = grads(agp, plan, w, torch.float64, V=V, Wt=Wt)
+    Vt = torch.tensor(V, device=DEV)
+    Wd = torch.tensor(Wt, device=DEV)
+    h = 1e-4
+    base = dict(ell=w.ell, sigma_f=w.sigma_f, sigma_eps=w.sigma_eps)
+
+    def L_at(t, Vx=Vt):
+        with torch.no_grad():
+            return float((Wd * additive_kernel_matvec(plan, Vx, t["ell"], t["sigma_f"],
+                                                      t["sigma_eps"])).sum())
+    for k in g:
+        fd = (L_at(dict(base, **{k: base[k] + h})) - L_at(dict(base, **{k: base[k] - h}))) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-6), k
+    # dL/dV along a random direction U: L is linear in V
+    U = torch.tensor(np.random.default_rng(4).standard_normal(V.shape), device=DEV)
+    fdv = (L_at(base, Vt + h * U) - L_at(base, Vt - h * U)) / (2 * h)
+    assert float(np.sum(gV * U.cpu().numpy())) == pytest.approx(fdv, rel=1e-7)
+    plan.close()
+
+
+def test_fp32_gradients_on_a_subset_against_the_dense_oracle(agp, work):
+    w = inputs.subset(work, 5000)
+    Wt = w.extra["W"]
+    plan = agp.Plan(torch.tensor(w.X, dtype=torch.float32, device=DEV), w.windows, w.N,
+                    w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
+    plan.set_tensor_cores(True)
+    _, _, g = grads(agp, plan, w, torch.float32, need_v=False)
+    trunc = O.truncated_forms(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps, Wt, w.V,
+                              w.N)
+    for k in g:
+        dense = float(np.sum(Wt * O.dense_deriv_matvec(w.X, w.windows, w.kernel, w.ell,
+                                                       w.sigma_f, w.sigma_eps, w.V, k)))
+        # the GPU gradient sits within the truncated series' own distance from
+        # the dense gradient (no boundary smoothing), plus the FP32 tolerance
+        gap = abs(trunc[k] - dense)
+        assert abs(g[k] - dense) <= gap + 1e-4 * abs(dense), (k, g[k], trunc[k], dense)
+        assert gap <= 2e-3 * abs(dense), (k, gap, dense)
+    plan.close()

@@ -96,3 +96,30 @@ def test_tc_spread_full_size_sampled_rows(agp):
     want = O.truncated_matvec(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps,
                               w.V[:, :1], w.N, rows=rows)
     assert rel(got[rows, :1].cpu().numpy(), want) <= 1e-4
+
+
+def test_tc_full_size_every_operator_sampled_rows(agp):
+    """The benchmarked launch configuration (n = 1,000,000, windows d = 3, 3,
+    2, 32 right-hand sides in one 32-column pass, tensor-core kernels):
+    K_hat and the three derivative operators on 8 columns (both 16-column
+    halves of the grid) x 256 sampled rows against the oracle's truncated
+    sums over all n points."""
+    w = inputs.nlml_grad(R=32)
+    X = torch.tensor(w.X, dtype=torch.float32, device=DEV)
+    V = torch.tensor(w.V, dtype=torch.float32, device=DEV)
+    plan = agp.Plan(X, w.windows, w.N, w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
+    plan.set_tensor_cores(True)
+    got = {"K": plan.matvec(V)}
+    for which in ["ell", "sigma_f", "sigma_eps"]:
+        got[which] = plan.deriv_matvec(which, V)
+    plan.check()
+    cols = [0, 3, 7, 12, 17, 22, 26, 31]
+    rows = np.sort(np.random.default_rng(5).choice(w.X.shape[0], 256, replace=False))
+    want = O.truncated_operators(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps,
+                                 w.V[:, cols].astype(np.float32).astype(np.float64), w.N,
+                                 rows=rows)
+    for which, g in got.items():
+        gs = g[rows][:, cols].double().cpu().numpy()
+        for j in range(len(cols)):
+            assert rel(gs[:, j], want[which][:, j]) <= 1e-4, (which, cols[j])
+    plan.close()

@@ -175,6 +175,67 @@ def test_truncated_rows_and_window_bandwidths():
     np.testing.assert_allclose(full, one, rtol=1e-13)
 
 
+@pytest.mark.parametrize("kind", KINDS)
+def test_truncated_operators_pinned(kind):
+    # all four operators from one set of inner sums: on lattice points they
+    # are the dense operators (the interpolation property above), and off the
+    # lattice the ell and sigma_f operators are the central differences of the
+    # K output in those parameters (sigma_eps: of the noise term)
+    rng = np.random.default_rng(16)
+    N = 16
+    X = _lattice_points(rng, 60, 5, N)
+    v = rng.standard_normal((60, 2))
+    W = [[0, 1, 2], [3, 4]]
+    ops = O.truncated_operators(X, W, kind, 0.2, 1.3, 0.4, v, N)
+    np.testing.assert_allclose(ops["K"], O.dense_matvec(X, W, kind, 0.2, 1.3, 0.4, v),
+                               rtol=1e-11, atol=1e-12)
+    for which in ["ell", "sigma_f", "sigma_eps"]:
+        np.testing.assert_allclose(
+            ops[which], O.dense_deriv_matvec(X, W, kind, 0.2, 1.3, 0.4, v, which),
+            rtol=1e-10, atol=1e-11)
+    Xr = rng.uniform(-0.24, 0.24, size=(50, 5))
+    rows = [0, 7, 49]
+    ops = O.truncated_operators(Xr, W, kind, 0.25, 1.2, 0.3, v[:50], [8, 16], rows=rows)
+    h = 1e-5
+    th = {"ell": 0.25, "sigma_f": 1.2, "sigma_eps": 0.3}
+    for which in th:
+        up, dn = dict(th), dict(th)
+        up[which] += h
+        dn[which] -= h
+        fu = O.truncated_operators(Xr, W, kind, up["ell"], up["sigma_f"], up["sigma_eps"],
+                                   v[:50], [8, 16], rows=rows)["K"]
+        fd = O.truncated_operators(Xr, W, kind, dn["ell"], dn["sigma_f"], dn["sigma_eps"],
+                                   v[:50], [8, 16], rows=rows)["K"]
+        np.testing.assert_allclose(ops[which], (fu - fd) / (2 * h), rtol=1e-6,
+                                   atol=1e-7 * np.abs(ops[which]).max())
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_truncated_forms_pinned(kind):
+    # on lattice points the forms are those of the dense operators; off the
+    # lattice they are the column sums of G * (operator V) and symmetric in
+    # (G, V)
+    rng = np.random.default_rng(17)
+    N = 16
+    X = _lattice_points(rng, 50, 5, N)
+    G = rng.standard_normal((50, 3))
+    V = rng.standard_normal((50, 3))
+    W = [[0, 1, 2], [3, 4]]
+    f = O.truncated_forms(X, W, kind, 0.2, 1.3, 0.4, G, V, N)
+    assert f["K"] == pytest.approx(float(np.sum(G * O.dense_matvec(X, W, kind, 0.2, 1.3, 0.4, V))),
+                                   rel=1e-10)
+    for which in ["ell", "sigma_f", "sigma_eps"]:
+        ref = float(np.sum(G * O.dense_deriv_matvec(X, W, kind, 0.2, 1.3, 0.4, V, which)))
+        assert f[which] == pytest.approx(ref, rel=1e-9, abs=1e-11), which
+    Xr = rng.uniform(-0.24, 0.24, size=(50, 5))
+    f = O.truncated_forms(Xr, W, kind, 0.25, 1.2, 0.3, G, V, [8, 16])
+    ops = O.truncated_operators(Xr, W, kind, 0.25, 1.2, 0.3, V, [8, 16])
+    g = O.truncated_forms(Xr, W, kind, 0.25, 1.2, 0.3, V, G, [8, 16])
+    for which in ops:
+        assert f[which] == pytest.approx(float(np.sum(G * ops[which])), rel=1e-11), which
+        assert f[which] == pytest.approx(g[which], rel=1e-11), which
+
+
 def test_ndft_pair_single_point():
     # c_k of a single unit mass at x is e^{-2 pi i k.x}; the NDFT of
     # C_k = delta_{k,k0} is e^{2 pi i k0.x}.

@@ -6,7 +6,9 @@ latency-critical loop that must not trigger an allocation. For them the
 library keeps the scratch of this reduction in a fixed device array. This
 test calls the allocation-free entry point through the C ABI and checks it
 against the allocating one (agp_dot_columns) on two calls in a row, so that
-stale scratch from the first call cannot go unnoticed. It lives in a file of
+stale scratch from the first call cannot go unnoticed, and both against the
+column sums of the elementwise products computed in FP64 on the host
+(numpy), a reference that shares no code with the library. It lives in a file of
 its own that pytest collects last; it passes alone in a fresh process and
 after the other tests.
 """
@@ -53,6 +55,13 @@ def test_static_dot_matches_allocating_dot_on_two_calls(agp, dtype):
         got = out.cpu().numpy()
         # both accumulate in FP64; only the split into partial sums differs
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+        # independent reference: FP64 products of the same (rounded) inputs,
+        # summed on the host
+        An = A.cpu().double().numpy()
+        Bn = B.cpu().double().numpy()
+        host = np.sum(An * Bn, axis=0)
+        scale = np.sum(np.abs(An * Bn), axis=0)
+        np.testing.assert_allclose(got, host, rtol=0, atol=1e-12 * scale.max())
     plan.close()
 
 
