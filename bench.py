@@ -334,6 +334,7 @@ def run_gpu(args):
     # around a device synchronisation.
     plan.set_hyper(w.ell, w.sigma_f, w.sigma_eps)
     nl = time_nlml(agp, plan, V, args.nlml_reps, dev)
+    ag = time_autograd(plan, V, dev)
     nl_pc = None if args.no_nlml_pc else time_nlml_pc(agp, plan, V, dev,
                                                       n_landmarks=10 * len(w.windows))
     agp.agp_matvec(plan.handle, V, Out, True)
@@ -341,7 +342,7 @@ def run_gpu(args):
     # one right-hand side per call
     plain = None
     if not args.no_plain:
-        plain = time_plain_fp64(agp, w, V, Out, args.plain_reps, dev)
+        plain = time_plain_fp64(agp, w, V, Out, args.plain_reps, dev, nl)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -371,7 +372,7 @@ def run_gpu(args):
                 "stages_ms_per_step": {s: prof[s]["ms"] / args.steps for s in prof},
                 "stage_launches_per_step": {s: prof[s]["launches"] / args.steps for s in prof},
                 "clocks": clocks, "cpu_baseline": cpu,
-                "nlml_grad": nl, "nlml_grad_pc": nl_pc, "plain_fp64": plain}
+                "nlml_grad": nl, "nlml_grad_pc": nl_pc, "autograd": ag, "plain_fp64": plain}
         if plain is not None:
             plain["batched_fp32_over_plain_fp64"] = value / plain["value"]
         print(json.dumps(line), flush=True)
@@ -486,7 +487,43 @@ def time_nlml_pc(agp, plan, V, dev, n_landmarks=30, nz=16, steps=20):
     return res
 
 
-def time_plain_fp64(agp, w, V32, Out32, reps, dev):
+def time_autograd(plan, V, dev):
+    """Forward and backward of the autograd Function on the benchmark plan:
+    L = sum(W * K_hat(theta) V) with V fixed data and theta = (ell, sigma_f,
+    sigma_eps) requiring gradients. The backward forms only the spectra of W
+    (spread + forward DFT) and the spectral form of eq. (3.4); timed next to
+    one derivative matvec (the full spread-DFT-multiply-DFT-interpolate
+    pipeline the spectral form replaces)."""
+    import torch
+    from paper_2504_00480_gb300.autograd import additive_kernel_matvec
+    Wt = torch.flip(V, dims=[1]).contiguous()
+    th = [torch.tensor(v, dtype=torch.float64, requires_grad=True)
+          for v in (plan.ell, plan.sigma_f, plan.sigma_eps)]
+
+    def run():
+        L = (Wt.double() * additive_kernel_matvec(plan, V, *th).double()).sum()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g = torch.autograd.grad(L, th)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, g
+
+    run()
+    bw = [run()[0] for _ in range(3)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    D = plan.deriv_matvec("ell", V)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    del D
+    return {"rhs": V.shape[1], "backward_ms": 1e3 * statistics.median(bw),
+            "deriv_matvec_ms": e0.elapsed_time(e1),
+            "note": "backward (host-timed, synchronised): spectra of W + spectral forms + FP64 "
+                    "dot products; dL/dV not requested"}
+
+
+def time_plain_fp64(agp, w, V32, Out32, reps, dev, nl32=None):
     import torch
     X64 = torch.tensor(w.X, dtype=torch.float32, device=dev).double()
     p64 = agp.Plan(X64, w.windows, w.N, w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
@@ -504,9 +541,19 @@ def time_plain_fp64(agp, w, V32, Out32, reps, dev):
     ms = e0.elapsed_time(e1) / reps
     # accuracy of the batched FP32 result against the FP64 one (column 0)
     rel = float(torch.linalg.norm(Out32[:, 0].double() - o[:, 0]) / torch.linalg.norm(o[:, 0]))
+    # per-result error of the NLML estimate: the FP32 plan's value and
+    # gradient against the FP64 plan's on the same y, probes and steps
+    nl_err = None
+    if nl32 is not None and nl32.get("value") is not None:
+        y = V32[:, 0].double().contiguous()
+        Z = V32[:, 1:17].double()
+        nl64, g64 = p64.nlml_grad(y, Z, lanczos_steps=20)
+        nl_err = {"nlml_rel": abs(nl32["nlml"] - nl64) / abs(nl64),
+                  "grad_rel": {k: abs(nl32["grad"][k] - g64[k]) / abs(g64[k]) for k in g64},
+                  "fp64": {"nlml": nl64, "grad": g64}}
     p64.close()
     return {"value": 1e3 / ms, "unit": "MVM/s", "ms_per_mvm": ms, "reps": reps, "rhs": 1,
-            "dtype": "f64", "fp32_rel_l2_vs_fp64": rel}
+            "dtype": "f64", "fp32_rel_l2_vs_fp64": rel, "nlml_grad_fp32_vs_fp64": nl_err}
 
 
 def main():

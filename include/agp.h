@@ -262,7 +262,11 @@ agp_status agp_plan_landmarks(agp_plan plan, int n_landmarks, int32_t* idx, int 
  * operands split into a rounded part and its remainder, of which the tensor
  * cores use the TF32 bits (three products, about FP32 accuracy), accumulated
  * in FP32.
- * enable: 1 on (the default for FP32 plans), 0 off (FMA path only). */
+ * enable: 1 on (the default for FP32 plans; spreading by the persistent
+ * kernel with the A operand in tensor memory, interpolation by the kernel
+ * with both operands in shared memory -- the fastest pair measured), 2 both
+ * kernels with operands in shared memory, 3 both persistent tensor-memory
+ * kernels, 0 off (FMA path only). */
 agp_status agp_plan_set_tensor_cores(agp_plan plan, int enable);
 
 /* Outer boundary smoothing of the periodic kernel kappa_R (Sec. 3.1: the
@@ -320,6 +324,24 @@ agp_status agp_plan_set_wait_limit(agp_plan plan, int64_t polls);
 agp_status agp_nlml_grad(agp_plan plan, const void* Y, const void* Z, int64_t ldz, int nz,
                          int lanczos_steps, double rtol, int maxit, double* nlml, double* grad,
                          void* stream);
+
+/* agp_nlml_grad with n_probes Rademacher probes drawn on the device from
+ * `seed` (agp_rademacher), the form of the estimate that Sec. 1 describes;
+ * every argument as in agp_nlml_grad. Allocates the n x n_probes probe
+ * block on `stream` for the call. Synchronises `stream`. */
+agp_status agp_nlml_grad_seed(agp_plan plan, const void* Y, int n_probes, int lanczos_steps,
+                              uint64_t seed, double rtol, int maxit, double* nlml, double* grad,
+                              void* stream);
+
+/* Rademacher probe block for Hutchinson's trace estimator (Sec. 1): entry
+ * Z[i*ldz + c] (i < n, c < R) is +1 when the top bit of output i R + c of the
+ * counter-based SplitMix64 generator started at `seed` is 0, else -1
+ * (Steele, Lea and Flood, OOPSLA 2014: output j mixes the state
+ * seed + (j + 1) 0x9E3779B97F4A7C15). Z: device, element type `prec`.
+ * Asynchronous on `stream`. (The generator is not from the paper, which
+ * leaves the probes' source open.) */
+agp_status agp_rademacher(agp_prec prec, int64_t n, int R, uint64_t seed, void* Z, int64_t ldz,
+                          void* stream);
 
 /* The same estimate with the landmark preconditioner M = B K_LL^{-1} B^T +
  * sigma_eps^2 I of agp_pcg_solve (Sec. 2.3), as in Sec. 1 eqs. (1.3)-(1.5):

@@ -70,7 +70,7 @@ __all__ = [
     "nfft_adjoint", "nfft", "nfft_fastsum_matvec",
     "cg", "pcg", "farthest_point_sampling", "farthest_point_gaps", "additive_landmarks",
     "nystrom_preconditioner",
-    "lanczos_tridiag_from_cg", "slq_quadratic",
+    "splitmix64", "rademacher_probes", "lanczos_tridiag_from_cg", "slq_quadratic",
     "nlml_exact", "nlml_estimate",
     "landmark_jitter", "nystrom_blocks", "nystrom_matrix", "nystrom_logdet", "nystrom_probes", "pcg_lanczos",
     "nystrom_dM_quadratic", "nystrom_trace_Minv_dM", "nlml_estimate_preconditioned",
@@ -821,6 +821,29 @@ def nystrom_preconditioner(X, windows, kind, ell, sigma_f, sigma_eps, landmarks,
     M = KnL @ np.linalg.solve(KLL, KnL.T) + sigma_eps ** 2 * np.eye(n)
     M = 0.5 * (M + M.T)
     return lambda P: np.linalg.solve(M, P)
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    """Outputs 0 .. count-1 of the SplitMix64 generator (Steele, Lea and
+    Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014)
+    started from state ``seed``: output i mixes the state seed + (i + 1) g,
+    g = 0x9E3779B97F4A7C15, by z ^= z >> 30; z *= 0xBF58476D1CE4E5B9;
+    z ^= z >> 27; z *= 0x94D049BB133111EB; z ^= z >> 31 (mod 2^64). Output i
+    depends only on (seed, i): the generator is counter-based."""
+    i = np.arange(1, count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + i * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def rademacher_probes(n: int, R: int, seed: int) -> np.ndarray:
+    """n x R Rademacher probes (Hutchinson's estimator, Sec. 1): entry (i, c)
+    is +1 when the top bit of SplitMix64 output i R + c is 0, else -1."""
+    z = splitmix64(seed, n * R)
+    return np.where((z >> np.uint64(63)) == 0, 1.0, -1.0).reshape(n, R)
 
 
 def lanczos_tridiag_from_cg(alphas, betas):

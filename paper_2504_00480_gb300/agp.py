@@ -21,6 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libagp.so")
 
 AGP_OK, AGP_EINVAL, AGP_EDOMAIN, AGP_ECUDA, AGP_ENOMEM, AGP_NOT_CONVERGED, AGP_TIMEOUT, AGP_ENAN = range(8)
+AGP_F32, AGP_F64 = 0, 1
 KERNELS = {"gauss": 0, "matern12": 1, "matern32": 2, "imq": 3, "sinc": 4}
 PARAMS = {"ell": 0, "sigma_f": 1, "sigma_eps": 2}
 
@@ -67,6 +68,10 @@ _SIGS = {
                               c_int, c_int, POINTER(c_int), POINTER(c_double), c_void_p]),
     "agp_nlml_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int, c_double,
                               c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
+    "agp_nlml_grad_seed": (c_int, [c_void_p, c_void_p, c_int, c_int, ctypes.c_uint64, c_double,
+                                   c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
+    "agp_rademacher": (c_int, [c_int, c_int64, c_int, ctypes.c_uint64, c_void_p, c_int64,
+                               c_void_p]),
     "agp_plan_landmarks": (c_int, [c_void_p, c_int, c_void_p, c_int, POINTER(c_int), c_void_p]),
     "agp_plan_set_item_points": (c_int, [c_void_p, c_int, c_void_p]),
     "agp_plan_set_tensor_cores": (c_int, [c_void_p, c_int]),
@@ -150,7 +155,7 @@ def _block(t: torch.Tensor, dtype, what: str):
         if t.stride(0) != 1:
             raise ValueError(f"{what} must be contiguous")
         return t.data_ptr(), 1, 1
-    if t.dim() != 2 or t.stride(1) != 1:
+    if t.dim() != 2 or (t.stride(1) != 1 and t.shape[1] != 1):
         raise ValueError(f"{what} must be 2-D with unit column stride")
     return t.data_ptr(), t.stride(0), t.shape[1]
 
@@ -475,6 +480,28 @@ def agp_nlml_grad(plan: c_void_p, y: torch.Tensor, Z: torch.Tensor, lanczos_step
     return nl.value, {"ell": g[0], "sigma_f": g[1], "sigma_eps": g[2]}
 
 
+def agp_nlml_grad_seed(plan: c_void_p, y: torch.Tensor, n_probes: int, seed: int,
+                       lanczos_steps: int = 20, rtol: float = 0.0, maxit: int = 0):
+    """agp_nlml_grad with Rademacher probes drawn on the device from `seed`."""
+    if y.dim() != 1 or not y.is_contiguous():
+        raise ValueError("y must be a contiguous 1-D tensor")
+    nl = c_double()
+    g = (c_double * 3)()
+    _check(load_library().agp_nlml_grad_seed(plan, y.data_ptr(), int(n_probes),
+                                             int(lanczos_steps), int(seed), float(rtol),
+                                             int(maxit), byref(nl), g, _stream()))
+    return nl.value, {"ell": g[0], "sigma_f": g[1], "sigma_eps": g[2]}
+
+
+def agp_rademacher(n: int, R: int, seed: int, dtype=torch.float32, device="cuda") -> torch.Tensor:
+    """n x R Rademacher block from the library's counter-based generator."""
+    Z = torch.empty((n, R), dtype=dtype, device=device)
+    prec = AGP_F32 if dtype == torch.float32 else AGP_F64
+    _check(load_library().agp_rademacher(prec, int(n), int(R), int(seed), Z.data_ptr(), R,
+                                         _stream()))
+    return Z
+
+
 def agp_dot_columns(plan: c_void_p, A: torch.Tensor, B: torch.Tensor) -> np.ndarray:
     """FP64 column dot products of two [n][R] blocks (library kernels)."""
     ap, lda, R = _block(A, A.dtype, "A")
@@ -689,8 +716,11 @@ class Plan:
     def afn(self, n_landmarks: int, fill: int) -> Afn:
         return Afn(self, n_landmarks, fill)
 
-    def set_tensor_cores(self, enable: bool = True):
-        _check(load_library().agp_plan_set_tensor_cores(self._h, int(bool(enable))))
+    def set_tensor_cores(self, enable: int = 1):
+        """1: tensor-core kernels (the default: tensor-memory spreading,
+        shared-memory interpolation), 2: both with operands in shared memory,
+        3: both persistent tensor-memory kernels, 0: FMA pipes only."""
+        _check(load_library().agp_plan_set_tensor_cores(self._h, int(enable)))
 
     def set_boundary(self, eps_b: float, p: int):
         agp_plan_set_boundary(self._h, eps_b, p)
@@ -715,6 +745,10 @@ class Plan:
     def nlml_grad(self, y: torch.Tensor, Z: torch.Tensor, lanczos_steps: int = 20,
                   rtol: float = 0.0, maxit: int = 0):
         return agp_nlml_grad(self._h, y, Z, lanczos_steps, rtol, maxit)
+
+    def nlml_grad_seed(self, y: torch.Tensor, n_probes: int, seed: int, lanczos_steps: int = 20,
+                       rtol: float = 0.0, maxit: int = 0):
+        return agp_nlml_grad_seed(self._h, y, n_probes, seed, lanczos_steps, rtol, maxit)
 
     def profile(self, enable: bool = True):
         agp_profile_enable(self._h, enable)

@@ -699,6 +699,7 @@ void free_plan(agp_plan_s* pl) {
   }
   cudaFree(pl->items_all);
   cudaFree(pl->runs3);
+  cudaFree(pl->tiles3);
   cudaFree(pl->wins_dev);
   cudaFree(pl->err_dev);
   cudaFree(pl->bnd_poly);
@@ -761,7 +762,7 @@ agp_status build_items(agp_plan_s* pl, int cap, cudaStream_t st) {
   // runs of kRunCells cells along the last dimension for the tensor-core
   // kernels (host: cell_start of every d = 3 window, the non-empty runs)
   if (!pl->runs3) {
-    std::vector<int4> runs;
+    std::vector<int4> runs, tiles;
     for (int s = 0; s < pl->P; ++s) {
       const Window& w = pl->win[s];
       if (w.d != 3 || w.N % kRunCells != 0) continue;
@@ -773,12 +774,18 @@ agp_status build_items(agp_plan_s* pl, int cap, cudaStream_t st) {
         const int a = cs[c], b = cs[c + kRunCells];
         for (int q = a; q < b; q += kRunPoints)
           runs.push_back(make_int4(s | (kRunCells << 16), (int)c, q, std::min(kRunPoints, b - q)));
+        for (int q = a; q < b; q += kTilePoints)
+          tiles.push_back(make_int4(s | (kRunCells << 16), (int)c, q, std::min(kTilePoints, b - q)));
       }
     }
     pl->n_runs3 = (int64_t)runs.size();
+    pl->n_tiles3 = (int64_t)tiles.size();
     if (!runs.empty()) {
       AGP_CUDA(cudaMalloc(&pl->runs3, sizeof(int4) * runs.size()));
       AGP_CUDA(cudaMemcpyAsync(pl->runs3, runs.data(), sizeof(int4) * runs.size(),
+                               cudaMemcpyHostToDevice, st));
+      AGP_CUDA(cudaMalloc(&pl->tiles3, sizeof(int4) * tiles.size()));
+      AGP_CUDA(cudaMemcpyAsync(pl->tiles3, tiles.data(), sizeof(int4) * tiles.size(),
                                cudaMemcpyHostToDevice, st));
       AGP_CUDA(cudaStreamSynchronize(st));
     }
@@ -1047,7 +1054,13 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 0, st, dd);
-      if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 && spread_tc_supported(3, pl->s, rc))
+      if (dd == 3 && pl->runs3 && (pl->use_tc == 1 || pl->use_tc == 3) && sizeof(T) == 4 &&
+          spread_tm_supported(3, pl->s, rc, V + r0, ldv))
+        AGP_CUDA(spread_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->runs3,
+                                 pl->n_runs3, pl->s, reinterpret_cast<const float*>(V + r0), ldv,
+                                 Rc, rc, pl->err_dev, pl->wait_limit, st));
+      else if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 &&
+               spread_tc_supported(3, pl->s, rc))
         AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc, V + r0,
                                      ldv, Rc, 1, pl->err_dev, pl->wait_limit, st));
       else
@@ -1081,7 +1094,13 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 2, st, dd);
-      if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 && interp_tc_supported(3, pl->s, rc))
+      if (dd == 3 && pl->tiles3 && pl->use_tc == 3 && sizeof(T) == 4 &&
+          interp_tm_supported(3, pl->s, rc, Rc))
+        AGP_CUDA(interp_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->tiles3,
+                                 pl->n_tiles3, pl->s, reinterpret_cast<float*>(Out + r0), ldo, Rc,
+                                 (float)scale, rc, pl->err_dev, pl->wait_limit, st));
+      else if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 &&
+               interp_tc_supported(3, pl->s, rc))
         AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc,
                                      Out + r0, ldo, Rc, scale, 1, pl->err_dev, pl->wait_limit,
                                      st));
@@ -1448,8 +1467,8 @@ agp_status agp_profile_read(agp_plan pl, agp_profile_t* out, int reset, void* st
 }
 
 agp_status agp_plan_set_tensor_cores(agp_plan pl, int enable) {
-  if (!pl) return set_error(AGP_EINVAL, "bad arguments");
-  pl->use_tc = enable ? 1 : 0;
+  if (!pl || enable < 0 || enable > 3) return set_error(AGP_EINVAL, "bad arguments");
+  pl->use_tc = enable;
   return AGP_OK;
 }
 

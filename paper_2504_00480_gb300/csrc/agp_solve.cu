@@ -554,6 +554,26 @@ agp_status pcg_t(agp_plan_s* pl, const T* B, int64_t ldb, T* X, int64_t ldx, int
   return AGP_OK;
 }
 
+// Rademacher probes (Hutchinson's estimator, Sec. 1) from the counter-based
+// SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014): entry (i, c) of
+// an n x R block is +1 when the top bit of output i R + c is 0, else -1;
+// output j mixes the state seed + (j + 1) g, g = 0x9E3779B97F4A7C15.
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t j) {
+  uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_rademacher(T* __restrict__ Z, int64_t ldz, int64_t n, int R, uint64_t seed) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * R) return;
+  const int64_t i = e / R;
+  const int c = (int)(e - i * R);
+  Z[i * ldz + c] = (splitmix64_out(seed, (uint64_t)e) >> 63) ? T(-1) : T(1);
+}
+
 template <typename T>
 agp_status nlml_t(agp_plan_s* pl, const T* Y, const T* Z, int64_t ldz, int nz, int steps,
                   double rtol, int maxit, double* nlml, double* grad, cudaStream_t st) {
@@ -1221,6 +1241,39 @@ agp_status agp_dot_columns_static(agp_prec prec, const void* A, int64_t lda, con
                                                                 (const double*)B, ldb, n, R, scratch);
   k_dot_final<<<nblk(R, 128), 128, 0, st>>>(scratch, nb, R, out);
   return cuda_status(cudaGetLastError(), "agp_dot_columns_static");
+}
+
+agp_status agp_rademacher(agp_prec prec, int64_t n, int R, uint64_t seed, void* Z, int64_t ldz,
+                          void* stream) {
+  if (!Z || n < 1 || R < 1 || ldz < R || (prec != AGP_F32 && prec != AGP_F64))
+    return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == AGP_F32)
+    k_rademacher<float><<<nblk(n * R, 256), 256, 0, st>>>((float*)Z, ldz, n, R, seed);
+  else
+    k_rademacher<double><<<nblk(n * R, 256), 256, 0, st>>>((double*)Z, ldz, n, R, seed);
+  return cuda_status(cudaGetLastError(), "agp_rademacher");
+}
+
+agp_status agp_nlml_grad_seed(agp_plan pl, const void* Y, int n_probes, int lanczos_steps,
+                              uint64_t seed, double rtol, int maxit, double* nlml, double* grad,
+                              void* stream) {
+  if (!pl || !Y || n_probes < 1 || lanczos_steps < 1 || lanczos_steps > kMaxLanczos || !nlml ||
+      !grad || !(rtol >= 0) || (rtol > 0 && maxit < 1))
+    return set_error(AGP_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t es = pl->prec == AGP_F32 ? sizeof(float) : sizeof(double);
+  void* Z = nullptr;
+  AGP_CUDA(cudaMallocAsync(&Z, es * pl->n * n_probes, st));
+  agp_status s = agp_rademacher(pl->prec, pl->n, n_probes, seed, Z, n_probes, stream);
+  if (s == AGP_OK)
+    s = pl->prec == AGP_F32
+            ? nlml_t<float>(pl, (const float*)Y, (const float*)Z, n_probes, n_probes,
+                            lanczos_steps, rtol, maxit, nlml, grad, st)
+            : nlml_t<double>(pl, (const double*)Y, (const double*)Z, n_probes, n_probes,
+                             lanczos_steps, rtol, maxit, nlml, grad, st);
+  cudaFreeAsync(Z, st);
+  return with_timeout_check(pl, s, st);
 }
 
 agp_status agp_nlml_grad(agp_plan pl, const void* Y, const void* Z, int64_t ldz, int nz,

@@ -216,3 +216,33 @@ def test_autograd_autograd_workload_vs_fd_and_oracles(agp):
                                                           t["sigma_eps"])).sum())
         fd = (L_at(base[k] + h) - L_at(base[k] - h)) / (2 * h)
         assert got[k] == pytest.approx(fd, rel=1e-5), k
+
+
+# ---------------------------------------------------------------------------
+# device-drawn Rademacher probes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_rademacher_probes_match_the_oracle_generator(agp, dtype):
+    n, R, seed = 100_003, 17, 0xC0FFEE
+    Z = agp.agp_rademacher(n, R, seed, dtype=dtype, device=DEV).cpu().numpy()
+    np.testing.assert_array_equal(Z, O.rademacher_probes(n, R, seed))
+
+
+def test_nlml_grad_seed_equals_nlml_grad_with_the_same_probes(agp):
+    # well conditioned (sigma_eps = 1), so that 15 CG steps nearly converge and
+    # the order of the FP64 atomic additions moves the result only at
+    # rounding level
+    X, W, rng = small_problem(n=1200, seed=31)
+    plan = agp.Plan(torch.tensor(X, device=DEV), W, 32, 5, "gauss", 0.2, 1.0, 1.0)
+    y = torch.tensor(rng.standard_normal(1200), device=DEV)
+    seed = 424242
+    nl_s, g_s = plan.nlml_grad_seed(y, 12, seed, lanczos_steps=15)
+    Z = torch.tensor(O.rademacher_probes(1200, 12, seed), device=DEV)
+    nl, g = plan.nlml_grad(y, Z, lanczos_steps=15)
+    # the same probes: the two runs differ only by the order of the FP64
+    # atomic additions inside the matvecs, which the gradient (a difference
+    # of two larger terms) amplifies (measured: up to 8e-6 relative)
+    assert nl_s == pytest.approx(nl, rel=1e-9)
+    for k in g:
+        assert g_s[k] == pytest.approx(g[k], rel=1e-4, abs=1e-9), k
+    plan.close()

@@ -235,3 +235,25 @@ def test_nlml_preconditioned_exact_with_orthogonal_probes(kind):
     for w in ["ell", "sigma_f", "sigma_eps"]:
         fd = (Zexact(**{w: th[w] + h}) - Zexact(**{w: th[w] - h})) / (2 * h)
         assert g[w] == pytest.approx(fd, rel=1e-5, abs=1e-7), w
+
+
+def test_splitmix64_published_vectors():
+    # the first outputs of SplitMix64 from state 0, as printed by the
+    # generator's reference implementation (Steele, Lea and Flood, OOPSLA
+    # 2014; the splitmix64.c of Vigna's xorshift/xoroshiro distribution)
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    assert [int(v) for v in O.splitmix64(0, 4)] == want
+    # counter-based: output i of seed s is output i + 1 of seed s - g
+    g = 0x9E3779B97F4A7C15
+    a = O.splitmix64(12345, 10)
+    b = O.splitmix64((12345 - g) % (1 << 64), 11)
+    assert [int(v) for v in a] == [int(v) for v in b[1:]]
+
+
+def test_rademacher_probes_signs_and_balance():
+    Z = O.rademacher_probes(20000, 7, 99)
+    assert set(np.unique(Z)) == {-1.0, 1.0}
+    assert abs(Z.mean()) < 0.02
+    # entry (i, c) is output i R + c: the top bit decides the sign
+    z = O.splitmix64(99, 20000 * 7)
+    assert Z[3, 5] == (1.0 if int(z[3 * 7 + 5]) >> 63 == 0 else -1.0)
