@@ -335,6 +335,7 @@ def run_gpu(args):
     plan.set_hyper(w.ell, w.sigma_f, w.sigma_eps)
     nl = time_nlml(agp, plan, V, args.nlml_reps, dev)
     ag = time_autograd(plan, V, dev)
+    batch = None if args.no_batch else time_batch(agp, dev)
     nl_pc = None if args.no_nlml_pc else time_nlml_pc(agp, plan, V, dev,
                                                       n_landmarks=10 * len(w.windows))
     agp.agp_matvec(plan.handle, V, Out, True)
@@ -372,7 +373,8 @@ def run_gpu(args):
                 "stages_ms_per_step": {s: prof[s]["ms"] / args.steps for s in prof},
                 "stage_launches_per_step": {s: prof[s]["launches"] / args.steps for s in prof},
                 "clocks": clocks, "cpu_baseline": cpu,
-                "nlml_grad": nl, "nlml_grad_pc": nl_pc, "autograd": ag, "plain_fp64": plain}
+                "nlml_grad": nl, "nlml_grad_pc": nl_pc, "autograd": ag, "batch": batch,
+                "plain_fp64": plain}
         if plain is not None:
             plain["batched_fp32_over_plain_fp64"] = value / plain["value"]
         print(json.dumps(line), flush=True)
@@ -523,6 +525,68 @@ def time_autograd(plan, V, dev):
                     "dot products; dL/dV not requested"}
 
 
+def time_batch(agp, dev, reps=10):
+    """The uneven-batch workload: 64 independent problems, n log-uniform in
+    [1e4, 2e5], two d=3 windows each, per-problem lengthscale, FP32, N=32,
+    s=4, one right-hand side. One replay of a captured CUDA graph applies
+    K_hat and dK_hat/dell of every problem (one launch per stage over all
+    problems); timed with CUDA events next to the same work as per-problem
+    calls."""
+    import torch
+    ws = inputs.uneven_batch()
+    plans = [agp.Plan(torch.tensor(w.X, dtype=torch.float32, device=dev), w.windows, w.N,
+                      w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps) for w in ws]
+    Vs = [torch.tensor(w.V, dtype=torch.float32, device=dev) for w in ws]
+    Outs = [torch.zeros_like(v) for v in Vs]
+    Ders = [torch.zeros_like(v) for v in Vs]
+    b_mv, b_der = agp.Batch(plans), agp.Batch(plans)
+    b_mv.bind(Vs, Outs)
+    b_der.bind(Vs, Ders)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        b_mv.matvec()
+        b_der.matvec("ell")
+    torch.cuda.current_stream(dev).wait_stream(s)
+    with torch.cuda.graph(g):
+        b_mv.matvec()
+        b_der.matvec("ell")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    def singles():
+        for p, v, o, d in zip(plans, Vs, Outs, Ders):
+            agp.agp_matvec(p.handle, v, o, True)
+            agp.agp_deriv_matvec(p.handle, "ell", v, d)
+
+    ms_graph = timed(g.replay)
+    ms_single = timed(singles)
+    for p in plans:
+        p.check()
+    b_mv.close()
+    b_der.close()
+    for p in plans:
+        p.close()
+    n_total = sum(w.X.shape[0] for w in ws)
+    return {"problems": len(ws), "points": n_total, "rhs": 1,
+            "ms_per_replay": ms_graph, "mvm_per_s": len(ws) / (ms_graph / 1e3),
+            "deriv_mvm_per_s": len(ws) / (ms_graph / 1e3),
+            "points_per_s": 2 * n_total / (ms_graph / 1e3),
+            "per_problem_calls_ms": ms_single,
+            "graph_over_per_problem": ms_single / ms_graph,
+            "note": "one replay = K_hat v and dK_hat/dell v for every problem"}
+
+
 def time_plain_fp64(agp, w, V32, Out32, reps, dev, nl32=None):
     import torch
     X64 = torch.tensor(w.X, dtype=torch.float32, device=dev).double()
@@ -568,6 +632,8 @@ def main():
     ap.add_argument("--plain-reps", type=int, default=5)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-nlml-pc", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the uneven-batch (64 problems) measurement")
     ap.add_argument("--no-tc", action="store_true",
                     help="spread and interpolate on the FP32 FMA pipes instead of the tensor cores")
     args = ap.parse_args()

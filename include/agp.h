@@ -195,14 +195,26 @@ agp_status agp_plan_coeffs(agp_plan plan, int window, int deriv, double* b, void
  * `stream`. (Not from the paper: a property of the GPU layout.) */
 agp_status agp_plan_set_item_points(agp_plan plan, int points, void* stream);
 
-/* Autotuner for the work-item size: for each candidate in {64, 128, 256,
- * 512, 1024} rebuilds the work items and times `reps` applications of K_hat
- * to R columns (device scratch allocated and freed here, CUDA events on
- * `stream`), then keeps the fastest. points, ms: optional host outputs, the
- * chosen size and its mean time per call in milliseconds. Batches must be
- * created after this call. Synchronises `stream`. */
+/* Autotuner: times `reps` applications of K_hat to R columns (device
+ * scratch allocated and freed here, CUDA events on `stream`) first for each
+ * kernel family of agp_plan_set_tensor_cores (FP32 plans: 1, 2, 3 and 0) at
+ * the current work-item size, then, with the fastest family, for each
+ * work-item size in {64, 128, 256, 512, 1024}, and keeps the fastest pair.
+ * Results are cached for the process, keyed by precision, cutoff, pass
+ * width, R, the windows' (d, N) and floor(log2 n): a later plan with the
+ * same key takes the cached choice without timing. points, ms: optional host
+ * outputs, the chosen size and its mean time per call in milliseconds
+ * (agp_plan_tensor_cores gives the chosen family). Batches must be created
+ * after this call. Synchronises `stream`. (Not from the paper: a property of
+ * the GPU layout.) */
 agp_status agp_plan_autotune(agp_plan plan, int R, int reps, int* points, double* ms,
                              void* stream);
+
+/* The plan's kernel family (the value of agp_plan_set_tensor_cores). */
+agp_status agp_plan_tensor_cores(agp_plan plan, int* mode);
+
+/* Forget every cached autotuner result of the process. */
+agp_status agp_autotune_clear_cache(void);
 
 /* Size queries: n, number of windows, and the number of work items (point
  * chunks) of one window. */

@@ -77,6 +77,8 @@ _SIGS = {
     "agp_plan_set_tensor_cores": (c_int, [c_void_p, c_int]),
     "agp_plan_set_boundary": (c_int, [c_void_p, c_double, c_int, c_void_p]),
     "agp_plan_check": (c_int, [c_void_p, c_void_p]),
+    "agp_plan_tensor_cores": (c_int, [c_void_p, POINTER(c_int)]),
+    "agp_autotune_clear_cache": (c_int, []),
     "agp_plan_autotune": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_double),
                                   c_void_p]),
     "agp_nlml_grad_pc": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, POINTER(c_double), c_int,
@@ -734,7 +736,14 @@ class Plan:
         _check(load_library().agp_plan_set_wait_limit(self._h, int(polls)))
 
     def autotune(self, R: int = 32, reps: int = 3):
+        """(points per work item, ms per matvec) of the fastest choice; the
+        chosen kernel family is tensor_cores()."""
         return agp_plan_autotune(self._h, R, reps)
+
+    def tensor_cores(self) -> int:
+        m = c_int()
+        _check(load_library().agp_plan_tensor_cores(self._h, byref(m)))
+        return m.value
 
     def set_item_points(self, points: int):
         agp_plan_set_item_points(self._h, points)

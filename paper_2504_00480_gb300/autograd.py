@@ -11,10 +11,11 @@ Backward, for an upstream gradient G (every product runs in libagp.so):
                   (Sec. 3.2 eq. (3.4): the derivative sits on the Fourier
                   coefficients, so only the spectra g of G are formed -- one
                   spread and one forward DFT -- and paired with V's)
-  dL/dsigma_f   = sum_r G_r^T (2/sigma_f) (Out_r - sigma_eps^2 V_r)
+  dL/dsigma_f   = sum_r G_r^T (2 sigma_f sum_s K_s V_r)
+                = 2 sigma_f sum_s sum_k D_k Re(conj(g_k) v_k)   (same spectra)
   dL/dsigma_eps = sum_r G_r^T 2 sigma_eps V_r
 When V needs a gradient the spectra of G come out of the K_hat G matvec at no
-extra cost. Column dot products are FP64 reductions of the library. The
+extra cost. The sigma_eps term is an FP64 column dot product of the library. The
 plan's coefficients are recomputed only if its hyperparameters changed
 between forward and backward. After the backward the library's timeout flag
 is checked (AGP_TIMEOUT raises). This is the derivative the hyperparameter
@@ -43,12 +44,12 @@ class AdditiveKernelMatvec(torch.autograd.Function):
         ctx.plan = plan
         ctx.theta = theta
         ctx.vdim = V.dim()
-        ctx.save_for_backward(V2, out, spec)
+        ctx.save_for_backward(V2, spec)
         return out if V.dim() == 2 else out.squeeze(1)
 
     @staticmethod
     def backward(ctx, G):
-        V, out, specV = ctx.saved_tensors
+        V, specV = ctx.saved_tensors
         plan = ctx.plan
         ell, sf, se = ctx.theta
         plan.ensure_hyper(ell, sf, se)
@@ -56,18 +57,14 @@ class AdditiveKernelMatvec(torch.autograd.Function):
         R = G2.shape[1]
         gV = g_ell = g_sf = g_se = None
         dt = torch.float64
-        if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
+        if any(ctx.needs_input_grad[:3]):
             gV, specG = plan.spectra(G2, out=True if ctx.needs_input_grad[0] else None)
             if gV is not None and ctx.vdim == 1:
                 gV = gV.squeeze(1)
             if ctx.needs_input_grad[1]:
                 g_ell = plan.spectral_form("ell", specG, specV, R).sum().cpu().to(dt)
-        if ctx.needs_input_grad[2]:
-            if sf != 0.0:   # (2/sigma_f) (G.Out - sigma_eps^2 G.V): no extra matvec
-                g = (2.0 / sf) * (_dot(plan, G2, out) - se * se * _dot(plan, G2, V))
-            else:
-                g = _dot(plan, G2, plan.deriv_matvec("sigma_f", V))
-            g_sf = torch.tensor(g, dtype=dt)
+            if ctx.needs_input_grad[2]:
+                g_sf = plan.spectral_form("sigma_f", specG, specV, R).sum().cpu().to(dt)
         if ctx.needs_input_grad[3]:
             g_se = torch.tensor(2.0 * se * _dot(plan, G2, V), dtype=dt)
         plan.check()

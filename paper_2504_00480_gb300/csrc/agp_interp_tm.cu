@@ -2,30 +2,32 @@
 // persistent, warp-specialised kernel with the A operand in tensor memory.
 //
 // The contraction is the one of agp_interp_tc.cu: for a run of up to four
-// cells along the last dimension, a tile of up to 128 of its points and 16
+// cells along the last dimension (one work unit of at most 256 points) and 16
 // right-hand sides,
 //     H[p, (u, r)] = sum_{(t1, t2)} A[p, (t1, t2)] B[(u, r), (t1, t2)],
 //     A = psi1_p(t1) psi2_p(t2),   B = G[t1, t2, u][r]  (the run's grid block),
-// M = 128 points, N = 16 (2s + L - 1), K = the (2s)^2 grid rows in chunks of
-// 16, split-TF32 products (A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi) with FP32
+// with split-TF32 products (A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi) and FP32
 // accumulation; then h_p(r) = sum_t3 psi3_p(t3) H[p, (t3 + delta_p, r)] and
 // Out[perm p][r] += scale h_p(r) with vector atomics.
 //
 // Design (one CTA per SM, 18 warps, all 512 tensor-memory columns):
-//  * A lives in tensor memory, one point per lane: the thread of a lane
-//    keeps its point's psi1 and psi2 in registers and writes each chunk's 16
-//    products (hi and lo) with tcgen05.st.
-//  * Warps 10-17 read each chunk's grid values from L2 (one chunk ahead, in
-//    registers) and store them split into hi and lo in shared memory (B);
-//    warp 1 issues the MMAs from one thread; warps 2-5 form A; warps 6-9
-//    contract finished accumulators with psi3 and add the results into the
-//    output. Two accumulators of 208 columns let the epilogue of one work
-//    item overlap the main loop of the next; roles hand buffers over through
-//    mbarriers only.
-//  * Work items (tile of at most 128 points of one run, 16-column half) in a
-//    fixed stride;
-//    every wait is bounded and watches the CTA's abort word (as in
-//    agp_spread_tm.cu).
+//  * The unit's points form two M tiles of 128 (one tensor-memory lane per
+//    point), and every chunk of the grid block (B, K = 8 grid rows) feeds the
+//    MMAs of both tiles: the block is read from L2 once per 256 points.
+//  * A lives in tensor memory: the thread of a lane holds psi1 and psi2 of
+//    its points of both tiles in registers (prefetched into shared memory
+//    with cp.async during the previous unit) and writes each chunk's
+//    products (hi and lo) with tcgen05.st; the chunk loop is unrolled, so
+//    every product's factors are fixed at compile time.
+//  * Warps 10-17 read each chunk's grid values from L2 (two chunks ahead, in
+//    registers) and store them split into hi and lo in shared memory; warp 1
+//    issues the MMAs from one thread; warps 2-5 form A; warps 6-9 contract
+//    finished accumulators with psi3 and add the results into the output.
+//    The two tiles' accumulators (208 columns each) are drained one after
+//    the other, each with its own mbarrier, so the next unit's MMAs on tile
+//    0 start while tile 1 is still being read.
+//  * Work items (unit, 16-column half) in a fixed stride; every wait is
+//    bounded and watches the CTA's abort word (as in agp_spread_tm.cu).
 #include <algorithm>
 #include <type_traits>
 
@@ -35,19 +37,21 @@
 namespace agp {
 namespace {
 
-constexpr int kImKC = 16;                       // grid rows (t1, t2) per chunk (K)
+constexpr int kImKC = 8;                        // grid rows (t1, t2) per chunk (K)
 constexpr int kImRH = 16;                       // right-hand sides per work item
-constexpr int kImMP = kTilePoints;              // points per tile (M)
-constexpr int kImNB = 3;                        // B operand ring
+constexpr int kImMP = 128;                      // points per M tile
+constexpr int kImMT = kRunPoints / kImMP;       // M tiles per unit
+constexpr int kImNB = 4;                        // B operand ring
 constexpr int kImLBO = 128;
 constexpr int kImSBO = (kImKC / 4) * 128;
+constexpr int kImBG = 4;                        // groups of 64 B-forming threads
 constexpr int kImWarps = 18;
 constexpr int kImThreads = kImWarps * 32;
 constexpr int kIWMma = 1, kIWA0 = 2, kIWE0 = 6, kIWB0 = 10;
-constexpr int kImDCols = 208;
-constexpr int kImACol = 2 * kImDCols;
+constexpr int kImDCols = 208;                   // one tile's accumulator
+constexpr int kImACol = kImMT * kImDCols;       // A buffers after the accumulators
 constexpr int kImCols = 512;
-static_assert(kImMP == 128, "one tensor-memory lane per point");
+static_assert(kImMT == 2, "two M tiles per unit");
 
 template <int S>
 struct ImShape {
@@ -57,18 +61,21 @@ struct ImShape {
   static constexpr int T3M = TT + kRunCells - 1;
   static constexpr int NN = T3M * kImRH;
   static constexpr int NRG = NN / 8;                            // B row groups
-  static constexpr int BPER = NRG / 2;                          // row groups per B thread
+  static constexpr int BPER = (NRG + kImBG - 1) / kImBG;        // row groups per B thread (max)
   static constexpr int WPP = wpp_of(3, S);
-  static constexpr int B_BYTES = NN * kImKC * 4;
-  static constexpr int SMEM = kImNB * 2 * B_BYTES;
-  static_assert(NN <= kImDCols && NRG % 2 == 0, "tile shape");
-  static_assert(kImACol + 64 <= kImCols, "tensor memory budget");
+  static constexpr int PSI = 2 * TTP;                           // psi1, psi2 of a point as stored
+  static constexpr int B_BYTES = NN * kImKC * 4;                // one of hi / lo
+  static constexpr int OFF_P = kImNB * 2 * B_BYTES;             // A formers' prefetch slots
+  static constexpr int SMEM = OFF_P + 2 * kImMP * kImMT * PSI * 4;
+  static_assert(NN <= kImDCols, "tile shape");
+  static_assert(kImACol + 2 * 32 <= kImCols, "tensor memory budget");
+  static_assert(PSI % 4 == 0 && OFF_P % 16 == 0, "16-byte prefetch pieces");
 };
 
 struct ImBars {
   uint64_t a_full[2], a_empty[2];
   uint64_t b_full[kImNB], b_empty[kImNB];
-  uint64_t d_full[2], d_empty[2];
+  uint64_t d_full, d_empty[kImMT];
   uint64_t drain;
 };
 
@@ -79,7 +86,7 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
             int* __restrict__ err, long long spin) {
   using Sh = ImShape<S>;
   constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ImBars bars;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;
@@ -93,13 +100,13 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bars.a_full[b], 4);
       mbar_init(&bars.a_empty[b], 1);
-      mbar_init(&bars.d_full[b], 1);
-      mbar_init(&bars.d_empty[b], 4);
     }
     for (int b = 0; b < kImNB; ++b) {
       mbar_init(&bars.b_full[b], 8);
       mbar_init(&bars.b_empty[b], 1);
     }
+    mbar_init(&bars.d_full, 1);
+    for (int t = 0; t < kImMT; ++t) mbar_init(&bars.d_empty[t], 4);
     mbar_init(&bars.drain, 1);
     abort_word = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -114,21 +121,19 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  // work item i = (tile, half): a tile is a run's unit of at most 128 points
+  // work item i = (unit, half); every item holds points and columns (the
+  // dispatcher requires R > rc - 16, and units are never empty)
   struct Item {
     int4 u;
-    int p0, np, r0;
+    int r0, mt;       // first column, M tiles holding points
   };
-  // the tile of work item i (loaded one item ahead by every role)
   auto unit_at = [&](int64_t i) -> int4 {
     return i < n_items ? __ldg(units + i / nh) : make_int4(0, 0, 0, 0);
   };
-  auto item_from = [&](int64_t i, int4 u, Item& it) -> bool {
+  auto item_from = [&](int64_t i, int4 u, Item& it) {
     it.u = u;
-    it.p0 = 0;
-    it.np = min(kImMP, it.u.w);
     it.r0 = (int)(i % nh) * kImRH;
-    return it.r0 < R && it.np > 0;
+    it.mt = u.w > kImMP ? 2 : 1;
   };
 
   if (warp == kIWMma) {
@@ -137,83 +142,105 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
     int4 un = unit_at(blockIdx.x);
     for (int64_t i = blockIdx.x; i < n_items && !warp_aborted(abort); i += gridDim.x) {
       const int4 uc = un;
-      un = unit_at(i + gridDim.x);               // next item, in flight
+      un = unit_at(i + gridDim.x);
       Item it;
-      if (!item_from(i, uc, it)) continue;
+      item_from(i, uc, it);
       const int L = max(1, it.u.x >> 16), nu = TT + L - 1;
-      const int db = (int)(nd & 1);
-      if (!warp_wait(&bars.d_empty[db], (uint32_t)(((nd >> 1) & 1) ^ 1), spin, abort)) break;
       const uint32_t idesc = umma_idesc_tf32(kImMP, nu * kImRH);
-      const uint32_t dt = tmem + (uint32_t)(db * kImDCols);
       bool ok = true;
       for (int c = 0; c < Sh::NCH; ++c, ++g) {
         const int ab = (int)(g & 1), bb = (int)(g % kImNB);
+        // tile t's accumulator is free once the epilogue has read the previous
+        // item's (waited before the item's first MMA on it)
         if (!warp_wait(&bars.a_full[ab], (uint32_t)((g >> 1) & 1), spin, abort) ||
-            !warp_wait(&bars.b_full[bb], (uint32_t)((g / kImNB) & 1), spin, abort)) {
+            !warp_wait(&bars.b_full[bb], (uint32_t)((g / kImNB) & 1), spin, abort) ||
+            (c == 0 && !warp_wait(&bars.d_empty[0], (uint32_t)((nd & 1) ^ 1), spin, abort))) {
           ok = false;
           break;
         }
         tc_fence_after();
+        const float* bh = bbuf(bb);
+        const uint64_t dh = umma_desc(smem_u32(bh), kImLBO, kImSBO);
+        const uint64_t dl = umma_desc(smem_u32(bh) + Sh::B_BYTES, kImLBO, kImSBO);
+        const uint32_t a0 = tmem + (uint32_t)(kImACol + ab * 32);
         if (lane == 0) {
-          const uint32_t a0 = tmem + (uint32_t)(kImACol + ab * 32);
-          const float* bh = bbuf(bb);
-          const uint64_t dh = umma_desc(smem_u32(bh), kImLBO, kImSBO);
-          const uint64_t dl = umma_desc(smem_u32(bh) + Sh::B_BYTES, kImLBO, kImSBO);
-#pragma unroll
-          for (int s2 = 0; s2 < kImKC / 8; ++s2) {
-            const uint64_t off = (uint64_t)(s2 * 2 * kImLBO) >> 4;
-            const uint32_t ah = a0 + (uint32_t)(s2 * 8), al = ah + 16;
-            mma_tf32_tmem_a(dt, ah, dh + off, idesc, (c > 0 || s2 > 0) ? 1u : 0u);
-            mma_tf32_tmem_a(dt, ah, dl + off, idesc, 1u);
-            mma_tf32_tmem_a(dt, al, dh + off, idesc, 1u);
+          mma_tf32_tmem_a(tmem, a0, dh, idesc, c > 0 ? 1u : 0u);
+          mma_tf32_tmem_a(tmem, a0, dl, idesc, 1u);
+          mma_tf32_tmem_a(tmem, a0 + 8, dh, idesc, 1u);
+        }
+        __syncwarp();
+        if (c == 0 && !warp_wait(&bars.d_empty[1], (uint32_t)((nd & 1) ^ 1), spin, abort)) {
+          ok = false;
+          break;
+        }
+        if (it.mt > 1) {
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t d1 = tmem + (uint32_t)kImDCols;
+            mma_tf32_tmem_a(d1, a0 + 16, dh, idesc, c > 0 ? 1u : 0u);
+            mma_tf32_tmem_a(d1, a0 + 16, dl, idesc, 1u);
+            mma_tf32_tmem_a(d1, a0 + 24, dh, idesc, 1u);
           }
+        }
+        if (lane == 0) {
           mma_commit(&bars.a_empty[ab]);
           mma_commit(&bars.b_empty[bb]);
         }
         __syncwarp();
       }
       if (!ok) break;
-      if (lane == 0) mma_commit(&bars.d_full[db]);
+      if (lane == 0) mma_commit(&bars.d_full);
       __syncwarp();
       ++nd;
     }
   } else if (warp >= kIWA0 && warp < kIWA0 + 4) {
-    // ---- A = psi1 psi2 into tensor memory, one point (lane) per thread ---------
-    // The thread's point keeps psi1, psi2 in registers; the chunk loop is
-    // unrolled, so every product picks its two factors at compile time. The
-    // next item's values are loaded when an item starts.
+    // ---- A = psi1 psi2 into tensor memory, one point per lane and tile -------------
     const int qd = warp & 3;
     const int p = qd * 32 + lane;
     const uint32_t tq = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)kImACol;
-    struct Psi {
-      float a[TT], b[TT];
-    };
-    auto psi_load = [&](const Item& it, bool valid) -> Psi {
-      const bool live = valid && p < it.np;
-      const float* pw =
-          wins[valid ? it.u.x & 0xFFFF : 0].wts + (live ? (int64_t)(it.u.z + it.p0 + p) * WPP : 0);
-      Psi v;
+    // this thread's two prefetch slots (alternate items): psi1, psi2 (as
+    // stored) of its point in each tile
+    float* slots = reinterpret_cast<float*>(smem_raw + Sh::OFF_P) + p * (kImMT * Sh::PSI);
+    auto slot_of = [&](int64_t j) { return slots + (j & 1) * (kImMP * kImMT * Sh::PSI); };
+    auto prefetch = [&](const Item& it, float* slot) {
+      const WinDev<float> w = wins[it.u.x & 0xFFFF];
 #pragma unroll
-      for (int t = 0; t < TT; ++t) {
-        v.a[t] = live ? __ldg(pw + t) : 0.0f;
-        v.b[t] = live ? __ldg(pw + TTP + t) : 0.0f;
+      for (int t = 0; t < kImMT; ++t) {
+        const int pt = t * kImMP + p;
+        const bool live = pt < it.u.w;
+        const float* src = w.wts + (int64_t)(it.u.z + (live ? pt : 0)) * WPP;
+#pragma unroll
+        for (int q = 0; q < Sh::PSI / 4; ++q)
+          cp_async16_zfill(slot + t * Sh::PSI + q * 4, src + q * 4, live ? 16 : 0);
       }
-      return v;
     };
-    int64_t g = 0, pre = -1;                          // pre: the item whose values are in nv
-    Psi cv, nv;
+    int64_t g = 0, j = 0;
     int4 un = unit_at(blockIdx.x);
-    for (int64_t i = blockIdx.x; i < n_items && !warp_aborted(abort); i += gridDim.x) {
+    if (blockIdx.x < n_items) {
+      Item first;
+      item_from(blockIdx.x, un, first);
+      prefetch(first, slot_of(0));
+    }
+    for (int64_t i = blockIdx.x; i < n_items && !warp_aborted(abort); i += gridDim.x, ++j) {
       const int4 uc = un;
-      un = unit_at(i + gridDim.x);               // next item, in flight
+      un = unit_at(i + gridDim.x);
       Item it;
-      if (!item_from(i, uc, it)) continue;
-      if (pre != i) nv = psi_load(it, true);          // not prefetched: load now
-      cv = nv;
-      Item nx;
-      const bool nvalid = item_from(i + gridDim.x, un, nx);
-      nv = psi_load(nx, nvalid);                      // the next item's values, in flight
-      pre = nvalid ? i + gridDim.x : -1;
+      item_from(i, uc, it);
+      cp_async_wait_all();                            // this item's values, staged earlier
+      const float* slot = slot_of(j);
+      float a[kImMT][TT], b[kImMT][TT];
+#pragma unroll
+      for (int t = 0; t < kImMT; ++t)
+#pragma unroll
+        for (int q = 0; q < TT; ++q) {
+          a[t][q] = slot[t * Sh::PSI + q];
+          b[t][q] = slot[t * Sh::PSI + TTP + q];
+        }
+      if (i + gridDim.x < n_items) {                  // the next item's values, in flight
+        Item nx;
+        item_from(i + gridDim.x, un, nx);
+        prefetch(nx, slot_of(j + 1));
+      }
       bool ok = true;
 #pragma unroll
       for (int c = 0; c < Sh::NCH; ++c) {
@@ -222,18 +249,23 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
           ok = false;
           break;
         }
-        uint32_t hi[kImKC], lo[kImKC];
+        uint32_t hl[kImMT][2][kImKC];
 #pragma unroll
-        for (int k = 0; k < kImKC; ++k) {
-          const int kk = c * kImKC + k;                  // grid row (t1, t2), a constant
-          const float x = kk < Sh::ROWS ? cv.a[kk / TT] * cv.b[kk % TT] : 0.0f;
-          const float h = tf32_round(x);
-          hi[k] = __float_as_uint(h);
-          lo[k] = __float_as_uint(x - h);
-        }
+        for (int t = 0; t < kImMT; ++t)
+#pragma unroll
+          for (int k = 0; k < kImKC; ++k) {
+            const int kk = c * kImKC + k;                // grid row (t1, t2), a constant
+            const float x = kk < Sh::ROWS ? a[t][kk / TT] * b[t][kk % TT] : 0.0f;
+            const float h = tf32_round(x);
+            hl[t][0][k] = __float_as_uint(h);
+            hl[t][1][k] = __float_as_uint(x - h);
+          }
         tc_fence_after();
-        tmem_st16(tq + (uint32_t)(ab * 32), hi);
-        tmem_st16(tq + (uint32_t)(ab * 32 + 16), lo);
+        const uint32_t ta = tq + (uint32_t)(ab * 32);
+        tmem_st8(ta, hl[0][0]);
+        tmem_st8(ta + 8, hl[0][1]);
+        tmem_st8(ta + 16, hl[1][0]);
+        tmem_st8(ta + 24, hl[1][1]);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
@@ -242,25 +274,27 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       if (!ok) break;
       g += Sh::NCH;
     }
+    cp_async_wait_all();
   } else if (warp >= kIWB0 && warp < kIWB0 + 8) {
     // ---- B = the run's grid block (hi and lo) into shared memory ----------------
     // The chunks of all items form one sequence g = 0, 1, 2, ...; two register
     // sets take the even and the odd chunks, so that the L2 loads of chunk
-    // g + 2 are in flight while chunks g and g + 1 are stored.
+    // g + 2 are in flight while chunks g and g + 1 are stored. Thread slot:
+    // row r8 and column k4 of the core matrices of column quad kq; group grp
+    // (of kImBG) takes row groups [grp NRG / kImBG, (grp + 1) NRG / kImBG).
     const int bt = tid - kIWB0 * 32;
-    const int kq = (bt >> 5) & 3, r8 = lane >> 2, k4 = lane & 3, grp = bt >> 7;
+    const int kq = (bt >> 5) & 1, r8 = lane >> 2, k4 = lane & 3, grp = bt >> 6;
     const int kk4 = kq * 4 + k4;                      // grid row within the chunk
     const int o = kq * 32 + lane;
+    const int rga = grp * Sh::NRG / kImBG, rgb = (grp + 1) * Sh::NRG / kImBG;
     constexpr int CORE = (kImKC / 4) * 32;
     struct BCur {
       int64_t i;            // work item (n_items: done)
       int c;                // chunk within the item
       int W, nu;
       const float* gp0;     // grid column r0 + r8 at the unit's first cell
-      int4 un;              // the next item's tile, loaded ahead
+      int4 un;              // the next item's unit, loaded ahead
     };
-    // enter item b.i whose tile is u (every item is valid: tiles hold points
-    // and both halves hold columns)
     auto benter = [&](BCur& b, int4 u) {
       b.un = unit_at(b.i + gridDim.x);
       if (b.i >= n_items) return;
@@ -279,8 +313,6 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       b.i += gridDim.x;
       benter(b, b.un);
     };
-    // this thread's B elements of chunk b.c: grid row kk = c KC + kk4, row
-    // groups rg = grp BPER + q: plane rg / 2, columns r0 + 8 (rg % 2) + r8
     auto bload = [&](const BCur& b, float* gb) {
       if (b.i >= n_items) return;
       const int kk = b.c * kImKC + kk4;
@@ -289,12 +321,12 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       const float* gp = b.gp0 + ((int64_t)t1 * b.W + t2) * b.W * rc;
 #pragma unroll
       for (int q = 0; q < Sh::BPER; ++q) {
-        const int rg = grp * Sh::BPER + q;
-        gb[q] = (krow && rg < 2 * b.nu) ? __ldg(gp + (rg >> 1) * rc + (rg & 1) * 8) : 0.0f;
+        const int rg = rga + q;
+        gb[q] = (krow && rg < rgb && rg < 2 * b.nu) ? __ldg(gp + (rg >> 1) * rc + (rg & 1) * 8)
+                                                    : 0.0f;
       }
     };
     int64_t g = 0;
-    // store chunk `b` (values in gb), then move b two chunks on and load it
     auto step = [&](BCur& b, float* gb) -> bool {
       if (b.i >= n_items || warp_aborted(abort)) return false;
       const int bb = (int)(g % kImNB);
@@ -304,11 +336,13 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       float* bl = bh + Sh::B_BYTES / 4;
 #pragma unroll
       for (int q = 0; q < Sh::BPER; ++q) {
-        const int rg = grp * Sh::BPER + q;
-        const float x = gb[q];
-        const float h = tf32_round(x);
-        bh[rg * CORE + o] = h;
-        bl[rg * CORE + o] = x - h;
+        const int rg = rga + q;
+        if (rg < rgb) {
+          const float x = gb[q];
+          const float h = tf32_round(x);
+          bh[rg * CORE + o] = h;
+          bl[rg * CORE + o] = x - h;
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;");
       __syncwarp();
@@ -336,60 +370,71 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
     int4 un = unit_at(blockIdx.x);
     for (int64_t i = blockIdx.x; i < n_items && !warp_aborted(abort); i += gridDim.x) {
       const int4 uc = un;
-      un = unit_at(i + gridDim.x);               // next item, in flight
+      un = unit_at(i + gridDim.x);
       Item it;
-      if (!item_from(i, uc, it)) continue;
+      item_from(i, uc, it);
       const WinDev<float> w = wins[it.u.x & 0xFFFF];
       const int L = max(1, it.u.x >> 16), nu = TT + L - 1;
-      const int p = qd * 32 + lane;
-      const bool live = p < it.np;
-      const int jj = it.u.z + it.p0 + (live ? p : 0);
-      int delta = 0;
+      // this thread's point of each tile: perm index, cell within the run, psi3
+      int64_t pi[kImMT];
+      int delta[kImMT];
+      float p3[kImMT][TT];
 #pragma unroll
-      for (int q = 1; q < kRunCells; ++q)
-        delta += (q < L && jj >= __ldg(w.cell_start + it.u.y + q)) ? 1 : 0;
-      float p3[TT];
-      const float* pw = w.wts + (int64_t)jj * WPP + 2 * TTP;
+      for (int t = 0; t < kImMT; ++t) {
+        const int pt = t * kImMP + qd * 32 + lane;
+        const bool live = pt < it.u.w;
+        const int jj = it.u.z + (live ? pt : 0);
+        delta[t] = 0;
 #pragma unroll
-      for (int t = 0; t < TT; ++t) p3[t] = live ? __ldg(pw + 2 * t) : 0.0f;
-      const int64_t pi = live ? (int64_t)__ldg(w.perm + jj) : 0;
-      const int db = (int)(nd & 1);
-      if (!warp_wait(&bars.d_full[db], (uint32_t)((nd >> 1) & 1), spin, abort)) break;
-      tc_fence_after();
-      float acc[kImRH];
+        for (int q = 1; q < kRunCells; ++q)
+          delta[t] += (q < L && jj >= __ldg(w.cell_start + it.u.y + q)) ? 1 : 0;
+        const float* pw = w.wts + (int64_t)jj * WPP + 2 * TTP;
 #pragma unroll
-      for (int q = 0; q < kImRH; ++q) acc[q] = 0.0f;
-#pragma unroll 1
-      for (int u = 0; u < nu; ++u) {
-        uint32_t v[kImRH];
-        tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(db * kImDCols + u * kImRH), v);
-        tmem_wait_ld();
-        const int t3 = u - delta;
-        float ps = 0.0f;
-#pragma unroll
-        for (int t = 0; t < TT; ++t) ps = (t == t3) ? p3[t] : ps;
-#pragma unroll
-        for (int q = 0; q < kImRH; ++q) acc[q] = fmaf(ps, __uint_as_float(v[q]), acc[q]);
+        for (int q = 0; q < TT; ++q) p3[t][q] = live ? __ldg(pw + 2 * q) : 0.0f;
+        pi[t] = live ? (int64_t)__ldg(w.perm + jj) : -1;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars.d_empty[db]);
-      ++nd;
-      if (live) {
-        float* dst = Out + pi * ldo + it.r0;
+      if (!warp_wait(&bars.d_full, (uint32_t)(nd & 1), spin, abort)) break;
+      tc_fence_after();
 #pragma unroll
-        for (int c4 = 0; c4 < kImRH; c4 += 4) {
-          if (it.r0 + c4 >= R) break;
-          const float4 val = make_float4(scale * acc[c4], scale * acc[c4 + 1],
-                                         scale * acc[c4 + 2], scale * acc[c4 + 3]);
-          if (vec && it.r0 + c4 + 4 <= R) {
-            atomicAdd(reinterpret_cast<float4*>(dst + c4), val);
-          } else {
-            const float vv[4] = {val.x, val.y, val.z, val.w};
-            for (int q = 0; q < 4 && it.r0 + c4 + q < R; ++q) atomicAdd(dst + c4 + q, vv[q]);
+      for (int t = 0; t < kImMT; ++t) {
+        float acc[kImRH];
+#pragma unroll
+        for (int q = 0; q < kImRH; ++q) acc[q] = 0.0f;
+        if (t < it.mt) {
+#pragma unroll 1
+          for (int u = 0; u < nu; ++u) {
+            uint32_t v[kImRH];
+            tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(t * kImDCols + u * kImRH),
+                      v);
+            tmem_wait_ld();
+            const int t3 = u - delta[t];
+            float ps = 0.0f;
+#pragma unroll
+            for (int q = 0; q < TT; ++q) ps = (q == t3) ? p3[t][q] : ps;
+#pragma unroll
+            for (int q = 0; q < kImRH; ++q) acc[q] = fmaf(ps, __uint_as_float(v[q]), acc[q]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.d_empty[t]);
+        if (t < it.mt && pi[t] >= 0) {
+          float* dst = Out + pi[t] * ldo + it.r0;
+#pragma unroll
+          for (int c4 = 0; c4 < kImRH; c4 += 4) {
+            if (it.r0 + c4 >= R) break;
+            const float4 val = make_float4(scale * acc[c4], scale * acc[c4 + 1],
+                                           scale * acc[c4 + 2], scale * acc[c4 + 3]);
+            if (vec && it.r0 + c4 + 4 <= R) {
+              atomicAdd(reinterpret_cast<float4*>(dst + c4), val);
+            } else {
+              const float vv[4] = {val.x, val.y, val.z, val.w};
+              for (int q = 0; q < 4 && it.r0 + c4 + q < R; ++q) atomicAdd(dst + c4 + q, vv[q]);
+            }
           }
         }
       }
+      ++nd;
     }
   }
 

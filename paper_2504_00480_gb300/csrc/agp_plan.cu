@@ -13,6 +13,8 @@
 //   out = sigma_eps^2 V; per block of RC right-hand sides: zero the grids,
 //   spread, forward DFT, multiply, inverse DFT, interpolate (+= sigma_f^2 h).
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -957,6 +959,16 @@ int pick_rc(const agp_plan_s* pl, int R) {
   return rhs_block_width(pl->prec, R);
 }
 
+// Autotuner results, shared by the plans of a process: key (precision,
+// cutoff, pass width, right-hand sides, window shapes, log2 n) -> the chosen
+// kernel family, work-item size and its time per matvec.
+struct TuneEntry {
+  int mode, points;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune_cache;
+
 // Stage timing: a pair of events around a group of launches on `st`.
 struct StageTimer {
   agp_plan_s* pl;
@@ -1094,10 +1106,10 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 2, st, dd);
-      if (dd == 3 && pl->tiles3 && pl->use_tc == 3 && sizeof(T) == 4 &&
+      if (dd == 3 && pl->runs3 && pl->use_tc == 3 && sizeof(T) == 4 &&
           interp_tm_supported(3, pl->s, rc, Rc))
-        AGP_CUDA(interp_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->tiles3,
-                                 pl->n_tiles3, pl->s, reinterpret_cast<float*>(Out + r0), ldo, Rc,
+        AGP_CUDA(interp_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->runs3,
+                                 pl->n_runs3, pl->s, reinterpret_cast<float*>(Out + r0), ldo, Rc,
                                  (float)scale, rc, pl->err_dev, pl->wait_limit, st));
       else if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 &&
                interp_tc_supported(3, pl->s, rc))
@@ -1535,6 +1547,24 @@ agp_status agp_plan_set_item_points(agp_plan pl, int points, void* stream) {
 agp_status agp_plan_autotune(agp_plan pl, int R, int reps, int* points, double* ms, void* stream) {
   if (!pl || R < 1 || reps < 1) return set_error(AGP_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // cache key: precision, cutoff, pass width, (d, N) of every window, log2 n
+  std::string key = std::to_string((int)pl->prec) + "/" + std::to_string(pl->s) + "/" +
+                    std::to_string(pick_rc(pl, R)) + "/" + std::to_string(std::min(R, 32)) + "/";
+  for (const auto& w : pl->win) key += std::to_string(w.d) + "x" + std::to_string(w.N) + ",";
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= pl->n) ++lg;
+  key += "/" + std::to_string(lg);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto f = g_tune_cache.find(key);
+    if (f != g_tune_cache.end()) {
+      pl->use_tc = f->second.mode;
+      AGP_TRY(build_items(pl, f->second.points, st));
+      if (points) *points = f->second.points;
+      if (ms) *ms = f->second.ms;
+      return AGP_OK;
+    }
+  }
   const size_t bytes = (size_t)pl->n * R * (pl->prec == AGP_F32 ? 4 : 8);
   void *V = nullptr, *Out = nullptr;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -1554,27 +1584,61 @@ agp_status agp_plan_autotune(agp_plan pl, int R, int reps, int* points, double* 
   AGP_CUDA(cudaMemsetAsync(V, 0, bytes, st));
   AGP_CUDA(cudaEventCreate(&a));
   AGP_CUDA(cudaEventCreate(&b));
-  const int cands[] = {64, 128, 256, 512, 1024};
-  int best = pl->item_points;
-  float best_ms = 0.0f;
-  for (int c : cands) {
-    AGP_TRY(build_items(pl, c, st));
+  auto time_it = [&](float* t) -> agp_status {
     AGP_TRY(agp_matvec(pl, V, R, Out, R, R, 1, st));   // warm-up
     AGP_CUDA(cudaEventRecord(a, st));
     for (int k = 0; k < reps; ++k) AGP_TRY(agp_matvec(pl, V, R, Out, R, R, 1, st));
     AGP_CUDA(cudaEventRecord(b, st));
     AGP_CUDA(cudaEventSynchronize(b));
+    AGP_CUDA(cudaEventElapsedTime(t, a, b));
+    *t /= reps;
+    return AGP_OK;
+  };
+  // stage 1: the kernel family (tensor-core pairings or FMA pipes; FP32
+  // plans only) at the current work-item size; stage 2: the work-item size
+  int best_mode = pl->use_tc, best_pts = pl->item_points;
+  float best_ms = 0.0f;
+  const int modes[] = {1, 2, 3, 0};
+  for (int md : modes) {
+    if (pl->prec != AGP_F32 && md != 0) continue;
+    pl->use_tc = md;
     float t = 0.0f;
-    AGP_CUDA(cudaEventElapsedTime(&t, a, b));
-    t /= reps;
+    AGP_TRY(time_it(&t));
     if (best_ms == 0.0f || t < best_ms) {
       best_ms = t;
-      best = c;
+      best_mode = md;
     }
   }
-  AGP_TRY(build_items(pl, best, st));
-  if (points) *points = best;
+  pl->use_tc = best_mode;
+  const int cands[] = {64, 128, 256, 512, 1024};
+  for (int c : cands) {
+    AGP_TRY(build_items(pl, c, st));
+    float t = 0.0f;
+    AGP_TRY(time_it(&t));
+    if (t < best_ms) {
+      best_ms = t;
+      best_pts = c;
+    }
+  }
+  AGP_TRY(build_items(pl, best_pts, st));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = TuneEntry{best_mode, best_pts, (double)best_ms};
+  }
+  if (points) *points = best_pts;
   if (ms) *ms = best_ms;
+  return AGP_OK;
+}
+
+agp_status agp_plan_tensor_cores(agp_plan pl, int* mode) {
+  if (!pl || !mode) return set_error(AGP_EINVAL, "bad arguments");
+  *mode = pl->use_tc;
+  return AGP_OK;
+}
+
+agp_status agp_autotune_clear_cache(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.clear();
   return AGP_OK;
 }
 

@@ -35,8 +35,19 @@ k_dot_partial(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, i
   const int c = blockIdx.y * 32 + lane;
   double acc = 0.0;
   if (c < R) {
-    for (int64_t i = (int64_t)blockIdx.x * kDotRows + grp; i < n; i += (int64_t)gridDim.x * kDotRows)
+    // four rows per trip with independent partial sums, so that four loads
+    // of each operand are in flight per thread
+    const int64_t step = (int64_t)gridDim.x * kDotRows;
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t i = (int64_t)blockIdx.x * kDotRows + grp;
+    for (; i + 3 * step < n; i += 4 * step) {
       acc += (double)A[i * lda + c] * (double)B[i * ldb + c];
+      a1 += (double)A[(i + step) * lda + c] * (double)B[(i + step) * ldb + c];
+      a2 += (double)A[(i + 2 * step) * lda + c] * (double)B[(i + 2 * step) * ldb + c];
+      a3 += (double)A[(i + 3 * step) * lda + c] * (double)B[(i + 3 * step) * ldb + c];
+    }
+    for (; i < n; i += step) acc += (double)A[i * lda + c] * (double)B[i * ldb + c];
+    acc = (acc + a1) + (a2 + a3);
   }
   red[grp][lane] = acc;
   __syncthreads();

@@ -115,7 +115,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
             int* __restrict__ err, long long spin) {
   using Sh = TmShape<S>;
   constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, WPS = Sh::WPS, VS = Sh::VS;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TmBars bars;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;

@@ -50,6 +50,7 @@ def test_item_points_do_not_change_results(agp, dtype, tol):
 
 
 def test_autotune_keeps_a_candidate(agp):
+    agp.load_library().agp_autotune_clear_cache()
     w = inputs.subset(inputs.nlml_grad(n=40000, R=8), 40000)
     plan = agp.Plan(torch.tensor(w.X, dtype=torch.float32, device=DEV), w.windows, w.N, w.cutoff,
                     w.kernel, w.ell, w.sigma_f, w.sigma_eps)
@@ -57,6 +58,7 @@ def test_autotune_keeps_a_candidate(agp):
     ref = plan.matvec(V).cpu().numpy()
     pts, ms = plan.autotune(R=8, reps=2)
     assert pts in (64, 128, 256, 512, 1024) and ms > 0
+    assert plan.tensor_cores() in (0, 1, 2, 3)
     assert rel(plan.matvec(V).cpu().numpy(), ref) <= 2e-6
     # a batch created after the autotuner uses the new items
     b = agp.Batch([plan])
@@ -74,3 +76,26 @@ def test_item_points_rejected(agp):
         with pytest.raises(agp.AgpError) as ei:
             plan.set_item_points(pts)
         assert ei.value.status == agp.AGP_EINVAL
+
+
+def test_autotune_family_and_cache(agp):
+    """With 32 right-hand sides the tensor-core families compete with the FMA
+    pipes; the choice is one of them, leaves the operator unchanged, and a
+    second plan of the same shape takes the cached choice."""
+    agp.load_library().agp_autotune_clear_cache()
+    w = inputs.subset(inputs.nlml_grad(n=50000, R=32), 50000)
+    mk = lambda: agp.Plan(torch.tensor(w.X, dtype=torch.float32, device=DEV), w.windows, w.N,
+                          w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
+    plan = mk()
+    V = torch.tensor(w.V, dtype=torch.float32, device=DEV)
+    plan.set_tensor_cores(0)
+    ref = plan.matvec(V).cpu().numpy()
+    pts, ms = plan.autotune(R=32, reps=2)
+    mode = plan.tensor_cores()
+    assert mode in (0, 1, 2, 3) and pts in (64, 128, 256, 512, 1024)
+    assert rel(plan.matvec(V).cpu().numpy(), ref) <= 1e-5
+    other = mk()
+    pts2, ms2 = other.autotune(R=32, reps=2)
+    assert (pts2, ms2, other.tensor_cores()) == (pts, ms, mode)
+    plan.close()
+    other.close()
