@@ -227,10 +227,11 @@ def run_gpu(args):
     V = torch.tensor(w.V, dtype=torch.float32, device=dev)
     Out = torch.empty_like(V)
     plan = agp.Plan(X, w.windows, w.N, w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
-    # spreading and interpolation of the d=3 windows on the tensor cores (the
-    # library default for FP32 plans), or on the FP32 FMA pipes with --no-tc
+    # spreading and interpolation of the d=3 windows by the persistent
+    # tensor-memory kernels (family 3, the library default for FP32 plans),
+    # or on the FP32 FMA pipes with --no-tc
     tc = not args.no_tc and R == 32
-    plan.set_tensor_cores(tc)
+    plan.set_tensor_cores(3 if tc else 0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ells = [w.ell * (1.0 + 1e-3 * k) for k in range(args.warmup + args.steps + 1)]
@@ -292,7 +293,7 @@ def run_gpu(args):
         peak = None if bf16 is None else bf16 * (1.1 / 2.25)
         peak_source = ("MEASURED_PEAKS.json bf16_tflops (burst) x 1.1/2.25 (nominal TF32/BF16 "
                        "dense ratio)")
-        kname = f"k_spread_tc<{w.cutoff}>" if dom == "spread" else f"k_interp_tc<{w.cutoff}>"
+        kname = f"k_spread_tm<{w.cutoff}>" if dom == "spread" else f"k_interp_tm<{w.cutoff}>"
         issued = {"products_per_flop": 3, "tflops": 3.0 * useful_tflops,
                   "frac_of_peak": None if peak is None else 3.0 * useful_tflops / peak}
     else:

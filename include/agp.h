@@ -274,11 +274,12 @@ agp_status agp_plan_landmarks(agp_plan plan, int n_landmarks, int32_t* idx, int 
  * operands split into a rounded part and its remainder, of which the tensor
  * cores use the TF32 bits (three products, about FP32 accuracy), accumulated
  * in FP32.
- * enable: 1 on (the default for FP32 plans; spreading by the persistent
- * kernel with the A operand in tensor memory, interpolation by the kernel
- * with both operands in shared memory -- the fastest pair measured), 2 both
- * kernels with operands in shared memory, 3 both persistent tensor-memory
- * kernels, 0 off (FMA path only). */
+ * enable: 3 (the default for FP32 plans) both persistent warp-specialised
+ * kernels with the A operand in tensor memory -- the fastest family
+ * measured (interpolation needs R > RC - 16, else its pass runs on the
+ * shared-memory kernel); 1 spreading by the persistent kernel,
+ * interpolation by the kernel with both operands in shared memory; 2 both
+ * kernels with operands in shared memory; 0 off (FMA path only). */
 agp_status agp_plan_set_tensor_cores(agp_plan plan, int enable);
 
 /* Outer boundary smoothing of the periodic kernel kappa_R (Sec. 3.1: the

@@ -718,10 +718,10 @@ class Plan:
     def afn(self, n_landmarks: int, fill: int) -> Afn:
         return Afn(self, n_landmarks, fill)
 
-    def set_tensor_cores(self, enable: int = 1):
-        """1: tensor-core kernels (the default: tensor-memory spreading,
-        shared-memory interpolation), 2: both with operands in shared memory,
-        3: both persistent tensor-memory kernels, 0: FMA pipes only."""
+    def set_tensor_cores(self, enable: int = 3):
+        """3: both persistent tensor-memory kernels (the default), 1:
+        tensor-memory spreading with shared-memory interpolation, 2: both with
+        operands in shared memory, 0: FMA pipes only."""
         _check(load_library().agp_plan_set_tensor_cores(self._h, int(enable)))
 
     def set_boundary(self, eps_b: float, p: int):

@@ -218,7 +218,7 @@ struct agp_plan_s {
   double kb_b = 0, kb_norm = 0;
   int rc_max = 32;
   int item_points = agp::kItemPoints;   // points per work item (bin size), see agp_plan_autotune
-  int use_tc = 1;                // spreading and interpolation on the tensor cores where supported
+  int use_tc = 3;                // kernel family of spreading and interpolation (agp_plan_set_tensor_cores)
   double bnd_eps = 0.0;          // outer boundary smoothing of kappa_R: layer width (0: off)
   int bnd_p = 0;                 // ... and its order (derivatives matched at each end)
   double* bnd_poly = nullptr;    // [2][kBndStride] boundary polynomials (kernel, ell-derivative)
@@ -279,13 +279,13 @@ cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, c
 // (agp_spread_tm.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5, V rows
 // 16-byte aligned (ldv % 4 == 0); units are the cell runs of the plan.
 bool spread_tm_supported(int d, int s, int RC, const void* V, int64_t ldv);
-cudaError_t spread_units_tm(const WinDev<float>* wins, const int4* units, int64_t n_units, int s,
+cudaError_t spread_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,
                             const float* V, int64_t ldv, int R, int rc, int* err, long long spin,
                             cudaStream_t st);
 // Persistent warp-specialised tensor-core interpolation with A in tensor
 // memory (agp_interp_tm.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5.
 bool interp_tm_supported(int d, int s, int RC, int R);
-cudaError_t interp_units_tm(const WinDev<float>* wins, const int4* units, int64_t n_units, int s,
+cudaError_t interp_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,
                             float* Out, int64_t ldo, int R, float scale, int rc, int* err,
                             long long spin, cudaStream_t st);
 // spread_items, or spread_items_tc when `tc` is set and the case is supported

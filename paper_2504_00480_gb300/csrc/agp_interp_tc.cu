@@ -221,7 +221,7 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
         if (g == 0) it_form_a<S, 0>(w1, w2, np, r8, krow, ahi + o, alo + o);
         else it_form_a<S, 1>(w1, w2, np, r8, krow, ahi + o, alo + o);
       }
-      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");
       ok = __syncthreads_and(ok);                // CTA-wide outcome of the waits so far
       if (!ok) break;
@@ -265,12 +265,12 @@ k_interp_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t3 * RH);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-            "%13,%14,%15}, [%16];"
+            "%13,%14,%15}, [%16];\n"
+            "tcgen05.wait::ld.sync.aligned;"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
         const int tp = t3 - dp;                     // this point's tap
         const float ps = (p < np && tp >= 0 && tp < TT) ? ws[p * WPP + 2 * TTP + 2 * tp] : 0.0f;
 #pragma unroll

@@ -81,7 +81,7 @@ struct ImBars {
 
 template <int S>
 __global__ void __launch_bounds__(kImThreads, 1)
-k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ units,
+k_interp_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __restrict__ units,
             int64_t n_units, float* __restrict__ Out, int64_t ldo, int R, float scale, int rc,
             int* __restrict__ err, long long spin) {
   using Sh = ImShape<S>;
@@ -90,12 +90,14 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
   __shared__ ImBars bars;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;
+  __shared__ WinDev<float> s_win[kMaxWindows];   // the plan's windows, read by every role
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int nh = rc / kImRH;
   const int64_t n_items = n_units * nh;
   volatile int* abort = &abort_word;
   auto bbuf = [&](int b) { return reinterpret_cast<float*>(smem_raw + b * 2 * Sh::B_BYTES); };
 
+  for (int q = tid; q < n_win; q += blockDim.x) s_win[q] = wins[q];
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bars.a_full[b], 4);
@@ -128,11 +130,11 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
     int r0, mt;       // first column, M tiles holding points
   };
   auto unit_at = [&](int64_t i) -> int4 {
-    return i < n_items ? __ldg(units + i / nh) : make_int4(0, 0, 0, 0);
+    return i < n_items ? __ldg(units + (nh == 2 ? i >> 1 : i)) : make_int4(0, 0, 0, 0);
   };
   auto item_from = [&](int64_t i, int4 u, Item& it) {
     it.u = u;
-    it.r0 = (int)(i % nh) * kImRH;
+    it.r0 = (nh == 2 ? (int)(i & 1) : 0) * kImRH;
     it.mt = u.w > kImMP ? 2 : 1;
   };
 
@@ -203,7 +205,7 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
     float* slots = reinterpret_cast<float*>(smem_raw + Sh::OFF_P) + p * (kImMT * Sh::PSI);
     auto slot_of = [&](int64_t j) { return slots + (j & 1) * (kImMP * kImMT * Sh::PSI); };
     auto prefetch = [&](const Item& it, float* slot) {
-      const WinDev<float> w = wins[it.u.x & 0xFFFF];
+      const WinDev<float> w = s_win[it.u.x & 0xFFFF];
 #pragma unroll
       for (int t = 0; t < kImMT; ++t) {
         const int pt = t * kImMP + p;
@@ -300,7 +302,7 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       if (b.i >= n_items) return;
       Item it;
       item_from(b.i, u, it);
-      const WinDev<float> w = wins[it.u.x & 0xFFFF];
+      const WinDev<float> w = s_win[it.u.x & 0xFFFF];
       int cc[3];
       decode_cell<3>(it.u.y, w.N, cc);
       b.W = w.W;
@@ -344,7 +346,7 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
           bl[rg * CORE + o] = x - h;
         }
       }
-      asm volatile("fence.proxy.async.shared::cta;");
+      fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.b_full[bb]);
       ++g;
@@ -373,7 +375,7 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       un = unit_at(i + gridDim.x);
       Item it;
       item_from(i, uc, it);
-      const WinDev<float> w = wins[it.u.x & 0xFFFF];
+      const WinDev<float> w = s_win[it.u.x & 0xFFFF];
       const int L = max(1, it.u.x >> 16), nu = TT + L - 1;
       // this thread's point of each tile: perm index, cell within the run, psi3
       int64_t pi[kImMT];
@@ -406,7 +408,6 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
             uint32_t v[kImRH];
             tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(t * kImDCols + u * kImRH),
                       v);
-            tmem_wait_ld();
             const int t3 = u - delta[t];
             float ps = 0.0f;
 #pragma unroll
@@ -457,7 +458,7 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
 }
 
 template <int S>
-cudaError_t interp_tm_s(const WinDev<float>* wins, const int4* units, int64_t n_units, float* Out,
+cudaError_t interp_tm_s(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, float* Out,
                         int64_t ldo, int R, float scale, int rc, int* err, long long spin,
                         cudaStream_t st) {
   using Sh = ImShape<S>;
@@ -465,13 +466,14 @@ cudaError_t interp_tm_s(const WinDev<float>* wins, const int4* units, int64_t n_
                                        Sh::SMEM);
   if (e != cudaSuccess) return e;
   if (n_units <= 0) return cudaSuccess;
+  if (n_win < 1 || n_win > kMaxWindows) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int64_t items = n_units * (rc / kImRH);
   const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-  k_interp_tm<S><<<grid, kImThreads, Sh::SMEM, st>>>(wins, units, n_units, Out, ldo, R, scale,
+  k_interp_tm<S><<<grid, kImThreads, Sh::SMEM, st>>>(wins, n_win, units, n_units, Out, ldo, R, scale,
                                                      rc, err, spin);
   return cudaGetLastError();
 }
@@ -484,12 +486,12 @@ bool interp_tm_supported(int d, int s, int RC, int R) {
   return d == 3 && (RC == 32 || RC == 16) && (s == 4 || s == 5) && R > RC - kImRH;
 }
 
-cudaError_t interp_units_tm(const WinDev<float>* wins, const int4* units, int64_t n_units, int s,
+cudaError_t interp_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,
                             float* Out, int64_t ldo, int R, float scale, int rc, int* err,
                             long long spin, cudaStream_t st) {
   switch (s) {
-    case 4: return interp_tm_s<4>(wins, units, n_units, Out, ldo, R, scale, rc, err, spin, st);
-    case 5: return interp_tm_s<5>(wins, units, n_units, Out, ldo, R, scale, rc, err, spin, st);
+    case 4: return interp_tm_s<4>(wins, n_win, units, n_units, Out, ldo, R, scale, rc, err, spin, st);
+    case 5: return interp_tm_s<5>(wins, n_win, units, n_units, Out, ldo, R, scale, rc, err, spin, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -1068,7 +1068,7 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       StageTimer tm(pl, 0, st, dd);
       if (dd == 3 && pl->runs3 && (pl->use_tc == 1 || pl->use_tc == 3) && sizeof(T) == 4 &&
           spread_tm_supported(3, pl->s, rc, V + r0, ldv))
-        AGP_CUDA(spread_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->runs3,
+        AGP_CUDA(spread_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->P, pl->runs3,
                                  pl->n_runs3, pl->s, reinterpret_cast<const float*>(V + r0), ldv,
                                  Rc, rc, pl->err_dev, pl->wait_limit, st));
       else if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 &&
@@ -1108,7 +1108,7 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       StageTimer tm(pl, 2, st, dd);
       if (dd == 3 && pl->runs3 && pl->use_tc == 3 && sizeof(T) == 4 &&
           interp_tm_supported(3, pl->s, rc, Rc))
-        AGP_CUDA(interp_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->runs3,
+        AGP_CUDA(interp_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->P, pl->runs3,
                                  pl->n_runs3, pl->s, reinterpret_cast<float*>(Out + r0), ldo, Rc,
                                  (float)scale, rc, pl->err_dev, pl->wait_limit, st));
       else if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 &&

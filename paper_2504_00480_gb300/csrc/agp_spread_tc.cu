@@ -279,7 +279,7 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
       }
     }
     cp_async_wait<PD - 1>();              // chunk c + 1 staged (this thread's copies)
-    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     // operands of chunk c and staging of c + 1 complete; the CTA agrees on
     // whether every wait so far succeeded (on failure: issue nothing more)
@@ -333,12 +333,12 @@ k_spread_tc(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restri
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t3 * RH);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-          "%14,%15}, [%16];"
+          "%14,%15}, [%16];\n"
+            "tcgen05.wait::ld.sync.aligned;"
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
             "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
             "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
           : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         *reinterpret_cast<float4*>(tile + lane * 16 + ((c ^ ((lane >> 1) & 3)) << 2)) =

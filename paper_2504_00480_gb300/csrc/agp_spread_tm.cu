@@ -110,7 +110,7 @@ struct TmBars {
 
 template <int S>
 __global__ void __launch_bounds__(kTmThreads, 1)
-k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ units,
+k_spread_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __restrict__ units,
             int64_t n_units, const float* __restrict__ V, int64_t ldv, int R, int rc,
             int* __restrict__ err, long long spin) {
   using Sh = TmShape<S>;
@@ -119,6 +119,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
   __shared__ TmBars bars;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;
+  __shared__ WinDev<float> s_win[kMaxWindows];   // the plan's windows, read by every role
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int nh = rc / kTmRH;
   const int64_t n_items = n_units * nh;
@@ -128,6 +129,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
     return reinterpret_cast<float*>(smem_raw + Sh::OFF_B + b * 2 * Sh::B_BYTES);
   };
 
+  for (int q = tid; q < n_win; q += blockDim.x) s_win[q] = wins[q];
   if (tid == 0) {
     for (int s = 0; s < kTmNS; ++s) {
       mbar_init(&bars.st_full[s], 1 + 32);             // bulk bytes + one cp.async arrival per lane
@@ -164,11 +166,11 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
   };
   // the unit of work item i (loaded one item ahead by every role)
   auto unit_at = [&](int64_t i) -> int4 {
-    return i < n_items ? __ldg(units + i / nh) : make_int4(0, 0, 0, 0);
+    return i < n_items ? __ldg(units + (nh == 2 ? i >> 1 : i)) : make_int4(0, 0, 0, 0);
   };
   auto item_from = [&](int64_t i, int4 u, Item& it) -> bool {
     it.u = u;
-    it.r0 = (int)(i % nh) * kTmRH;
+    it.r0 = (nh == 2 ? (int)(i & 1) : 0) * kTmRH;
     it.nchunk = (it.u.w + kTmKC - 1) / kTmKC;
     return it.r0 < R && it.u.w > 0;
   };
@@ -184,7 +186,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       int32_t v[PQ];
     };
     auto perms = [&](const Item& it, bool valid) -> Perms {
-      const int32_t* pp = wins[valid ? it.u.x & 0xFFFF : 0].perm + (valid ? it.u.z : 0);
+      const int32_t* pp = s_win[valid ? it.u.x & 0xFFFF : 0].perm + (valid ? it.u.z : 0);
       const int m = valid ? it.u.w : 0;
       Perms pr;
 #pragma unroll
@@ -208,7 +210,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       const bool nv = item_from(i + gridDim.x, un, nx);
       pn = perms(nx, nv);                             // the next item's indices, in flight
       pre = nv ? i + gridDim.x : -1;
-      const WinDev<float> w = wins[it.u.x & 0xFFFF];
+      const WinDev<float> w = s_win[it.u.x & 0xFFFF];
       bool ok = true;
       for (int c = 0; c < it.nchunk; ++c, ++g) {
         const int s = (int)(g % kTmNS);
@@ -356,7 +358,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
     };
     auto bounds = [&](const Item& it, bool valid) -> Bnd {
       const int L = valid ? max(1, it.u.x >> 16) : 1;
-      const int32_t* cs = wins[valid ? it.u.x & 0xFFFF : 0].cell_start + (valid ? it.u.y : 0);
+      const int32_t* cs = s_win[valid ? it.u.x & 0xFFFF : 0].cell_start + (valid ? it.u.y : 0);
       Bnd b;
 #pragma unroll
       for (int q = 0; q < kRunCells - 1; ++q) b.v[q] = (q + 1 < L) ? __ldg(cs + q + 1) : 0x7FFFFFFF;
@@ -406,7 +408,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
           tm_form_b<S, 1>(pw + 2 * TTP, live, delta, nu, v0, v1, bh + o, bl + o);
         else
           tm_form_b<S, 2>(pw + 2 * TTP, live, delta, nu, v0, v1, bh + o, bl + o);
-        asm volatile("fence.proxy.async.shared::cta;");
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&bars.b_full[bb]);
@@ -430,7 +432,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       const int db = (int)(nd & 1);
       if (!warp_wait(&bars.d_full[db], (uint32_t)((nd >> 1) & 1), spin, abort)) break;
       tc_fence_after();
-      const WinDev<float> w = wins[it.u.x & 0xFFFF];
+      const WinDev<float> w = s_win[it.u.x & 0xFFFF];
       const int L = max(1, it.u.x >> 16), nu = TT + L - 1;
       int cc[3];
       decode_cell<3>(it.u.y, w.N, cc);
@@ -438,7 +440,6 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
       for (int u = 0; u < nu; ++u) {
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(db * kTmDCols + u * kTmRH), v);
-        tmem_wait_ld();
         // through shared memory so that four lanes cover one row's 16
         // contiguous values; 16-byte chunk c of row l sits at chunk c ^ ((l >> 1) & 3)
 #pragma unroll
@@ -488,7 +489,7 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, const int4* __restrict__ uni
 }
 
 template <int S>
-cudaError_t spread_tm_s(const WinDev<float>* wins, const int4* units, int64_t n_units,
+cudaError_t spread_tm_s(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units,
                         const float* V, int64_t ldv, int R, int rc, int* err, long long spin,
                         cudaStream_t st) {
   using Sh = TmShape<S>;
@@ -496,13 +497,14 @@ cudaError_t spread_tm_s(const WinDev<float>* wins, const int4* units, int64_t n_
                                        Sh::SMEM);
   if (e != cudaSuccess) return e;
   if (n_units <= 0) return cudaSuccess;
+  if (n_win < 1 || n_win > kMaxWindows) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int64_t items = n_units * (rc / kTmRH);
   const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-  k_spread_tm<S><<<grid, kTmThreads, Sh::SMEM, st>>>(wins, units, n_units, V, ldv, R, rc, err,
+  k_spread_tm<S><<<grid, kTmThreads, Sh::SMEM, st>>>(wins, n_win, units, n_units, V, ldv, R, rc, err,
                                                      spin);
   return cudaGetLastError();
 }
@@ -514,12 +516,12 @@ bool spread_tm_supported(int d, int s, int RC, const void* V, int64_t ldv) {
          (reinterpret_cast<uintptr_t>(V) & 15) == 0;
 }
 
-cudaError_t spread_units_tm(const WinDev<float>* wins, const int4* units, int64_t n_units, int s,
+cudaError_t spread_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,
                             const float* V, int64_t ldv, int R, int rc, int* err, long long spin,
                             cudaStream_t st) {
   switch (s) {
-    case 4: return spread_tm_s<4>(wins, units, n_units, V, ldv, R, rc, err, spin, st);
-    case 5: return spread_tm_s<5>(wins, units, n_units, V, ldv, R, rc, err, spin, st);
+    case 4: return spread_tm_s<4>(wins, n_win, units, n_units, V, ldv, R, rc, err, spin, st);
+    case 5: return spread_tm_s<5>(wins, n_win, units, n_units, V, ldv, R, rc, err, spin, st);
   }
   return cudaErrorInvalidValue;
 }

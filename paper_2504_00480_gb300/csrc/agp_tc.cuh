@@ -55,7 +55,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-               ::"r"(smem_u32(bar)));
+               ::"r"(smem_u32(bar))
+               : "memory");
 }
 
 // bounded wait for the given phase parity (at most `limit` polls); false on
@@ -70,13 +71,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done) : "r"(a), "r"(parity));
+      : "=r"(done) : "r"(a), "r"(parity)
+      : "memory");
   if (done) return true;
   for (long long it = 1; it < limit; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done) : "r"(a), "r"(parity));
+        : "=r"(done) : "r"(a), "r"(parity)
+        : "memory");
     if (done) return true;
   }
   return false;

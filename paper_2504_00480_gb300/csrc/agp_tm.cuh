@@ -24,7 +24,8 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(
-      smem_u32(bar)));
+      smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
@@ -32,7 +33,8 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity));
+      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
   return done != 0;
 }
 
@@ -41,7 +43,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity));
+      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
   return done != 0;
 }
 
@@ -74,7 +77,8 @@ __device__ __forceinline__ bool warp_aborted(volatile int* abort) {
 // copies that complete on it).
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
-               ::"r"(smem_u32(bar)), "r"(bytes));
+               ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
 }
 
 // Bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16)
@@ -90,13 +94,20 @@ __device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, uint32_t 
 // The calling thread's earlier cp.async copies arrive on `bar` when complete
 // (the arrival is counted in the barrier's expected count).
 __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)));
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
                "r"(src_bytes)
                : "memory");
+}
+
+// generic-proxy shared-memory writes made visible to the async proxy (the
+// tensor cores read the B operand through it)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -119,10 +130,13 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
 }
 
+// 16 consecutive tensor-memory columns of the warp's 32 lanes, waited for in
+// the same statement (the registers are valid when it returns)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
+      "%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
         "=r"(v[14]), "=r"(v[15])
@@ -130,7 +144,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
 }
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;");
 }

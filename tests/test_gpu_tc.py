@@ -1,7 +1,9 @@
 """Spreading and interpolation on the tensor cores (tcgen05, split TF32):
-the matvec and the derivative operators with the tensor-core kernels
-against the oracle at the FP32 tolerance, against the FMA-pipe kernels of
-the same plan, for both supported cutoffs, a ragged right-hand-side count,
+the matvec and the derivative operators with each tensor-core kernel
+family (3, the default: both persistent kernels with A in tensor memory; 1:
+tensor-memory spreading, shared-memory interpolation; 2: both with operands
+in shared memory) against the oracle at the FP32 tolerance, against the
+FMA-pipe kernels of the same plan, for both supported cutoffs, a ragged right-hand-side count,
 strided blocks and the full-size workload on sampled rows. 17 .. 32
 right-hand sides run in passes of 32 grid columns, 9 .. 16 in passes of 16."""
 import numpy as np
@@ -35,9 +37,10 @@ def points(rng, n, p):
     return inputs.to_precision(X, np.float32).astype(np.float64)
 
 
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("s,N,R", [(5, 32, 32), (5, 32, 17), (4, 16, 32), (5, 16, 25),
                                    (5, 32, 12), (4, 16, 9)])
-def test_tc_spread_matches_oracle_and_fma_path(agp, s, N, R):
+def test_tc_spread_matches_oracle_and_fma_path(agp, s, N, R, mode):
     rng = np.random.default_rng(100 + s + R)
     n = 4000
     X = points(rng, n, 7)
@@ -48,7 +51,7 @@ def test_tc_spread_matches_oracle_and_fma_path(agp, s, N, R):
     Vt = torch.tensor(V, dtype=torch.float32, device=DEV)
     plan.set_tensor_cores(False)
     ref = plan.matvec(Vt).cpu().numpy()
-    plan.set_tensor_cores(True)
+    plan.set_tensor_cores(mode)
     got = plan.matvec(Vt).cpu().numpy()
     plan.check()
     want = O.truncated_matvec(X, W, "gauss", 0.15, 0.9, 0.2, V, N)
@@ -68,7 +71,7 @@ def test_tc_spread_strided_and_adjoint_nfft(agp):
     V = rng.standard_normal((n, 40))
     plan = agp.Plan(torch.tensor(X, dtype=torch.float32, device=DEV), [[0, 1, 2]], 32, 5,
                     "matern12", 0.2, 1.0, 0.1)
-    plan.set_tensor_cores(True)              # the default for FP32 plans
+    plan.set_tensor_cores(1)
     Vt = torch.tensor(V, dtype=torch.float32, device=DEV)[:, 3:35]   # ldv = 40, unaligned start
     got = plan.matvec(Vt).cpu().numpy()
     want = O.truncated_matvec(X, [[0, 1, 2]], "matern12", 0.2, 1.0, 0.1, V[:, 3:35], 32)
@@ -108,18 +111,19 @@ def test_tc_full_size_every_operator_sampled_rows(agp):
     X = torch.tensor(w.X, dtype=torch.float32, device=DEV)
     V = torch.tensor(w.V, dtype=torch.float32, device=DEV)
     plan = agp.Plan(X, w.windows, w.N, w.cutoff, w.kernel, w.ell, w.sigma_f, w.sigma_eps)
-    plan.set_tensor_cores(True)
-    got = {"K": plan.matvec(V)}
-    for which in ["ell", "sigma_f", "sigma_eps"]:
-        got[which] = plan.deriv_matvec(which, V)
-    plan.check()
     cols = [0, 3, 7, 12, 17, 22, 26, 31]
     rows = np.sort(np.random.default_rng(5).choice(w.X.shape[0], 256, replace=False))
     want = O.truncated_operators(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps,
                                  w.V[:, cols].astype(np.float32).astype(np.float64), w.N,
                                  rows=rows)
-    for which, g in got.items():
-        gs = g[rows][:, cols].double().cpu().numpy()
-        for j in range(len(cols)):
-            assert rel(gs[:, j], want[which][:, j]) <= 1e-4, (which, cols[j])
+    for mode in [3, 1, 2]:                   # the default family first
+        plan.set_tensor_cores(mode)
+        got = {"K": plan.matvec(V)}
+        for which in ["ell", "sigma_f", "sigma_eps"]:
+            got[which] = plan.deriv_matvec(which, V)
+        plan.check()
+        for which, g in got.items():
+            gs = g[rows][:, cols].double().cpu().numpy()
+            for j in range(len(cols)):
+                assert rel(gs[:, j], want[which][:, j]) <= 1e-4, (mode, which, cols[j])
     plan.close()
