@@ -78,6 +78,8 @@ _SIGS = {
     "agp_plan_set_boundary": (c_int, [c_void_p, c_double, c_int, c_void_p]),
     "agp_plan_check": (c_int, [c_void_p, c_void_p]),
     "agp_plan_tensor_cores": (c_int, [c_void_p, POINTER(c_int)]),
+    "agp_plan_kernel_families": (c_int, [c_void_p, c_int, ctypes.c_int64, POINTER(c_int),
+                                         POINTER(c_int)]),
     "agp_autotune_clear_cache": (c_int, []),
     "agp_plan_autotune": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_double),
                                   c_void_p]),
@@ -744,6 +746,16 @@ class Plan:
         m = c_int()
         _check(load_library().agp_plan_tensor_cores(self._h, byref(m)))
         return m.value
+
+    def kernel_families(self, R: int, ldv: int | None = None) -> tuple[int, int]:
+        """(spreading, interpolation) kernel family of the d = 3 windows for an
+        R-column application: 3 tensor-memory, 2 shared-memory tensor-core
+        over cell runs, 1 tensor-core over work items, 0 FMA, -1 no d = 3
+        window."""
+        sp, ip = c_int(), c_int()
+        _check(load_library().agp_plan_kernel_families(self._h, int(R), int(ldv or R),
+                                                       byref(sp), byref(ip)))
+        return sp.value, ip.value
 
     def set_item_points(self, points: int):
         agp_plan_set_item_points(self._h, points)

@@ -53,8 +53,6 @@ constexpr int kRunCells = 4;
 // FP32 accumulation error grows with the number of MMAs summed into one
 // accumulator).
 constexpr int kRunPoints = 256;
-// Points per interpolation tile (one tensor-memory lane per point).
-constexpr int kTilePoints = 128;
 // Outer boundary smoothing: largest order p, and the stride of one boundary
 // polynomial record (2p coefficients, padded, then the constant kappa(1/2)).
 constexpr int kBndMaxP = 8;
@@ -231,8 +229,6 @@ struct agp_plan_s {
   int4* items_all = nullptr;     // work items of every window, grouped by d
   int4* runs3 = nullptr;         // tensor-core work units (cell runs) of the d = 3 windows
   int64_t n_runs3 = 0;
-  int4* tiles3 = nullptr;        // the same runs cut into tiles of at most kTilePoints points
-  int64_t n_tiles3 = 0;
   int64_t items_by_d[agp::kMaxDim + 1] = {0, 0, 0, 0};   // offsets of each d group
   std::vector<agp::FftGroup> groups;   // windows grouped by (d, N) for the DFT stages
   int* err_dev = nullptr;        // device error flags
@@ -285,8 +281,8 @@ cudaError_t spread_units_tm(const WinDev<float>* wins, int n_win, const int4* un
 // Persistent warp-specialised tensor-core interpolation with A in tensor
 // memory (agp_interp_tm.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5.
 bool interp_tm_supported(int d, int s, int RC, int R);
-cudaError_t interp_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,
-                            float* Out, int64_t ldo, int R, float scale, int rc, int* err,
+cudaError_t interp_units_tm(const WinDev<float>* wins, int n_win, const int4* units,
+                            int64_t n_units, int s, float* Out, int64_t ldo, int R, float scale, int rc, int* err,
                             long long spin, cudaStream_t st);
 // spread_items, or spread_items_tc when `tc` is set and the case is supported
 // (spin: polls per bounded wait of the tensor-core kernel)

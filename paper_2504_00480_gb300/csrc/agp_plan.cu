@@ -701,7 +701,6 @@ void free_plan(agp_plan_s* pl) {
   }
   cudaFree(pl->items_all);
   cudaFree(pl->runs3);
-  cudaFree(pl->tiles3);
   cudaFree(pl->wins_dev);
   cudaFree(pl->err_dev);
   cudaFree(pl->bnd_poly);
@@ -764,7 +763,7 @@ agp_status build_items(agp_plan_s* pl, int cap, cudaStream_t st) {
   // runs of kRunCells cells along the last dimension for the tensor-core
   // kernels (host: cell_start of every d = 3 window, the non-empty runs)
   if (!pl->runs3) {
-    std::vector<int4> runs, tiles;
+    std::vector<int4> runs;
     for (int s = 0; s < pl->P; ++s) {
       const Window& w = pl->win[s];
       if (w.d != 3 || w.N % kRunCells != 0) continue;
@@ -776,18 +775,12 @@ agp_status build_items(agp_plan_s* pl, int cap, cudaStream_t st) {
         const int a = cs[c], b = cs[c + kRunCells];
         for (int q = a; q < b; q += kRunPoints)
           runs.push_back(make_int4(s | (kRunCells << 16), (int)c, q, std::min(kRunPoints, b - q)));
-        for (int q = a; q < b; q += kTilePoints)
-          tiles.push_back(make_int4(s | (kRunCells << 16), (int)c, q, std::min(kTilePoints, b - q)));
       }
     }
     pl->n_runs3 = (int64_t)runs.size();
-    pl->n_tiles3 = (int64_t)tiles.size();
     if (!runs.empty()) {
       AGP_CUDA(cudaMalloc(&pl->runs3, sizeof(int4) * runs.size()));
       AGP_CUDA(cudaMemcpyAsync(pl->runs3, runs.data(), sizeof(int4) * runs.size(),
-                               cudaMemcpyHostToDevice, st));
-      AGP_CUDA(cudaMalloc(&pl->tiles3, sizeof(int4) * tiles.size()));
-      AGP_CUDA(cudaMemcpyAsync(pl->tiles3, tiles.data(), sizeof(int4) * tiles.size(),
                                cudaMemcpyHostToDevice, st));
       AGP_CUDA(cudaStreamSynchronize(st));
     }
@@ -969,6 +962,28 @@ struct TuneEntry {
 std::mutex g_tune_mu;
 std::map<std::string, TuneEntry> g_tune_cache;
 
+// Kernel family of a pass's d = 3 spreading / interpolation (rc grid
+// columns, Rc of them in use, V or Out at the given address and stride):
+// 3 the persistent tensor-memory kernel over cell runs, 2 the shared-memory
+// tensor-core kernel over cell runs, 1 the tensor-core kernel over work items
+// where it supports the case, else 0, the FMA kernel over work items.
+int spread_family3(const agp_plan_s* pl, int rc, const void* V, int64_t ldv) {
+  if (pl->prec != AGP_F32 || !pl->use_tc) return 0;
+  if (pl->runs3 && (pl->use_tc == 1 || pl->use_tc == 3) &&
+      spread_tm_supported(3, pl->s, rc, V, ldv))
+    return 3;
+  if (pl->runs3 && spread_tc_supported(3, pl->s, rc)) return 2;
+  return spread_tc_supported(3, pl->s, rc) ? 1 : 0;
+}
+
+int interp_family3(const agp_plan_s* pl, int rc, int Rc) {
+  if (pl->prec != AGP_F32 || !pl->use_tc) return 0;
+  if (pl->runs3 && pl->use_tc == 3 && interp_tm_supported(3, pl->s, rc, Rc))
+    return 3;
+  if (pl->runs3 && interp_tc_supported(3, pl->s, rc)) return 2;
+  return interp_tc_supported(3, pl->s, rc) ? 1 : 0;
+}
+
 // Stage timing: a pair of events around a group of launches on `st`.
 struct StageTimer {
   agp_plan_s* pl;
@@ -1066,13 +1081,12 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 0, st, dd);
-      if (dd == 3 && pl->runs3 && (pl->use_tc == 1 || pl->use_tc == 3) && sizeof(T) == 4 &&
-          spread_tm_supported(3, pl->s, rc, V + r0, ldv))
+      const int fam = dd == 3 ? spread_family3(pl, rc, V + r0, ldv) : 0;
+      if (fam == 3)
         AGP_CUDA(spread_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->P, pl->runs3,
                                  pl->n_runs3, pl->s, reinterpret_cast<const float*>(V + r0), ldv,
                                  Rc, rc, pl->err_dev, pl->wait_limit, st));
-      else if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 &&
-               spread_tc_supported(3, pl->s, rc))
+      else if (fam == 2)
         AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc, V + r0,
                                      ldv, Rc, 1, pl->err_dev, pl->wait_limit, st));
       else
@@ -1106,13 +1120,12 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
       StageTimer tm(pl, 2, st, dd);
-      if (dd == 3 && pl->runs3 && pl->use_tc == 3 && sizeof(T) == 4 &&
-          interp_tm_supported(3, pl->s, rc, Rc))
+      const int fam = dd == 3 ? interp_family3(pl, rc, Rc) : 0;
+      if (fam == 3)
         AGP_CUDA(interp_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->P, pl->runs3,
                                  pl->n_runs3, pl->s, reinterpret_cast<float*>(Out + r0), ldo, Rc,
                                  (float)scale, rc, pl->err_dev, pl->wait_limit, st));
-      else if (dd == 3 && pl->runs3 && pl->use_tc && sizeof(T) == 4 &&
-               interp_tc_supported(3, pl->s, rc))
+      else if (fam == 2)
         AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc,
                                      Out + r0, ldo, Rc, scale, 1, pl->err_dev, pl->wait_limit,
                                      st));
@@ -1633,6 +1646,19 @@ agp_status agp_plan_autotune(agp_plan pl, int R, int reps, int* points, double* 
 agp_status agp_plan_tensor_cores(agp_plan pl, int* mode) {
   if (!pl || !mode) return set_error(AGP_EINVAL, "bad arguments");
   *mode = pl->use_tc;
+  return AGP_OK;
+}
+
+agp_status agp_plan_kernel_families(agp_plan pl, int R, int64_t ldv, int* spread, int* interp) {
+  if (!pl || R < 1 || ldv < R || !spread || !interp) return set_error(AGP_EINVAL, "bad arguments");
+  *spread = *interp = -1;
+  bool d3 = false;
+  for (const Window& w : pl->win) d3 = d3 || w.d == 3;
+  if (!d3) return AGP_OK;
+  const int rc = pick_rc(pl, R);
+  const void* aligned = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));
+  *spread = spread_family3(pl, rc, aligned, ldv);
+  *interp = interp_family3(pl, rc, std::min(rc, R));
   return AGP_OK;
 }
 

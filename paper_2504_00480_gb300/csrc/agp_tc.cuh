@@ -19,6 +19,10 @@ namespace agp {
 namespace {
 
 constexpr long long kTcSpinLimit = 1ll << 26;
+// Suspend-time hint of one try_wait poll (ns): a waiting thread sleeps until
+// the phase completes or the hint runs out, instead of spinning on the issue
+// slots that the working roles of the CTA need.
+constexpr uint32_t kTcSuspendNs = 1000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -60,9 +64,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 // bounded wait for the given phase parity (at most `limit` polls); false on
-// expiry. The first poll is a non-blocking test, the later ones may suspend
-// the thread for a while (try_wait), so a limit of 1 gives up at once unless
-// the phase is already complete.
+// expiry. The first poll is a non-blocking test, the later ones suspend the
+// thread for up to kTcSuspendNs (try_wait), so a limit of 1 gives up at once
+// unless the phase is already complete.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
                                           long long limit = kTcSpinLimit) {
   const uint32_t a = smem_u32(bar);
@@ -76,9 +80,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
   if (done) return true;
   for (long long it = 1; it < limit; ++it) {
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done) : "r"(a), "r"(parity)
+        : "=r"(done) : "r"(a), "r"(parity), "r"(kTcSuspendNs)
         : "memory");
     if (done) return true;
   }

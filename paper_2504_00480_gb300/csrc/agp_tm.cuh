@@ -4,8 +4,8 @@
 // stores and loads, and tcgen05.mma with the A operand in tensor memory.
 //
 // Wait discipline: a role that waits polls its mbarrier at most `limit`
-// times (the first poll a non-blocking test, the later ones may suspend the
-// thread for a while) and gives up early when another role has raised the
+// times (the first poll a non-blocking test, the later ones suspend the
+// thread for up to kTcSuspendNs, waking when the phase completes) and gives up early when another role has raised the
 // CTA's abort word; a wait that runs out raises it. Every role then leaves
 // its loop, so no thread of the CTA can be left waiting on a barrier that
 // will never complete.
@@ -41,9 +41,9 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity)
+      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity), "r"(kTcSuspendNs)
       : "memory");
   return done != 0;
 }

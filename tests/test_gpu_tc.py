@@ -52,6 +52,9 @@ def test_tc_spread_matches_oracle_and_fma_path(agp, s, N, R, mode):
     plan.set_tensor_cores(False)
     ref = plan.matvec(Vt).cpu().numpy()
     plan.set_tensor_cores(mode)
+    # the kernels that run: spreading's persistent kernel needs 16-byte rows
+    sp = 3 if mode in (1, 3) and R % 4 == 0 else 2
+    assert plan.kernel_families(R) == (sp, 3 if mode == 3 else 2)
     got = plan.matvec(Vt).cpu().numpy()
     plan.check()
     want = O.truncated_matvec(X, W, "gauss", 0.15, 0.9, 0.2, V, N)
@@ -116,6 +119,7 @@ def test_tc_full_size_every_operator_sampled_rows(agp):
     want = O.truncated_operators(w.X, w.windows, w.kernel, w.ell, w.sigma_f, w.sigma_eps,
                                  w.V[:, cols].astype(np.float32).astype(np.float64), w.N,
                                  rows=rows)
+    assert plan.tensor_cores() == 3 and plan.kernel_families(32) == (3, 3)
     for mode in [3, 1, 2]:                   # the default family first
         plan.set_tensor_cores(mode)
         got = {"K": plan.matvec(V)}
