@@ -209,7 +209,16 @@ agp_status batch_matvec(agp_batch_s* b, int which, cudaStream_t st) {
                                    b->R, b->plans[0]->use_tc, b->plans[0]->err_dev,
                                    b->plans[0]->wait_limit, st));
   }
+  // groups with d = 2 or 3: the three-launch DFT stage; the others per group
+  FftGroup fg[8];
+  int nf = 0;
+  for (const auto& g : b->groups)
+    if (dft_fused_supported(g) && nf < 8) fg[nf++] = g;
+  if (nf > 0) AGP_CUDA(dft_stage<T>(fg, nf, der, b->rc, st));
   for (const auto& g : b->groups) {
+    bool done = false;
+    for (int q = 0; q < nf; ++q) done = done || fg[q].tab == g.tab;
+    if (done) continue;
     AGP_CUDA(fft_forward<T>(g, b->rc, st));
     AGP_CUDA(spectral_multiply<T>(g, der, b->rc, st));
     AGP_CUDA(fft_inverse<T>(g, b->rc, st));

@@ -432,5 +432,10 @@ template <typename T>
 cudaError_t spectral_multiply(const FftGroup& g, int der, int RC, cudaStream_t st);
 template <typename T>
 cudaError_t zero_grids(const FftGroup& g, int RC, cudaStream_t st);
+// The whole DFT stage (forward, multiply, inverse) of groups with d = 2 or 3
+// in three launches (agp_dft.cu); the spectrum is not kept.
+bool dft_fused_supported(const FftGroup& g);
+template <typename T>
+cudaError_t dft_stage(const FftGroup* groups, int n_groups, int der, int RC, cudaStream_t st);
 
 }  // namespace agp

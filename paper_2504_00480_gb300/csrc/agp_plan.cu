@@ -1097,8 +1097,22 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
     }
     {
       StageTimer tm(pl, 1, st);
+      // groups with d = 2 or 3 take the three-launch stage unless their
+      // spectra are kept (at most 8 such groups: d in {2, 3} x 4 sizes N)
+      FftGroup fg[8];
+      int nf = 0;
+      if (!spec)
+        for (const auto& g : pl->groups)
+          if (dft_fused_supported(g) && nf < 8) fg[nf++] = g;
+      if (nf > 0) {
+        AGP_CUDA(dft_stage<T>(fg, nf, der, rc, st));
+        pl->launches[1] += 3;
+      }
       int64_t goff = 0;
       for (const auto& g : pl->groups) {
+        bool done = false;
+        for (int q = 0; q < nf; ++q) done = done || fg[q].tab == g.tab;
+        if (done) continue;
         AGP_CUDA(fft_forward<T>(g, rc, st));
         pl->launches[1] += g.d;
         if (spec) {

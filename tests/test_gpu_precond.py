@@ -165,12 +165,13 @@ def test_pcg_fp32_batched_pcg_workload_subset(agp):
     # near that floor (measured over three repeats: 21 of 24 columns at 262-308
     # steps, two at 550-800, one stalled at 2.9e-3 after 1000; FP64: 252-288
     # every time; plain FP32 CG: none of 8 within 1500; a later run: 7 of 8 at
-    # 262-313, one at 620). With residual replacement (the recomputed
-    # residual carries the FP32 operator's rounding into the recursion at
-    # every replacement) the FP32 solves take 270-420 steps, medians 1.09x to
-    # 1.28x the FP64 ones over six solves of the three tensor-core families.
-    # Checked: most columns converge, the median converged column needs at
-    # most 1.5x the FP64 steps and every converged column at most 3x, and every
+    # 262-313, one at 620). With residual replacement every column reaches
+    # the tolerance (the recomputed residual carries the FP32 operator's
+    # rounding into the recursion at every replacement, so the FP32 solves
+    # take 270-420 steps: medians 1.09x to 1.28x and every column at most
+    # 1.5x the FP64 steps over six solves of the three tensor-core families).
+    # Checked: every column converges, in at most 2x the FP64 steps, the
+    # median in at most 1.5x, and every
     # column's true residual (FP64 plan) obeys the bound of an exact solve of
     # the perturbed FP32 operator K + E, |E x| <= e_mv |K| |x|:
     # |b - K x| <= max(rtol, relres) |b| + 2 e_mv |K| |x|.
@@ -186,10 +187,9 @@ def test_pcg_fp32_batched_pcg_workload_subset(agp):
                                 raise_not_converged=False)
     _, it_d, rel_d = p64.solve(V64, rtol=1e-4, maxit=1000, n_landmarks=480)
     assert np.all(rel_d <= 1e-4)
-    conv = rel_p <= 1e-4
-    assert conv.sum() >= 6, (it_p, rel_p)
-    assert np.median(it_p[conv]) <= 1.5 * np.median(it_d[conv]), (it_p, it_d)
-    assert np.all(it_p[conv] <= 3 * it_d[conv]), (it_p, it_d)
+    assert np.all(rel_p <= 1e-4), (it_p, rel_p)
+    assert np.median(it_p) <= 1.5 * np.median(it_d), (it_p, it_d)
+    assert np.all(it_p <= 2 * it_d), (it_p, it_d)
     Xn = Xp.double()
     KX = p64.matvec(Xn)
     true = (torch.linalg.norm(V64 - KX, dim=0) / torch.linalg.norm(V64, dim=0)).cpu().numpy()
