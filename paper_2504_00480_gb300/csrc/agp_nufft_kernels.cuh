@@ -604,6 +604,89 @@ k_interp(const WinDev<T>* __restrict__ wins, const WinIO<T>* __restrict__ io,
   }
 }
 
+// Interpolation of one right-hand side, one thread per point. A CTA takes
+// kPtsItems consecutive work items and numbers their points through a prefix
+// sum in shared memory; each point reads its (2s)^d grid block straight from
+// the grid (a cell's block is shared by the cell's points through the L1
+// cache) and contracts it one dimension at a time. For sparse cells (a few
+// points per work item) this replaces a CTA per item that stages a whole
+// block for two or three points.
+constexpr int kPtsItems = 64;
+
+template <typename T, int D, int S>
+__global__ void __launch_bounds__(128)
+k_interp_pts(const WinDev<T>* __restrict__ wins, const WinIO<T>* __restrict__ io,
+             const int4* __restrict__ items, int64_t n_items, T* __restrict__ Out, int64_t ldo,
+             T scale) {
+  constexpr int TT = 2 * S, TTP = ttp_of(S), WPP = wpp_of(D, S);
+  __shared__ int4 its[kPtsItems];
+  __shared__ int pre[kPtsItems + 1];
+  const int64_t i0 = (int64_t)blockIdx.x * kPtsItems;
+  const int ni = (int)(n_items - i0 < kPtsItems ? n_items - i0 : kPtsItems);
+  if (threadIdx.x < ni) its[threadIdx.x] = items[i0 + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int q = 0; q < ni; ++q) {
+      pre[q] = acc;
+      acc += its[q].w;
+    }
+    pre[ni] = acc;
+  }
+  __syncthreads();
+  const int P = pre[ni];
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    int lo = 0, hi = ni - 1;                   // the item holding point p
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= p) lo = mid;
+      else hi = mid - 1;
+    }
+    const int4 it = its[lo];
+    const WinDev<T>& w = wins[it.x];
+    const int j = it.z + (p - pre[lo]);
+    int c[3] = {0, 0, 0};
+    decode_cell<D>(it.y, w.N, c);
+    const T* pw = w.wts + (int64_t)j * WPP;
+    const T* pl = pw + (D - 1) * TTP;          // last dimension: (v, v) pairs
+    const int64_t W = w.W;
+    T acc = T(0);
+    if constexpr (D == 3) {
+      for (int t1 = 0; t1 < TT; ++t1) {
+        T u1 = T(0);
+        for (int t2 = 0; t2 < TT; ++t2) {
+          const T* g = w.grid + ((c[0] + t1) * W + (c[1] + t2)) * W + c[2];
+          T u2 = T(0);
+#pragma unroll
+          for (int t3 = 0; t3 < TT; ++t3) u2 = fma(pl[2 * t3], g[t3], u2);
+          u1 = fma(pw[TTP + t2], u2, u1);
+        }
+        acc = fma(pw[t1], u1, acc);
+      }
+    } else if constexpr (D == 2) {
+      for (int t1 = 0; t1 < TT; ++t1) {
+        const T* g = w.grid + (c[0] + t1) * W + c[1];
+        T u = T(0);
+#pragma unroll
+        for (int t2 = 0; t2 < TT; ++t2) u = fma(pl[2 * t2], g[t2], u);
+        acc = fma(pw[t1], u, acc);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < TT; ++t) acc = fma(pl[2 * t], w.grid[c[0] + t], acc);
+    }
+    T* out = Out;
+    int64_t ld = ldo;
+    T sc = scale;
+    if (io) {
+      out = io[it.x].Out;
+      ld = io[it.x].ldo;
+      sc = io[it.x].scale;
+    }
+    atomicAdd(out + (int64_t)__ldg(w.perm + j) * ld, sc * acc);
+  }
+}
+
 // FP32 interpolation with pairs of right-hand sides: one CTA per (work item,
 // slice of RS right-hand sides), block staged as in k_interp. Lane = (a pair
 // of neighbouring right-hand sides, PP = 4 points): a block pair read with one
@@ -806,6 +889,10 @@ cudaError_t interp_one(const WinDev<T>* wins, const WinIO<T>* io, const int4* it
     }
     dim3 grid((unsigned)n_items, (RC + Sh2::RS - 1) / Sh2::RS);
     k_interp2<D, S, RC><<<grid, Sh2::THREADS, Sh2::SMEM, st>>>(wins, io, items, Out, ldo, R, scale);
+    return cudaGetLastError();
+  } else if constexpr (RC == 1) {
+    const unsigned grid = (unsigned)((n_items + kPtsItems - 1) / kPtsItems);
+    k_interp_pts<T, D, S><<<grid, 128, 0, st>>>(wins, io, items, n_items, Out, ldo, scale);
     return cudaGetLastError();
   } else {
     using Sh = InterpShape<T, D, S, RC>;
