@@ -66,10 +66,14 @@ struct ImShape {
   static constexpr int PSI = 2 * TTP;                           // psi1, psi2 of a point as stored
   static constexpr int B_BYTES = NN * kImKC * 4;                // one of hi / lo
   static constexpr int OFF_P = kImNB * 2 * B_BYTES;             // A formers' prefetch slots
-  static constexpr int SMEM = OFF_P + 2 * kImMP * kImMT * PSI * 4;
+  // floats per point in a slot: both tiles' psi1, psi2, plus 4 of padding so
+  // that the 16-byte reads of 8 consecutive lanes fall on distinct banks
+  static constexpr int PST = kImMT * PSI + 4;
+  static constexpr int SMEM = OFF_P + 2 * kImMP * PST * 4;
   static_assert(NN <= kImDCols, "tile shape");
   static_assert(kImACol + 2 * 32 <= kImCols, "tensor memory budget");
-  static_assert(PSI % 4 == 0 && OFF_P % 16 == 0, "16-byte prefetch pieces");
+  static_assert(PSI % 4 == 0 && OFF_P % 16 == 0 && (PST / 4) % 2 == 1,
+                "16-byte prefetch pieces, an odd number of them per point");
 };
 
 struct ImBars {
@@ -202,8 +206,8 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __res
     const uint32_t tq = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)kImACol;
     // this thread's two prefetch slots (alternate items): psi1, psi2 (as
     // stored) of its point in each tile
-    float* slots = reinterpret_cast<float*>(smem_raw + Sh::OFF_P) + p * (kImMT * Sh::PSI);
-    auto slot_of = [&](int64_t j) { return slots + (j & 1) * (kImMP * kImMT * Sh::PSI); };
+    float* slots = reinterpret_cast<float*>(smem_raw + Sh::OFF_P) + p * Sh::PST;
+    auto slot_of = [&](int64_t j) { return slots + (j & 1) * (kImMP * Sh::PST); };
     auto prefetch = [&](const Item& it, float* slot) {
       const WinDev<float> w = s_win[it.u.x & 0xFFFF];
 #pragma unroll
@@ -234,9 +238,15 @@ k_interp_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __res
 #pragma unroll
       for (int t = 0; t < kImMT; ++t)
 #pragma unroll
-        for (int q = 0; q < TT; ++q) {
-          a[t][q] = slot[t * Sh::PSI + q];
-          b[t][q] = slot[t * Sh::PSI + TTP + q];
+        for (int q4 = 0; q4 < Sh::PSI / 4; ++q4) {   // 16-byte shared-memory reads
+          const float4 v = reinterpret_cast<const float4*>(slot + t * Sh::PSI)[q4];
+          const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int q = 4 * q4 + c;
+            if (q < TT) a[t][q] = e[c];
+            else if (q >= TTP && q - TTP < TT) b[t][q - TTP] = e[c];
+          }
         }
       if (i + gridDim.x < n_items) {                  // the next item's values, in flight
         Item nx;
