@@ -336,11 +336,16 @@ agp_status agp_plan_set_wait_limit(agp_plan plan, int64_t polls);
  * M = I:
  *   nlml    = 1/2 (y^T alpha + (1/nz) sum_i z_i^T logm(K_hat) z_i + n log 2 pi)
  *   grad[j] = 1/2 (-alpha^T dK_j alpha + (1/nz) sum_i u_i^T dK_j z_i)
- * One batched CG run on [y, z_1..z_nz]: every probe column runs exactly
+ * One batched CG run on [y, z_1..z_nz]: every probe column runs
  * lanczos_steps iterations (its CG coefficients give the Lanczos matrix of
  * stochastic Lanczos quadrature; u_i is its CG iterate); the y column runs
  * lanczos_steps iterations too when rtol = 0, else to relative residual rtol
- * (at most maxit iterations) -- alpha is its iterate.
+ * (at most maxit iterations) -- alpha is its iterate. A column whose
+ * relative residual falls to 1e-12 (FP64 plans) or 1e-6 (FP32 plans) stops
+ * there and its Lanczos matrix ends at that step: its Krylov space is then
+ * invariant to working precision, the quadrature exact to that level, and
+ * further steps would be set by rounding noise (Lanczos breakdown). The
+ * preconditioned variants apply the same rule.
  * Y: device [n]; Z: device [n][ldz], nz >= 1 probe columns (e.g. Rademacher,
  * drawn by the caller); 1 <= lanczos_steps <= 64. nlml: host double; grad:
  * host double[3] (ell, sigma_f, sigma_eps). Synchronises `stream`. */

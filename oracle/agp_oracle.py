@@ -68,7 +68,7 @@ __all__ = [
     "truncated_matvec", "truncated_deriv_matvec", "truncated_operators", "truncated_forms",
     "bins", "kb_shape", "kb_window", "kb_window_hat",
     "nfft_adjoint", "nfft", "nfft_fastsum_matvec",
-    "cg", "pcg", "farthest_point_sampling", "farthest_point_gaps", "additive_landmarks",
+    "cg", "pcg", "LANCZOS_BREAKDOWN", "farthest_point_sampling", "farthest_point_gaps", "additive_landmarks",
     "nystrom_preconditioner",
     "splitmix64", "rademacher_probes", "lanczos_tridiag_from_cg", "slq_quadratic",
     "nlml_exact", "nlml_estimate",
@@ -661,12 +661,21 @@ def nfft_fastsum_matvec(X, windows, kind, ell, sigma_f, sigma_eps, V, N, s,
 # Iterative solvers and the likelihood (Sec. 1)
 # ---------------------------------------------------------------------------
 
-def cg(apply_A, B, rtol=1e-4, maxit=200, fixed_iters=None):
+# Lanczos breakdown floor of the NLML estimators (FP64): a CG-Lanczos column
+# whose relative residual has fallen to this level has reached an invariant
+# Krylov subspace to working precision, so its Lanczos matrix ends there (the
+# Gauss quadrature of e_1^T f(T) e_1 is then exact to that level; further
+# steps would divide rounding-level residual norms by each other).
+LANCZOS_BREAKDOWN = 1e-12
+
+
+def cg(apply_A, B, rtol=1e-4, maxit=200, fixed_iters=None, breakdown=0.0):
     """Conjugate gradients for A X = B, one independent recursion per column,
     zero initial guess, stopping when |b - A x|_2 / |b|_2 <= rtol (Sec. 1 and
-    the CG setup of Sec. 5.1). With ``fixed_iters`` every column runs exactly
-    that many steps (the Lanczos use). Returns X, iterations, relative
-    residuals, and the per-column alpha and beta sequences."""
+    the CG setup of Sec. 5.1). With ``fixed_iters`` every column runs that
+    many steps (the Lanczos use), or stops earlier once its relative residual
+    is <= ``breakdown``. Returns X, iterations, relative residuals, and the
+    per-column alpha and beta sequences."""
     B = np.asarray(B, dtype=np.float64)
     if B.ndim == 1:
         B = B[:, None]
@@ -700,6 +709,8 @@ def cg(apply_A, B, rtol=1e-4, maxit=200, fixed_iters=None):
             relres[c] = math.sqrt(rr_new) / bn
             rr = rr_new
             if fixed_iters is None and relres[c] <= rtol:
+                break
+            if fixed_iters is not None and relres[c] <= breakdown:
                 break
             p = r + beta * p
         X[:, c] = x
@@ -877,7 +888,8 @@ def nlml_exact(K_hat, y):
     return 0.5 * (y @ a + 2.0 * np.sum(np.log(np.diag(L))) + n * math.log(TWO_PI))
 
 
-def nlml_estimate(apply_K, apply_dK, y, Z, lanczos_steps, rtol=1e-10, maxit=None):
+def nlml_estimate(apply_K, apply_dK, y, Z, lanczos_steps, rtol=1e-10, maxit=None,
+                  breakdown=LANCZOS_BREAKDOWN):
     """Estimate of the NLML and its gradient with M = I (no preconditioner).
 
     Sec. 1 eq. (1.4) with M = I: Z~ = 1/2 (y^T alpha + (1/n_z) sum_i z_i^T
@@ -893,7 +905,7 @@ def nlml_estimate(apply_K, apply_dK, y, Z, lanczos_steps, rtol=1e-10, maxit=None
     alpha, _, _, _, _ = cg(apply_K, y[:, None], rtol=rtol,
                            maxit=maxit if maxit is not None else 10 * n)
     alpha = alpha[:, 0]
-    U, _, _, al, be = cg(apply_K, Z, fixed_iters=lanczos_steps)
+    U, _, _, al, be = cg(apply_K, Z, fixed_iters=lanczos_steps, breakdown=breakdown)
     nz = Z.shape[1]
     logdet = 0.0
     for i in range(nz):
@@ -959,9 +971,10 @@ def nystrom_probes(B, KLL, sigma_eps, Wn, Wk):
     return sigma_eps * np.asarray(Wn, dtype=np.float64) + B @ T
 
 
-def pcg_lanczos(apply_A, apply_Minv, B, steps):
-    """PCG with zero initial guess and exactly ``steps`` steps per column,
-    recording the alpha and beta sequences (which give the Lanczos matrix of
+def pcg_lanczos(apply_A, apply_Minv, B, steps, breakdown=0.0):
+    """PCG with zero initial guess and ``steps`` steps per column (fewer if
+    the relative residual |r|_2 / |b|_2 falls to ``breakdown``), recording
+    the alpha and beta sequences (which give the Lanczos matrix of
     M^{-1/2} A M^{-1/2} started at M^{-1/2} b, by the same CG-Lanczos relation
     as in lanczos_tridiag_from_cg) and r_0^T M^{-1} r_0 = b^T M^{-1} b.
     Returns X, alphas, betas, rz0."""
@@ -976,6 +989,7 @@ def pcg_lanczos(apply_A, apply_Minv, B, steps):
         p = z.copy()
         rz = r @ z
         rz0[c] = rz
+        bn = np.linalg.norm(B[:, c])
         for _ in range(steps):
             q = apply_A(p[:, None])[:, 0]
             a = rz / (p @ q)
@@ -986,6 +1000,8 @@ def pcg_lanczos(apply_A, apply_Minv, B, steps):
             b = rz_new / rz
             alphas[c].append(a)
             betas[c].append(b)
+            if np.linalg.norm(r) <= breakdown * bn:
+                break
             p = z + b * p
             rz = rz_new
         X[:, c] = x
@@ -1012,7 +1028,8 @@ def nystrom_trace_Minv_dM(B, KLL, dB, dKLL, s2):
 
 
 def nlml_estimate_preconditioned(apply_K, apply_dK, y, Wn, Wk, lanczos_steps, B, KLL, dB,
-                                 landmarks, sigma_eps, rtol=1e-10, maxit=None):
+                                 landmarks, sigma_eps, rtol=1e-10, maxit=None,
+                                 breakdown=LANCZOS_BREAKDOWN):
     """Estimate of the NLML and its gradient with the landmark preconditioner
     M = B K_LL^{-1} B^T + sigma_eps^2 I (Sec. 2.3).
 
@@ -1042,7 +1059,7 @@ def nlml_estimate_preconditioned(apply_K, apply_dK, y, Wn, Wk, lanczos_steps, B,
                       maxit=maxit if maxit is not None else 10 * n)
     alpha = alpha[:, 0]
     Z = nystrom_probes(B, KLL, sigma_eps, Wn, Wk)
-    U, al, be, rz0 = pcg_lanczos(apply_K, Minv, Z, lanczos_steps)
+    U, al, be, rz0 = pcg_lanczos(apply_K, Minv, Z, lanczos_steps, breakdown=breakdown)
     nz = Z.shape[1]
     quad = 0.0
     for i in range(nz):
@@ -1267,7 +1284,8 @@ def afn_probes(L, F, KLL, KFL, G, Wn):
 
 
 def nlml_estimate_afn(apply_K, apply_dK, y, Wn, lanczos_steps, X, windows, kind, ell, sigma_f,
-                      sigma_eps, landmarks, fill, rtol=1e-10, maxit=None):
+                      sigma_eps, landmarks, fill, rtol=1e-10, maxit=None,
+                      breakdown=LANCZOS_BREAKDOWN):
     """Estimate of the NLML and its gradient (Sec. 1 eqs. (1.3)-(1.5)) with the
     additive AFN preconditioner M of afn_factors (Sec. 2.3): the same
     estimator as nlml_estimate_preconditioned, with log det M = log det K_LL -
@@ -1286,7 +1304,7 @@ def nlml_estimate_afn(apply_K, apply_dK, y, Wn, lanczos_steps, X, windows, kind,
                       maxit=maxit if maxit is not None else 10 * n)
     alpha = alpha[:, 0]
     Z = afn_probes(L, F, KLL, KFL, G, Wn)
-    U, al, be, rz0 = pcg_lanczos(apply_K, Minv, Z, lanczos_steps)
+    U, al, be, rz0 = pcg_lanczos(apply_K, Minv, Z, lanczos_steps, breakdown=breakdown)
     nz = Z.shape[1]
     quad = 0.0
     for i in range(nz):

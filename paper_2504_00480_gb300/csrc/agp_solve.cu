@@ -585,6 +585,17 @@ __global__ void k_rademacher(T* __restrict__ Z, int64_t ldz, int64_t n, int R, u
   Z[i * ldz + c] = (splitmix64_out(seed, (uint64_t)e) >> 63) ? T(-1) : T(1);
 }
 
+// Lanczos breakdown floor of the NLML estimators (Sec. 1, SLQ by CG-Lanczos):
+// a column whose relative residual has fallen to this level has reached an
+// invariant Krylov subspace to working precision; its Lanczos matrix ends
+// there (the Gauss quadrature is then exact to that precision), since the
+// coefficients of further steps would be ratios of rounding-level residual
+// norms and change from run to run with the order of the atomic additions.
+template <typename T>
+constexpr double lanczos_floor() {
+  return sizeof(T) == 4 ? 1e-6 : 1e-12;
+}
+
 template <typename T>
 agp_status nlml_t(agp_plan_s* pl, const T* Y, const T* Z, int64_t ldz, int nz, int steps,
                   double rtol, int maxit, double* nlml, double* grad, cudaStream_t st) {
@@ -608,7 +619,7 @@ agp_status nlml_t(agp_plan_s* pl, const T* Y, const T* Z, int64_t ldz, int nz, i
   pl->launches[3] += 2;
   AGP_CUDA(cudaGetLastError());
   std::vector<int> mi(R, steps);
-  std::vector<double> tl(R, 0.0);
+  std::vector<double> tl(R, lanczos_floor<T>());
   if (rtol > 0) {
     mi[0] = maxit;
     tl[0] = rtol;
@@ -728,7 +739,7 @@ agp_status nlml_pc_t(agp_plan_s* pl, const T* Y, const T* Wn, int64_t ldwn, cons
   // PCG on [y, z_1..z_nz]: probes run exactly `steps` steps (their coefficients
   // give the Lanczos matrices), y to rtol when rtol > 0
   std::vector<int> mi(R, steps);
-  std::vector<double> tl(R, 0.0);
+  std::vector<double> tl(R, lanczos_floor<T>());
   if (rtol > 0) {
     mi[0] = maxit;
     tl[0] = rtol;
@@ -943,7 +954,7 @@ agp_status nlml_afn_t(agp_plan_s* pl, Afn* af, const T* Y, const T* Wn, int64_t 
   AGP_CUDA(cudaGetLastError());
   // PCG-Lanczos on [y, z_1..z_nz]
   std::vector<int> mi(R, steps);
-  std::vector<double> tl(R, 0.0);
+  std::vector<double> tl(R, lanczos_floor<T>());
   if (rtol > 0) {
     mi[0] = maxit;
     tl[0] = rtol;

@@ -229,20 +229,23 @@ def test_rademacher_probes_match_the_oracle_generator(agp, dtype):
 
 
 def test_nlml_grad_seed_equals_nlml_grad_with_the_same_probes(agp):
-    # well conditioned (sigma_eps = 1), so that 15 CG steps nearly converge and
-    # the order of the FP64 atomic additions moves the result only at
-    # rounding level
+    # 6 CG-Lanczos steps: on this matrix (eigenvalues 0.96 .. 119 and one at
+    # 1905) finite-precision CG loses orthogonality after about six steps,
+    # and from then on its iterates depend on the rounding sequence, which
+    # the order of the FP64 atomic additions changes from run to run
+    # (measured run-to-run iterate differences 1e-16, 1e-10, 2e-7, 5e-3
+    # after 2, 6, 8, 10 steps; the CPU oracle's CG shows the same growth
+    # under a 1e-11 change of the operator)
     X, W, rng = small_problem(n=1200, seed=31)
     plan = agp.Plan(torch.tensor(X, device=DEV), W, 32, 5, "gauss", 0.2, 1.0, 1.0)
     y = torch.tensor(rng.standard_normal(1200), device=DEV)
     seed = 424242
-    nl_s, g_s = plan.nlml_grad_seed(y, 12, seed, lanczos_steps=15)
+    nl_s, g_s = plan.nlml_grad_seed(y, 12, seed, lanczos_steps=6)
     Z = torch.tensor(O.rademacher_probes(1200, 12, seed), device=DEV)
-    nl, g = plan.nlml_grad(y, Z, lanczos_steps=15)
+    nl, g = plan.nlml_grad(y, Z, lanczos_steps=6)
     # the same probes: the two runs differ only by the order of the FP64
-    # atomic additions inside the matvecs, which the gradient (a difference
-    # of two larger terms) amplifies (measured: up to 8e-6 relative)
+    # atomic additions inside the matvecs
     assert nl_s == pytest.approx(nl, rel=1e-9)
     for k in g:
-        assert g_s[k] == pytest.approx(g[k], rel=1e-4, abs=1e-9), k
+        assert g_s[k] == pytest.approx(g[k], rel=1e-6, abs=1e-9), k
     plan.close()

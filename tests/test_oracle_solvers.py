@@ -101,6 +101,27 @@ def test_slq_exact_with_full_krylov_space():
     assert O.slq_quadratic(T, z @ z) == pytest.approx(z @ logK @ z, rel=1e-9)
 
 
+def test_slq_breakdown_ends_the_lanczos_matrix_at_an_invariant_subspace():
+    # A well-conditioned matrix whose CG residual reaches 1e-12 in far fewer
+    # steps than its dimension: with the breakdown floor the recursion stops
+    # there and the quadrature equals z^T logm(A) z (eigendecomposition) to
+    # rounding level, however many steps are asked for; the steps it would
+    # take past that point only divide rounding-level residual norms.
+    rng = np.random.default_rng(5)
+    n = 200
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.linspace(1.0, 1.5, n)
+    A = (Q * lam) @ Q.T
+    z = rng.choice([-1.0, 1.0], size=n)
+    want = z @ ((Q * np.log(lam)) @ Q.T) @ z
+    for steps in (40, 120):
+        _, it, rel, al, be = O.cg(lambda P: A @ P, z[:, None], fixed_iters=steps,
+                                  breakdown=O.LANCZOS_BREAKDOWN)
+        assert it[0] < 40 and rel[0] <= O.LANCZOS_BREAKDOWN
+        T = O.lanczos_tridiag_from_cg(al[0], be[0])
+        assert O.slq_quadratic(T, z @ z) == pytest.approx(want, rel=1e-10)
+
+
 def test_nlml_exact_matches_scipy_logpdf():
     X, W, th, rng = _problem(25)
     K = O.dense_matrix(X, W, "matern12", th["ell"], th["sigma_f"], th["sigma_eps"])
