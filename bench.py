@@ -373,6 +373,9 @@ def run_gpu(args):
                              "frac_of_fp32_fma_peak": useful_tflops / fp32_peak},
                 "hbm": hbm,
                 "stages_ms_per_step": {s: prof[s]["ms"] / args.steps for s in prof},
+                "stages_note": "per-stage CUDA-event intervals; the d=2 window's spreading and "
+                               "interpolation run on a second stream next to the d=3 launch, so "
+                               "their intervals overlap it and the stages sum to more than a step",
                 "stage_launches_per_step": {s: prof[s]["launches"] / args.steps for s in prof},
                 "clocks": clocks, "cpu_baseline": cpu,
                 "nlml_grad": nl, "nlml_grad_pc": nl_pc, "autograd": ag, "batch": batch,

@@ -232,6 +232,10 @@ struct agp_plan_s {
   int64_t items_by_d[agp::kMaxDim + 1] = {0, 0, 0, 0};   // offsets of each d group
   std::vector<agp::FftGroup> groups;   // windows grouped by (d, N) for the DFT stages
   int* err_dev = nullptr;        // device error flags
+  // second stream for the d < 3 windows' spreading and interpolation while
+  // the d = 3 launch runs (fork / join events), created with the plan
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   long long wait_limit = agp::kDefaultWaitLimit;   // polls per bounded mbarrier wait
   // stage profiler
   bool prof = false;

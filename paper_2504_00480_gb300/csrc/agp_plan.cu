@@ -703,6 +703,9 @@ void free_plan(agp_plan_s* pl) {
   cudaFree(pl->runs3);
   cudaFree(pl->wins_dev);
   cudaFree(pl->err_dev);
+  if (pl->side) cudaStreamDestroy(pl->side);
+  if (pl->fork_ev) cudaEventDestroy(pl->fork_ev);
+  if (pl->join_ev) cudaEventDestroy(pl->join_ev);
   cudaFree(pl->bnd_poly);
   cudaFree(pl->coef_jobs);
   cudaFree(pl->coef_scratch);
@@ -932,6 +935,9 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
                              cudaMemcpyHostToDevice, st));
   }
   AGP_TRY(compute_coeffs<T>(pl, st));
+  AGP_CUDA(cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking));
+  AGP_CUDA(cudaEventCreateWithFlags(&pl->fork_ev, cudaEventDisableTiming));
+  AGP_CUDA(cudaEventCreateWithFlags(&pl->join_ev, cudaEventDisableTiming));
   AGP_CUDA(cudaStreamSynchronize(st));   // host tables go out of scope
   return AGP_OK;
 }
@@ -1077,10 +1083,20 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       for (const auto& g : pl->groups) AGP_CUDA(zero_grids<T>(g, rc, st));
       pl->launches[3] += (int64_t)pl->groups.size();
     }
-    for (int dd = 1; dd <= kMaxDim; ++dd) {
+    // the d = 3 windows first on `st`; the others on the side stream next to
+    // it when both are present (separate grids; forked and joined by events)
+    const bool split = pl->items_by_d[3] > pl->items_by_d[2] &&
+                       pl->items_by_d[2] > pl->items_by_d[0] && pl->side;
+    if (split) {
+      AGP_CUDA(cudaEventRecord(pl->fork_ev, st));
+      AGP_CUDA(cudaStreamWaitEvent(pl->side, pl->fork_ev, 0));
+    }
+    for (int q = 0; q < kMaxDim; ++q) {
+      const int dd = kMaxDim - q;
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
-      StageTimer tm(pl, 0, st, dd);
+      cudaStream_t sd = (split && dd < 3) ? pl->side : st;
+      StageTimer tm(pl, 0, sd, dd);
       const int fam = dd == 3 ? spread_family3(pl, rc, V + r0, ldv) : 0;
       if (fam == 3)
         AGP_CUDA(spread_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->P, pl->runs3,
@@ -1092,8 +1108,12 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       else
         AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
                                      V + r0, ldv, Rc, pl->use_tc, pl->err_dev, pl->wait_limit,
-                                     st));
+                                     sd));
       pl->launches[0] += 1;
+    }
+    if (split) {
+      AGP_CUDA(cudaEventRecord(pl->join_ev, pl->side));
+      AGP_CUDA(cudaStreamWaitEvent(st, pl->join_ev, 0));
     }
     {
       StageTimer tm(pl, 1, st);
@@ -1130,10 +1150,16 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       }
     }
     if (spec_only) continue;
-    for (int dd = 1; dd <= kMaxDim; ++dd) {
+    if (split) {
+      AGP_CUDA(cudaEventRecord(pl->fork_ev, st));
+      AGP_CUDA(cudaStreamWaitEvent(pl->side, pl->fork_ev, 0));
+    }
+    for (int q = 0; q < kMaxDim; ++q) {
+      const int dd = kMaxDim - q;
       const int64_t a = pl->items_by_d[dd - 1], b = pl->items_by_d[dd];
       if (b == a) continue;
-      StageTimer tm(pl, 2, st, dd);
+      cudaStream_t sd = (split && dd < 3) ? pl->side : st;
+      StageTimer tm(pl, 2, sd, dd);
       const int fam = dd == 3 ? interp_family3(pl, rc, Rc) : 0;
       if (fam == 3)
         AGP_CUDA(interp_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->P, pl->runs3,
@@ -1146,8 +1172,12 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       else
         AGP_CUDA(interp_items_sel<T>(wins, nullptr, pl->items_all + a, b - a, dd, pl->s, rc,
                                      Out + r0, ldo, Rc, scale, pl->use_tc, pl->err_dev,
-                                     pl->wait_limit, st));
+                                     pl->wait_limit, sd));
       pl->launches[2] += 1;
+    }
+    if (split) {
+      AGP_CUDA(cudaEventRecord(pl->join_ev, pl->side));
+      AGP_CUDA(cudaStreamWaitEvent(st, pl->join_ev, 0));
     }
   }
   return AGP_OK;
