@@ -58,13 +58,24 @@ k_dot_partial(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, i
   }
 }
 
-__global__ void k_dot_final(const double* __restrict__ partial, int nb, int R,
-                            double* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= R) return;
+// out[c] = sum_b partial[b][c]: one CTA per column, each thread a strided
+// share of the blocks, then a fixed-order tree in shared memory (the same
+// summation order on every call)
+constexpr int kDotFinalThreads = 256;
+__global__ void __launch_bounds__(kDotFinalThreads)
+k_dot_final(const double* __restrict__ partial, int nb, int R, double* __restrict__ out) {
+  __shared__ double red[kDotFinalThreads];
+  const int c = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * R + c];
-  out[c] = s;
+  for (int b = threadIdx.x; b < nb; b += kDotFinalThreads) s += partial[(int64_t)b * R + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+#pragma unroll
+  for (int h = kDotFinalThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
 }
 
 template <typename TS, typename TD>
@@ -400,7 +411,7 @@ agp_status col_dot(const TA* A, int64_t lda, const TB* B, int64_t ldb, int64_t n
   const int nb = (int)std::min<int64_t>(kMaxDotBlocks, (n + kDotRows - 1) / kDotRows);
   dim3 grid(nb, (R + 31) / 32);
   k_dot_partial<TA, TB><<<grid, kDotThreads, 0, st>>>(A, lda, B, ldb, n, R, partial);
-  k_dot_final<<<nblk(R, 128), 128, 0, st>>>(partial, nb, R, out);
+  k_dot_final<<<R, kDotFinalThreads, 0, st>>>(partial, nb, R, out);
   pl->launches[3] += 2;
   return cuda_status(cudaGetLastError(), "col_dot");
 }
@@ -1261,7 +1272,7 @@ agp_status agp_dot_columns_static(agp_prec prec, const void* A, int64_t lda, con
   else
     k_dot_partial<double, double><<<grid, kDotThreads, 0, st>>>((const double*)A, lda,
                                                                 (const double*)B, ldb, n, R, scratch);
-  k_dot_final<<<nblk(R, 128), 128, 0, st>>>(scratch, nb, R, out);
+  k_dot_final<<<R, kDotFinalThreads, 0, st>>>(scratch, nb, R, out);
   return cuda_status(cudaGetLastError(), "agp_dot_columns_static");
 }
 
