@@ -214,13 +214,14 @@ agp_status agp_plan_autotune(agp_plan plan, int R, int reps, int* points, double
 agp_status agp_plan_tensor_cores(agp_plan plan, int* mode);
 
 /* Which kernels run the d = 3 spreading and interpolation of the first pass
- * of an R-column application (V or Out rows with stride ldv, 16-byte
- * aligned): 3 the persistent tensor-memory kernel over cell runs, 2 the
- * shared-memory tensor-core kernel over cell runs, 1 the tensor-core kernel over work
- * items, 0 the FMA kernel; -1 when the plan has no d = 3 window. Depends on
- * the plan's precision, cutoff, kernel family (agp_plan_set_tensor_cores) and
- * on R; a family-3 plan takes family 2 for an interpolation pass whose
- * second 16-column half would be empty (R <= RC - 16). */
+ * of an R-column application (V or Out rows with stride ldv >= R; the
+ * kernels take any stride and alignment): 3 the persistent tensor-memory
+ * kernel over cell runs, 2 the shared-memory tensor-core kernel over cell
+ * runs, 1 the tensor-core kernel over work items, 0 the FMA kernel; -1 when
+ * the plan has no d = 3 window. Depends on the plan's precision, cutoff,
+ * kernel family (agp_plan_set_tensor_cores) and on R; a family-3 plan takes
+ * family 2 for an interpolation pass whose second 16-column half would be
+ * empty (R <= RC - 16). */
 agp_status agp_plan_kernel_families(agp_plan plan, int R, int64_t ldv, int* spread, int* interp);
 
 /* Forget every cached autotuner result of the process. */

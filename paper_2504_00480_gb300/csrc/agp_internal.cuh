@@ -276,9 +276,10 @@ cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, c
                             int64_t n_items, int s, const float* V, int64_t ldv, int R, int rc,
                             int* err, long long spin, cudaStream_t st);
 // Persistent warp-specialised tensor-core spreading with A in tensor memory
-// (agp_spread_tm.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5, V rows
-// 16-byte aligned (ldv % 4 == 0); units are the cell runs of the plan.
-bool spread_tm_supported(int d, int s, int RC, const void* V, int64_t ldv);
+// (agp_spread_tm.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5 (V rows are
+// staged 16 bytes at a time when 16-byte aligned, else 4); units are the cell
+// runs of the plan.
+bool spread_tm_supported(int d, int s, int RC);
 cudaError_t spread_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,
                             const float* V, int64_t ldv, int R, int rc, int* err, long long spin,
                             cudaStream_t st);

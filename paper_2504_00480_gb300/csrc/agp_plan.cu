@@ -969,14 +969,14 @@ std::mutex g_tune_mu;
 std::map<std::string, TuneEntry> g_tune_cache;
 
 // Kernel family of a pass's d = 3 spreading / interpolation (rc grid
-// columns, Rc of them in use, V or Out at the given address and stride):
+// columns, Rc of them in use):
 // 3 the persistent tensor-memory kernel over cell runs, 2 the shared-memory
 // tensor-core kernel over cell runs, 1 the tensor-core kernel over work items
 // where it supports the case, else 0, the FMA kernel over work items.
-int spread_family3(const agp_plan_s* pl, int rc, const void* V, int64_t ldv) {
+int spread_family3(const agp_plan_s* pl, int rc) {
   if (pl->prec != AGP_F32 || !pl->use_tc) return 0;
   if (pl->runs3 && (pl->use_tc == 1 || pl->use_tc == 3) &&
-      spread_tm_supported(3, pl->s, rc, V, ldv))
+      spread_tm_supported(3, pl->s, rc))
     return 3;
   if (pl->runs3 && spread_tc_supported(3, pl->s, rc)) return 2;
   return spread_tc_supported(3, pl->s, rc) ? 1 : 0;
@@ -1097,7 +1097,7 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       if (b == a) continue;
       cudaStream_t sd = (split && dd < 3) ? pl->side : st;
       StageTimer tm(pl, 0, sd, dd);
-      const int fam = dd == 3 ? spread_family3(pl, rc, V + r0, ldv) : 0;
+      const int fam = dd == 3 ? spread_family3(pl, rc) : 0;
       if (fam == 3)
         AGP_CUDA(spread_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->P, pl->runs3,
                                  pl->n_runs3, pl->s, reinterpret_cast<const float*>(V + r0), ldv,
@@ -1700,8 +1700,7 @@ agp_status agp_plan_kernel_families(agp_plan pl, int R, int64_t ldv, int* spread
   for (const Window& w : pl->win) d3 = d3 || w.d == 3;
   if (!d3) return AGP_OK;
   const int rc = pick_rc(pl, R);
-  const void* aligned = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));
-  *spread = spread_family3(pl, rc, aligned, ldv);
+  *spread = spread_family3(pl, rc);
   *interp = interp_family3(pl, rc, std::min(rc, R));
   return AGP_OK;
 }

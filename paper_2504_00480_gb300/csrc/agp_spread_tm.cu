@@ -111,8 +111,8 @@ struct TmBars {
 template <int S>
 __global__ void __launch_bounds__(kTmThreads, 1)
 k_spread_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __restrict__ units,
-            int64_t n_units, const float* __restrict__ V, int64_t ldv, int R, int rc,
-            int* __restrict__ err, long long spin) {
+            int64_t n_units, const float* __restrict__ V, int64_t ldv, int vec, int R,
+            int rc, int* __restrict__ err, long long spin) {
   using Sh = TmShape<S>;
   constexpr int TT = Sh::TT, TTP = Sh::TTP, WPP = Sh::WPP, WPS = Sh::WPS, VS = Sh::VS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -239,8 +239,15 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __res
           const int64_t pi = __shfl_sync(0xFFFFFFFFu, slot, (c & 1) * 16 + q);
           if (q < ns) {
             const int valid = max(0, min(4, R - (it.r0 + vk)));
-            cp_async16_zfill(sv + q * VS + vk, V + pi * ldv + (valid > 0 ? it.r0 + vk : 0),
-                             valid * 4);
+            if (vec) {
+              cp_async16_zfill(sv + q * VS + vk, V + pi * ldv + (valid > 0 ? it.r0 + vk : 0),
+                               valid * 4);
+            } else {                                   // rows not 16-byte aligned
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                cp_async4_zfill(sv + q * VS + vk + e,
+                                V + pi * ldv + (e < valid ? it.r0 + vk + e : 0), e < valid ? 4 : 0);
+            }
           }
         }
         cp_async_arrive(&bars.st_full[s]);
@@ -504,16 +511,16 @@ cudaError_t spread_tm_s(const WinDev<float>* wins, int n_win, const int4* units,
   if (e != cudaSuccess) return e;
   const int64_t items = n_units * (rc / kTmRH);
   const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-  k_spread_tm<S><<<grid, kTmThreads, Sh::SMEM, st>>>(wins, n_win, units, n_units, V, ldv, R, rc, err,
+  const int vec = (ldv % 4 == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0) ? 1 : 0;
+  k_spread_tm<S><<<grid, kTmThreads, Sh::SMEM, st>>>(wins, n_win, units, n_units, V, ldv, vec, R, rc, err,
                                                      spin);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool spread_tm_supported(int d, int s, int RC, const void* V, int64_t ldv) {
-  return d == 3 && (RC == 32 || RC == 16) && (s == 4 || s == 5) && ldv % 4 == 0 &&
-         (reinterpret_cast<uintptr_t>(V) & 15) == 0;
+bool spread_tm_supported(int d, int s, int RC) {
+  return d == 3 && (RC == 32 || RC == 16) && (s == 4 || s == 5);
 }
 
 cudaError_t spread_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,

@@ -52,9 +52,9 @@ def test_tc_spread_matches_oracle_and_fma_path(agp, s, N, R, mode):
     plan.set_tensor_cores(False)
     ref = plan.matvec(Vt).cpu().numpy()
     plan.set_tensor_cores(mode)
-    # the kernels that run: spreading's persistent kernel needs 16-byte rows
-    sp = 3 if mode in (1, 3) and R % 4 == 0 else 2
-    assert plan.kernel_families(R) == (sp, 3 if mode == 3 else 2)
+    # the kernels that run (rows of R values: 16-byte aligned only when R % 4
+    # == 0, which the persistent spreading kernel stages either way)
+    assert plan.kernel_families(R) == (3 if mode in (1, 3) else 2, 3 if mode == 3 else 2)
     got = plan.matvec(Vt).cpu().numpy()
     plan.check()
     want = O.truncated_matvec(X, W, "gauss", 0.15, 0.9, 0.2, V, N)
