@@ -854,6 +854,147 @@ k_interp2(const WinDev<float>* __restrict__ wins, const WinIO<float>* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Spreading of one right-hand side by rows of cells (d = 2, 3)
+// ---------------------------------------------------------------------------
+// A row is the cells that share every coordinate but the last; its points
+// touch a (2s)^(d-1) x (N + 2s - 1) block of the grid. A CTA takes
+// kRowItems consecutive work items (cells in order, so mostly one row),
+// splits them into segments of one (window, row) and accumulates each
+// segment's block in shared memory: the segment's points (a contiguous range
+// of sorted points) are staged kRowStage at a time -- window values with
+// coalesced loads, the right-hand side through the permutation, each point's
+// cell -- and a thread that owns one block row (t1, t2) adds each point's 2s
+// products into its own row, so the accumulation needs no atomics; GROUPS
+// groups of threads take every GROUPS-th point into copies of the block,
+// which are summed when the block goes into the grid (global atomics for its
+// non-zero values only). For sparse cells this replaces a CTA and (2s)^d
+// global atomics per cell with about one atomic per block value and row.
+constexpr int kRowItems = 32;
+constexpr int kRowMaxN = 64;                  // the largest grid size N of a plan
+constexpr int kRowThreads = 256;
+constexpr int kRowStage = 128;                // points staged at a time
+
+template <typename T, int D, int S>
+struct RowShape {
+  static constexpr int TT = 2 * S;
+  static constexpr int ROWS = (D == 3) ? TT * TT : TT;           // block rows
+  static constexpr int ROWSP = (ROWS + 31) / 32 * 32;            // threads per group
+  static constexpr int GROUPS = kRowThreads / ROWSP;
+  static constexpr int BWMAX = kRowMaxN + TT - 1;                // block width (cells + taps)
+  static constexpr int WPP = wpp_of(D, S);
+  static constexpr size_t BLK = (size_t)GROUPS * ROWS * BWMAX;   // elements of the block copies
+  static constexpr size_t SMEM = sizeof(T) * (BLK + (size_t)kRowStage * (WPP + 1)) +
+                                 sizeof(int) * kRowStage;
+  static_assert(GROUPS >= 1, "block rows per group");
+};
+
+template <typename T, int D, int S>
+__global__ void __launch_bounds__(kRowThreads)
+k_spread_rows(const WinDev<T>* __restrict__ wins, const WinIO<T>* __restrict__ io,
+              const int4* __restrict__ items, int64_t n_items, const T* __restrict__ V,
+              int64_t ldv) {
+  using Sh = RowShape<T, D, S>;
+  constexpr int TT = Sh::TT, TTP = ttp_of(S), WPP = Sh::WPP, ROWS = Sh::ROWS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* blk = reinterpret_cast<T*>(smem_raw);      // [GROUPS][ROWS][BW]
+  T* sw = blk + Sh::BLK;                        // [kRowStage][WPP] staged window values
+  T* sv = sw + kRowStage * WPP;                 // [kRowStage] right-hand side values
+  int* sc = reinterpret_cast<int*>(sv + kRowStage);   // [kRowStage] cell along the last dim
+  __shared__ int4 its[kRowItems];
+  __shared__ int pre[kRowItems + 1];
+  const int64_t i0 = (int64_t)blockIdx.x * kRowItems;
+  const int ni = (int)(n_items - i0 < kRowItems ? n_items - i0 : kRowItems);
+  if (threadIdx.x < ni) its[threadIdx.x] = items[i0 + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int q = 0; q < ni; ++q) {
+      pre[q] = acc;
+      acc += its[q].w;
+    }
+    pre[ni] = acc;
+  }
+  __syncthreads();
+  const int grp = threadIdx.x / Sh::ROWSP, row = threadIdx.x - grp * Sh::ROWSP;
+  const bool active = grp < Sh::GROUPS && row < ROWS;
+  const int t1 = (D == 3) ? row / TT : row, t2 = (D == 3) ? row - (row / TT) * TT : 0;
+  int sa = 0;
+  while (sa < ni) {
+    // the segment [sa, sb): items of one window and one row of cells, whose
+    // points are the contiguous sorted range j0 .. j0 + P - 1
+    const int win = its[sa].x;
+    const WinDev<T>& w = wins[win];
+    const int N = w.N, crow = its[sa].y / N;
+    int sb = sa + 1;
+    while (sb < ni && its[sb].x == win && its[sb].y / N == crow) ++sb;
+    const int BW = N + TT - 1;
+    const int j0 = its[sa].z, P = pre[sb] - pre[sa];
+    for (int e = threadIdx.x; e < Sh::GROUPS * ROWS * BW; e += blockDim.x) blk[e] = T(0);
+    const T* Vw = V;
+    int64_t ld = ldv;
+    if (io) {
+      Vw = io[win].V;
+      ld = io[win].ldv;
+    }
+    T* b = blk + ((int64_t)(active ? grp : 0) * ROWS + row) * BW;
+    for (int q0 = 0; q0 < P; q0 += kRowStage) {
+      const int ns = min(kRowStage, P - q0);
+      __syncthreads();                          // the previous stage is consumed, the block zeroed
+      const T* src = w.wts + (int64_t)(j0 + q0) * WPP;
+      for (int e = threadIdx.x; e < ns * WPP; e += blockDim.x) sw[e] = src[e];
+      for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+        const int pp = pre[sa] + q0 + q;
+        int lo = sa, hi = sb - 1;               // the item holding point pp
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (pre[mid] <= pp) lo = mid;
+          else hi = mid - 1;
+        }
+        sc[q] = its[lo].y - crow * N;
+        sv[q] = Vw[(int64_t)__ldg(w.perm + j0 + q0 + q) * ld];
+      }
+      __syncthreads();
+      if (active) {
+        for (int q = grp; q < ns; q += Sh::GROUPS) {
+          const T* pw = sw + q * WPP;
+          const T a = (D == 3) ? pw[t1] * pw[TTP + t2] * sv[q] : pw[t1] * sv[q];
+          const T* pl = pw + (D - 1) * TTP;     // last dimension: (v, v) pairs
+          T* bq = b + sc[q];
+#pragma unroll
+          for (int t3 = 0; t3 < TT; ++t3) bq[t3] = fma(a, pl[2 * t3], bq[t3]);
+        }
+      }
+    }
+    __syncthreads();
+    // the block (summed over the groups) into the grid: rows (c0 + t1, c1 + t2)
+    const int64_t W = w.W;
+    int c0 = 0, c1 = 0;
+    if constexpr (D == 3) {
+      c0 = crow / N;
+      c1 = crow - c0 * N;
+    } else {
+      c0 = crow;
+    }
+    for (int e = threadIdx.x; e < ROWS * BW; e += blockDim.x) {
+      T x = T(0);
+#pragma unroll
+      for (int q = 0; q < Sh::GROUPS; ++q) x += blk[(int64_t)q * ROWS * BW + e];
+      if (x == T(0)) continue;
+      const int r = e / BW, u = e - r * BW;
+      int64_t gi;
+      if constexpr (D == 3) {
+        gi = ((c0 + r / TT) * W + (c1 + r % TT)) * W + u;
+      } else {
+        gi = (c0 + r) * W + u;
+      }
+      atomicAdd(w.grid + gi, x);
+    }
+    __syncthreads();
+    sa = sb;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Dispatch over (d, s, RC)
 // ---------------------------------------------------------------------------
 template <typename T, int D, int S, int RC>
@@ -861,6 +1002,20 @@ cudaError_t spread_one(const WinDev<T>* wins, const WinIO<T>* io, const int4* it
                        int64_t n_items, const T* V, int64_t ldv, int R, cudaStream_t st) {
   using Sh = SpreadShape<T, D, S, RC>;
   if (n_items <= 0) return cudaSuccess;
+  if constexpr (RC == 1 && D >= 2) {
+    using Rs = RowShape<T, D, S>;
+    static bool rattr_set = false;   // per instantiation
+    if (!rattr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_spread_rows<T, D, S>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)Rs::SMEM);
+      if (e != cudaSuccess) return e;
+      rattr_set = true;
+    }
+    const unsigned grid = (unsigned)((n_items + kRowItems - 1) / kRowItems);
+    k_spread_rows<T, D, S><<<grid, kRowThreads, Rs::SMEM, st>>>(wins, io, items, n_items, V, ldv);
+    return cudaGetLastError();
+  }
   static bool attr_set = false;   // per instantiation
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_spread<T, D, S, RC>,
