@@ -37,7 +37,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("N3,N2,R,s", [(8, 64, 3, 4), (16, 32, 5, 5), (32, 16, 8, 5),
-                                        (64, 16, 2, 5)])
+                                        (64, 16, 2, 5), (32, 64, 1, 4)])
 def test_fp64_matches_oracle_nfft_fastsum(agp, N3, N2, R, s):
     rng = np.random.default_rng(N3 + 7 * N2 + R)
     n = 1500
