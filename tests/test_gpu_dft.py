@@ -5,7 +5,8 @@ use for their d = 2 and d = 3 windows.
   * FP64: the plan's matvec and ell-derivative matvec equal the oracle's CPU
     NFFT fast sum (adjoint NFFT, coefficients, NFFT; the same window and
     cutoff) to rounding, for grids of every size N in {8, 16, 32, 64}, mixed
-    with a d = 1 window (which keeps the per-group stages);
+    with a d = 1 window (which keeps the per-group stages), one-column passes
+    included (row spreading, one-thread-per-point interpolation);
   * FP32, 32 right-hand sides in one pass (the benchmarked shape): the matvec
     equals the per-group stages, which the spectra call still runs (it keeps
     the forward spectrum), to FP32 rounding.
