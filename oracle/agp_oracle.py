@@ -50,8 +50,12 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
   estimate is exact with a full pattern and equals the dense Hutchinson
   average with a full Krylov space.
 * ``cg``: dense Cholesky solve; ``slq_quadratic``: eigendecomposition-based
-  matrix logarithm with full Krylov space; ``nlml_exact``: scipy's
+  matrix logarithm with full Krylov space, and at the Lanczos breakdown floor
+  (``LANCZOS_BREAKDOWN``) well before it; ``nlml_exact``: scipy's
   multivariate normal log density.
+* ``splitmix64``/``rademacher_probes``: the generator's published output
+  values; ``farthest_point_sampling``/``fsai_pattern``: brute-force FP64
+  distances on small sets.
 """
 from __future__ import annotations
 
