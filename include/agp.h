@@ -26,6 +26,10 @@
  *    data_ptr()). `stream` is a cudaStream_t (NULL = legacy default stream).
  *  - Asynchrony: compute calls only enqueue work on `stream` and return;
  *    calls that return host values (marked "synchronises") wait for it.
+ *    A plan with windows of d = 3 and of d < 3 runs the latter's spreading
+ *    and interpolation on a second stream of its own, forked from and
+ *    joined back to `stream` by events inside the call, so the call still
+ *    orders like a single launch on `stream` (and can be captured with it).
  *  - Errors: every call returns an agp_status; nothing is printed and nothing
  *    exits. agp_status_string() names a status; agp_last_error() gives the
  *    message of the last failing call on this thread.
