@@ -226,6 +226,7 @@ struct agp_plan_s {
   int64_t coef_cells_max = 0, coef_dmul_max = 0;
   std::vector<agp::Window> win;
   void* wins_dev = nullptr;      // WinDev<T>[P]
+  void* grid_maps = nullptr;     // FP32 plans with d = 3 windows: grid tensor maps [2][P] (RC 16, 32)
   int4* items_all = nullptr;     // work items of every window, grouped by d
   int4* runs3 = nullptr;         // tensor-core work units (cell runs) of the d = 3 windows
   int64_t n_runs3 = 0;
@@ -278,11 +279,22 @@ cudaError_t spread_items_tc(const WinDev<float>* wins, const WinIO<float>* io, c
 // Persistent warp-specialised tensor-core spreading with A in tensor memory
 // (agp_spread_tm.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5 (V rows are
 // staged 16 bytes at a time when 16-byte aligned, else 4); units are the cell
-// runs of the plan.
+// runs of the plan. Each unit's accumulator block is added into the grid by
+// one bulk tensor reduction through `grid_maps`, the window's grid tensor map
+// for this RC (encode_grid_maps; n_win maps, those of the d = 3 windows set).
 bool spread_tm_supported(int d, int s, int RC);
-cudaError_t spread_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,
-                            const float* V, int64_t ldv, int R, int rc, int* err, long long spin,
+cudaError_t spread_units_tm(const WinDev<float>* wins, const void* grid_maps, int n_win,
+                            const int4* units, int64_t n_units, int s, const float* V,
+                            int64_t ldv, int R, int rc, int* err, long long spin,
                             cudaStream_t st);
+// Tensor maps of the grids of a plan's d = 3 windows (FP32) for the
+// spreading epilogue's bulk reductions: RC = 16 maps then RC = 32 maps, n_win
+// each, written to `out` (host memory, 64-byte aligned, 2 n_win maps of 128
+// bytes). Entries of other windows are zero. False if the driver's encoder is
+// unavailable or refuses a map.
+constexpr int kGridMapBytes = 128;
+bool encode_grid_maps(const WinDev<float>* wins_host, const int* win_d, int n_win, int s,
+                      void* out);
 // Persistent warp-specialised tensor-core interpolation with A in tensor
 // memory (agp_interp_tm.cu): FP32, d = 3, RC = 16 or 32, s = 4 or 5.
 bool interp_tm_supported(int d, int s, int RC, int R);

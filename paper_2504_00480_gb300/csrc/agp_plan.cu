@@ -702,6 +702,7 @@ void free_plan(agp_plan_s* pl) {
   cudaFree(pl->items_all);
   cudaFree(pl->runs3);
   cudaFree(pl->wins_dev);
+  cudaFree(pl->grid_maps);
   cudaFree(pl->err_dev);
   if (pl->side) cudaStreamDestroy(pl->side);
   if (pl->fork_ev) cudaEventDestroy(pl->fork_ev);
@@ -906,6 +907,27 @@ agp_status plan_build(agp_plan_s* pl, const agp_plan_desc* d, cudaStream_t st) {
   AGP_CUDA(cudaMalloc(&pl->wins_dev, sizeof(WinDev<T>) * pl->P));
   AGP_CUDA(cudaMemcpyAsync(pl->wins_dev, wd.data(), sizeof(WinDev<T>) * pl->P,
                            cudaMemcpyHostToDevice, st));
+  // FP32: tensor maps of the d = 3 grids for the tensor-memory spreading
+  // kernel's bulk reductions (without them that kernel is not selected)
+  if constexpr (std::is_same<T, float>::value) {
+    std::vector<int> win_d(pl->P);
+    bool any3 = false;
+    for (int s = 0; s < pl->P; ++s) {
+      win_d[s] = pl->win[s].d;
+      any3 = any3 || win_d[s] == 3;
+    }
+    struct alignas(64) MapSlot {
+      unsigned char b[kGridMapBytes];
+    };
+    std::vector<MapSlot> maps(2 * (size_t)pl->P);
+    if (any3 && spread_tm_supported(3, pl->s, 32) &&
+        encode_grid_maps(wd.data(), win_d.data(), pl->P, pl->s, maps.data())) {
+      AGP_CUDA(cudaMalloc(&pl->grid_maps, sizeof(MapSlot) * maps.size()));
+      AGP_CUDA(cudaMemcpyAsync(pl->grid_maps, maps.data(), sizeof(MapSlot) * maps.size(),
+                               cudaMemcpyHostToDevice, st));
+      AGP_CUDA(cudaStreamSynchronize(st));
+    }
+  }
   // DFT buffer tables: one per window, and one per (d, N) group of windows
   std::vector<FftWin> fw(pl->P);
   for (int s = 0; s < pl->P; ++s) {
@@ -975,7 +997,7 @@ std::map<std::string, TuneEntry> g_tune_cache;
 // where it supports the case, else 0, the FMA kernel over work items.
 int spread_family3(const agp_plan_s* pl, int rc) {
   if (pl->prec != AGP_F32 || !pl->use_tc) return 0;
-  if (pl->runs3 && (pl->use_tc == 1 || pl->use_tc == 3) &&
+  if (pl->runs3 && pl->grid_maps && (pl->use_tc == 1 || pl->use_tc == 3) &&
       spread_tm_supported(3, pl->s, rc))
     return 3;
   if (pl->runs3 && spread_tc_supported(3, pl->s, rc)) return 2;
@@ -1099,9 +1121,12 @@ agp_status apply_windows(agp_plan_s* pl, const T* V, int64_t ldv, T* Out, int64_
       StageTimer tm(pl, 0, sd, dd);
       const int fam = dd == 3 ? spread_family3(pl, rc) : 0;
       if (fam == 3)
-        AGP_CUDA(spread_units_tm(reinterpret_cast<const WinDev<float>*>(wins), pl->P, pl->runs3,
-                                 pl->n_runs3, pl->s, reinterpret_cast<const float*>(V + r0), ldv,
-                                 Rc, rc, pl->err_dev, pl->wait_limit, st));
+        AGP_CUDA(spread_units_tm(
+            reinterpret_cast<const WinDev<float>*>(wins),
+            static_cast<const unsigned char*>(pl->grid_maps) +
+                (size_t)(rc == 32 ? pl->P : 0) * kGridMapBytes,
+            pl->P, pl->runs3, pl->n_runs3, pl->s, reinterpret_cast<const float*>(V + r0), ldv, Rc,
+            rc, pl->err_dev, pl->wait_limit, st));
       else if (fam == 2)
         AGP_CUDA(spread_items_sel<T>(wins, nullptr, pl->runs3, pl->n_runs3, dd, pl->s, rc, V + r0,
                                      ldv, Rc, 1, pl->err_dev, pl->wait_limit, st));

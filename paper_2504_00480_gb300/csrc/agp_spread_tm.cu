@@ -20,17 +20,23 @@
 //  * Roles: warp 0 stages each chunk's window values and V rows with
 //    cp.async (completion arrives on the stage's mbarrier); warp 1 issues
 //    the MMAs from one thread; warps 2-5 form A (one row per thread); warps
-//    10-21 form B (hi and lo) in shared memory; warps 6-9 read finished
-//    accumulators and add them into the grid with vector atomics. The roles
-//    hand buffers to each other through mbarriers only -- there is no
-//    CTA-wide barrier in the loop.
+//    10-21 form B (hi and lo) in shared memory; warps 6-9 copy finished
+//    accumulators into a shared-memory tile laid out as the unit's grid box,
+//    which one bulk tensor reduction (cp.reduce.async.bulk.tensor, add) adds
+//    into the grid, so the grid update costs the load/store unit only the
+//    tile's stores. The roles hand buffers to each other through mbarriers
+//    only -- there is no CTA-wide barrier in the loop.
 //  * Work items (unit, 16-column half) are taken in a fixed stride
 //    (blockIdx.x + k gridDim.x), so every role walks the same sequence.
 //  * Every wait is bounded (the plan's wait limit) and watches the CTA's
 //    abort word; on expiry all roles leave their loops, the MMA thread
 //    drains what it issued, the CTA records AGP_TIMEOUT and frees its
 //    tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "agp_nufft_kernels.cuh"
@@ -69,8 +75,12 @@ struct TmShape {
   static constexpr int STG = STG_W + kTmKC * VS;                    // floats per stage
   static constexpr int B_BYTES = NN * kTmKC * 4;                    // one of hi / lo
   static constexpr int OFF_B = kTmNS * STG * 4;
+  // epilogue tile: a unit's accumulator block as the grid box it adds into,
+  // [t1][t2][u][16 right-hand sides] in 64-byte rows with the tensor map's
+  // 64-byte swizzle; placed at the first 1024-byte boundary after OFF_E
+  static constexpr int EP_BYTES = T3M * ROWS * kTmRH * 4;
   static constexpr int OFF_E = OFF_B + kTmNB * 2 * B_BYTES;
-  static constexpr int SMEM = OFF_E + 4 * 32 * 16 * 4;
+  static constexpr int SMEM = OFF_E + 1024 + EP_BYTES;
   static_assert(ROWS <= 128 && NN <= kTmDCols && NN % 16 == 0, "tile shape");
   static_assert(OFF_B % 128 == 0 && (2 * B_BYTES) % 128 == 0, "operand alignment");
   static_assert(kTmACol + 64 <= kTmCols, "tensor memory budget");
@@ -105,12 +115,14 @@ struct TmBars {
   uint64_t a_full[2], a_empty[2];
   uint64_t b_full[kTmNB], b_empty[kTmNB];
   uint64_t d_full[2], d_empty[2];
+  uint64_t e_full, e_empty;                     // epilogue tile written / read by the reduction
   uint64_t drain;
 };
 
 template <int S>
 __global__ void __launch_bounds__(kTmThreads, 1)
-k_spread_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __restrict__ units,
+k_spread_tm(const WinDev<float>* __restrict__ wins, const unsigned char* __restrict__ grid_maps,
+            int n_win, const int4* __restrict__ units,
             int64_t n_units, const float* __restrict__ V, int64_t ldv, int vec, int R,
             int rc, int* __restrict__ err, long long spin) {
   using Sh = TmShape<S>;
@@ -145,6 +157,8 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __res
       mbar_init(&bars.b_full[b], 4 * kTmBG);
       mbar_init(&bars.b_empty[b], 1);
     }
+    mbar_init(&bars.e_full, 4);
+    mbar_init(&bars.e_empty, 1);
     mbar_init(&bars.drain, 1);
     abort_word = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -425,10 +439,21 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __res
       if (!ok) break;
     }
   } else if (warp >= kWE0 && warp < kWE0 + 4) {
-    // ---- epilogue: accumulator -> grid, 16-byte atomics, four lanes per row ----
+    // ---- epilogue: accumulator -> shared tile -> one bulk tensor add into the grid ----
+    // Each warp copies its 32 accumulator rows (t1, t2), one 16-column plane
+    // u at a time, into the tile at their place in the unit's grid box
+    // [t1][t2][u][r]; planes u >= nu are written as zeros. When all four
+    // warps are done, lane 0 of the first adds the whole box into the grid
+    // with one bulk reduction and waits until it has read the tile before
+    // the tile is written again.
     const int qd = warp & 3;
-    float* tile = reinterpret_cast<float*>(smem_raw + Sh::OFF_E) + qd * (32 * 16);
-    const int c4 = (lane & 3) * 4;
+    const int row = qd * 32 + lane;
+    const bool wrow = row < Sh::ROWS;
+    const bool wwarp = qd * 32 < Sh::ROWS;             // the warp holds rows of the block
+    const uint32_t sbase = smem_u32(smem_raw);
+    const uint32_t toff = ((sbase + (uint32_t)Sh::OFF_E + 1023u) & ~1023u) - sbase;
+    unsigned char* tile = smem_raw + toff;
+    const bool issuer = warp == kWE0;
     int64_t nd = 0;
     int4 un = unit_at(blockIdx.x);
     for (int64_t i = blockIdx.x; i < n_items && !warp_aborted(abort); i += gridDim.x) {
@@ -437,43 +462,59 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __res
       Item it;
       if (!item_from(i, uc, it)) continue;
       const int db = (int)(nd & 1);
-      if (!warp_wait(&bars.d_full[db], (uint32_t)((nd >> 1) & 1), spin, abort)) break;
+      if (!warp_wait(&bars.d_full[db], (uint32_t)((nd >> 1) & 1), spin, abort) ||
+          !warp_wait(&bars.e_empty, (uint32_t)((nd & 1) ^ 1), spin, abort))
+        break;
       tc_fence_after();
-      const WinDev<float> w = s_win[it.u.x & 0xFFFF];
       const int L = max(1, it.u.x >> 16), nu = TT + L - 1;
-      int cc[3];
-      decode_cell<3>(it.u.y, w.N, cc);
 #pragma unroll 1
-      for (int u = 0; u < nu; ++u) {
+      for (int u = 0; u < Sh::T3M; ++u) {
         uint32_t v[16];
-        tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(db * kTmDCols + u * kTmRH), v);
-        // through shared memory so that four lanes cover one row's 16
-        // contiguous values; 16-byte chunk c of row l sits at chunk c ^ ((l >> 1) & 3)
+        if (wwarp && u < nu) {
+          tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(db * kTmDCols + u * kTmRH), v);
+        } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          *reinterpret_cast<float4*>(tile + lane * 16 + ((c ^ ((lane >> 1) & 3)) << 2)) =
-              make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
-                          __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
-        __syncwarp();
+          for (int q = 0; q < 16; ++q) v[q] = 0u;
+        }
+        if (wrow) {
+          // 16-byte chunk c of the row: logical offset (row T3M + u) 64 + 16 c,
+          // address bits 4-5 XOR bits 7-8 (64-byte swizzle; the tile is
+          // 1024-byte aligned); eight consecutive rows fall on distinct banks
+          const uint32_t l0 = (uint32_t)(row * Sh::T3M + u) * 64u;
 #pragma unroll
-        for (int q8 = 0; q8 < 4; ++q8) {
-          const int rl = q8 * 8 + (lane >> 2);
-          const int row = qd * 32 + rl;
-          if (row < Sh::ROWS && it.r0 + c4 < R) {
-            const int t1 = row / TT, t2 = row - (row / TT) * TT;
-            const int64_t base = ((int64_t)(cc[0] + t1) * w.W + (cc[1] + t2)) * w.W + cc[2] + u;
-            const float4 val = *reinterpret_cast<const float4*>(
-                tile + rl * 16 + (((lane & 3) ^ ((rl >> 1) & 3)) << 2));
-            atomicAdd(reinterpret_cast<float4*>(w.grid + base * rc + it.r0 + c4), val);
+          for (int c = 0; c < 4; ++c) {
+            const uint32_t lo = l0 + (uint32_t)c * 16u;
+            *reinterpret_cast<float4*>(tile + (lo ^ (((lo >> 7) & 3u) << 4))) =
+                make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
+                            __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
           }
         }
-        __syncwarp();
       }
+      // the accumulator is read: back to the MMA warp
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.d_empty[db]);
+      // the tile's writes are ordered before the bulk copy engine reads it
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.e_full);
+      if (issuer) {
+        if (!warp_wait(&bars.e_full, (uint32_t)(nd & 1), spin, abort)) break;
+        if (lane == 0) {
+          const int win = it.u.x & 0xFFFF;
+          int cc[3];
+          decode_cell<3>(it.u.y, s_win[win].N, cc);
+          bulk_reduce_add_4d(grid_maps + (size_t)win * kGridMapBytes, smem_u32(tile), it.r0,
+                             cc[2], cc[1], cc[0]);
+          bulk_wait_read();
+          mbar_arrive(&bars.e_empty);
+        }
+        __syncwarp();
+      }
       ++nd;
     }
+    // the last reductions' global adds are done before the CTA leaves
+    if (issuer && lane == 0) bulk_wait_all();
   }
 
   // ---- teardown ------------------------------------------------------------------
@@ -496,15 +537,15 @@ k_spread_tm(const WinDev<float>* __restrict__ wins, int n_win, const int4* __res
 }
 
 template <int S>
-cudaError_t spread_tm_s(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units,
-                        const float* V, int64_t ldv, int R, int rc, int* err, long long spin,
-                        cudaStream_t st) {
+cudaError_t spread_tm_s(const WinDev<float>* wins, const void* grid_maps, int n_win,
+                        const int4* units, int64_t n_units, const float* V, int64_t ldv, int R,
+                        int rc, int* err, long long spin, cudaStream_t st) {
   using Sh = TmShape<S>;
   cudaError_t e = cudaFuncSetAttribute(k_spread_tm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Sh::SMEM);
   if (e != cudaSuccess) return e;
   if (n_units <= 0) return cudaSuccess;
-  if (n_win < 1 || n_win > kMaxWindows) return cudaErrorInvalidValue;
+  if (n_win < 1 || n_win > kMaxWindows || grid_maps == nullptr) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -512,8 +553,9 @@ cudaError_t spread_tm_s(const WinDev<float>* wins, int n_win, const int4* units,
   const int64_t items = n_units * (rc / kTmRH);
   const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
   const int vec = (ldv % 4 == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0) ? 1 : 0;
-  k_spread_tm<S><<<grid, kTmThreads, Sh::SMEM, st>>>(wins, n_win, units, n_units, V, ldv, vec, R, rc, err,
-                                                     spin);
+  k_spread_tm<S><<<grid, kTmThreads, Sh::SMEM, st>>>(
+      wins, static_cast<const unsigned char*>(grid_maps), n_win, units, n_units, V, ldv, vec, R, rc,
+      err, spin);
   return cudaGetLastError();
 }
 
@@ -523,14 +565,63 @@ bool spread_tm_supported(int d, int s, int RC) {
   return d == 3 && (RC == 32 || RC == 16) && (s == 4 || s == 5);
 }
 
-cudaError_t spread_units_tm(const WinDev<float>* wins, int n_win, const int4* units, int64_t n_units, int s,
-                            const float* V, int64_t ldv, int R, int rc, int* err, long long spin,
+cudaError_t spread_units_tm(const WinDev<float>* wins, const void* grid_maps, int n_win,
+                            const int4* units, int64_t n_units, int s, const float* V,
+                            int64_t ldv, int R, int rc, int* err, long long spin,
                             cudaStream_t st) {
   switch (s) {
-    case 4: return spread_tm_s<4>(wins, n_win, units, n_units, V, ldv, R, rc, err, spin, st);
-    case 5: return spread_tm_s<5>(wins, n_win, units, n_units, V, ldv, R, rc, err, spin, st);
+    case 4:
+      return spread_tm_s<4>(wins, grid_maps, n_win, units, n_units, V, ldv, R, rc, err, spin, st);
+    case 5:
+      return spread_tm_s<5>(wins, grid_maps, n_win, units, n_units, V, ldv, R, rc, err, spin, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+bool encode_grid_maps(const WinDev<float>* wins_host, const int* win_d, int n_win, int s,
+                      void* out) {
+  static_assert(sizeof(CUtensorMap) == kGridMapBytes, "tensor map size");
+  if ((reinterpret_cast<uintptr_t>(out) & 63) != 0 || n_win < 1 || (s != 4 && s != 5))
+    return false;
+  unsigned char* o = static_cast<unsigned char*>(out);
+  std::memset(o, 0, (size_t)2 * n_win * kGridMapBytes);
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (encode == nullptr) return false;
+  const cuuint32_t tt = (cuuint32_t)(2 * s), t3m = (cuuint32_t)(2 * s + kRunCells - 1);
+  for (int h = 0; h < 2; ++h) {
+    const cuuint64_t rc = h ? 32 : 16;
+    for (int q = 0; q < n_win; ++q) {
+      if (win_d[q] != 3) continue;
+      const WinDev<float>& w = wins_host[q];
+      // grid element (r, a3, a2, a1) at ((a1 W + a2) W + a3) rc + r
+      const cuuint64_t W = (cuuint64_t)w.W;
+      const cuuint64_t dims[4] = {rc, W, W, W};
+      const cuuint64_t strides[3] = {rc * 4, W * rc * 4, W * W * rc * 4};
+      const cuuint32_t box[4] = {(cuuint32_t)kTmRH, t3m, tt, tt};
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      CUtensorMap* m = reinterpret_cast<CUtensorMap*>(o + ((size_t)h * n_win + q) * kGridMapBytes);
+      if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, w.grid, dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+          CUDA_SUCCESS)
+        return false;
+    }
+  }
+  return true;
 }
 
 }  // namespace agp

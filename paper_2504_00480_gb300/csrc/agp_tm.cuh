@@ -110,6 +110,28 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Element-wise add of a shared-memory box into global memory through a 4-d
+// tensor map (coordinates innermost first), as one bulk copy of this
+// thread's bulk group; the adds are atomic per element.
+__device__ __forceinline__ void bulk_reduce_add_4d(const void* map, uint32_t smem, int c0, int c1,
+                                                   int c2, int c3) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.4d.global.shared::cta.add.bulk_group [%0, {%2, %3, %4, %5}], [%1];"
+      ::"l"(map), "r"(smem), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until this thread's bulk copies have read their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Wait until this thread's bulk copies are complete (their global writes done).
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // 4-byte cp.async (zero-filled past src_bytes), for rows that are not 16-byte aligned
 __device__ __forceinline__ void cp_async4_zfill(void* smem, const void* gmem, int src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
