@@ -225,7 +225,11 @@ agp_status agp_plan_tensor_cores(agp_plan plan, int* mode);
  * the plan has no d = 3 window. Depends on the plan's precision, cutoff,
  * kernel family (agp_plan_set_tensor_cores) and on R; a family-3 plan takes
  * family 2 for an interpolation pass whose second 16-column half would be
- * empty (R <= RC - 16). */
+ * empty (R <= RC - 16). The persistent spreading kernel adds each unit's
+ * block into the grid by one bulk tensor reduction through tensor maps of
+ * the plan's grids, encoded at plan creation with the driver's
+ * cuTensorMapEncodeTiled; if the driver offers no encoder or refuses a map,
+ * the plan's spreading reports and runs family 2 instead. */
 agp_status agp_plan_kernel_families(agp_plan plan, int R, int64_t ldv, int* spread, int* interp);
 
 /* Forget every cached autotuner result of the process. */
